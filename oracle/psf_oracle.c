@@ -1,0 +1,819 @@
+/*
+ * psf_oracle.c -- plain FP64 CPU oracle for the P-SPIR PSF system matrix
+ * (Sun et al., "Fast and accurate generation method of PSF-based system
+ * matrix for PET reconstruction", Chinese Physics C, 2016).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file: only the tests, the smoke check of the package entry and
+ * the CPU-baseline leg of the benchmark do.  It shares no code, header, table
+ * or constant with the CUDA library; both sides receive the same plain
+ * numbers (scanner, table and image descriptions, LOR lists, images) from the
+ * seeded input module.
+ *
+ * Everything is double precision and written to be checked against the paper
+ * by eye, not to be fast: brute-force box clipping instead of incremental
+ * tracing, dense accumulators, no symmetry reuse.  OpenMP only splits
+ * independent LORs across threads.
+ *
+ * Readings of passages where the paper is silent or garbled are stated at the
+ * function that takes them.  Parity status per function:
+ *   orc_trace_response  pinned (closed form, Monte Carlo, normalisation sums)
+ *   orc_table_build     pinned (via orc_trace_response + node grid checks)
+ *   orc_composed        pinned (sigma=0, R->inf reduction to one flat array)
+ *   orc_spread          pinned (rank-1 case, sum rules, ring symmetries)
+ *   orc_siddon          pinned (axis-aligned chords, brute slab-clip tracer)
+ *   orc_rows_psf        pinned (definition A = S G checked on scatter identity)
+ *   orc_csr_fwd / back  pinned (dot-product identity, MLEM count identity)
+ *   agreement of the analytic response with GATE: parity unpinned (the
+ *   paper's response curves, Figs. 2-5, are not in the text).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------------- */
+/* Geometry (Sec. 3 scanner description; Fig. 6 for the block layout)     */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int R;          /* blocks per ring (R of Eq. 2)                         */
+    int Nb;         /* transaxial crystals per block                        */
+    int Na;         /* axial crystals per block                             */
+    int NBR;        /* block rings                                          */
+    double wt, wa;  /* crystal face width, transaxial (lambda of Eq. 5) / axial */
+    double depth;   /* crystal depth                                        */
+    double gt, ga;  /* air gap between neighbouring crystals inside a block */
+    double radius;  /* scanner axis to the block front-face centre          */
+    double bga;     /* axial air gap between block rings                    */
+    double mu;      /* linear attenuation coefficient (1/mm)                */
+} orc_scanner;
+
+typedef struct {
+    int Kt, Ka;           /* angle nodes: transaxial / polar                */
+    int Pt, Pa;           /* sub-positions per crystal face (x of Sec. 2.1.1) */
+    int Mt, Ma;           /* stored crystal offsets along travel            */
+    double amax_t_deg;    /* node spacing = amax / K                        */
+    double amax_a_deg;
+} orc_table;
+
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double ox, oy, oz;    /* corner of voxel (0,0,0)                        */
+} orc_image;
+
+static int orc_nt(const orc_scanner *s) { return s->R * s->Nb; }
+static int orc_nrings(const orc_scanner *s) { return s->NBR * s->Na; }
+static double orc_pt(const orc_scanner *s) { return s->wt + s->gt; }
+static double orc_pa(const orc_scanner *s) { return s->wa + s->ga; }
+static double orc_block_width(const orc_scanner *s)
+{
+    return s->Nb * s->wt + (s->Nb - 1) * s->gt;
+}
+
+/* Gap sigma = AB = BC of Fig. 6: B is where the front-face lines of two
+ * neighbouring blocks meet, C the corner of block0 and A the corner of
+ * block1.  The face line of a block lies at distance `radius` from the axis,
+ * so B sits r*tan(pi/R) from the block centre along the face. */
+double orc_sigma(const orc_scanner *s)
+{
+    return s->radius * tan(ORC_PI / s->R) - 0.5 * orc_block_width(s);
+}
+
+/* Axial centre of crystal ring k; rings are centred on z = 0. */
+static double orc_ring_z(const orc_scanner *s, int k)
+{
+    int br = k / s->Na, ia = k % s->Na;
+    double H = s->Na * s->wa + (s->Na - 1) * s->ga;
+    double Z = s->NBR * H + (s->NBR - 1) * s->bga;
+    return br * (H + s->bga) + ia * orc_pa(s) + 0.5 * s->wa - 0.5 * Z;
+}
+
+/* Crystal id = ring * Nt + block * Nb + i.  Block b is centred at angle
+ * 2 pi b / R; crystal i of a block sits at tangential offset
+ * (i - (Nb-1)/2) * pitch, the index growing counter-clockwise. */
+typedef struct {
+    int ring, block, i, ct;
+    double n[2], t[2];        /* outward normal, counter-clockwise tangent */
+    double s_centre;          /* tangential coordinate of the crystal centre */
+    double z_centre;
+} orc_xtal;
+
+static orc_xtal orc_decode(const orc_scanner *s, int id)
+{
+    orc_xtal x;
+    int Nt = orc_nt(s);
+    x.ring = id / Nt;
+    x.ct = id % Nt;
+    x.block = x.ct / s->Nb;
+    x.i = x.ct % s->Nb;
+    double phi = 2.0 * ORC_PI * x.block / s->R;
+    x.n[0] = cos(phi);
+    x.n[1] = sin(phi);
+    x.t[0] = -sin(phi);
+    x.t[1] = cos(phi);
+    x.s_centre = (x.i - 0.5 * (s->Nb - 1)) * orc_pt(s);
+    x.z_centre = orc_ring_z(s, x.ring);
+    return x;
+}
+
+/* Point on the front face of crystal `id`, displaced by (off_t, off_a) from
+ * the face centre along the tangent and the axis. */
+void orc_face_point(const orc_scanner *s, int id, double off_t, double off_a,
+                    double P[3])
+{
+    orc_xtal x = orc_decode(s, id);
+    double st = x.s_centre + off_t;
+    P[0] = s->radius * x.n[0] + st * x.t[0];
+    P[1] = s->radius * x.n[1] + st * x.t[1];
+    P[2] = x.z_centre + off_a;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Single-photon response (Sec. 2.1.1, Eq. 1; normalisation Sec. 2.1.3)   */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Response of one ray entering a flat crystal array (Sec. 2.1.1).  The paper
+ * counts M_i/M (Eq. 1) in a GATE simulation; here the count ratio is replaced
+ * by its analytic expectation without scatter: the probability that the first
+ * interaction happens in crystal i is exp(-mu * L_before) * (1 - exp(-mu L_i)),
+ * with L_i the path length inside crystal i and L_before the path length in
+ * crystal material met earlier along the ray (gaps are air).
+ *
+ * Frame of the array: x lateral along the transaxial travel direction, y
+ * axial along the axial travel direction, z depth from the front face.
+ * Crystal (kx, ky) occupies [kx*pt, kx*pt+wt] x [ky*pa, ky*pa+wa] x [0, D].
+ * The ray enters crystal (0,0) at (u*wt, v*wa, 0): u, v are measured from the
+ * crystal edge the ray moves away from.  Its direction has transaxial angle
+ * alpha_t to the face normal (in the transaxial plane) and polar angle theta
+ * to the transaxial plane, i.e. per unit depth it moves tan(alpha_t)
+ * laterally and tan(theta)/cos(alpha_t) axially.
+ *
+ * T[kx*My + ky] receives the first-interaction probability of crystal (kx,ky)
+ * for kx < Mx, ky < My.  *eta receives the total over all crystals the ray
+ * meets (the counting rate eta of Eq. 6 for unit activity and time), so that
+ * rho = eta * rho0 (Eq. 7) with rho0 = T / eta summing to one.
+ *
+ * Each crystal box is clipped against the ray independently (slab method),
+ * and the attenuation before a crystal is the sum over the boxes the ray
+ * entered earlier.
+ */
+void orc_trace_response(const orc_scanner *s, double alpha_t, double theta,
+                        double u, double v, int Mx, int My, double *T,
+                        double *eta)
+{
+    const double pt = orc_pt(s), pa = orc_pa(s), D = s->depth;
+    const double tx = tan(alpha_t), ty = tan(theta) / cos(alpha_t);
+    const double x0 = u * s->wt, y0 = v * s->wa;
+    const double ds = sqrt(1.0 + tx * tx + ty * ty);
+    int kxmax = (int)floor((x0 + D * tx) / pt) + 1;
+    int kymax = (int)floor((y0 + D * ty) / pa) + 1;
+    int nbox = (kxmax + 1) * (kymax + 1);
+    double *zin = (double *)malloc(sizeof(double) * nbox);
+    double *len = (double *)malloc(sizeof(double) * nbox);
+    int *kxs = (int *)malloc(sizeof(int) * nbox);
+    int *kys = (int *)malloc(sizeof(int) * nbox);
+    int nb = 0;
+    for (int kx = 0; kx <= kxmax; ++kx) {
+        for (int ky = 0; ky <= kymax; ++ky) {
+            double lo = 0.0, hi = D;
+            double ax = kx * pt, bx = ax + s->wt;
+            double ay = ky * pa, by = ay + s->wa;
+            if (tx > 0.0) {
+                double z0 = (ax - x0) / tx, z1 = (bx - x0) / tx;
+                if (z0 > lo) lo = z0;
+                if (z1 < hi) hi = z1;
+            } else if (!(x0 >= ax && x0 <= bx)) {
+                continue;
+            }
+            if (ty > 0.0) {
+                double z0 = (ay - y0) / ty, z1 = (by - y0) / ty;
+                if (z0 > lo) lo = z0;
+                if (z1 < hi) hi = z1;
+            } else if (!(y0 >= ay && y0 <= by)) {
+                continue;
+            }
+            if (hi > lo) {
+                zin[nb] = lo;
+                len[nb] = (hi - lo) * ds;
+                kxs[nb] = kx;
+                kys[nb] = ky;
+                ++nb;
+            }
+        }
+    }
+    for (int k = 0; k < Mx * My; ++k) T[k] = 0.0;
+    double total = 0.0;
+    for (int a = 0; a < nb; ++a) {
+        double before = 0.0;
+        for (int b = 0; b < nb; ++b)
+            if (zin[b] < zin[a]) before += len[b];
+        double p = exp(-s->mu * before) * (1.0 - exp(-s->mu * len[a]));
+        total += p;
+        if (kxs[a] < Mx && kys[a] < My) T[kxs[a] * My + kys[a]] = p;
+    }
+    *eta = total;
+    free(zin);
+    free(len);
+    free(kxs);
+    free(kys);
+}
+
+/* Table layout: T[((((kt*Ka + ka)*Pt + iu)*Pa + iv)*Mt + dx)*Ma + dz],
+ * eta[((kt*Ka + ka)*Pt + iu)*Pa + iv]. */
+static size_t orc_tidx(const orc_table *tb, int kt, int ka, int iu, int iv)
+{
+    return (((size_t)kt * tb->Ka + ka) * tb->Pt + iu) * tb->Pa + iv;
+}
+
+/*
+ * The P-SPIR table (Sec. 2.1.1): one response per incidence angle and entry
+ * sub-position.  Reading of the angle grid: the SPIR model samples the
+ * incidence angle on a uniform grid starting at 0 (0..60 degrees in 5-degree
+ * steps); here node k sits at k * amax / K degrees, k = 0..K-1.  Each crystal
+ * bar is divided into P equal parts (x = 8 in the paper); sub-position p is
+ * evaluated at its centre (p + 1/2) / P.
+ */
+void orc_table_build(const orc_scanner *s, const orc_table *tb, double *T,
+                     double *eta)
+{
+    const double dt = tb->amax_t_deg / tb->Kt * ORC_PI / 180.0;
+    const double da = tb->amax_a_deg / tb->Ka * ORC_PI / 180.0;
+#pragma omp parallel for collapse(2) schedule(dynamic)
+    for (int kt = 0; kt < tb->Kt; ++kt)
+        for (int ka = 0; ka < tb->Ka; ++ka)
+            for (int iu = 0; iu < tb->Pt; ++iu)
+                for (int iv = 0; iv < tb->Pa; ++iv) {
+                    size_t e = orc_tidx(tb, kt, ka, iu, iv);
+                    orc_trace_response(s, kt * dt, ka * da,
+                                       (iu + 0.5) / tb->Pt, (iv + 0.5) / tb->Pa,
+                                       tb->Mt, tb->Ma,
+                                       T + e * tb->Mt * tb->Ma, eta + e);
+                }
+}
+
+/* Nearest node of the grid (reading of the table lookup; no interpolation). */
+int orc_node(double ang, double amax_deg, int K)
+{
+    double step = amax_deg / K * ORC_PI / 180.0;
+    int k = (int)floor(ang / step + 0.5);
+    return k > K - 1 ? K - 1 : k;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Response seen from the ring, with two-block penetration (Sec. 2.1.2)   */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int dt;       /* transaxial offset in ring crystal index (wraps mod Nt) */
+    int da;       /* crystal-ring offset                                    */
+    double val;   /* first-interaction probability                          */
+} orc_entry;
+
+/*
+ * Gap construction of Fig. 6 for a photon entering block0 at distance nu from
+ * its edge C (nu = CP0) with incidence angle alpha toward block1:
+ *   beta = alpha - 2 pi / R                                        (Eq. 2)
+ *   AP1  = sigma + sin(pi/2 - alpha) / sin(pi/2 + beta) * (sigma + nu)  (Eq. 4)
+ * (the law of sines in triangle B P0 P1, whose angle at B is 2 pi / R).
+ * *run receives the side P0 P1 of the same triangle, the transaxial distance
+ * the photon covers between P0 and the extended face line BD of block1.
+ */
+void orc_gap_eq(const orc_scanner *s, double alpha, double nu, double *beta,
+                double *AP1, double *run)
+{
+    double sigma = orc_sigma(s);
+    *beta = alpha - 2.0 * ORC_PI / s->R;
+    *AP1 = sigma + sin(0.5 * ORC_PI - alpha) / sin(0.5 * ORC_PI + *beta) * (sigma + nu);
+    *run = (sigma + nu) * sin(2.0 * ORC_PI / s->R) / sin(0.5 * ORC_PI + *beta);
+}
+
+/*
+ * Response of the crystals around crystal `id` to a photon that enters its
+ * front face at sub-position (ipt, ipa) -- indices counted from the -tangent
+ * and -axial edges -- travelling along `dir` (any length, pointing out of the
+ * ring).  Offsets are in ring crystal index and crystal ring.
+ *
+ * Block0 (the struck block) takes the table entries of its own crystals;
+ * entries that would lie beyond its lateral edge are dropped.  If the
+ * incidence angle exceeds the angle between neighbouring block normals, the
+ * neighbouring block in the travel direction (block1) is reached through the
+ * gap by the construction of Fig. 6:
+ *   beta = alpha - 2 pi / R                                   (Eq. 2)
+ *   AP1  = sigma + sin(pi/2 - alpha) / sin(pi/2 + beta) * (sigma + nu)  (Eq. 4)
+ *   n    = AP1 / lambda                                       (Eq. 5)
+ * with nu = CP0 the distance from the entry point to the block edge.  The
+ * photon is taken to enter a virtual crystal of block1's array, extended
+ * beyond its corner A, at distance AP1 from A; block1's real crystal j (j = 0
+ * next to A) then sits floor(n) + 1 + j crystals further along the travel
+ * direction, and its response is read from the same table at (beta, the
+ * entry position within the virtual crystal).
+ * Readings: with intra-block gaps the virtual crystals repeat with the block
+ * pitch, and an entry point that falls into a virtual gap enters the next
+ * virtual crystal toward A at its trailing edge.  In 3D the transaxial
+ * construction is done in the transaxial projection (the polar angle is
+ * unchanged by the rotation between blocks), and the axial entry position is
+ * the ray's axial coordinate at P1 on a uniform ring lattice.
+ *
+ * Returns the number of entries written to out; *eta_out receives their sum.
+ */
+int orc_composed(const orc_scanner *s, const orc_table *tb, const double *T,
+                 int id, int ipt, int ipa, const double dir[3],
+                 orc_entry *out, int cap, double *eta_out)
+{
+    orc_xtal x = orc_decode(s, id);
+    double vn = dir[0] * x.n[0] + dir[1] * x.n[1];
+    double vt = dir[0] * x.t[0] + dir[1] * x.t[1];
+    double vz = dir[2];
+    int ne = 0;
+    *eta_out = 0.0;
+    if (!(vn > 0.0)) return 0;
+    double alpha = atan2(fabs(vt), vn);
+    double theta = atan2(fabs(vz), sqrt(vn * vn + vt * vt));
+    int sgt = vt >= 0.0 ? 1 : -1;
+    int sga = vz >= 0.0 ? 1 : -1;
+    int iu = sgt > 0 ? ipt : tb->Pt - 1 - ipt;
+    int iv = sga > 0 ? ipa : tb->Pa - 1 - ipa;
+    int kt = orc_node(alpha, tb->amax_t_deg, tb->Kt);
+    int ka = orc_node(theta, tb->amax_a_deg, tb->Ka);
+    const double *Tb = T + orc_tidx(tb, kt, ka, iu, iv) * tb->Mt * tb->Ma;
+    double sum = 0.0;
+
+    /* block0: crystals i + sgt*dx inside the block */
+    for (int dx = 0; dx < tb->Mt; ++dx) {
+        int ii = x.i + sgt * dx;
+        if (ii < 0 || ii >= s->Nb) break;
+        for (int dz = 0; dz < tb->Ma; ++dz) {
+            double val = Tb[dx * tb->Ma + dz];
+            if (val == 0.0) continue;
+            if (ne < cap) {
+                out[ne].dt = sgt * dx;
+                out[ne].da = sga * dz;
+                out[ne].val = val;
+            }
+            ++ne;
+            sum += val;
+        }
+    }
+
+    /* block1 through the gap (Eq. 2, 4, 5) */
+    double beta, AP1, run;
+    orc_gap_eq(s, alpha, 0.5 * orc_block_width(s) -
+                   sgt * (x.s_centre + ((ipt + 0.5) / tb->Pt - 0.5) * s->wt),
+               &beta, &AP1, &run);
+    if (beta > 0.0) {
+        double ze = x.z_centre + ((ipa + 0.5) / tb->Pa - 0.5) * s->wa;
+        double pt = orc_pt(s);
+        double q = AP1 - s->gt;
+        if (q < 0.0) q = 0.0;
+        int m = (int)floor(q / pt);
+        double f = q - m * pt;
+        double u1 = f < s->wt ? (s->wt - f) / s->wt : 0.0;
+        int iu1 = (int)floor(u1 * tb->Pt);
+        if (iu1 > tb->Pt - 1) iu1 = tb->Pt - 1;
+        double z1 = ze + sga * run * tan(theta);
+        double pa = orc_pa(s);
+        double zlo0 = orc_ring_z(s, 0) - 0.5 * s->wa;
+        int k1 = (int)floor((z1 - zlo0) / pa);
+        double fa = (z1 - zlo0) - k1 * pa;
+        double v1;
+        if (fa <= s->wa) {
+            v1 = sga > 0 ? fa / s->wa : (s->wa - fa) / s->wa;
+        } else {
+            if (sga > 0) k1 += 1;
+            v1 = 0.0;
+        }
+        int iv1 = (int)floor(v1 * tb->Pa);
+        if (iv1 > tb->Pa - 1) iv1 = tb->Pa - 1;
+        int kt1 = orc_node(beta, tb->amax_t_deg, tb->Kt);
+        const double *T1 = T + orc_tidx(tb, kt1, ka, iu1, iv1) * tb->Mt * tb->Ma;
+        for (int j = 0; j < s->Nb; ++j) {
+            int dx = m + 1 + j;
+            if (dx >= tb->Mt) break;
+            int dt = sgt > 0 ? (s->Nb - x.i + j) : -(x.i + 1 + j);
+            for (int dz = 0; dz < tb->Ma; ++dz) {
+                double val = T1[dx * tb->Ma + dz];
+                if (val == 0.0) continue;
+                if (ne < cap) {
+                    out[ne].dt = dt;
+                    out[ne].da = (k1 - x.ring) + sga * dz;
+                    out[ne].val = val;
+                }
+                ++ne;
+                sum += val;
+            }
+        }
+    }
+    *eta_out = sum;
+    return ne;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Homogenization spread of a LOR (Sec. 2.2 Eq. 10, Sec. 2.3 Eq. 11-12)   */
+/* ---------------------------------------------------------------------- */
+
+enum { ORC_NORM_NONE = 0, ORC_NORM_EFF = 1, ORC_NORM_UNIT = 2 };
+
+/*
+ * Spread of each listed LOR (crystal ids lors[2k], lors[2k+1]) over the
+ * crystal pairs within +-Wt transaxially and +-Wa axially of its two ends.
+ *
+ * Reading of the homogenization model: the equally weighted LORs through the
+ * emission point are taken as the sub-LORs that join the sub-position centres
+ * of the two crystal faces (Pt*Pa positions per face, every pairing equally
+ * weighted).  Each sub-LOR gives the detected pair (c1+d1, c2+d2) the product
+ * of the two single-photon responses (Eq. 10); summing over sub-LORs is the
+ * sum of Eq. 12.  Pairs of crystals in the same block get no spread (their
+ * chord runs along the block face and enters neither crystal).
+ *
+ * Output w[k][e1][e2], e = (dt + Wt)*(2Wa+1) + (da + Wa), end 1 = lors[2k].
+ * Normalisation (the paper fixes none):
+ *   NONE: the truncated window as summed;
+ *   EFF : rescaled so the window total equals the untruncated total
+ *         mean over sub-LORs of eta1*eta2 (the efficiency of Eq. 7 is kept,
+ *         the truncation loss is returned);
+ *   UNIT: rescaled to total one.
+ */
+void orc_spread(const orc_scanner *s, const orc_table *tb, const double *T,
+                const int32_t *lors, int64_t n, int Wt, int Wa, int norm,
+                double *w)
+{
+    const int E = (2 * Wt + 1) * (2 * Wa + 1);
+    const int cap = 4 * (tb->Mt * tb->Ma) + 16;
+#pragma omp parallel
+    {
+        orc_entry *r1 = (orc_entry *)malloc(sizeof(orc_entry) * cap);
+        orc_entry *r2 = (orc_entry *)malloc(sizeof(orc_entry) * cap);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t k = 0; k < n; ++k) {
+            double *acc = w + (size_t)k * E * E;
+            for (int e = 0; e < E * E; ++e) acc[e] = 0.0;
+            int id1 = lors[2 * k], id2 = lors[2 * k + 1];
+            orc_xtal x1 = orc_decode(s, id1), x2 = orc_decode(s, id2);
+            if (x1.block == x2.block) continue;
+            double sfull = 0.0;
+            for (int p1 = 0; p1 < tb->Pt; ++p1)
+            for (int q1 = 0; q1 < tb->Pa; ++q1)
+            for (int p2 = 0; p2 < tb->Pt; ++p2)
+            for (int q2 = 0; q2 < tb->Pa; ++q2) {
+                double E1[3], E2[3], d1[3], d2[3];
+                orc_face_point(s, id1, ((p1 + 0.5) / tb->Pt - 0.5) * s->wt,
+                               ((q1 + 0.5) / tb->Pa - 0.5) * s->wa, E1);
+                orc_face_point(s, id2, ((p2 + 0.5) / tb->Pt - 0.5) * s->wt,
+                               ((q2 + 0.5) / tb->Pa - 0.5) * s->wa, E2);
+                for (int c = 0; c < 3; ++c) {
+                    d1[c] = E1[c] - E2[c];
+                    d2[c] = -d1[c];
+                }
+                double eta1, eta2;
+                int n1 = orc_composed(s, tb, T, id1, p1, q1, d1, r1, cap, &eta1);
+                int n2 = orc_composed(s, tb, T, id2, p2, q2, d2, r2, cap, &eta2);
+                sfull += eta1 * eta2;
+                for (int a = 0; a < n1; ++a) {
+                    if (abs(r1[a].dt) > Wt || abs(r1[a].da) > Wa) continue;
+                    int e1 = (r1[a].dt + Wt) * (2 * Wa + 1) + (r1[a].da + Wa);
+                    for (int b = 0; b < n2; ++b) {
+                        if (abs(r2[b].dt) > Wt || abs(r2[b].da) > Wa) continue;
+                        int e2 = (r2[b].dt + Wt) * (2 * Wa + 1) + (r2[b].da + Wa);
+                        acc[e1 * E + e2] += r1[a].val * r2[b].val;
+                    }
+                }
+            }
+            double nsub = (double)tb->Pt * tb->Pa * tb->Pt * tb->Pa;
+            double swin = 0.0;
+            for (int e = 0; e < E * E; ++e) {
+                acc[e] /= nsub;
+                swin += acc[e];
+            }
+            sfull /= nsub;
+            double scale = 1.0;
+            if (norm == ORC_NORM_EFF && swin > 0.0) scale = sfull / swin;
+            if (norm == ORC_NORM_UNIT && swin > 0.0) scale = 1.0 / swin;
+            for (int e = 0; e < E * E; ++e) acc[e] *= scale;
+        }
+        free(r1);
+        free(r2);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Geometric rows: chord lengths of a segment through the voxel grid      */
+/* ---------------------------------------------------------------------- */
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+typedef struct { int64_t idx; double len; } orc_vl;
+static int cmp_vl(const void *a, const void *b)
+{
+    int64_t x = ((const orc_vl *)a)->idx, y = ((const orc_vl *)b)->idx;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Chord lengths (mm) of the segment a->b through the voxels of `im`, by the
+ * parametric method: every grid-plane crossing inside the grid is collected,
+ * the parameters are sorted, and each interval between consecutive crossings
+ * belongs to the voxel containing its midpoint.  Voxels are half-open
+ * [lo, hi) on every axis, so a segment lying on a grid plane belongs to the
+ * voxel above it.  Output sorted by voxel index (x fastest); returns the
+ * count, or -1 if cap is too small.
+ */
+int orc_siddon(const orc_image *im, const double a[3], const double b[3],
+               int64_t *idx, double *len, int cap)
+{
+    const int nn[3] = {im->nx, im->ny, im->nz};
+    const double dd[3] = {im->dx, im->dy, im->dz};
+    const double oo[3] = {im->ox, im->oy, im->oz};
+    double d[3], L = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        d[c] = b[c] - a[c];
+        L += d[c] * d[c];
+    }
+    L = sqrt(L);
+    double amin = 0.0, amax = 1.0;
+    for (int c = 0; c < 3; ++c) {
+        double lo = oo[c], hi = oo[c] + nn[c] * dd[c];
+        if (d[c] != 0.0) {
+            double t0 = (lo - a[c]) / d[c], t1 = (hi - a[c]) / d[c];
+            if (t0 > t1) { double t = t0; t0 = t1; t1 = t; }
+            if (t0 > amin) amin = t0;
+            if (t1 < amax) amax = t1;
+        } else if (!(a[c] >= lo && a[c] < hi)) {
+            return 0;
+        }
+    }
+    if (!(amax > amin)) return 0;
+    int np = 2 + nn[0] + nn[1] + nn[2] + 3;
+    double *al = (double *)malloc(sizeof(double) * np);
+    int k = 0;
+    al[k++] = amin;
+    al[k++] = amax;
+    for (int c = 0; c < 3; ++c) {
+        if (d[c] == 0.0) continue;
+        for (int i = 0; i <= nn[c]; ++i) {
+            double t = (oo[c] + i * dd[c] - a[c]) / d[c];
+            if (t > amin && t < amax) al[k++] = t;
+        }
+    }
+    qsort(al, k, sizeof(double), cmp_double);
+    orc_vl *tmp = (orc_vl *)malloc(sizeof(orc_vl) * (k + 1));
+    int nv = 0;
+    for (int j = 0; j + 1 < k; ++j) {
+        if (!(al[j + 1] > al[j])) continue;
+        double mid = 0.5 * (al[j] + al[j + 1]);
+        int v[3], ok = 1;
+        for (int c = 0; c < 3; ++c) {
+            v[c] = (int)floor((a[c] + mid * d[c] - oo[c]) / dd[c]);
+            if (v[c] < 0 || v[c] >= nn[c]) ok = 0;
+        }
+        if (!ok) continue;
+        tmp[nv].idx = ((int64_t)v[2] * nn[1] + v[1]) * nn[0] + v[0];
+        tmp[nv].len = (al[j + 1] - al[j]) * L;
+        ++nv;
+    }
+    qsort(tmp, nv, sizeof(orc_vl), cmp_vl);
+    int out = 0;
+    for (int j = 0; j < nv; ++j) {
+        if (out > 0 && idx && idx[out - 1] == tmp[j].idx) {
+            len[out - 1] += tmp[j].len;
+            continue;
+        }
+        if (out >= cap) { out = -1; break; }
+        idx[out] = tmp[j].idx;
+        len[out] = tmp[j].len;
+        ++out;
+    }
+    free(al);
+    free(tmp);
+    return out;
+}
+
+/*
+ * Second, independent tracer for small grids: clip the segment against every
+ * voxel box separately (slab method, half-open boxes) and keep positive
+ * chords.  Same output convention as orc_siddon.
+ */
+int orc_slabclip(const orc_image *im, const double a[3], const double b[3],
+                 int64_t *idx, double *len, int cap)
+{
+    double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const int nn[3] = {im->nx, im->ny, im->nz};
+    const double dd[3] = {im->dx, im->dy, im->dz};
+    const double oo[3] = {im->ox, im->oy, im->oz};
+    int out = 0;
+    for (int iz = 0; iz < nn[2]; ++iz)
+    for (int iy = 0; iy < nn[1]; ++iy)
+    for (int ix = 0; ix < nn[0]; ++ix) {
+        int v[3] = {ix, iy, iz};
+        double t0 = 0.0, t1 = 1.0;
+        int ok = 1;
+        for (int c = 0; c < 3 && ok; ++c) {
+            double lo = oo[c] + v[c] * dd[c], hi = lo + dd[c];
+            if (d[c] != 0.0) {
+                double s0 = (lo - a[c]) / d[c], s1 = (hi - a[c]) / d[c];
+                if (s0 > s1) { double t = s0; s0 = s1; s1 = t; }
+                if (s0 > t0) t0 = s0;
+                if (s1 < t1) t1 = s1;
+            } else if (!(a[c] >= lo && a[c] < hi)) {
+                ok = 0;
+            }
+        }
+        if (!ok || !(t1 > t0)) continue;
+        if (out >= cap) return -1;
+        idx[out] = ((int64_t)iz * nn[1] + iy) * nn[0] + ix;
+        len[out] = (t1 - t0) * L;
+        ++out;
+    }
+    return out;
+}
+
+/* Geometric LOR of a crystal pair: front-face centre to front-face centre. */
+static void orc_lor_ends(const orc_scanner *s, int id1, int id2, double a[3],
+                         double b[3])
+{
+    orc_face_point(s, id1, 0.0, 0.0, a);
+    orc_face_point(s, id2, 0.0, 0.0, b);
+}
+
+/* Row lengths of the geometric matrix G for a LOR list (first pass). */
+void orc_rows_geom_count(const orc_scanner *s, const orc_image *im,
+                         const int32_t *lors, int64_t n, int64_t *counts)
+{
+    int cap = im->nx + im->ny + im->nz + 8;
+#pragma omp parallel
+    {
+        int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * cap);
+        double *len = (double *)malloc(sizeof(double) * cap);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t k = 0; k < n; ++k) {
+            double a[3], b[3];
+            orc_lor_ends(s, lors[2 * k], lors[2 * k + 1], a, b);
+            counts[k] = orc_siddon(im, a, b, idx, len, cap);
+        }
+        free(idx);
+        free(len);
+    }
+}
+
+/* Fill G in CSR given row_ptr from the counts. */
+void orc_rows_geom_fill(const orc_scanner *s, const orc_image *im,
+                        const int32_t *lors, int64_t n, const int64_t *row_ptr,
+                        int64_t *col, double *val)
+{
+    int cap = im->nx + im->ny + im->nz + 8;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+        double a[3], b[3];
+        orc_lor_ends(s, lors[2 * k], lors[2 * k + 1], a, b);
+        orc_siddon(im, a, b, col + row_ptr[k], val + row_ptr[k], cap);
+    }
+}
+
+/*
+ * Measured crystal pair that window entry (e1, e2) of a LOR lands on.
+ * Transaxial indices wrap around the ring; crystal rings outside the scanner
+ * and pairs of one crystal with itself give -1.  Otherwise the two crystal
+ * ids are written to X, Y.
+ */
+int orc_window_pair(const orc_scanner *s, int id1, int id2, int Wt, int Wa,
+                    int e1, int e2, int *X, int *Y)
+{
+    int Nt = orc_nt(s), NR = orc_nrings(s);
+    int W2a = 2 * Wa + 1;
+    int dt1 = e1 / W2a - Wt, da1 = e1 % W2a - Wa;
+    int dt2 = e2 / W2a - Wt, da2 = e2 % W2a - Wa;
+    int r1 = id1 / Nt + da1, r2 = id2 / Nt + da2;
+    if (r1 < 0 || r1 >= NR || r2 < 0 || r2 >= NR) return -1;
+    int c1 = ((id1 % Nt + dt1) % Nt + Nt) % Nt;
+    int c2 = ((id2 % Nt + dt2) % Nt + Nt) % Nt;
+    *X = r1 * Nt + c1;
+    *Y = r2 * Nt + c2;
+    if (*X == *Y) return -1;
+    return 0;
+}
+
+/*
+ * PSF rows, dense: A[m][v] = sum over listed LORs g and window entries
+ * (e1,e2) landing on the pair of LOR m of w_g[e1][e2] * G_g[v]
+ * (Sec. 2.3: each geometric LOR's photons are detected on the neighbouring
+ * crystal pairs with the proportions of Eq. 12).  `pair_row` maps an
+ * unordered crystal pair (X*Ncrys + Y, both orders) to its row or -1.
+ * Small problems only: A is n x nvox doubles.
+ */
+void orc_rows_psf_dense(const orc_scanner *s, int64_t n, const int32_t *lors,
+                        const int64_t *g_ptr, const int64_t *g_col,
+                        const double *g_val, const double *w, int Wt, int Wa,
+                        const int64_t *pair_row, int64_t nvox, double *A)
+{
+    const int E = (2 * Wt + 1) * (2 * Wa + 1);
+    const int64_t Nc = (int64_t)orc_nt(s) * orc_nrings(s);
+    memset(A, 0, sizeof(double) * n * nvox);
+    for (int64_t g = 0; g < n; ++g) {
+        for (int e1 = 0; e1 < E; ++e1)
+            for (int e2 = 0; e2 < E; ++e2) {
+                double wv = w[(size_t)g * E * E + e1 * E + e2];
+                if (wv == 0.0) continue;
+                int X, Y;
+                if (orc_window_pair(s, lors[2 * g], lors[2 * g + 1], Wt, Wa, e1, e2, &X, &Y))
+                    continue;
+                int64_t m = pair_row[(int64_t)X * Nc + Y];
+                if (m < 0) continue;
+                for (int64_t j = g_ptr[g]; j < g_ptr[g + 1]; ++j)
+                    A[m * nvox + g_col[j]] += wv * g_val[j];
+            }
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Projectors (used inside MLEM, Sec. 3)                                  */
+/* ---------------------------------------------------------------------- */
+
+void orc_csr_fwd(int64_t n, const int64_t *ptr, const int64_t *col,
+                 const double *val, const double *x, double *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < n; ++m) {
+        double acc = 0.0;
+        for (int64_t j = ptr[m]; j < ptr[m + 1]; ++j) acc += val[j] * x[col[j]];
+        y[m] = acc;
+    }
+}
+
+void orc_csr_back(int64_t n, const int64_t *ptr, const int64_t *col,
+                  const double *val, const double *y, int64_t nvox, double *x)
+{
+    memset(x, 0, sizeof(double) * nvox);
+    for (int64_t m = 0; m < n; ++m)
+        for (int64_t j = ptr[m]; j < ptr[m + 1]; ++j) x[col[j]] += val[j] * y[m];
+}
+
+/*
+ * Factored PSF projection y = S (G x) for a LOR list: p = G x on the
+ * geometric LORs, then each LOR's p is spread onto the measured pairs of its
+ * window with the weights w (the same proportions as orc_rows_psf_dense,
+ * without forming A).  Both directions, plain loops.
+ */
+void orc_spread_apply(const orc_scanner *s, int64_t n, const int32_t *lors,
+                      const double *w, int Wt, int Wa, const int64_t *pair_row,
+                      const double *p, double *y)
+{
+    const int E = (2 * Wt + 1) * (2 * Wa + 1);
+    const int64_t Nc = (int64_t)orc_nt(s) * orc_nrings(s);
+    memset(y, 0, sizeof(double) * n);
+    for (int64_t g = 0; g < n; ++g) {
+        if (p[g] == 0.0) continue;
+        for (int e1 = 0; e1 < E; ++e1)
+            for (int e2 = 0; e2 < E; ++e2) {
+                double wv = w[(size_t)g * E * E + e1 * E + e2];
+                if (wv == 0.0) continue;
+                int X, Y;
+                if (orc_window_pair(s, lors[2 * g], lors[2 * g + 1], Wt, Wa, e1, e2, &X, &Y))
+                    continue;
+                int64_t m = pair_row[(int64_t)X * Nc + Y];
+                if (m >= 0) y[m] += wv * p[g];
+            }
+    }
+}
+
+void orc_spread_adjoint(const orc_scanner *s, int64_t n, const int32_t *lors,
+                        const double *w, int Wt, int Wa, const int64_t *pair_row,
+                        const double *r, double *q)
+{
+    const int E = (2 * Wt + 1) * (2 * Wa + 1);
+    const int64_t Nc = (int64_t)orc_nt(s) * orc_nrings(s);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < n; ++g) {
+        double acc = 0.0;
+        for (int e1 = 0; e1 < E; ++e1)
+            for (int e2 = 0; e2 < E; ++e2) {
+                double wv = w[(size_t)g * E * E + e1 * E + e2];
+                if (wv == 0.0) continue;
+                int X, Y;
+                if (orc_window_pair(s, lors[2 * g], lors[2 * g + 1], Wt, Wa, e1, e2, &X, &Y))
+                    continue;
+                int64_t m = pair_row[(int64_t)X * Nc + Y];
+                if (m >= 0) acc += wv * r[m];
+            }
+        q[g] = acc;
+    }
+}
+
+/* Number of OpenMP threads the oracle runs with (for the baseline record). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
