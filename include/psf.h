@@ -1,0 +1,210 @@
+/*
+ * psf.h -- C ABI of the GB300 P-SPIR PSF system-matrix library (libpsf.so).
+ *
+ * Method: Sun et al., "Fast and accurate generation method of PSF-based
+ * system matrix for PET reconstruction", Chinese Physics C (2016).  The
+ * library builds the positional single-photon incidence response (P-SPIR)
+ * tables (Sec. 2.1.1-2.1.3), the homogenization spread of every LOR over its
+ * neighbouring crystal pairs (Sec. 2.2-2.3), the PSF-weighted geometric rows,
+ * and the forward / back projectors used inside MLEM (Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers marked (device) are device pointers owned by the caller; the
+ *    library never frees caller memory and never retains a caller pointer
+ *    past the call, except where psf_matrix_create says so.  Pointers marked
+ *    (host) are host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously on it unless the entry point
+ *    says it synchronises.
+ *  - Return value: PSF_OK (0) or a negative PSF_E* code; psf_strerror()
+ *    describes it.  On an error nothing has been enqueued unless stated.
+ *  - Crystal id = ring * Nt + block * Nb + i, Nt = n_blocks * nt_block; block
+ *    b is centred at angle 2*pi*b/n_blocks, crystal i of a block at
+ *    tangential offset (i - (Nb-1)/2) * (xtal_w_t + gap_t), the index growing
+ *    counter-clockwise; crystal rings are centred on z = 0.
+ *  - Image voxel index = (iz * ny + iy) * nx + ix; voxels are half-open boxes
+ *    [o + i*d, o + (i+1)*d) on every axis.
+ *  - Floating-point work is FP32 except the FP64 normalisation sums named
+ *    below.
+ */
+#ifndef PSF_H
+#define PSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSF_OK 0
+#define PSF_EINVAL (-1)    /* bad argument or unsupported combination        */
+#define PSF_ECAPACITY (-2) /* output buffer too small; *nnz_out = required   */
+#define PSF_ECUDA (-3)     /* a CUDA runtime call failed                     */
+#define PSF_ETIMEOUT (-4)  /* a bounded device-side wait gave up             */
+#define PSF_EDEBUG (-5)    /* a device-side bounds check recorded a fault    */
+
+/* Ring scanner of flat blocks (Sec. 3; Fig. 6 for the block corner layout). */
+typedef struct {
+    int32_t n_blocks;       /* R: blocks per ring (Eq. 2)                     */
+    int32_t nt_block;       /* Nb: transaxial crystals per block              */
+    int32_t na_block;       /* axial crystals per block                       */
+    int32_t n_block_rings;  /* block rings (1 with na_block 1 = planar ring)  */
+    double xtal_w_t;        /* lambda of Eq. 5: transaxial crystal width (mm) */
+    double xtal_w_a;        /* axial crystal width (mm)                       */
+    double depth;           /* crystal depth (mm)                             */
+    double gap_t, gap_a;    /* air gap between crystals inside a block (mm)   */
+    double radius;          /* axis to block front-face centre (mm)           */
+    double block_gap_a;     /* axial gap between block rings (mm); must equal
+                               gap_a when n_block_rings > 1                   */
+    double mu;              /* linear attenuation coefficient (1/mm)          */
+} psf_scanner;
+
+/* P-SPIR table description (Sec. 2.1.1).  Incidence-angle nodes sit at
+ * k * ang_max/n_ang, k = 0..n_ang-1 (transaxial angle to the face normal;
+ * polar angle to the transaxial plane) and are looked up nearest-node; each
+ * crystal face is cut into n_sub_t x n_sub_a entry sub-positions evaluated at
+ * their centres; max_off_t x max_off_a crystal offsets along the travel
+ * direction are stored per entry. */
+typedef struct {
+    int32_t n_ang_t, n_ang_a;
+    int32_t n_sub_t, n_sub_a;
+    int32_t max_off_t, max_off_a;
+    double ang_max_t_deg, ang_max_a_deg;
+} psf_table_desc;
+
+/* Voxel grid; (ox, oy, oz) is the outer corner of voxel (0,0,0). */
+typedef struct {
+    int32_t nx, ny, nz, reserved;
+    double dx, dy, dz;
+    double ox, oy, oz;
+} psf_image;
+
+/* Structured LOR set of a ring scanner: transaxial pairs (a, b), a < b, with
+ * Nt/2 - fan_half <= b - a <= Nt/2 + fan_half, times ordered crystal-ring
+ * pairs (ra, rb) with |ra - rb| <= max_ring_diff.  Row order: transaxial pair
+ * major (lexicographic), ring pair minor (lexicographic); LOR = (ra*Nt + a,
+ * rb*Nt + b).  fan_half = Nt/2 - 1 on a planar ring lists all crystal pairs. */
+typedef struct {
+    int32_t fan_half;
+    int32_t max_ring_diff;
+} psf_lor_set;
+
+typedef enum { PSF_F32 = 0, PSF_BF16 = 1, PSF_F16 = 2 } psf_dtype;
+typedef enum { PSF_NORM_NONE = 0, PSF_NORM_EFF = 1, PSF_NORM_UNIT = 2 } psf_norm;
+
+const char *psf_strerror(int code);
+
+/* Sizes of the outputs of psf_response_build for a table description. */
+int psf_table_size(const psf_table_desc *desc, int64_t *n_table, int64_t *n_eta);
+
+/*
+ * P-SPIR response table (Sec. 2.1.1, Eq. 1; normalisation Sec. 2.1.3, Eq. 6-7).
+ * The GATE count ratio M_i/M of Eq. 1 is replaced by the analytic
+ * first-interaction probability exp(-mu L_before)(1 - exp(-mu L_i)) of a ray
+ * entering a flat crystal array (gaps are air).
+ *   table (device, float) [n_ang_t][n_ang_a][n_sub_t][n_sub_a][max_off_t][max_off_a]
+ *         entry (dx, dz) = crystal dx laterally / dz axially along the travel
+ *         direction from the entry crystal; sub-positions counted from the
+ *         edge the ray moves away from.
+ *   eta   (device, double) [n_ang_t][n_ang_a][n_sub_t][n_sub_a][max_off_t + 1]
+ *         FP64 prefix sums over dx of the table summed over dz:
+ *         eta[..][k] = sum_{dx < k} sum_dz table[..][dx][dz], so eta[..][max_off_t]
+ *         is the counting rate eta of Eq. 6 (rho0 = table / eta sums to 1).
+ * PSF_EINVAL if max_off_t/max_off_a cannot hold the lateral/axial reach of the
+ * largest node angle (every crystal a ray can reach must be stored).
+ */
+int psf_response_build(const psf_scanner *scanner, const psf_table_desc *desc, float *table,
+                       double *eta, void *stream);
+
+/*
+ * Homogenization spread (Sec. 2.2 Eq. 10, Sec. 2.3 Eq. 11-12, Sec. 2.1.2
+ * Eq. 2, 4, 5 for the neighbouring-block path).  For each LOR (lors[2k],
+ * lors[2k+1], device int32 crystal ids) the sub-LORs joining the
+ * n_sub_t*n_sub_a sub-position centres of the two crystal faces are averaged;
+ * each contributes the product of the two single-photon responses.  Pairs in
+ * the same transaxial block get zero.
+ *   spread (device, float) [n_lors][E][E], E = (2*half_t+1)*(2*half_a+1),
+ *          e = (dt + half_t)*(2*half_a+1) + (da + half_a); end 1 = lors[2k].
+ *   norm   PSF_NORM_EFF: window total = untruncated mean of eta1*eta2 (FP64);
+ *          PSF_NORM_UNIT: total 1; PSF_NORM_NONE: as summed.
+ * table/eta are the outputs of psf_response_build for the same scanner/desc.
+ */
+int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *desc, const float *table,
+                   const double *eta, const int32_t *lors, int64_t n_lors, int32_t half_t,
+                   int32_t half_a, int32_t norm, float *spread, void *stream);
+
+/* Number of LORs of a structured set, and of its spread classes (one per
+ * transaxial pair with a < nt_block times ring difference; every LOR of the
+ * set has the spread of its class by the ring's rotation and axial
+ * translation symmetry). */
+int psf_lor_set_size(const psf_scanner *scanner, const psf_lor_set *set, int64_t *n_lors,
+                     int64_t *n_classes);
+
+/* Writes the LORs of the set (device int32 [n_lors][2]) in row order. */
+int psf_lor_set_list(const psf_scanner *scanner, const psf_lor_set *set, int32_t *lors,
+                     void *stream);
+
+/* Writes one representative LOR per spread class (device int32 [n_classes][2]),
+ * in class order; feed them to psf_bin_spread to get the class spreads. */
+int psf_lor_set_classes(const psf_scanner *scanner, const psf_lor_set *set, int32_t *lors,
+                        void *stream);
+
+/*
+ * System-matrix rows in CSR (row_ptr int64 [n_lors+1], col int32 sorted
+ * ascending, duplicates merged).
+ *  spread == NULL: geometric rows G -- chord lengths (mm) of the segment
+ *    joining the two crystals' front-face centres through the voxel grid; a
+ *    voxel belongs to a row iff its chord is positive.
+ *  spread != NULL: PSF rows A = S G over the listed LORs: row m is the sum of
+ *    w_g[e1][e2] * G_g over every listed LOR g and window entry landing on
+ *    LOR m's crystal pair (pairs outside the list are dropped).  Supported
+ *    when the image has at most 49152 voxels (dense merge in shared memory);
+ *    use the factored projector otherwise.
+ *  val: float (PSF_F32) or bf16/fp16 (PSF_BF16/PSF_F16) with row_scale
+ *    (device float [n_lors]) holding each row's FP32 scale (stored value =
+ *    value / scale, scale = row max); row_scale must be NULL for PSF_F32.
+ *  col == NULL: size query, only row_ptr and *nnz_out are written.
+ *  capacity < nnz: PSF_ECAPACITY with *nnz_out = required nnz.
+ * Synchronises `stream` once (to read nnz).  *nnz_out (host).
+ */
+int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *image, const int32_t *lors,
+                    int64_t n_lors, const float *spread, int32_t half_t, int32_t half_a,
+                    int32_t dtype, int64_t *row_ptr, int32_t *col, void *val, float *row_scale,
+                    int64_t capacity, int64_t *nnz_out, void *stream);
+
+/*
+ * Projector plan over caller CSR (pointers retained until destroy; the caller
+ * keeps them alive).  The plan owns its scratch (allocated here).
+ */
+typedef struct psf_matrix psf_matrix;
+
+int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_cols, const int64_t *row_ptr,
+                      const int32_t *col, const void *val, int32_t dtype, const float *row_scale,
+                      void *stream);
+
+/* Factored PSF form A = S G (Sec. 2.3) for a structured LOR set: the rows of
+ * the plan are G in set order, and S applies the class spreads
+ * (device float [n_classes][E][E], kept by pointer) in LOR space. */
+int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner, const psf_lor_set *set,
+                          int32_t half_t, int32_t half_a, const float *class_spread);
+
+int psf_matrix_destroy(psf_matrix *m);
+
+/* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]). */
+int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream);
+
+/* x = A^T y (overwrite). */
+int psf_back(const psf_matrix *m, const float *y, float *x, void *stream);
+
+/* MLEM steps (Sec. 3): ratio[i] = y[i] / yhat[i] (0 where yhat[i] <= 0). */
+int psf_em_ratio(const float *y, const float *yhat, float *ratio, int64_t n, void *stream);
+
+/* x[v] = x[v] * bp[v] / sens[v] where sens[v] >= floor, else 0. */
+int psf_em_update(float *x, const float *bp, const float *sens, float floor, int64_t n,
+                  void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSF_H */

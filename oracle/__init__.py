@@ -21,6 +21,7 @@ from .oracle import (  # noqa: F401
     table_build,
     composed,
     spread,
+    tie_margin,
     siddon,
     slabclip,
     rows_geom,

@@ -95,6 +95,7 @@ def _load():
                 "orc_spread_apply": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
                 "orc_spread_adjoint": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
                 "orc_threads": (C.c_int, []),
+                "orc_tie_margin": (None, [_P, _P, _P, _P, C.c_int64, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -208,6 +209,18 @@ def spread(scanner: dict, table: dict, T: np.ndarray, lors, Wt: int, Wa: int,
     _load().orc_spread(C.byref(s), C.byref(t), _ptr(T), _ptr(L), L.shape[0], int(Wt), int(Wa),
                        int(norm), _ptr(w))
     return w
+
+
+def tie_margin(scanner: dict, table: dict, T: np.ndarray, lors) -> np.ndarray:
+    """Per LOR, the smallest distance of a rounding decision to its boundary
+    (see orc_tie_margin); LORs below working precision have several correct
+    spreads."""
+    s, t = _scanner(scanner), _table(table)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    L = _lors(lors)
+    out = np.zeros(L.shape[0])
+    _load().orc_tie_margin(C.byref(s), C.byref(t), _ptr(T), _ptr(L), L.shape[0], _ptr(out))
+    return out
 
 
 def _trace(fn, image: dict, a, b):

@@ -500,9 +500,113 @@ void orc_spread(const orc_scanner *s, const orc_table *tb, const double *T,
     }
 }
 
+/*
+ * Diagnostic for parity tests: the smallest distance, over every sub-LOR of
+ * each listed LOR, between a rounding decision of orc_composed and its
+ * boundary -- nearest angle node (in node spacings), and on the gap path the
+ * virtual crystal / sub-position / ring decisions (in their own spacings).
+ * A LOR whose margin is below the working precision of another implementation
+ * has more than one correct spread.  Decisions that cannot change the result
+ * (a gap path that reaches no crystal) are not counted.
+ */
+static double frac_margin(double x)
+{
+    return fabs(x - rint(x));
+}
+
+void orc_tie_margin(const orc_scanner *s, const orc_table *tb, const double *T,
+                    const int32_t *lors, int64_t n, double *margin)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < n; ++k) {
+        int id1 = lors[2 * k], id2 = lors[2 * k + 1];
+        double best = 1.0;
+        orc_xtal x1 = orc_decode(s, id1), x2 = orc_decode(s, id2);
+        if (x1.block != x2.block) {
+            for (int p1 = 0; p1 < tb->Pt; ++p1)
+            for (int q1 = 0; q1 < tb->Pa; ++q1)
+            for (int p2 = 0; p2 < tb->Pt; ++p2)
+            for (int q2 = 0; q2 < tb->Pa; ++q2) {
+                double E1[3], E2[3];
+                orc_face_point(s, id1, ((p1 + 0.5) / tb->Pt - 0.5) * s->wt,
+                               ((q1 + 0.5) / tb->Pa - 0.5) * s->wa, E1);
+                orc_face_point(s, id2, ((p2 + 0.5) / tb->Pt - 0.5) * s->wt,
+                               ((q2 + 0.5) / tb->Pa - 0.5) * s->wa, E2);
+                for (int end = 0; end < 2; ++end) {
+                    orc_xtal x = end ? x2 : x1;
+                    int ipt = end ? p2 : p1, ipa = end ? q2 : q1;
+                    double d[3];
+                    for (int c = 0; c < 3; ++c) d[c] = end ? E2[c] - E1[c] : E1[c] - E2[c];
+                    double vn = d[0] * x.n[0] + d[1] * x.n[1];
+                    double vt = d[0] * x.t[0] + d[1] * x.t[1];
+                    if (!(vn > 0.0)) continue;
+                    double alpha = atan2(fabs(vt), vn);
+                    double theta = atan2(fabs(d[2]), sqrt(vn * vn + vt * vt));
+                    double st = tb->amax_t_deg / tb->Kt * ORC_PI / 180.0;
+                    double sa = tb->amax_a_deg / tb->Ka * ORC_PI / 180.0;
+                    /* nearest node: boundaries where angle/step + 1/2 is an integer */
+                    if (alpha / st < tb->Kt - 1) best = fmin(best, frac_margin(alpha / st + 0.5));
+                    if (theta / sa < tb->Ka - 1) best = fmin(best, frac_margin(theta / sa + 0.5));
+                    int sgt = vt >= 0.0 ? 1 : -1, sga = d[2] >= 0.0 ? 1 : -1;
+                    double beta, AP1, run;
+                    orc_gap_eq(s, alpha, 0.5 * orc_block_width(s) -
+                                   sgt * (x.s_centre + ((ipt + 0.5) / tb->Pt - 0.5) * s->wt),
+                               &beta, &AP1, &run);
+                    if (!(beta > 0.0)) continue;
+                    /* does the gap path reach any stored crystal? */
+                    double q = AP1 - s->gt;
+                    if (q < 0.0) q = 0.0;
+                    int m = (int)floor(q / orc_pt(s));
+                    int kt1 = orc_node(beta, tb->amax_t_deg, tb->Kt);
+                    int ka = orc_node(theta, tb->amax_a_deg, tb->Ka);
+                    double reach = 0.0;
+                    for (int iu = 0; iu < tb->Pt; ++iu)
+                        for (int iv = 0; iv < tb->Pa; ++iv)
+                            for (int dx = m; dx < tb->Mt && dx <= m + 2; ++dx)
+                                for (int dz = 0; dz < tb->Ma; ++dz)
+                                    reach += T[(orc_tidx(tb, kt1, ka, iu, iv) * tb->Mt + dx) * tb->Ma + dz];
+                    if (reach == 0.0) continue;
+                    if (beta / st < tb->Kt - 1) best = fmin(best, frac_margin(beta / st + 0.5));
+                    best = fmin(best, frac_margin(q / orc_pt(s)));
+                    double f = q - m * orc_pt(s);
+                    best = fmin(best, fabs(f - s->wt) / orc_pt(s));
+                    if (f < s->wt) best = fmin(best, frac_margin((s->wt - f) / s->wt * tb->Pt));
+                    if (tb->Pa > 1 || orc_nrings(s) > 1) {
+                        double z1 = x.z_centre + ((ipa + 0.5) / tb->Pa - 0.5) * s->wa +
+                                    sga * run * tan(theta);
+                        double zl = z1 - (orc_ring_z(s, 0) - 0.5 * s->wa);
+                        best = fmin(best, frac_margin(zl / orc_pa(s)));
+                        double fa = zl - floor(zl / orc_pa(s)) * orc_pa(s);
+                        best = fmin(best, fabs(fa - s->wa) / orc_pa(s));
+                        if (fa <= s->wa) best = fmin(best, frac_margin(fa / s->wa * tb->Pa));
+                    }
+                }
+            }
+        }
+        margin[k] = best;
+    }
+}
+
 /* ---------------------------------------------------------------------- */
 /* Geometric rows: chord lengths of a segment through the voxel grid      */
 /* ---------------------------------------------------------------------- */
+
+/*
+ * Reading of "a segment lying on a grid plane belongs to the voxel above": the
+ * crystal positions of a ring are computed with rounded sines and cosines, so
+ * a LOR that lies on a grid plane by symmetry comes out tilted by ~1e-15 mm.
+ * A coordinate that changes by less than 1e-9 voxel over the whole segment is
+ * taken as constant, and a constant coordinate within 1e-9 voxel of a plane
+ * is taken to lie on it.  Returns 1 and the voxel index for such an axis.
+ */
+static int orc_parallel_axis(double a, double b, double o, double d, int *idx)
+{
+    if (!(fabs((b - a) / d) < 1e-9)) return 0;
+    double u = (a - o) / d;
+    if (fabs(u - rint(u)) < 1e-9) u = rint(u);
+    *idx = (int)floor(u);
+    return 1;
+}
 
 static int cmp_double(const void *a, const void *b)
 {
@@ -539,14 +643,16 @@ int orc_siddon(const orc_image *im, const double a[3], const double b[3],
     }
     L = sqrt(L);
     double amin = 0.0, amax = 1.0;
+    int par[3], fix[3];
     for (int c = 0; c < 3; ++c) {
         double lo = oo[c], hi = oo[c] + nn[c] * dd[c];
-        if (d[c] != 0.0) {
+        par[c] = orc_parallel_axis(a[c], b[c], oo[c], dd[c], &fix[c]);
+        if (!par[c]) {
             double t0 = (lo - a[c]) / d[c], t1 = (hi - a[c]) / d[c];
             if (t0 > t1) { double t = t0; t0 = t1; t1 = t; }
             if (t0 > amin) amin = t0;
             if (t1 < amax) amax = t1;
-        } else if (!(a[c] >= lo && a[c] < hi)) {
+        } else if (fix[c] < 0 || fix[c] >= nn[c]) {
             return 0;
         }
     }
@@ -557,7 +663,7 @@ int orc_siddon(const orc_image *im, const double a[3], const double b[3],
     al[k++] = amin;
     al[k++] = amax;
     for (int c = 0; c < 3; ++c) {
-        if (d[c] == 0.0) continue;
+        if (par[c]) continue;
         for (int i = 0; i <= nn[c]; ++i) {
             double t = (oo[c] + i * dd[c] - a[c]) / d[c];
             if (t > amin && t < amax) al[k++] = t;
@@ -571,7 +677,7 @@ int orc_siddon(const orc_image *im, const double a[3], const double b[3],
         double mid = 0.5 * (al[j] + al[j + 1]);
         int v[3], ok = 1;
         for (int c = 0; c < 3; ++c) {
-            v[c] = (int)floor((a[c] + mid * d[c] - oo[c]) / dd[c]);
+            v[c] = par[c] ? fix[c] : (int)floor((a[c] + mid * d[c] - oo[c]) / dd[c]);
             if (v[c] < 0 || v[c] >= nn[c]) ok = 0;
         }
         if (!ok) continue;
@@ -610,6 +716,8 @@ int orc_slabclip(const orc_image *im, const double a[3], const double b[3],
     const double dd[3] = {im->dx, im->dy, im->dz};
     const double oo[3] = {im->ox, im->oy, im->oz};
     int out = 0;
+    int par[3], fix[3];
+    for (int c = 0; c < 3; ++c) par[c] = orc_parallel_axis(a[c], b[c], oo[c], dd[c], &fix[c]);
     for (int iz = 0; iz < nn[2]; ++iz)
     for (int iy = 0; iy < nn[1]; ++iy)
     for (int ix = 0; ix < nn[0]; ++ix) {
@@ -618,7 +726,9 @@ int orc_slabclip(const orc_image *im, const double a[3], const double b[3],
         int ok = 1;
         for (int c = 0; c < 3 && ok; ++c) {
             double lo = oo[c] + v[c] * dd[c], hi = lo + dd[c];
-            if (d[c] != 0.0) {
+            if (par[c]) {
+                if (fix[c] != v[c]) ok = 0;
+            } else if (d[c] != 0.0) {
                 double s0 = (lo - a[c]) / d[c], s1 = (hi - a[c]) / d[c];
                 if (s0 > s1) { double t = s0; s0 = s1; s1 = t; }
                 if (s0 > t0) t0 = s0;

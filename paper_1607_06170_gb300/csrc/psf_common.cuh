@@ -1,0 +1,118 @@
+// Shared definitions of the GB300 P-SPIR library: derived scanner constants,
+// argument validation, error plumbing and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "psf.h"
+
+namespace psf {
+
+// Last CUDA error seen by an entry point (for psf_strerror on PSF_ECUDA).
+void set_cuda_error(cudaError_t e);
+
+#define PSF_TRY(call)                                \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) {                     \
+            ::psf::set_cuda_error(e_);               \
+            return PSF_ECUDA;                        \
+        }                                            \
+    } while (0)
+
+#define PSF_LAUNCHED()                               \
+    do {                                             \
+        cudaError_t e_ = cudaGetLastError();         \
+        if (e_ != cudaSuccess) {                     \
+            ::psf::set_cuda_error(e_);               \
+            return PSF_ECUDA;                        \
+        }                                            \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Scanner constants as the kernels use them (passed by value).
+struct Scan {
+    int R, Nb, Nt, NR;          // blocks, crystals/block, crystals/ring, rings
+    float wt, wa, depth;        // crystal width (transaxial / axial), depth
+    float gt, ga, pt, pa;       // intra-block gaps and pitches
+    float mu, radius;
+    float half_w;               // half the transaxial block width
+    float sigma;                // corner gap AB = BC of the gap construction
+    float z0;                   // axial centre of ring 0 (rings on a uniform pitch)
+    float two_pi_R;             // angle between neighbouring block normals
+    float sin_two_pi_R;
+    double radius64, pt64, pa64, z064;
+};
+
+// Table layout constants.
+struct Tab {
+    int Kt, Ka, Pt, Pa, Mt, Ma;
+    float dt, da;               // node spacing (radians)
+    float inv_dt, inv_da;
+};
+
+struct Img {
+    int nx, ny, nz;
+    double dx, dy, dz, ox, oy, oz;
+};
+
+// Validation + derivation (host).  Return PSF_OK or PSF_EINVAL.
+int make_scan(const psf_scanner *s, Scan *out);
+int make_tab(const psf_table_desc *d, const Scan &sc, Tab *out, bool check_reach);
+int make_img(const psf_image *im, Img *out);
+
+// Grid for a grid-stride loop over n items: at most 8 CTAs per SM.
+int grid_for(int64_t n, int block);
+
+__host__ __device__ inline int64_t table_entry(const Tab &t, int kt, int ka, int iu, int iv) {
+    return (((int64_t)kt * t.Ka + ka) * t.Pt + iu) * t.Pa + iv;
+}
+
+// Conversions with the device intrinsics' rounding, usable from host code.
+__host__ __device__ __forceinline__ int f2i_rd(float x) {
+#ifdef __CUDA_ARCH__
+    return __float2int_rd(x);
+#else
+    return (int)floorf(x);
+#endif
+}
+
+__host__ __device__ __forceinline__ long long d2ll_rn(double x) {
+#ifdef __CUDA_ARCH__
+    return __double2ll_rn(x);
+#else
+    return llrint(x);
+#endif
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ T ldg(const T *p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+// Nearest angle node (nodes at k * spacing, clamped to the last node).
+__host__ __device__ __forceinline__ int angle_node(float ang, float inv_step, int K) {
+    int k = f2i_rd(fmaf(ang, inv_step, 0.5f));
+    return k < K - 1 ? k : K - 1;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace psf

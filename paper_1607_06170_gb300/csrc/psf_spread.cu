@@ -1,0 +1,251 @@
+// K3: homogenization spread of each LOR (Sec. 2.2 Eq. 10, Sec. 2.3 Eq. 11-12)
+// with the neighbouring-block path of Sec. 2.1.2 (Eq. 2, 4, 5).
+//
+// One CTA per LOR.  The sub-position centres of both crystal faces are staged
+// in shared memory; each thread takes one sub-LOR (pair of sub-positions) at a
+// time and evaluates the two single-photon responses restricted to the window
+// quadrant the photon travels into (the response is one-sided).  Sub-LORs are
+// grouped by their pair of travel directions, and each group's contribution is
+// a small dense product sum_s r1_s (x) r2_s accumulated by the threads that own
+// the outputs, chunk by chunk (FP32, deterministic order).  The per-LOR
+// normalisation totals are FP64 block reductions.
+#include "psf_common.cuh"
+#include "psf_end.cuh"
+
+namespace psf {
+
+constexpr int SP_THREADS = 256;
+constexpr int SP_PATS = 16;  // travel-sign patterns of the two ends
+struct SpreadSmem {
+    float *R1, *R2;        // [SP_THREADS][Q]
+    float *accp;           // [SP_PATS][Q*Q]
+    float *wwin;           // [E*E]
+    float *pts;            // end points: [2][Pt*Pa][4] = (x, y, z, s_entry)
+    int *pat;              // [SP_THREADS]
+    int *order;            // [SP_THREADS]
+    int *cnt;              // [SP_PATS + 1] starts
+    int *wcnt;             // [8 warps][SP_PATS]
+    double *red;           // [2 * 8]
+};
+
+__global__ void __launch_bounds__(SP_THREADS) spread_kernel(
+    Scan sc, Tab tb, const float *__restrict__ T, const double *__restrict__ eta,
+    const int32_t *__restrict__ lors, int64_t n_lors, int Wt, int Wa, int norm,
+    float *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int Q = (Wt + 1) * (Wa + 1);
+    const int E = (2 * Wt + 1) * (2 * Wa + 1);
+    const int NP = tb.Pt * tb.Pa;
+    const int nsub = NP * NP;
+    SpreadSmem s;
+    {
+        unsigned char *p = smraw;
+        s.red = (double *)p; p += sizeof(double) * 16;
+        s.R1 = (float *)p; p += sizeof(float) * SP_THREADS * Q;
+        s.R2 = (float *)p; p += sizeof(float) * SP_THREADS * Q;
+        s.accp = (float *)p; p += sizeof(float) * SP_PATS * Q * Q;
+        s.wwin = (float *)p; p += sizeof(float) * E * E;
+        s.pts = (float *)p; p += sizeof(float) * 2 * NP * 4;
+        s.pat = (int *)p; p += sizeof(int) * SP_THREADS;
+        s.order = (int *)p; p += sizeof(int) * SP_THREADS;
+        s.cnt = (int *)p; p += sizeof(int) * (SP_PATS + 1);
+        s.wcnt = (int *)p;
+    }
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int64_t lor = blockIdx.x; lor < n_lors; lor += gridDim.x) {
+        const int id1 = lors[2 * lor], id2 = lors[2 * lor + 1];
+        const int ring1 = id1 / sc.Nt, c1 = id1 - ring1 * sc.Nt;
+        const int ring2 = id2 / sc.Nt, c2 = id2 - ring2 * sc.Nt;
+        const int b1 = c1 / sc.Nb, i1 = c1 - b1 * sc.Nb;
+        const int b2 = c2 / sc.Nb, i2 = c2 - b2 * sc.Nb;
+        float *o = out + lor * (int64_t)E * E;
+        const int nc = sc.Nt * sc.NR;
+        // same block: the chord runs along a block face and enters neither
+        // crystal; invalid crystal ids also get no spread
+        if (b1 == b2 || id1 < 0 || id2 < 0 || id1 >= nc || id2 >= nc) {
+            for (int k = t; k < E * E; k += SP_THREADS) o[k] = 0.0f;
+            continue;
+        }
+        float sb1, cb1, sb2, cb2;
+        sincospif(2.0f * b1 / sc.R, &sb1, &cb1);
+        sincospif(2.0f * b2 / sc.R, &sb2, &cb2);
+        // stage the sub-position centres of both faces
+        for (int k = t; k < 2 * NP; k += SP_THREADS) {
+            int end = k / NP, sp = k - end * NP;
+            int p = sp / tb.Pa, q = sp - p * tb.Pa;
+            int i = end ? i2 : i1, ring = end ? ring2 : ring1;
+            float cb = end ? cb2 : cb1, sb = end ? sb2 : sb1;
+            float se = (i - 0.5f * (sc.Nb - 1)) * sc.pt + ((p + 0.5f) / tb.Pt - 0.5f) * sc.wt;
+            float ze = sc.z0 + ring * sc.pa + ((q + 0.5f) / tb.Pa - 0.5f) * sc.wa;
+            float *P = s.pts + k * 4;
+            P[0] = sc.radius * cb - se * sb;
+            P[1] = sc.radius * sb + se * cb;
+            P[2] = ze;
+            P[3] = se;
+        }
+        for (int k = t; k < SP_PATS * Q * Q; k += SP_THREADS) s.accp[k] = 0.0f;
+        double sfull = 0.0, swin = 0.0;
+        __syncthreads();
+        for (int base = 0; base < nsub; base += SP_THREADS) {
+            int sidx = base + t;
+            int pt_ = SP_PATS;  // empty slot
+            if (sidx < nsub) {
+                int s1 = sidx / NP, s2 = sidx - s1 * NP;
+                const float *P1 = s.pts + s1 * 4;
+                const float *P2 = s.pts + (NP + s2) * 4;
+                float dx = P1[0] - P2[0], dy = P1[1] - P2[1], dz = P1[2] - P2[2];
+                EndResp r1, r2;
+                end_response(sc, tb, T, eta, i1, ring1, cb1, sb1, s1 / tb.Pa, s1 % tb.Pa, P1[3],
+                             P1[2], dx, dy, dz, Wt, Wa, r1);
+                end_response(sc, tb, T, eta, i2, ring2, cb2, sb2, s2 / tb.Pa, s2 % tb.Pa, P2[3],
+                             P2[2], -dx, -dy, -dz, Wt, Wa, r2);
+                if (r1.valid && r2.valid) {
+                    float w1 = 0.0f, w2 = 0.0f;
+                    for (int k = 0; k < Q; ++k) {
+                        s.R1[t * Q + k] = r1.q[k];
+                        s.R2[t * Q + k] = r2.q[k];
+                        w1 += r1.q[k];
+                        w2 += r2.q[k];
+                    }
+                    sfull += r1.eta * r2.eta;
+                    swin += (double)w1 * (double)w2;
+                    pt_ = ((r1.sgt > 0) << 3) | ((r1.sga > 0) << 2) | ((r2.sgt > 0) << 1) |
+                          (r2.sga > 0);
+                }
+            }
+            s.pat[t] = pt_;
+            // stable counting sort of this chunk by pattern (warp ballots)
+            for (int P = 0; P < SP_PATS; ++P) {
+                unsigned m = __ballot_sync(0xffffffffu, pt_ == P);
+                if (lane == 0) s.wcnt[warp * SP_PATS + P] = __popc(m);
+            }
+            __syncthreads();
+            if (t == 0) {
+                int acc = 0;
+                for (int P = 0; P < SP_PATS; ++P) {
+                    s.cnt[P] = acc;
+                    for (int w = 0; w < SP_THREADS / 32; ++w) {
+                        int c = s.wcnt[w * SP_PATS + P];
+                        s.wcnt[w * SP_PATS + P] = acc;
+                        acc += c;
+                    }
+                }
+                s.cnt[SP_PATS] = acc;
+            }
+            __syncthreads();
+            // rank within (warp, pattern)
+            for (int P = 0; P < SP_PATS; ++P) {
+                unsigned m = __ballot_sync(0xffffffffu, pt_ == P);
+                if (pt_ == P) {
+                    int r = __popc(m & ((1u << lane) - 1u));
+                    s.order[s.wcnt[warp * SP_PATS + P] + r] = t;
+                }
+            }
+            __syncthreads();
+            if (t < Q * Q) {
+                const int e1 = t / Q, e2 = t - e1 * Q;
+                for (int P = 0; P < SP_PATS; ++P) {
+                    int k0 = s.cnt[P], k1 = s.cnt[P + 1];
+                    if (k1 == k0) continue;
+                    float acc = 0.0f;
+                    for (int k = k0; k < k1; ++k) {
+                        int sl = s.order[k];
+                        acc = fmaf(s.R1[sl * Q + e1], s.R2[sl * Q + e2], acc);
+                    }
+                    s.accp[P * Q * Q + t] += acc;
+                }
+            }
+            __syncthreads();
+        }
+        // FP64 totals over the CTA
+        sfull = warp_sum_d(sfull);
+        swin = warp_sum_d(swin);
+        if (lane == 0) {
+            s.red[warp] = sfull;
+            s.red[8 + warp] = swin;
+        }
+        for (int k = t; k < E * E; k += SP_THREADS) s.wwin[k] = 0.0f;
+        __syncthreads();
+        if (t == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < SP_THREADS / 32; ++w) {
+                a += s.red[w];
+                b += s.red[8 + w];
+            }
+            s.red[0] = a;
+            s.red[8] = b;
+        }
+        // fold the pattern-local blocks into the window
+        const int W2a = 2 * Wa + 1;
+        for (int P = 0; P < SP_PATS; ++P) {
+            if (t < Q * Q) {
+                float v = s.accp[P * Q * Q + t];
+                if (v != 0.0f) {
+                    int sgt1 = (P >> 3) & 1 ? 1 : -1, sga1 = (P >> 2) & 1 ? 1 : -1;
+                    int sgt2 = (P >> 1) & 1 ? 1 : -1, sga2 = P & 1 ? 1 : -1;
+                    int e1 = t / Q, e2 = t - e1 * Q;
+                    int x1 = e1 / (Wa + 1), z1 = e1 - x1 * (Wa + 1);
+                    int x2 = e2 / (Wa + 1), z2 = e2 - x2 * (Wa + 1);
+                    int w1 = (sgt1 * x1 + Wt) * W2a + (sga1 * z1 + Wa);
+                    int w2 = (sgt2 * x2 + Wt) * W2a + (sga2 * z2 + Wa);
+                    s.wwin[w1 * E + w2] += v;
+                }
+            }
+            __syncthreads();
+        }
+        // wwin holds sums over sub-LORs; sw is its total, sf the untruncated one
+        double sf = s.red[0], sw = s.red[8];
+        double scale = 1.0 / nsub;                                     // NONE: mean
+        if (norm == PSF_NORM_EFF && sw > 0.0) scale = sf / (sw * nsub);  // total = mean eta1 eta2
+        if (norm == PSF_NORM_UNIT && sw > 0.0) scale = 1.0 / sw;         // total = 1
+        float fs = (float)scale;
+        for (int k = t; k < E * E; k += SP_THREADS) o[k] = s.wwin[k] * fs;
+        __syncthreads();
+    }
+}
+
+static size_t spread_smem(const Tab &tb, int Wt, int Wa) {
+    int Q = (Wt + 1) * (Wa + 1), E = (2 * Wt + 1) * (2 * Wa + 1);
+    int NP = tb.Pt * tb.Pa;
+    size_t b = sizeof(double) * 16;
+    b += sizeof(float) * 2 * SP_THREADS * Q;
+    b += sizeof(float) * SP_PATS * Q * Q;
+    b += sizeof(float) * E * E;
+    b += sizeof(float) * 2 * NP * 4;
+    b += sizeof(int) * (2 * SP_THREADS + SP_PATS + 1 + 8 * SP_PATS);
+    return b;
+}
+
+}  // namespace psf
+
+using namespace psf;
+
+extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *desc,
+                              const float *table, const double *eta, const int32_t *lors,
+                              int64_t n_lors, int32_t half_t, int32_t half_a, int32_t norm,
+                              float *spread, void *stream) {
+    Scan sc;
+    Tab tb;
+    int rc = make_scan(scanner, &sc);
+    if (rc) return rc;
+    rc = make_tab(desc, sc, &tb, true);
+    if (rc) return rc;
+    if (half_t < 0 || half_a < 0 || (half_t + 1) * (half_a + 1) > SP_QMAX) return PSF_EINVAL;
+    if (norm < PSF_NORM_NONE || norm > PSF_NORM_UNIT) return PSF_EINVAL;
+    if (n_lors < 0) return PSF_EINVAL;
+    if (n_lors == 0) return PSF_OK;
+    if (!table || !eta || !lors || !spread) return PSF_EINVAL;
+    if (tb.Pt * tb.Pa > 1024) return PSF_EINVAL;
+    size_t shm = spread_smem(tb, half_t, half_a);
+    if (shm > 200 * 1024) return PSF_EINVAL;
+    PSF_TRY(cudaFuncSetAttribute(spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = n_lors < (int64_t)sms * 8 ? n_lors : (int64_t)sms * 8;
+    spread_kernel<<<(int)grid, SP_THREADS, shm, as_stream(stream)>>>(
+        sc, tb, table, eta, lors, n_lors, half_t, half_a, norm, spread);
+    PSF_LAUNCHED();
+    return PSF_OK;
+}

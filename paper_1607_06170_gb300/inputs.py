@@ -105,7 +105,7 @@ WORKLOADS = {
     "RING3D_SMALL": dict(
         index=11,
         scanner=scanner(12, 4, 4, 2, 1.9, 1.9, 10.0, 0.3, 0.3, 30.0, 0.3, 0.087),
-        table=table(13, 4, 4, 4, 16, 8, 65.0, 40.0),
+        table=table(13, 4, 4, 4, 16, 8, 65.0, 36.0),
         image=image(24, 24, 16, 1.5, 1.5, 1.1),
         window=(3, 2),
         lors=dict(fan_half=10, max_ring_diff=3),

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libpsf.so (the C ABI declared in include/psf.h).
+
+Argument marshalling only: tensors are passed as device pointers together
+with torch's current CUDA stream; every step of the computation runs in the
+library's kernels.  There is no fallback: if the library is missing or the
+process has no GPU the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpsf.so")
+
+PSF_F32, PSF_BF16, PSF_F16 = 0, 1, 2
+NORM_NONE, NORM_EFF, NORM_UNIT = 0, 1, 2
+_DT = {"f32": PSF_F32, "bf16": PSF_BF16, "f16": PSF_F16}
+_TORCH_DT = {PSF_F32: torch.float32, PSF_BF16: torch.bfloat16, PSF_F16: torch.float16}
+
+FUNCTIONS = [
+    "psf_strerror", "psf_table_size", "psf_response_build", "psf_bin_spread",
+    "psf_lor_set_size", "psf_lor_set_list", "psf_lor_set_classes", "psf_sysmat_rows",
+    "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
+    "psf_back", "psf_em_ratio", "psf_em_update",
+]
+
+
+class PSFError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class Scanner(C.Structure):
+    _fields_ = [("n_blocks", C.c_int32), ("nt_block", C.c_int32), ("na_block", C.c_int32),
+                ("n_block_rings", C.c_int32), ("xtal_w_t", C.c_double), ("xtal_w_a", C.c_double),
+                ("depth", C.c_double), ("gap_t", C.c_double), ("gap_a", C.c_double),
+                ("radius", C.c_double), ("block_gap_a", C.c_double), ("mu", C.c_double)]
+
+
+class TableDesc(C.Structure):
+    _fields_ = [("n_ang_t", C.c_int32), ("n_ang_a", C.c_int32), ("n_sub_t", C.c_int32),
+                ("n_sub_a", C.c_int32), ("max_off_t", C.c_int32), ("max_off_a", C.c_int32),
+                ("ang_max_t_deg", C.c_double), ("ang_max_a_deg", C.c_double)]
+
+
+class Image(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("reserved", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("ox", C.c_double), ("oy", C.c_double), ("oz", C.c_double)]
+
+
+class LorSet(C.Structure):
+    _fields_ = [("fan_half", C.c_int32), ("max_ring_diff", C.c_int32)]
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_SIGS = {
+    "psf_strerror": (C.c_char_p, [C.c_int]),
+    "psf_table_size": (C.c_int, [_P, _P, _P]),
+    "psf_response_build": (C.c_int, [_P, _P, _P, _P, _P]),
+    "psf_bin_spread": (C.c_int, [_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _P, _P]),
+    "psf_lor_set_size": (C.c_int, [_P, _P, _P, _P]),
+    "psf_lor_set_list": (C.c_int, [_P, _P, _P, _P]),
+    "psf_lor_set_classes": (C.c_int, [_P, _P, _P, _P]),
+    "psf_sysmat_rows": (C.c_int, [_P, _P, _P, _I64, _P, _I32, _I32, _I32, _P, _P, _P, _P, _I64,
+                                  _P, _P]),
+    "psf_matrix_create": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _I32, _P, _P]),
+    "psf_matrix_set_spread": (C.c_int, [_P, _P, _P, _I32, _I32, _P]),
+    "psf_matrix_destroy": (C.c_int, [_P]),
+    "psf_forward": (C.c_int, [_P, _P, _P, _P]),
+    "psf_back": (C.c_int, [_P, _P, _P, _P]),
+    "psf_em_ratio": (C.c_int, [_P, _P, _P, _I64, _P]),
+    "psf_em_update": (C.c_int, [_P, _P, _P, C.c_float, _I64, _P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libpsf.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().psf_strerror(int(code)).decode()
+
+
+def _ok(rc: int, where: str):
+    if rc != 0:
+        raise PSFError(rc, where)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def scanner(d: dict) -> Scanner:
+    return Scanner(int(d["n_blocks"]), int(d["nt_block"]), int(d["na_block"]),
+                   int(d["n_block_rings"]), float(d["xtal_w_t"]), float(d["xtal_w_a"]),
+                   float(d["depth"]), float(d["gap_t"]), float(d["gap_a"]), float(d["radius"]),
+                   float(d["block_gap_a"]), float(d["mu"]))
+
+
+def table_desc(d: dict) -> TableDesc:
+    return TableDesc(int(d["n_ang_t"]), int(d["n_ang_a"]), int(d["n_sub_t"]), int(d["n_sub_a"]),
+                     int(d["max_off_t"]), int(d["max_off_a"]), float(d["ang_max_t_deg"]),
+                     float(d["ang_max_a_deg"]))
+
+
+def image(d: dict) -> Image:
+    return Image(int(d["nx"]), int(d["ny"]), int(d["nz"]), 0, float(d["dx"]), float(d["dy"]),
+                 float(d["dz"]), float(d["ox"]), float(d["oy"]), float(d["oz"]))
+
+
+def lor_set(d: dict) -> LorSet:
+    return LorSet(int(d["fan_half"]), int(d["max_ring_diff"]))
+
+
+# ------------------------------------------------------------------ calls
+def response_build(sc: dict, tb: dict, device="cuda"):
+    """P-SPIR table (float32) and FP64 counting-rate prefix sums."""
+    s, t = scanner(sc), table_desc(tb)
+    shp = (t.n_ang_t, t.n_ang_a, t.n_sub_t, t.n_sub_a)
+    T = torch.empty(shp + (t.max_off_t, t.max_off_a), dtype=torch.float32, device=device)
+    eta = torch.empty(shp + (t.max_off_t + 1,), dtype=torch.float64, device=device)
+    _ok(lib().psf_response_build(C.byref(s), C.byref(t), _ptr(T), _ptr(eta), _stream()),
+        "psf_response_build")
+    return T, eta
+
+
+def bin_spread(sc: dict, tb: dict, T, eta, lors, half_t: int, half_a: int,
+               norm: int = NORM_EFF, out=None):
+    """Homogenization spread [n, E, E] of each LOR (int32 [n, 2] crystal ids)."""
+    s, t = scanner(sc), table_desc(tb)
+    n = lors.shape[0]
+    E = (2 * half_t + 1) * (2 * half_a + 1)
+    if out is None:
+        out = torch.empty((n, E, E), dtype=torch.float32, device=lors.device)
+    _ok(lib().psf_bin_spread(C.byref(s), C.byref(t), _ptr(T), _ptr(eta), _ptr(lors), n,
+                             half_t, half_a, norm, _ptr(out), _stream()), "psf_bin_spread")
+    return out
+
+
+def lor_set_size(sc: dict, ls: dict):
+    s, l = scanner(sc), lor_set(ls)
+    n, k = C.c_int64(), C.c_int64()
+    _ok(lib().psf_lor_set_size(C.byref(s), C.byref(l), C.byref(n), C.byref(k)),
+        "psf_lor_set_size")
+    return n.value, k.value
+
+
+def lor_set_list(sc: dict, ls: dict, device="cuda"):
+    n, _ = lor_set_size(sc, ls)
+    s, l = scanner(sc), lor_set(ls)
+    out = torch.empty((n, 2), dtype=torch.int32, device=device)
+    _ok(lib().psf_lor_set_list(C.byref(s), C.byref(l), _ptr(out), _stream()), "psf_lor_set_list")
+    return out
+
+
+def lor_set_classes(sc: dict, ls: dict, device="cuda"):
+    _, k = lor_set_size(sc, ls)
+    s, l = scanner(sc), lor_set(ls)
+    out = torch.empty((k, 2), dtype=torch.int32, device=device)
+    _ok(lib().psf_lor_set_classes(C.byref(s), C.byref(l), _ptr(out), _stream()),
+        "psf_lor_set_classes")
+    return out
+
+
+def sysmat_rows(sc: dict, im: dict, lors, spread=None, half_t: int = 0, half_a: int = 0,
+                dtype: str = "f32"):
+    """CSR rows (row_ptr int64, col int32, val, row_scale or None).
+
+    Two calls through the C ABI: a size query, then the fill into buffers of
+    exactly the required size.
+    """
+    s, i = scanner(sc), image(im)
+    n = lors.shape[0]
+    dt = _DT[dtype]
+    dev = lors.device
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    row_scale = None if dt == PSF_F32 else torch.empty(n, dtype=torch.float32, device=dev)
+    nnz = C.c_int64()
+    L = lib()
+    _ok(L.psf_sysmat_rows(C.byref(s), C.byref(i), _ptr(lors), n, _ptr(spread), half_t, half_a,
+                          dt, _ptr(row_ptr), None, None, _ptr(row_scale), 0, C.byref(nnz),
+                          _stream()), "psf_sysmat_rows(size)")
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    val = torch.empty(max(nnz.value, 1), dtype=_TORCH_DT[dt], device=dev)
+    _ok(L.psf_sysmat_rows(C.byref(s), C.byref(i), _ptr(lors), n, _ptr(spread), half_t, half_a,
+                          dt, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(row_scale), nnz.value,
+                          C.byref(nnz), _stream()), "psf_sysmat_rows")
+    return row_ptr, col[: nnz.value], val[: nnz.value], row_scale
+
+
+class Matrix:
+    """Projector plan over CSR tensors (kept alive by this object)."""
+
+    def __init__(self, row_ptr, col, val, n_cols: int, row_scale=None):
+        dt = {torch.float32: PSF_F32, torch.bfloat16: PSF_BF16, torch.float16: PSF_F16}[val.dtype]
+        self._keep = [row_ptr, col, val, row_scale]
+        self.n_rows = row_ptr.shape[0] - 1
+        self.n_cols = int(n_cols)
+        self._h = C.c_void_p()
+        _ok(lib().psf_matrix_create(C.byref(self._h), self.n_rows, self.n_cols, _ptr(row_ptr),
+                                    _ptr(col), _ptr(val), dt, _ptr(row_scale), _stream()),
+            "psf_matrix_create")
+
+    def set_spread(self, sc: dict, ls: dict, half_t: int, half_a: int, class_spread):
+        self._keep.append(class_spread)
+        s, l = scanner(sc), lor_set(ls)
+        _ok(lib().psf_matrix_set_spread(self._h, C.byref(s), C.byref(l), half_t, half_a,
+                                        _ptr(class_spread)), "psf_matrix_set_spread")
+        return self
+
+    def forward(self, x, out=None):
+        if out is None:
+            out = torch.empty(self.n_rows, dtype=torch.float32, device=x.device)
+        _ok(lib().psf_forward(self._h, _ptr(x), _ptr(out), _stream()), "psf_forward")
+        return out
+
+    def back(self, y, out=None):
+        if out is None:
+            out = torch.empty(self.n_cols, dtype=torch.float32, device=y.device)
+        _ok(lib().psf_back(self._h, _ptr(y), _ptr(out), _stream()), "psf_back")
+        return out
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.psf_matrix_destroy(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+
+def em_ratio(y, yhat, out=None):
+    out = torch.empty_like(y) if out is None else out
+    _ok(lib().psf_em_ratio(_ptr(y), _ptr(yhat), _ptr(out), y.numel(), _stream()), "psf_em_ratio")
+    return out
+
+
+def em_update(x, bp, sens, floor: float):
+    _ok(lib().psf_em_update(_ptr(x), _ptr(bp), _ptr(sens), float(floor), x.numel(), _stream()),
+        "psf_em_update")
+    return x

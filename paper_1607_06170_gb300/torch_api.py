@@ -1,0 +1,57 @@
+"""PyTorch-facing layer: the PSF projector as a differentiable op and the MLEM
+driver.  Every arithmetic step runs in libpsf.so; torch provides the tensors
+and the stream."""
+from __future__ import annotations
+
+import torch
+
+from . import psf
+
+
+class PSFProject(torch.autograd.Function):
+    """y = A x with A the PSF system matrix; the backward pass is the
+    hand-written PSF back-projector A^T (psf_back)."""
+
+    @staticmethod
+    def forward(ctx, x, matrix):
+        ctx.matrix = matrix
+        return matrix.forward(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        return ctx.matrix.back(grad_y.contiguous()), None
+
+
+def project(x, matrix):
+    return PSFProject.apply(x, matrix)
+
+
+def sensitivity(matrix, n_rows: int, device="cuda"):
+    ones = torch.ones(n_rows, dtype=torch.float32, device=device)
+    return matrix.back(ones)
+
+
+def mlem(matrix, y, iters: int = 10, x0=None, sens=None):
+    """MLEM (Sec. 3): sens = A^T 1; x <- x * A^T(y / A x) / sens.
+
+    Voxels with sens < 1e-12 * max(sens) are held at zero, and 0/0 in the
+    ratio is zero.  All steps are library kernels (psf_forward, psf_em_ratio,
+    psf_back, psf_em_update).
+    """
+    if sens is None:
+        sens = sensitivity(matrix, y.numel(), y.device)
+    floor = 1e-12 * float(sens.max())
+    if x0 is None:
+        x = torch.ones_like(sens)
+        psf.em_update(x, sens, sens, floor)  # 1 on voxels the scanner sees, 0 elsewhere
+    else:
+        x = x0.clone()
+    yhat = torch.empty_like(y)
+    ratio = torch.empty_like(y)
+    bp = torch.empty_like(sens)
+    for _ in range(iters):
+        matrix.forward(x, out=yhat)
+        psf.em_ratio(y, yhat, out=ratio)
+        matrix.back(ratio, out=bp)
+        psf.em_update(x, bp, sens, floor)
+    return x
