@@ -1,0 +1,384 @@
+"""Benchmark of the P-SPIR hot path on the 3D ring workload.
+
+Workload (RING3D): 24 blocks x 13 x 13 crystals x 4 block rings (312 crystals
+per ring, 52 rings), 1.9 mm crystals on a 2.2 mm pitch, radius 130 mm; 8 x 8
+entry sub-positions, 32 x 8 angle nodes; 44,732,688 LORs (ring difference
+<= 15, fan +-104); spread +-3 x +-3 crystals; 160 x 160 x 104 voxels of
+0.8 mm; seeded uniform-cylinder phantom.
+
+One step = one pass of the whole hot path: response table, class spreads,
+geometric rows G (count, scan, fill), sensitivity A^T 1 and one MLEM iteration
+(forward y = S G x, ratio, back-projection G^T S^T r, update).  The matrix
+(~53 GB) is regenerated every step, so inputs are far larger than L2.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "RING3D"
+METRIC = "PSF matrix nonzeros/s (psf_sysmat_rows, whole step) and PSF fwd+back LOR*voxel/s"
+UNIT = "nnz/s"
+
+
+def _env_int(k, d):
+    return int(os.environ.get(k, d))
+
+
+def dist_info():
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU leg
+def cpu_sample(n_tclass: int = 2):
+    """Time the FP64 oracle on a bounded sample of the workload.
+
+    The sample is n_tclass transaxial spread classes with all their members:
+    every rotation of each class's crystal pair by whole blocks (24) times all
+    1,372 ring pairs, and the spreads of those classes for all 31 ring
+    differences.  The oracle builds the table, the spreads (one per class, the
+    same amortisation as the full job), the chord rows, and projects forward and
+    back with them.  Returns (nnz/s, seconds, threads, description)."""
+    import numpy as np
+
+    import oracle
+    from paper_1607_06170_gb300 import inputs as I
+
+    oracle.build()
+    w = I.workload(WORKLOAD)
+    s, t, im = w["scanner"], w["table"], w["image"]
+    Wt, Wa = w["window"]
+    nt, nb, R = I.n_transaxial(s), s["nt_block"], s["n_blocks"]
+    tp = I.transaxial_pairs(s, w["lors"]["fan_half"])
+    cls = tp[tp[:, 0] < nb]
+    pick = cls[np.linspace(0, len(cls) - 1, n_tclass).astype(int)]
+    rp = I.ring_pairs(s, w["lors"]["max_ring_diff"]).astype(np.int64)
+    lors = []
+    for a, b in pick:
+        for k in range(R):
+            ta, tb_ = (a + k * nb) % nt, (b + k * nb) % nt
+            lo, hi = min(ta, tb_), max(ta, tb_)
+            ra_, rb_ = (rp[:, 0], rp[:, 1]) if ta < tb_ else (rp[:, 1], rp[:, 0])
+            lors.append(np.stack([ra_ * nt + lo, rb_ * nt + hi], 1))
+    lors = np.concatenate(lors).astype(np.int32)
+    Dm = w["lors"]["max_ring_diff"]
+    reps = []
+    for a, b in pick:
+        for d in range(-Dm, Dm + 1):
+            ra = max(0, -d)
+            reps.append((ra * nt + a, (ra + d) * nt + b))
+    reps = np.array(reps, dtype=np.int32)
+    x = I.phantom_cylinder(im, 1).reshape(-1).astype(np.float64)
+    nv = x.size
+    t0 = time.perf_counter()
+    T, _ = oracle.table_build(s, t)
+    oracle.spread(s, t, T, reps, Wt, Wa)
+    G = oracle.rows_geom(s, im, lors)
+    y = oracle.csr_fwd(G, x)
+    oracle.csr_back(G, y, nv)
+    dt = time.perf_counter() - t0
+    nnz = int(G[0][-1])
+    desc = (f"{len(lors)} LORs ({n_tclass} transaxial classes x {R} rotations x {len(rp)} ring "
+            f"pairs, {nnz} nnz) + {len(reps)} class spreads + table; rows, forward, back")
+    return nnz / dt, dt, oracle.threads(), desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if world > 1 and rank != 0:
+        return
+    # each step: the oracle on one bounded sample (one transaxial class)
+    for _ in range(args.warmup):
+        cpu_sample(1)
+    rates, times = [], []
+    desc, cores = "", 1
+    for _ in range(args.steps):
+        r, dt, cores, desc = cpu_sample(1)
+        rates.append(r)
+        times.append(dt)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_1607_06170_gb300 import build as B
+    from paper_1607_06170_gb300 import inputs as I
+    from paper_1607_06170_gb300 import psf as P
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+    w = I.workload(WORKLOAD)
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    nv = im["nx"] * im["ny"] * im["nz"]
+    n_lors, n_cls = P.lor_set_size(s, ls)
+    # replicas: every rank runs the whole workload on its own GPU
+    x_host = torch.from_numpy(I.phantom_cylinder(im, 1).reshape(-1)).pin_memory()
+    x = x_host.to(dev)
+    L = P.lor_set_list(s, ls, device=dev)
+    row_ptr = torch.empty(n_lors + 1, dtype=torch.int64, device=dev)
+    # size query once, then buffers of that capacity are reused by every step
+    _, col, val, _ = P.sysmat_rows(s, im, L, buffers=None)
+    nnz = col.numel()
+    st = torch.cuda.current_stream()
+    stages = ["table", "classes", "spread", "rows", "sens", "forward", "ratio", "back", "update"]
+    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for k in stages}
+    y_meas = None
+
+    def step(x_in, y_in, record=None):
+        def mark(k, i):
+            if record is not None:
+                ev[k][i].record(st)
+
+        mark("table", 0)
+        T, eta = P.response_build(s, t, device=dev)
+        mark("table", 1)
+        mark("classes", 0)
+        C = P.lor_set_classes(s, ls, device=dev)
+        mark("classes", 1)
+        mark("spread", 0)
+        WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)
+        mark("spread", 1)
+        mark("rows", 0)
+        P.sysmat_rows(s, im, L, buffers=(row_ptr, col, val, None))
+        mark("rows", 1)
+        M.set_spread(s, ls, Wt, Wa, WC)
+        mark("sens", 0)
+        ones = torch.ones(n_lors, dtype=torch.float32, device=dev)
+        sens = M.back(ones)
+        mark("sens", 1)
+        mark("forward", 0)
+        yh = M.forward(x_in)
+        mark("forward", 1)
+        mark("ratio", 0)
+        r = P.em_ratio(y_in, yh)
+        mark("ratio", 1)
+        mark("back", 0)
+        bp = M.back(r)
+        mark("back", 1)
+        mark("update", 0)
+        x_out = x_in.clone()
+        P.em_update(x_out, bp, sens, 1e-12)
+        mark("update", 1)
+        return x_out
+
+    # one projector plan over the reused CSR buffers; measured data = noiseless
+    # projection of the phantom (computed once)
+    M = P.Matrix(row_ptr, col, val, nv)
+    T0, e0 = P.response_build(s, t, device=dev)
+    WC0 = P.bin_spread(s, t, T0, e0, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+    P.sysmat_rows(s, im, L, buffers=(row_ptr, col, val, None))
+    M.set_spread(s, ls, Wt, Wa, WC0)
+    y_meas = M.forward(x).clone()
+    y_host = y_meas.cpu().pin_memory()
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(x, y_meas)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    stage_ms = {k: [] for k in stages}
+    torch.cuda.synchronize()
+    t0.record(st)
+    xi = x
+    for _ in range(args.steps):
+        xi = step(x, y_meas, record=True)
+        torch.cuda.synchronize()  # rows stage synchronises anyway; read stage events
+        for k in stages:
+            stage_ms[k].append(ev[k][0].elapsed_time(ev[k][1]))
+    t1.record(st)
+    torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    clocks = clk.stop()
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = tt.item()
+    ms_step = total_ms / args.steps
+    value = world * nnz * args.steps / (total_ms * 1e-3)
+    med = {k: statistics.median(v) for k, v in stage_ms.items()}
+    rows_rate = nnz / (med["rows"] * 1e-3)
+    fb = 2 * nnz / ((med["forward"] + med["back"]) * 1e-3)
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    out_host = torch.empty_like(x_host).pin_memory()
+    for _ in range(e2e_steps):
+        xd = x_host.to(dev, non_blocking=True)
+        yd = y_host.to(dev, non_blocking=True)
+        xo = step(xd, yd)
+        out_host.copy_(xo, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te) / e2e_steps
+    e2e = {"value": world * nnz / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(x_host.numel() * 4 + y_host.numel() * 4),
+           "d2h_bytes_per_step": int(out_host.numel() * 4)}
+
+    # roofline of the dominant kernel stage
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_mhz = float(clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0))
+    E = (2 * Wt + 1) * (2 * Wa + 1)
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA TFLOP/s at the sampled clock
+    model = {
+        # algorithmic work per launch (the design doc lists these per unit)
+        "rows": ("hbm", (8.0 * nnz + 24.0 * n_lors) / 1e9, hbm, "GB/s"),
+        "forward": ("hbm", (8.0 * nnz + 12.0 * n_lors) / 1e9, hbm, "GB/s"),
+        "back": ("hbm", (8.0 * nnz + 12.0 * n_lors) / 1e9, hbm, "GB/s"),
+        "sens": ("hbm", (8.0 * nnz + 12.0 * n_lors) / 1e9, hbm, "GB/s"),
+        "spread": ("alu", 2.0 * n_cls * 4096 * 256 / 1e12, alu_peak, "TFLOP/s"),
+    }
+    top = max(med, key=med.get)
+    if top in model:
+        bound, work, peak, unit = model[top]
+        achieved = work / (med[top] * 1e-3)
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "kernel_stage": top,
+                "peak_source": "measured" if peaks else "fallback"}
+    else:
+        roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "kernel_stage": top}
+    launches = 1 + 1 + 1 + (1 + 3 + 1) + 2 + 2 + 1 + 2 + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_lors": n_lors, "nnz": nnz, "n_classes": n_cls,
+                   "image": [im["nx"], im["ny"], im["nz"]], "voxel_mm": im["dx"],
+                   "l2": "inputs larger than L2 (53 GB matrix regenerated per step)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "sysmat_nnz_per_s": rows_rate,
+        "fwdback_lor_voxel_per_s": fb,
+        "stage_ms": med,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, dt, cores, desc = cpu_sample(2)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,86 +84,145 @@ __global__ void __launch_bounds__(PJ_T) csr_back_kernel(int64_t n, const int64_t
     }
 }
 
-// y[m] = sum over geometric LORs g and window entries (e1, e2) landing on m of
-// w_class(g)[e1][e2] * p[g].
-__global__ void __launch_bounds__(PJ_T) spread_fwd_kernel(LorSet ls, int Wt, int Wa,
-                                                         const float *__restrict__ w,
-                                                         const float *__restrict__ p,
-                                                         float *__restrict__ y) {
-    extern __shared__ int32_t shp[];
-    int32_t *tp_start = shp, *rp_start = shp + ls.Nt + 1;
-    ls.stage_prefix(tp_start, rp_start);
-    __syncthreads();
-    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a;
-    const int64_t n = ls.ntp * ls.nrp;
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n;
-         m += (int64_t)gridDim.x * blockDim.x) {
-        int a, b, ra, rb;
-        ls.tp_decode(tp_start, m / ls.nrp, &a, &b);
-        ls.rp_decode(rp_start, m % ls.nrp, &ra, &rb);
-        float acc = 0.0f;
-        for (int cs = 0; cs < 2; ++cs) {
-            const int t1 = cs ? b : a, r1 = cs ? rb : ra, t2 = cs ? a : b, r2 = cs ? ra : rb;
-            for (int e1 = 0; e1 < E; ++e1) {
-                const int dt1 = e1 / W2a - Wt, da1 = e1 - (e1 / W2a) * W2a - Wa;
-                int g1t = t1 - dt1;
-                g1t += g1t < 0 ? ls.Nt : (g1t >= ls.Nt ? -ls.Nt : 0);
-                const int g1r = r1 - da1;
-                for (int e2 = 0; e2 < E; ++e2) {
-                    const int dt2 = e2 / W2a - Wt, da2 = e2 - (e2 / W2a) * W2a - Wa;
-                    int g2t = t2 - dt2;
-                    g2t += g2t < 0 ? ls.Nt : (g2t >= ls.Nt ? -ls.Nt : 0);
-                    const int g2r = r2 - da2;
-                    if (!ls.member(g1t, g2t, g1r, g2r)) continue;
-                    int64_t g = ls.row_of(tp_start, rp_start, g1t, g2t, g1r, g2r);
-                    int64_t c = ls.class_of(tp_start, g1t, g2t, g1r, g2r);
-                    acc = fmaf(__ldg(w + c * E * E + e1 * E + e2), __ldg(p + g), acc);
-                }
-            }
-        }
-        y[m] = acc;
-    }
+// Tiled S and S^T.  The window of a LOR splits into 49 transaxial offsets
+// (dt1, dt2) times 7 x 7 axial offsets (da1, da2).  For a fixed transaxial
+// pair and a fixed (dt1, dt2), all ring pairs of the pair talk to all ring
+// pairs of one other transaxial pair, and the weight depends only on the
+// source's ring difference -- a 2D stencil over the ring-pair plane.  One CTA
+// owns one transaxial pair (all its ring pairs, accumulated in registers) and
+// walks the 49 partner pairs; each partner's values and weights are staged
+// densely in shared memory (zero padded, so out-of-set ring pairs contribute
+// nothing without a branch).
+constexpr int ST_T = 256;
+constexpr int ST_OUT = 8;  // ring pairs per thread (NR*NR <= ST_T*ST_OUT)
+
+struct StencilSmem {
+    int32_t *tp_start, *rp_start;
+    short2 *rp;        // [nrp] ring pair of each row offset
+    float *plane;      // [(NR+2Wa)^2] partner values, indexed [ring at end1 side][ring at end2 side]
+    float *wt;         // [(2Dm+1+4Wa)][W2a][W2a] weights by source ring difference
+};
+
+__device__ __forceinline__ void stencil_smem(StencilSmem &s, unsigned char *raw, const LorSet &ls,
+                                             int Wa) {
+    const int P = ls.NR + 2 * Wa, W2a = 2 * Wa + 1, ND = 2 * ls.Dm + 1 + 4 * Wa;
+    s.plane = reinterpret_cast<float *>(raw);
+    s.wt = s.plane + P * P;
+    s.rp = reinterpret_cast<short2 *>(s.wt + ND * W2a * W2a);
+    s.tp_start = reinterpret_cast<int32_t *>(s.rp + ls.nrp);
+    s.rp_start = s.tp_start + ls.Nt + 1;
 }
 
-// q[g] = sum over window entries (e1, e2) of g of w_class(g)[e1][e2] * r[m(e1, e2)].
-__global__ void __launch_bounds__(PJ_T) spread_adj_kernel(LorSet ls, int Wt, int Wa,
-                                                         const float *__restrict__ w,
-                                                         const float *__restrict__ r,
-                                                         float *__restrict__ q) {
-    extern __shared__ int32_t shp[];
-    int32_t *tp_start = shp, *rp_start = shp + ls.Nt + 1;
-    ls.stage_prefix(tp_start, rp_start);
+static size_t stencil_smem_bytes(const LorSet &ls, int Wa) {
+    const int P = ls.NR + 2 * Wa, W2a = 2 * Wa + 1, ND = 2 * ls.Dm + 1 + 4 * Wa;
+    return sizeof(float) * (P * P + ND * W2a * W2a) + sizeof(short2) * ls.nrp +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 16;
+}
+
+__device__ __forceinline__ int tp_index(const LorSet &ls, const int32_t *tp_start, int a, int b) {
+    return tp_start[a] + (b - ls.tp_lo(a));
+}
+
+__device__ __forceinline__ bool tp_member(const LorSet &ls, int a, int b) {
+    int d = b - a;
+    return a < b && d >= ls.Nt / 2 - ls.F && d <= ls.Nt / 2 + ls.F;
+}
+
+// adjoint == false: y[m] = sum_g w_g[e(g->m)] p[g]   (rows of this CTA are outputs m)
+// adjoint == true : q[g] = sum_m w_g[e(g->m)] r[m]   (rows of this CTA are sources g)
+template <bool adjoint>
+__global__ void __launch_bounds__(ST_T) stencil_kernel(LorSet ls, int Wt, int Wa,
+                                                       const float *__restrict__ w,
+                                                       const float *__restrict__ in,
+                                                       float *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    StencilSmem s;
+    stencil_smem(s, raw, ls, Wa);
+    ls.stage_prefix(s.tp_start, s.rp_start);
     __syncthreads();
-    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a;
-    const int64_t n = ls.ntp * ls.nrp;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        int g1t, g2t, g1r, g2r;
-        ls.tp_decode(tp_start, g / ls.nrp, &g1t, &g2t);
-        ls.rp_decode(rp_start, g % ls.nrp, &g1r, &g2r);
-        const float *wc = w + ls.class_of(tp_start, g1t, g2t, g1r, g2r) * E * E;
-        float acc = 0.0f;
-        for (int e1 = 0; e1 < E; ++e1) {
-            const int dt1 = e1 / W2a - Wt, da1 = e1 - (e1 / W2a) * W2a - Wa;
-            int xt = g1t + dt1;
-            xt += xt < 0 ? ls.Nt : (xt >= ls.Nt ? -ls.Nt : 0);
-            const int xr = g1r + da1;
-            if (xr < 0 || xr >= ls.NR) continue;
-            for (int e2 = 0; e2 < E; ++e2) {
-                const int dt2 = e2 / W2a - Wt, da2 = e2 - (e2 / W2a) * W2a - Wa;
-                int yt = g2t + dt2;
-                yt += yt < 0 ? ls.Nt : (yt >= ls.Nt ? -ls.Nt : 0);
-                const int yr = g2r + da2;
-                if (yr < 0 || yr >= ls.NR || yt == xt) continue;
-                const bool sw = yt < xt;
-                const int a = sw ? yt : xt, b = sw ? xt : yt;
-                const int ra = sw ? yr : xr, rb = sw ? xr : yr;
-                if (!ls.member(a, b, ra, rb)) continue;
-                acc = fmaf(__ldg(wc + e1 * E + e2),
-                           __ldg(r + ls.row_of(tp_start, rp_start, a, b, ra, rb)), acc);
+    for (int j = threadIdx.x; j < ls.nrp; j += ST_T) {
+        int r1, r2;
+        ls.rp_decode(s.rp_start, j, &r1, &r2);
+        s.rp[j] = make_short2((short)r1, (short)r2);
+    }
+    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, P = ls.NR + 2 * Wa;
+    const int ND = 2 * ls.Dm + 1 + 4 * Wa, D0 = ls.Dm + 2 * Wa;  // weight slot of difference 0
+    const int nrp = (int)ls.nrp;
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        int a, b;
+        ls.tp_decode(s.tp_start, T, &a, &b);
+        float acc[ST_OUT];
+#pragma unroll
+        for (int k = 0; k < ST_OUT; ++k) acc[k] = 0.0f;
+        // this CTA's own transaxial class (adjoint: weights of the sources = own rows)
+        const int a0 = a % ls.Nb;
+        const int own_cls = tp_index(ls, s.tp_start, a0, b - (a - a0));
+        for (int dt = 0; dt < (2 * Wt + 1) * (2 * Wt + 1); ++dt) {
+            const int dt1 = dt / (2 * Wt + 1) - Wt, dt2 = dt % (2 * Wt + 1) - Wt;
+            // partner crystals on the side of a and of b
+            int pa = adjoint ? a + dt1 : a - dt1, pb = adjoint ? b + dt2 : b - dt2;
+            pa += pa < 0 ? ls.Nt : (pa >= ls.Nt ? -ls.Nt : 0);
+            pb += pb < 0 ? ls.Nt : (pb >= ls.Nt ? -ls.Nt : 0);
+            if (pa == pb) continue;
+            const bool sw = pa > pb;  // partner's canonical first crystal is pb
+            const int c1 = sw ? pb : pa, c2 = sw ? pa : pb;
+            if (!tp_member(ls, c1, c2)) continue;
+            const int64_t prow = (int64_t)tp_index(ls, s.tp_start, c1, c2) * nrp;
+            __syncthreads();  // previous partner fully consumed
+            for (int i = threadIdx.x; i < P * P; i += ST_T) s.plane[i] = 0.0f;
+            for (int i = threadIdx.x; i < ND * W2a * W2a; i += ST_T) s.wt[i] = 0.0f;
+            __syncthreads();
+            // partner values, oriented [ring on a's side][ring on b's side]
+            for (int j = threadIdx.x; j < nrp; j += ST_T) {
+                short2 rr = s.rp[j];
+                int ra = sw ? rr.y : rr.x, rb = sw ? rr.x : rr.y;
+                s.plane[(ra + Wa) * P + (rb + Wa)] = __ldg(in + prow + j);
+            }
+            // weights: forward uses the partner's class, adjoint its own; the
+            // window entry of the end on a's side is (dt1, da1)
+            const int cls = adjoint ? own_cls : tp_index(ls, s.tp_start, c1 % ls.Nb,
+                                                         c2 - (c1 - c1 % ls.Nb));
+            const bool wsw = adjoint ? false : sw;  // whose end 1 sits on a's side
+            for (int i = threadIdx.x; i < (2 * ls.Dm + 1) * W2a * W2a; i += ST_T) {
+                const int dl = i / (W2a * W2a) - ls.Dm;          // ring difference, a->b frame
+                const int da1 = (i / W2a) % W2a, da2 = i % W2a;  // offset indices
+                const int e_a = (dt1 + Wt) * W2a + da1, e_b = (dt2 + Wt) * W2a + da2;
+                const int e1 = wsw ? e_b : e_a, e2 = wsw ? e_a : e_b;
+                const int dc = wsw ? -dl : dl;  // canonical ring difference
+                s.wt[(dl + D0) * W2a * W2a + da1 * W2a + da2] =
+                    __ldg(w + ((int64_t)cls * (2 * ls.Dm + 1) + dc + ls.Dm) * E * E + e1 * E + e2);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < ST_OUT; ++k) {
+                const int j = threadIdx.x + k * ST_T;
+                if (j >= nrp) break;
+                const short2 rr = s.rp[j];
+                const int ra = rr.x, rb = rr.y;  // this row's rings (end on a's side, b's side)
+                float v = 0.0f;
+                // L1, L2 index the window offsets o = L - Wa of the ends on a's
+                // and b's side.  Forward: the source sits at rings (ra - o1,
+                // rb - o2) and its own ring difference picks the weight; adjoint:
+                // the target sits at (ra + o1, rb + o2), weight by this row's
+                // difference.  Plane rows/cols are ring + Wa.
+                for (int L1 = 0; L1 < W2a; ++L1) {
+                    for (int L2 = 0; L2 < W2a; ++L2) {
+                        const int pr = adjoint ? ra + L1 : ra + 2 * Wa - L1;
+                        const int pc = adjoint ? rb + L2 : rb + 2 * Wa - L2;
+                        const int dl = adjoint ? rb - ra : (rb - ra) - (L2 - L1);
+                        v = fmaf(s.wt[(dl + D0) * W2a * W2a + L1 * W2a + L2], s.plane[pr * P + pc], v);
+                    }
+                }
+                acc[k] += v;
             }
         }
-        q[g] = acc;
+        const int64_t orow = T * nrp;
+#pragma unroll
+        for (int k = 0; k < ST_OUT; ++k) {
+            const int j = threadIdx.x + k * ST_T;
+            if (j < nrp) out[orow + j] = acc[k];
+        }
+        __syncthreads();
     }
 }
 
@@ -195,6 +254,27 @@ static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t
         PSF_LAUNCHED();
         return PSF_OK;
     });
+}
+
+// S (adjoint == false) or S^T on LOR-space vectors of a factored plan.
+static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoint,
+                   cudaStream_t st) {
+    const size_t shm = stencil_smem_bytes(m->ls, m->Wa);
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
+    if (adjoint) {
+        PSF_TRY(cudaFuncSetAttribute(stencil_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        stencil_kernel<true><<<(int)grid, ST_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, in, out);
+    } else {
+        PSF_TRY(cudaFuncSetAttribute(stencil_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        stencil_kernel<false><<<(int)grid, ST_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, in, out);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
 }
 
 }  // namespace psf
@@ -239,6 +319,7 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;
     if (ls.ntp * ls.nrp != m->n_rows) return PSF_EINVAL;
+    if (ls.nrp > ST_T * ST_OUT || stencil_smem_bytes(ls, half_a) > 200 * 1024) return PSF_EINVAL;
     m->factored = true;
     m->ls = ls;
     m->Wt = half_t;
@@ -263,11 +344,7 @@ extern "C" int psf_forward(const psf_matrix *m, const float *x, float *y, void *
     if (!m->factored) return rows_fwd(m, x, y, st);
     int rc = rows_fwd(m, x, m->p, st);
     if (rc) return rc;
-    size_t shm = sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2);
-    spread_fwd_kernel<<<grid_for(m->n_rows, PJ_T), PJ_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls,
-                                                                    m->p, y);
-    PSF_LAUNCHED();
-    return PSF_OK;
+    return stencil(m, m->p, y, false, st);
 }
 
 extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *stream) {
@@ -278,9 +355,7 @@ extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *str
         return PSF_OK;
     }
     if (!m->factored) return rows_back(m, y, x, st);
-    size_t shm = sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2);
-    spread_adj_kernel<<<grid_for(m->n_rows, PJ_T), PJ_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls,
-                                                                    y, m->q);
-    PSF_LAUNCHED();
+    int rc = stencil(m, y, m->q, true, st);
+    if (rc) return rc;
     return rows_back(m, m->q, x, st);
 }

@@ -74,34 +74,69 @@ __global__ void __launch_bounds__(ROWS_THREADS) g_count_kernel(
     }
 }
 
-__global__ void __launch_bounds__(ROWS_THREADS) g_fill_kernel(
+// K6: each lane of a warp traces one LOR with a resumable cursor and stages
+// up to 32 of its voxels in shared memory; the warp then writes every lane's
+// chunk with full 128-byte stores (one row segment per store instruction).
+constexpr int FILL_WARPS = 8;
+constexpr int FILL_PAD = 33;  // staging row stride (conflict-free lane-major writes)
+
+__global__ void __launch_bounds__(FILL_WARPS * 32) g_fill_kernel(
     Scan sc, Img im, const int32_t *__restrict__ lors, int64_t n,
     const int64_t *__restrict__ row_ptr, int32_t *__restrict__ col, float *__restrict__ val,
     int *__restrict__ status) {
     extern __shared__ double cs[];
     stage_blocks(sc, cs);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *scol = reinterpret_cast<int32_t *>(cs + 2 * sc.R) + warp * 32 * FILL_PAD;
+    float *sval = reinterpret_cast<float *>(reinterpret_cast<int32_t *>(cs + 2 * sc.R) +
+                                            FILL_WARPS * 32 * FILL_PAD) +
+                  warp * 32 * FILL_PAD;
     __syncthreads();
     const int nx = im.nx, nxy = im.nx * im.ny;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t base = ((int64_t)blockIdx.x * FILL_WARPS + warp) * 32; base < n;
+         base += (int64_t)gridDim.x * FILL_WARPS * 32) {
+        const int64_t k = base + lane;
         Ray r;
-        lor_ray(r, sc, im, cs, lors[2 * k], lors[2 * k + 1]);
-        int64_t pos = row_ptr[k];
-        const int64_t end = row_ptr[k + 1];
-        const float to_mm = (float)(r.len_mm / FX);
-        const Axis &X = r.ax[0];
-        bool ok = trace_rows(r, [&](int iz, int iy, int x0, int x1, long long lo, long long hi) {
-            int base = iz * nxy + iy * nx;
-            for (int ix = x0; ix <= x1; ++ix) {
-                long long c = chord_in_row(X, ix, lo, hi);
-                if (pos < end) {
-                    col[pos] = base + ix;
-                    val[pos] = (float)c * to_mm;
-                }
-                ++pos;
+        VoxelCursor c;
+        int64_t pos = 0, end = 0;
+        float to_mm = 0.0f;
+        c.done = true;
+        c.ok = true;
+        if (k < n) {
+            lor_ray(r, sc, im, cs, lors[2 * k], lors[2 * k + 1]);
+            cursor_start(r, c);
+            pos = row_ptr[k];
+            end = row_ptr[k + 1];
+            to_mm = (float)(r.len_mm / FX);
+        }
+        bool bad = false;
+        while (__any_sync(0xffffffffu, !c.done)) {
+            int cnt = 0;
+            while (cnt < 32 && !c.done) {
+                int iz, iy, ix;
+                long long ch;
+                cursor_take(r, c, iz, iy, ix, ch);
+                scol[lane * FILL_PAD + cnt] = iz * nxy + iy * nx + ix;
+                sval[lane * FILL_PAD + cnt] = (float)ch * to_mm;
+                ++cnt;
             }
-        });
-        if (!ok || pos != end) atomicExch(status, PSF_EDEBUG);
+            if (pos + cnt > end) {  // never for a consistent count pass; stay in the row
+                bad = true;
+                cnt = (int)(end - pos > 0 ? end - pos : 0);
+            }
+            __syncwarp();
+            for (int j = 0; j < 32; ++j) {
+                const int cj = __shfl_sync(0xffffffffu, cnt, j);
+                const int64_t pj = __shfl_sync(0xffffffffu, pos, j);
+                if (lane < cj) {
+                    col[pj + lane] = scol[j * FILL_PAD + lane];
+                    val[pj + lane] = sval[j * FILL_PAD + lane];
+                }
+            }
+            pos += cnt;
+            __syncwarp();
+        }
+        if (k < n && (!c.ok || bad || pos != end)) atomicExch(status, PSF_EDEBUG);
     }
 }
 
@@ -347,7 +382,13 @@ static int geom_rows(const Scan &sc, const Img &im, const int32_t *lors, int64_t
     if (h_status) return h_status;
     if (!col) return PSF_OK;
     if (nnz > capacity) return PSF_ECAPACITY;
-    g_fill_kernel<<<grid, ROWS_THREADS, shm, st>>>(sc, im, lors, n, row_ptr, col, val, status);
+    const size_t fshm = shm + sizeof(int32_t) * 2 * FILL_WARPS * 32 * FILL_PAD;
+    PSF_TRY(cudaFuncSetAttribute(g_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fshm));
+    int64_t fgrid = (n + FILL_WARPS * 32 - 1) / (FILL_WARPS * 32);
+    if (fgrid > (int64_t)sm_count() * 3) fgrid = (int64_t)sm_count() * 3;
+    g_fill_kernel<<<(int)fgrid, FILL_WARPS * 32, fshm, st>>>(sc, im, lors, n, row_ptr, col, val,
+                                                            status);
     PSF_LAUNCHED();
     PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     PSF_TRY(cudaStreamSynchronize(st));

@@ -201,4 +201,92 @@ __host__ __device__ __forceinline__ bool trace_rows(const Ray &r, RowFn &&row) {
     return ok;
 }
 
+// Resumable form of trace_rows: yields one voxel per call, in the same
+// ascending order and with the same trimming, so a kernel can interleave the
+// voxels of several rays (row-by-row state: slab, row, voxel).
+struct VoxelCursor {
+    int iz, z1, iy, y1, ix, x1;
+    long long zl, zh, yl, yh;
+    bool done, ok;
+};
+
+// Move to the first voxel of the next non-empty row (or set done).
+__host__ __device__ __forceinline__ void cursor_next_row(const Ray &r, VoxelCursor &c) {
+    const Axis &X = r.ax[0], &Y = r.ax[1], &Z = r.ax[2];
+    for (;;) {
+        ++c.iy;
+        if (c.iy > c.y1) {
+            ++c.iz;
+            if (c.iz > c.z1) {
+                c.done = true;
+                return;
+            }
+            slab(Z, c.iz, c.zl, c.zh);
+            c.zl = c.zl > r.amin ? c.zl : r.amin;
+            c.zh = c.zh < r.amax ? c.zh : r.amax;
+            if (c.zh <= c.zl) {
+                c.y1 = c.iy - 1;  // empty slab: no rows
+                --c.iy;
+                continue;
+            }
+            int ya, yb;
+            c.ok &= voxel_at(Y, c.zl, ya);
+            c.ok &= voxel_at(Y, c.zh - 1, yb);
+            int y0 = ya < yb ? ya : yb, y1 = ya < yb ? yb : ya;
+            y0 = y0 < 0 ? 0 : y0;
+            c.y1 = y1 > Y.n - 1 ? Y.n - 1 : y1;
+            c.iy = y0;
+            if (c.iy > c.y1) {
+                --c.iy;
+                continue;
+            }
+        }
+        slab(Y, c.iy, c.yl, c.yh);
+        c.yl = c.yl > c.zl ? c.yl : c.zl;
+        c.yh = c.yh < c.zh ? c.yh : c.zh;
+        if (c.yh <= c.yl) continue;
+        int xa, xb;
+        c.ok &= voxel_at(X, c.yl, xa);
+        c.ok &= voxel_at(X, c.yh - 1, xb);
+        int x0 = xa < xb ? xa : xb, x1 = xa < xb ? xb : xa;
+        x0 = x0 < 0 ? 0 : x0;
+        x1 = x1 > X.n - 1 ? X.n - 1 : x1;
+        if (x1 >= x0 && chord_in_row(X, x0, c.yl, c.yh) < r.min_units) ++x0;
+        if (x1 >= x0 && chord_in_row(X, x1, c.yl, c.yh) < r.min_units) --x1;
+        if (x1 >= x0) {
+            c.ix = x0;
+            c.x1 = x1;
+            return;
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ void cursor_start(const Ray &r, VoxelCursor &c) {
+    c.done = r.empty;
+    c.ok = true;
+    if (c.done) return;
+    const Axis &Z = r.ax[2];
+    int za, zb;
+    c.ok &= voxel_at(Z, r.amin, za);
+    c.ok &= voxel_at(Z, r.amax - 1, zb);
+    int z0 = za < zb ? za : zb, z1 = za < zb ? zb : za;
+    z0 = z0 < 0 ? 0 : z0;
+    c.z1 = z1 > Z.n - 1 ? Z.n - 1 : z1;
+    c.iz = z0 - 1;
+    c.iy = 0;
+    c.y1 = -1;
+    c.zl = c.zh = 0;
+    cursor_next_row(r, c);
+}
+
+// Current voxel (slab, row, x) and chord; then advance.  Requires !c.done.
+__host__ __device__ __forceinline__ void cursor_take(const Ray &r, VoxelCursor &c, int &iz, int &iy,
+                                                     int &ix, long long &chord) {
+    iz = c.iz;
+    iy = c.iy;
+    ix = c.ix;
+    chord = chord_in_row(r.ax[0], c.ix, c.yl, c.yh);
+    if (++c.ix > c.x1) cursor_next_row(r, c);
+}
+
 }  // namespace psf

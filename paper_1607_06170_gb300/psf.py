@@ -196,20 +196,27 @@ def lor_set_classes(sc: dict, ls: dict, device="cuda"):
 
 
 def sysmat_rows(sc: dict, im: dict, lors, spread=None, half_t: int = 0, half_a: int = 0,
-                dtype: str = "f32"):
+                dtype: str = "f32", buffers=None):
     """CSR rows (row_ptr int64, col int32, val, row_scale or None).
 
-    Two calls through the C ABI: a size query, then the fill into buffers of
-    exactly the required size.
+    Without `buffers`: a size query, then the fill into buffers of exactly the
+    required size.  With buffers=(row_ptr, col, val, row_scale) of sufficient
+    capacity: one call that fills them (PSFError with PSF_ECAPACITY if short).
     """
     s, i = scanner(sc), image(im)
     n = lors.shape[0]
     dt = _DT[dtype]
     dev = lors.device
-    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
-    row_scale = None if dt == PSF_F32 else torch.empty(n, dtype=torch.float32, device=dev)
     nnz = C.c_int64()
     L = lib()
+    if buffers is not None:
+        row_ptr, col, val, row_scale = buffers
+        _ok(L.psf_sysmat_rows(C.byref(s), C.byref(i), _ptr(lors), n, _ptr(spread), half_t,
+                              half_a, dt, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(row_scale),
+                              col.numel(), C.byref(nnz), _stream()), "psf_sysmat_rows")
+        return row_ptr, col[: nnz.value], val[: nnz.value], row_scale
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    row_scale = None if dt == PSF_F32 else torch.empty(n, dtype=torch.float32, device=dev)
     _ok(L.psf_sysmat_rows(C.byref(s), C.byref(i), _ptr(lors), n, _ptr(spread), half_t, half_a,
                           dt, _ptr(row_ptr), None, None, _ptr(row_scale), 0, C.byref(nnz),
                           _stream()), "psf_sysmat_rows(size)")
@@ -235,7 +242,7 @@ class Matrix:
             "psf_matrix_create")
 
     def set_spread(self, sc: dict, ls: dict, half_t: int, half_a: int, class_spread):
-        self._keep.append(class_spread)
+        self._spread = class_spread  # the plan keeps the pointer; keep the tensor alive
         s, l = scanner(sc), lor_set(ls)
         _ok(lib().psf_matrix_set_spread(self._h, C.byref(s), C.byref(l), half_t, half_a,
                                         _ptr(class_spread)), "psf_matrix_set_spread")

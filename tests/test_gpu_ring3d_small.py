@@ -1,0 +1,107 @@
+"""GPU parity on a small 3D ring (12 blocks x 4 x 4 crystals x 2 block rings,
+22176 LORs): table, class spreads, chord rows and the factored PSF projector
+A = S G against the FP64 oracle (which uses one spread per LOR, no classes)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1607_06170_gb300 import inputs as I
+from parity import assert_close, compare_chord_rows
+
+pytestmark = pytest.mark.gpu
+NAME = "RING3D_SMALL"
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1607_06170_gb300 import build, psf
+
+    build.build()
+    return psf
+
+
+@pytest.fixture(scope="module")
+def ref(orc):
+    w = I.workload(NAME)
+    s, t, im = w["scanner"], w["table"], w["image"]
+    Wt, Wa = w["window"]
+    T, eta = orc.table_build(s, t)
+    L = I.workload_lors(w)
+    W = orc.spread(s, t, T, L, Wt, Wa)
+    G = orc.rows_geom(s, im, L)
+    return dict(w=w, T=T, eta=eta, L=L, W=W, G=G, nv=im["nx"] * im["ny"] * im["nz"],
+                margin=orc.tie_margin(s, t, T, L))
+
+
+@pytest.fixture(scope="module")
+def gpu(P, ref):
+    w = ref["w"]
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    T, eta = P.response_build(s, t)
+    L = P.lor_set_list(s, ls)
+    C = P.lor_set_classes(s, ls)
+    WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)
+    G = P.sysmat_rows(s, im, L)
+    M = P.Matrix(G[0], G[1], G[2], ref["nv"]).set_spread(s, ls, Wt, Wa, WC)
+    torch.cuda.synchronize()
+    return dict(T=T, eta=eta, L=L, C=C, WC=WC, G=G, M=M)
+
+
+def test_table(gpu, ref):
+    assert_close(gpu["T"].cpu().numpy(), ref["T"], 1e-5, 1e-7, "table")
+    assert_close(gpu["eta"].cpu().numpy()[..., -1], ref["eta"], 1e-6, 1e-12, "eta")
+
+
+def test_lor_set_order(gpu, ref):
+    np.testing.assert_array_equal(gpu["L"].cpu().numpy(), ref["L"])
+    w = ref["w"]
+    s, Dm = w["scanner"], w["lors"]["max_ring_diff"]
+    nt = I.n_transaxial(s)
+    tp = I.transaxial_pairs(s, w["lors"]["fan_half"])
+    tp = tp[tp[:, 0] < s["nt_block"]]
+    want = []
+    for a, b in tp:
+        for d in range(-Dm, Dm + 1):
+            ra = max(0, -d)
+            want.append((ra * nt + a, (ra + d) * nt + b))
+    np.testing.assert_array_equal(gpu["C"].cpu().numpy(), np.array(want, dtype=np.int32))
+
+
+def test_class_spreads(gpu, ref, orc):
+    w = ref["w"]
+    Wt, Wa = w["window"]
+    C = gpu["C"].cpu().numpy()
+    Wo = orc.spread(w["scanner"], w["table"], ref["T"], C, Wt, Wa)
+    m = orc.tie_margin(w["scanner"], w["table"], ref["T"], C)
+    ok = m >= 1e-5
+    assert ok.mean() > 0.99
+    scale = np.abs(Wo).reshape(len(C), -1).max(1)[:, None, None]
+    assert_close(gpu["WC"].cpu().numpy()[ok], Wo[ok], 1e-5, 1e-12 * scale[ok] + 1e-30, "class spread")
+
+
+def test_geometric_rows(gpu, ref):
+    ptr, col, val = [a.cpu().numpy() for a in gpu["G"][:3]]
+    compare_chord_rows((ptr, col, val), ref["G"], ref["nv"])
+
+
+def test_factored_projector(gpu, ref, orc):
+    w = ref["w"]
+    s = w["scanner"]
+    Wt, Wa = w["window"]
+    assert (ref["margin"] >= 1e-5).all()
+    M = gpu["M"]
+    x = I.random_image(w["image"], 500).reshape(-1)
+    y = M.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    yo = orc.spread_apply(s, ref["L"], ref["W"], Wt, Wa, orc.csr_fwd(ref["G"], x))
+    assert_close(y, yo, 2e-5, 1e-6 * yo.max(), "factored forward")
+    r = I.random_lor_values(len(ref["L"]), 501)
+    b = M.back(torch.from_numpy(r).cuda()).cpu().numpy()
+    bo = orc.csr_back(ref["G"], orc.spread_adjoint(s, ref["L"], ref["W"], Wt, Wa, r), ref["nv"])
+    assert_close(b, bo, 2e-5, 1e-6 * bo.max(), "factored back")
+    for k in range(3):
+        xk = torch.from_numpy(I.random_image(w["image"], 600 + k).reshape(-1)).cuda()
+        yk = torch.from_numpy(I.random_lor_values(len(ref["L"]), 700 + k)).cuda()
+        lhs = torch.dot(M.forward(xk).double(), yk.double()).item()
+        rhs = torch.dot(xk.double(), M.back(yk).double()).item()
+        assert lhs == pytest.approx(rhs, rel=1e-5)

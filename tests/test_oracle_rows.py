@@ -37,6 +37,20 @@ def test_ray_on_a_grid_plane_belongs_to_upper_voxel(orc):
     assert len(idx) == 0
 
 
+@pytest.mark.parametrize("eps", [0.0, 1e-13, -1e-13])
+def test_ray_within_rounding_of_a_plane_is_on_it(orc, eps):
+    # A LOR on a grid plane by symmetry, tilted or shifted by rounding noise,
+    # still belongs wholly to the voxel row above the plane, in both tracers.
+    for fn in (orc.siddon, orc.slabclip):
+        idx, ln = fn(IM2, [-100.0, 3.0 + eps, 0.0], [100.0, 3.0 - eps, 0.0])
+        iy = int(round((3.0 - IM2["oy"]) / IM2["dy"]))
+        assert np.all(idx // 16 == iy) and len(idx) == 16
+        np.testing.assert_allclose(ln, 1.0, rtol=1e-12)
+    # a genuinely tilted ray (1e-6 voxel) is not snapped
+    idx, _ = orc.siddon(IM2, [-100.0, 3.0 + 1e-6, 0.0], [100.0, 3.0 - 1e-6, 0.0])
+    assert set(idx // 16) == {iy - 1, iy}
+
+
 def _compare(a, b, tol_set=1e-9):
     ia, la = a
     ib, lb = b
