@@ -121,7 +121,8 @@ def cpu_sample(n_tclass: int = 2):
     nt, nb, R = I.n_transaxial(s), s["nt_block"], s["n_blocks"]
     tp = I.transaxial_pairs(s, w["lors"]["fan_half"])
     cls = tp[tp[:, 0] < nb]
-    pick = cls[np.linspace(0, len(cls) - 1, n_tclass).astype(int)]
+    # classes at evenly spaced quantiles of the list (central to oblique chords)
+    pick = cls[((np.arange(n_tclass) + 0.5) / n_tclass * len(cls)).astype(int)]
     rp = I.ring_pairs(s, w["lors"]["max_ring_diff"]).astype(np.int64)
     lors = []
     for a, b in pick:
@@ -159,11 +160,11 @@ def run_reference(args):
         return
     # each step: the oracle on one bounded sample (one transaxial class)
     for _ in range(args.warmup):
-        cpu_sample(1)
+        cpu_sample(16)
     rates, times = [], []
     desc, cores = "", 1
     for _ in range(args.steps):
-        r, dt, cores, desc = cpu_sample(1)
+        r, dt, cores, desc = cpu_sample(16)
         rates.append(r)
         times.append(dt)
     value = statistics.median(rates)
@@ -207,7 +208,7 @@ def run_gpu(args):
     L = P.lor_set_list(s, ls, device=dev)
     row_ptr = torch.empty(n_lors + 1, dtype=torch.int64, device=dev)
     # size query once, then buffers of that capacity are reused by every step
-    _, col, val, _ = P.sysmat_rows(s, im, L, buffers=None)
+    _, col, val = P.sysmat_rows_set(s, im, ls, device=dev)
     nnz = col.numel()
     st = torch.cuda.current_stream()
     stages = ["table", "classes", "spread", "rows", "sens", "forward", "ratio", "back", "update"]
@@ -230,7 +231,7 @@ def run_gpu(args):
         WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)
         mark("spread", 1)
         mark("rows", 0)
-        P.sysmat_rows(s, im, L, buffers=(row_ptr, col, val, None))
+        P.sysmat_rows_set(s, im, ls, buffers=(row_ptr, col, val))
         mark("rows", 1)
         M.set_spread(s, ls, Wt, Wa, WC)
         mark("sens", 0)
@@ -257,7 +258,7 @@ def run_gpu(args):
     M = P.Matrix(row_ptr, col, val, nv)
     T0, e0 = P.response_build(s, t, device=dev)
     WC0 = P.bin_spread(s, t, T0, e0, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
-    P.sysmat_rows(s, im, L, buffers=(row_ptr, col, val, None))
+    P.sysmat_rows_set(s, im, ls, buffers=(row_ptr, col, val))
     M.set_spread(s, ls, Wt, Wa, WC0)
     y_meas = M.forward(x).clone()
     y_host = y_meas.cpu().pin_memory()
@@ -357,13 +358,56 @@ def run_gpu(args):
         "gpu_launches": launches * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, dt, cores, desc = cpu_sample(2)
+        r, dt, cores, desc = cpu_sample(48)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_profile_case(args):
+    """One stage of the step on a configuration small enough for a kernel
+    capture (a few GB on the device): 'spread' = all class spreads; 'stencil' =
+    S and S^T over the full LOR space with an empty G; 'rows' = chord rows of
+    the first 2M LORs; 'csr' = forward/back with those rows."""
+    import torch
+
+    from paper_1607_06170_gb300 import build as B
+    from paper_1607_06170_gb300 import inputs as I
+    from paper_1607_06170_gb300 import psf as P
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    w = I.workload(WORKLOAD)
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    nv = im["nx"] * im["ny"] * im["nz"]
+    case = args.profile_case
+    for _ in range(2):
+        if case in ("spread", "stencil"):
+            T, eta = P.response_build(s, t, device=dev)
+            WC = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+        if case == "stencil":
+            n, _ = P.lor_set_size(s, ls)
+            rp = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+            M = P.Matrix(rp, torch.zeros(1, dtype=torch.int32, device=dev),
+                         torch.zeros(1, device=dev), nv).set_spread(s, ls, Wt, Wa, WC)
+            x = torch.rand(nv, device=dev)
+            y = M.forward(x)
+            M.back(y)
+        if case == "rows_set":
+            P.sysmat_rows_set(s, im, ls, device=dev)
+        if case in ("rows", "csr"):
+            L = P.lor_set_list(s, ls, device=dev)[: 2_000_000].contiguous()
+            rp, col, val, _ = P.sysmat_rows(s, im, L)
+            if case == "csr":
+                M = P.Matrix(rp, col, val, nv)
+                y = M.forward(torch.rand(nv, device=dev))
+                M.back(y)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "ok": True}))
 
 
 def main():
@@ -373,8 +417,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--profile-case", choices=["spread", "stencil", "rows", "rows_set", "csr"],
+                    help="run one stage on a small-memory setup (for kernel captures)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

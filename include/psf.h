@@ -174,6 +174,19 @@ int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *image, const in
                     int64_t capacity, int64_t *nnz_out, void *stream);
 
 /*
+ * Geometric rows G of a structured LOR set (rows in set order), the same
+ * matrix psf_sysmat_rows returns for the list psf_lor_set_list writes, with
+ * the same conventions, size query, capacity rule and synchronisation.  All
+ * ring pairs of a transaxial pair share the transaxial projection of their
+ * segment, so its crossings with the x and y planes are traced once per pair
+ * and only split at each ring pair's z-plane crossings.  F32 values only.
+ * PSF_EINVAL if nx + ny + 1 > 1024.
+ */
+int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
+                        const psf_lor_set *set, int64_t *row_ptr, int32_t *col, float *val,
+                        int64_t capacity, int64_t *nnz_out, void *stream);
+
+/*
  * Projector plan over caller CSR (pointers retained until destroy; the caller
  * keeps them alive).  The plan owns its scratch (allocated here).
  */

@@ -105,6 +105,9 @@ int make_img(const psf_image *im, Img *o) {
     o->ox = im->ox;
     o->oy = im->oy;
     o->oz = im->oz;
+    o->idx = 1.0 / im->dx;
+    o->idy = 1.0 / im->dy;
+    o->idz = 1.0 / im->dz;
     return PSF_OK;
 }
 

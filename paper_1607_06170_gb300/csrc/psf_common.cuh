@@ -59,6 +59,7 @@ struct Tab {
 struct Img {
     int nx, ny, nz;
     double dx, dy, dz, ox, oy, oz;
+    double idx, idy, idz;  // 1 / voxel size
 };
 
 // Validation + derivation (host).  Return PSF_OK or PSF_EINVAL.

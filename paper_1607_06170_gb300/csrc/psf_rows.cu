@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 
 #include "psf_common.cuh"
+#include "psf_lorset.cuh"
 #include "psf_rows.cuh"
 
 namespace psf {
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(FILL_WARPS * 32) g_fill_kernel(
             cursor_start(r, c);
             pos = row_ptr[k];
             end = row_ptr[k + 1];
-            to_mm = (float)(r.len_mm / FX);
+            to_mm = r.len_mm * (float)(1.0 / FX);
         }
         bool bad = false;
         while (__any_sync(0xffffffffu, !c.done)) {
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(FILL_WARPS * 32) g_fill_kernel(
                 long long ch;
                 cursor_take(r, c, iz, iy, ix, ch);
                 scol[lane * FILL_PAD + cnt] = iz * nxy + iy * nx + ix;
-                sval[lane * FILL_PAD + cnt] = (float)ch * to_mm;
+                sval[lane * FILL_PAD + cnt] = units_to_f(ch) * to_mm;
                 ++cnt;
             }
             if (pos + cnt > end) {  // never for a consistent count pass; stay in the row
@@ -395,9 +396,492 @@ static int geom_rows(const Scan &sc, const Img &im, const int32_t *lors, int64_t
     return h_status;
 }
 
+// ------------------------------------------------- rows of a structured set
+// One CTA per transaxial pair.  Its segment's transaxial projection is the
+// same for every ring pair, and so are the fixed-point parameters of its x
+// and y plane crossings.  One thread builds the ordered list of 2D cells
+// (x, y voxel and parameter interval, contiguous and non-empty) once; every
+// ring pair then cuts the list at its own z-plane crossings.  A voxel's
+// parameter interval is the intersection of its three slabs, exactly as in
+// the per-LOR tracer, so the rows are the same numbers.
+constexpr int SET_T = 256;
+constexpr int SET_MAXC = 1024;  // 2D cells per transaxial pair (nx + ny + 1 <= 1024)
+constexpr int SET_MAXF = 64;    // short cells checked one by one against each ring pair
+
+struct Cells2D {
+    long long *bnd;  // [n + 1] parameter boundaries
+    short *ix, *iy;  // [n] voxel of each cell
+    short *run;      // [n] run (constant iy) of each cell
+    short *rstart;   // [nruns + 1] first cell of each run
+    short *flag;     // [nflag] cells shorter than twice the transaxial chord threshold
+    int *hdr;        // n, nruns, nflag, xinc, yinc
+    Axis *X, *Y;
+    long long *clip;  // amin2, amax2
+    double *xy;       // endpoints (x1, y1, x2, y2)
+};
+
+__device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsigned char *p) {
+    c.bnd = reinterpret_cast<long long *>(p);
+    p += sizeof(long long) * (SET_MAXC + 1);
+    c.clip = reinterpret_cast<long long *>(p);
+    p += sizeof(long long) * 2;
+    c.xy = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 4;
+    c.X = reinterpret_cast<Axis *>(p);
+    p += sizeof(Axis);
+    c.Y = reinterpret_cast<Axis *>(p);
+    p += sizeof(Axis);
+    c.ix = reinterpret_cast<short *>(p);
+    p += sizeof(short) * SET_MAXC;
+    c.iy = reinterpret_cast<short *>(p);
+    p += sizeof(short) * SET_MAXC;
+    c.run = reinterpret_cast<short *>(p);
+    p += sizeof(short) * SET_MAXC;
+    c.rstart = reinterpret_cast<short *>(p);
+    p += sizeof(short) * (SET_MAXC + 1);
+    c.flag = reinterpret_cast<short *>(p);
+    p += sizeof(short) * SET_MAXF;
+    c.hdr = reinterpret_cast<int *>(p);
+    p += sizeof(int) * 8;
+    return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+}
+
+static size_t cells_bytes() {
+    return sizeof(long long) * (SET_MAXC + 3) + sizeof(double) * 4 + 2 * sizeof(Axis) +
+           sizeof(short) * (4 * SET_MAXC + 1 + SET_MAXF) + sizeof(int) * 8 + 32;
+}
+
+// One thread: the 2D cells of transaxial pair (a, b).
+__device__ void build_cells(const Scan &sc, const Img &im, const double *cs, int a, int b,
+                            Cells2D &c) {
+    double px, py, pz, qx, qy, qz;
+    face_centre(sc, cs, a, px, py, pz);
+    face_centre(sc, cs, b, qx, qy, qz);
+    c.xy[0] = px;
+    c.xy[1] = py;
+    c.xy[2] = qx;
+    c.xy[3] = qy;
+    bool empty = false;
+    Axis &X = *c.X, &Y = *c.Y;
+    make_axis(X, (px - im.ox) * im.idx, (qx - im.ox) * im.idx, im.nx, empty);
+    make_axis(Y, (py - im.oy) * im.idy, (qy - im.oy) * im.idy, im.ny, empty);
+    long long amin = 0, amax = (long long)FX;
+    for (int k = 0; k < 2; ++k) {
+        const Axis &A = k ? Y : X;
+        if (A.kind == 0) continue;
+        long long p = plane_alpha(A, 0), q = plane_alpha(A, A.n);
+        long long lo = p < q ? p : q, hi = p < q ? q : p;
+        amin = lo > amin ? lo : amin;
+        amax = hi < amax ? hi : amax;
+    }
+    c.clip[0] = amin;
+    c.clip[1] = amax;
+    int n = 0, nruns = 0, nflag = 0;
+    bool ok = true;
+    if (!empty && amax > amin) {
+        int cx, cy;
+        ok &= voxel_at(X, amin, cx);
+        ok &= voxel_at(Y, amin, cy);
+        long long cur = amin;
+        c.bnd[0] = amin;
+        const float lx = (float)(qx - px), ly = (float)(qy - py);
+        const float len2 = sqrtf(lx * lx + ly * ly);
+        // the 3D threshold is at most the transaxial one (3D segments are longer)
+        const long long thr2 = 2 * (long long)ceilf((float)MIN_CHORD_MM / len2 * (float)FX);
+        for (int it = 0; it < im.nx + im.ny + 4 && n < SET_MAXC; ++it) {
+            long long lo, ex_, ey_;
+            if (X.kind == 0) ex_ = FX_BIG; else slab(X, cx, lo, ex_);
+            if (Y.kind == 0) ey_ = FX_BIG; else slab(Y, cy, lo, ey_);
+            long long nxt = ex_ < ey_ ? ex_ : ey_;
+            nxt = nxt < amax ? nxt : amax;
+            if (nxt > cur) {
+                c.ix[n] = (short)(cx < 0 ? 0 : (cx >= im.nx ? im.nx - 1 : cx));
+                c.iy[n] = (short)(cy < 0 ? 0 : (cy >= im.ny ? im.ny - 1 : cy));
+                if (n == 0 || c.iy[n] != c.iy[n - 1]) c.rstart[nruns++] = (short)n;
+                c.run[n] = (short)(nruns - 1);
+                if (nxt - cur < thr2) {
+                    if (nflag < SET_MAXF) c.flag[nflag] = (short)n;
+                    ++nflag;
+                }
+                ++n;
+                c.bnd[n] = nxt;
+            }
+            if (nxt >= amax) break;
+            if (ex_ == nxt) cx += X.inc ? 1 : -1;
+            if (ey_ == nxt) cy += Y.inc ? 1 : -1;
+            cur = nxt;
+        }
+        if (n >= SET_MAXC && c.bnd[n] < amax) ok = false;
+    }
+    c.rstart[nruns] = (short)n;
+    c.hdr[0] = n;
+    c.hdr[1] = nruns;
+    c.hdr[2] = nflag;
+    c.hdr[3] = ok;
+}
+
+// First cell whose interval ends after al / last cell that starts before al.
+__device__ __forceinline__ int first_cell_after(const long long *bnd, int n, long long al) {
+    int lo = 0, hi = n - 1;  // smallest c with bnd[c+1] > al
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (bnd[mid + 1] > al) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int last_cell_before(const long long *bnd, int n, long long al) {
+    int lo = 0, hi = n - 1;  // largest c with bnd[c] < al
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (bnd[mid] < al) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per ring pair: the z axis, clip and chord scale of the 3D segment.
+struct ZRay {
+    Axis Z;
+    long long amin, amax, min_units;
+    float to_mm;
+    bool empty;
+};
+
+__device__ __forceinline__ void make_zray(ZRay &r, const Scan &sc, const Img &im,
+                                          const Cells2D &c, int ra, int rb) {
+    const double za = sc.z064 + ra * sc.pa64, zb = sc.z064 + rb * sc.pa64;
+    r.empty = c.hdr[0] == 0;
+    make_axis(r.Z, (za - im.oz) * im.idz, (zb - im.oz) * im.idz, im.nz, r.empty);
+    long long amin = c.clip[0], amax = c.clip[1];
+    if (r.Z.kind != 0) {
+        long long p = plane_alpha(r.Z, 0), q = plane_alpha(r.Z, im.nz);
+        long long lo = p < q ? p : q, hi = p < q ? q : p;
+        amin = lo > amin ? lo : amin;
+        amax = hi < amax ? hi : amax;
+    }
+    r.amin = amin;
+    r.amax = amax;
+    if (amax <= amin) r.empty = true;
+    const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
+    const float lz = (float)(zb - za);
+    const float len = sqrtf(lx * lx + ly * ly + lz * lz);
+    r.min_units = (long long)ceilf((float)MIN_CHORD_MM / len * (float)FX);
+    r.to_mm = len * (float)(1.0 / FX);
+}
+
+__device__ __forceinline__ long long piece(const long long *bnd, int cc, long long zl,
+                                           long long zh) {
+    long long lo = bnd[cc] > zl ? bnd[cc] : zl, hi = bnd[cc + 1] < zh ? bnd[cc + 1] : zh;
+    return hi - lo;
+}
+
+__global__ void __launch_bounds__(SET_T) set_count_kernel(Scan sc, Img im, LorSet ls,
+                                                          int64_t *__restrict__ counts,
+                                                          int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    Cells2D c;
+    double *cs = reinterpret_cast<double *>(cells_layout(c, raw));
+    int32_t *tp_start = reinterpret_cast<int32_t *>(cs + 2 * sc.R);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    short2 *rps = reinterpret_cast<short2 *>(rp_start + ls.NR + 1);
+    stage_blocks(sc, cs);
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    for (int j = threadIdx.x; j < ls.nrp; j += SET_T) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rps[j] = make_short2((short)r1, (short)r2);
+    }
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int a, b;
+            ls.tp_decode(tp_start, T, &a, &b);
+            build_cells(sc, im, cs, a, b, c);
+            if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
+        }
+        __syncthreads();
+        const int n = c.hdr[0], nflag = c.hdr[2];
+        for (int j = threadIdx.x; j < ls.nrp; j += SET_T) {
+            const short2 rr = rps[j];
+            ZRay r;
+            make_zray(r, sc, im, c, rr.x, rr.y);
+            int64_t cnt = 0;
+            if (!r.empty) {
+                int za, zb;
+                bool ok = voxel_at(r.Z, r.amin, za);
+                ok &= voxel_at(r.Z, r.amax - 1, zb);
+                int z0 = za < zb ? za : zb, z1 = za < zb ? zb : za;
+                z0 = z0 < 0 ? 0 : z0;
+                z1 = z1 > im.nz - 1 ? im.nz - 1 : z1;
+                for (int iz = z0; iz <= z1; ++iz) {
+                    long long zl, zh;
+                    slab(r.Z, iz, zl, zh);
+                    zl = zl > r.amin ? zl : r.amin;
+                    zh = zh < r.amax ? zh : r.amax;
+                    if (zh <= zl) continue;
+                    const int ca = first_cell_after(c.bnd, n, zl);
+                    const int cb = last_cell_before(c.bnd, n, zh);
+                    if (cb < ca) continue;
+                    cnt += cb - ca + 1;
+                    if (piece(c.bnd, ca, zl, zh) < r.min_units) --cnt;
+                    if (cb != ca && piece(c.bnd, cb, zl, zh) < r.min_units) --cnt;
+                    if (nflag <= SET_MAXF) {
+                        for (int f = 0; f < nflag; ++f) {
+                            const int cc = c.flag[f];
+                            if (cc > ca && cc < cb && c.bnd[cc + 1] - c.bnd[cc] < r.min_units) --cnt;
+                        }
+                    } else {
+                        for (int cc = ca + 1; cc < cb; ++cc)
+                            if (c.bnd[cc + 1] - c.bnd[cc] < r.min_units) --cnt;
+                    }
+                }
+                if (!ok) atomicExch(status, PSF_EDEBUG);
+            }
+            counts[T * ls.nrp + j] = cnt;
+        }
+    }
+}
+
+// Resumable walk over the voxels of one ring pair in ascending voxel order.
+struct SetCursor {
+    int iz, z1, ca, cb;
+    int r, r_last, rdir;  // run being emitted, last run, step
+    int cc, c_last, cdir;  // cell being emitted, last cell of the run, step
+    long long zl, zh;
+    bool done;
+};
+
+__device__ __forceinline__ bool set_next_run(const Cells2D &c, SetCursor &s) {
+    // next run of the current slab (false when the slab is exhausted)
+    if (s.r == s.r_last) return false;
+    s.r += s.rdir;
+    return true;
+}
+
+__device__ __forceinline__ void set_start_run(const Cells2D &c, SetCursor &s, bool xinc) {
+    int lo = c.rstart[s.r], hi = c.rstart[s.r + 1] - 1;
+    lo = lo > s.ca ? lo : s.ca;
+    hi = hi < s.cb ? hi : s.cb;
+    s.cc = xinc ? lo : hi;
+    s.c_last = xinc ? hi : lo;
+    s.cdir = xinc ? 1 : -1;
+}
+
+// Position on the next slab with overlapping cells (or done).
+__device__ __forceinline__ void set_next_slab(const Cells2D &c, const ZRay &zr, SetCursor &s,
+                                              bool xinc, bool yinc) {
+    const int n = c.hdr[0];
+    while (++s.iz <= s.z1) {
+        slab(zr.Z, s.iz, s.zl, s.zh);
+        s.zl = s.zl > zr.amin ? s.zl : zr.amin;
+        s.zh = s.zh < zr.amax ? s.zh : zr.amax;
+        if (s.zh <= s.zl) continue;
+        s.ca = first_cell_after(c.bnd, n, s.zl);
+        s.cb = last_cell_before(c.bnd, n, s.zh);
+        if (s.cb < s.ca) continue;
+        const int ra = c.run[s.ca], rb = c.run[s.cb];
+        s.r = yinc ? ra : rb;
+        s.r_last = yinc ? rb : ra;
+        s.rdir = yinc ? 1 : -1;
+        set_start_run(c, s, xinc);
+        return;
+    }
+    s.done = true;
+}
+
+// Next stored voxel: returns false when the row is exhausted.
+__device__ __forceinline__ bool set_take(const Cells2D &c, const ZRay &zr, SetCursor &s,
+                                         bool xinc, bool yinc, int &iz, int &cell,
+                                         long long &len) {
+    while (!s.done) {
+        const int cc = s.cc, izc = s.iz;
+        const long long L = piece(c.bnd, cc, s.zl, s.zh);
+        if (s.cc == s.c_last) {  // advance to the next run, or the next slab
+            if (set_next_run(c, s)) set_start_run(c, s, xinc);
+            else set_next_slab(c, zr, s, xinc, yinc);
+        } else {
+            s.cc += s.cdir;
+        }
+        if (L >= zr.min_units) {
+            iz = izc;
+            cell = cc;
+            len = L;
+            return true;
+        }
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(SET_T) set_fill_kernel(Scan sc, Img im, LorSet ls,
+                                                         const int64_t *__restrict__ row_ptr,
+                                                         int32_t *__restrict__ col,
+                                                         float *__restrict__ val,
+                                                         int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    Cells2D c;
+    double *cs = reinterpret_cast<double *>(cells_layout(c, raw));
+    int32_t *tp_start = reinterpret_cast<int32_t *>(cs + 2 * sc.R);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    short2 *rps = reinterpret_cast<short2 *>(rp_start + ls.NR + 1);
+    unsigned char *stg = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(rps + ls.nrp) + 15) & ~uintptr_t(15));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *scol = reinterpret_cast<int32_t *>(stg) + warp * 32 * FILL_PAD;
+    float *sval = reinterpret_cast<float *>(reinterpret_cast<int32_t *>(stg) +
+                                            (SET_T / 32) * 32 * FILL_PAD) +
+                  warp * 32 * FILL_PAD;
+    stage_blocks(sc, cs);
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    for (int j = threadIdx.x; j < ls.nrp; j += SET_T) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rps[j] = make_short2((short)r1, (short)r2);
+    }
+    const int nx = im.nx, nxy = im.nx * im.ny;
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int a, b;
+            ls.tp_decode(tp_start, T, &a, &b);
+            build_cells(sc, im, cs, a, b, c);
+        }
+        __syncthreads();
+        const bool xinc = c.X->kind == 0 || c.X->inc;
+        const bool yinc = c.Y->kind == 0 || c.Y->inc;
+        for (int base = warp * 32; base < ls.nrp; base += SET_T) {
+            const int j = base + lane;
+            ZRay zr;
+            SetCursor s;
+            s.done = true;
+            int64_t pos = 0, end = 0;
+            if (j < ls.nrp) {
+                const short2 rr = rps[j];
+                make_zray(zr, sc, im, c, rr.x, rr.y);
+                pos = row_ptr[T * ls.nrp + j];
+                end = row_ptr[T * ls.nrp + j + 1];
+                if (!zr.empty) {
+                    int za, zb;
+                    voxel_at(zr.Z, zr.amin, za);
+                    voxel_at(zr.Z, zr.amax - 1, zb);
+                    int z0 = za < zb ? za : zb, z1 = za < zb ? zb : za;
+                    s.iz = (z0 < 0 ? 0 : z0) - 1;
+                    s.z1 = z1 > im.nz - 1 ? im.nz - 1 : z1;
+                    s.done = false;
+                    set_next_slab(c, zr, s, xinc, yinc);
+                }
+            }
+            bool bad = false;
+            while (__any_sync(0xffffffffu, !s.done)) {
+                int cnt = 0;
+                while (cnt < 32 && !s.done) {
+                    int iz, cell;
+                    long long L;
+                    if (!set_take(c, zr, s, xinc, yinc, iz, cell, L)) break;
+                    scol[lane * FILL_PAD + cnt] = iz * nxy + c.iy[cell] * nx + c.ix[cell];
+                    sval[lane * FILL_PAD + cnt] = units_to_f(L) * zr.to_mm;
+                    ++cnt;
+                }
+                if (pos + cnt > end) {
+                    bad = true;
+                    cnt = (int)(end - pos > 0 ? end - pos : 0);
+                }
+                __syncwarp();
+                for (int q = 0; q < 32; ++q) {
+                    const int cq = __shfl_sync(0xffffffffu, cnt, q);
+                    const int64_t pq = __shfl_sync(0xffffffffu, pos, q);
+                    if (lane < cq) {
+                        col[pq + lane] = scol[q * FILL_PAD + lane];
+                        val[pq + lane] = sval[q * FILL_PAD + lane];
+                    }
+                }
+                pos += cnt;
+                __syncwarp();
+            }
+            if (j < ls.nrp && (bad || pos != end)) atomicExch(status, PSF_EDEBUG);
+        }
+    }
+}
+
+static size_t set_smem(const Scan &sc, const LorSet &ls, bool fill) {
+    size_t b = cells_bytes() + sizeof(double) * 2 * sc.R + sizeof(int32_t) * (ls.Nt + ls.NR + 2) +
+               sizeof(short2) * ls.nrp + 32;
+    if (fill) b += sizeof(int32_t) * 2 * (SET_T / 32) * 32 * FILL_PAD;
+    return b;
+}
+
 }  // namespace psf
 
 using namespace psf;
+
+extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
+                                   const psf_lor_set *set, int64_t *row_ptr, int32_t *col,
+                                   float *val, int64_t capacity, int64_t *nnz_out, void *stream) {
+    Scan sc;
+    Img im;
+    LorSet ls;
+    int rc = make_scan(scanner, &sc);
+    if (rc) return rc;
+    rc = make_img(image, &im);
+    if (rc) return rc;
+    rc = make_lorset(scanner, set, &ls);
+    if (rc) return rc;
+    if (!row_ptr || !nnz_out || (col && !val)) return PSF_EINVAL;
+    if (im.nx + im.ny + 1 > SET_MAXC || im.nx > 32767 || im.ny > 32767) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const int64_t n = ls.ntp * ls.nrp;
+    *nnz_out = 0;
+    PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
+    if (n == 0) return PSF_OK;
+    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE + 1;
+    void *scratch = nullptr;
+    PSF_TRY(cudaMallocAsync(&scratch, sizeof(int64_t) * ntiles + 256, st));
+    int64_t *tiles = (int64_t *)scratch;
+    int *status = (int *)(tiles + ntiles);
+    cudaMemsetAsync(status, 0, sizeof(int), st);
+    const int grid_max = sm_count() * 4;
+    const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
+    const size_t cshm = set_smem(sc, ls, false), fshm = set_smem(sc, ls, true);
+    int h_status = 0;
+    int64_t nnz = 0;
+    rc = PSF_OK;
+    if (cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cshm) != cudaSuccess ||
+        cudaFuncSetAttribute(set_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fshm) != cudaSuccess)
+        rc = PSF_ECUDA;
+    if (!rc) {
+        set_count_kernel<<<grid, SET_T, cshm, st>>>(sc, im, ls, row_ptr + 1, status);
+        if (cudaGetLastError() != cudaSuccess) rc = PSF_ECUDA;
+    }
+    if (!rc) rc = inclusive_scan(row_ptr + 1, n, tiles, st);
+    if (!rc && (cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess))
+        rc = PSF_ECUDA;
+    if (!rc) {
+        *nnz_out = nnz;
+        if (h_status) rc = h_status;
+    }
+    if (!rc && col) {
+        if (nnz > capacity) {
+            rc = PSF_ECAPACITY;
+        } else {
+            set_fill_kernel<<<grid, SET_T, fshm, st>>>(sc, im, ls, row_ptr, col, val, status);
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                rc = PSF_ECUDA;
+            else if (h_status)
+                rc = h_status;
+        }
+    }
+    cudaFreeAsync(scratch, st);
+    return rc;
+}
 
 extern "C" int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *image,
                                const int32_t *lors, int64_t n_lors, const float *spread,

@@ -18,10 +18,26 @@ namespace psf {
 constexpr double FX = 1099511627776.0;  // 2^40 units per segment
 constexpr long long FX_BIG = (long long)1 << 62;
 
+__host__ __device__ __forceinline__ float u32_to_f(unsigned v) {
+#ifdef __CUDA_ARCH__
+    return __uint2float_rn(v);
+#else
+    return (float)v;
+#endif
+}
+
+// Non-negative parameter difference (< 2^48) to float, rounded once: both
+// 24-bit halves convert exactly and the FMA rounds hi * 2^24 + lo once.
+__host__ __device__ __forceinline__ float units_to_f(long long v) {
+    const unsigned hi = (unsigned)(v >> 24), lo = (unsigned)(v & ((1 << 24) - 1));
+    return fmaf(u32_to_f(hi), 16777216.0f, u32_to_f(lo));
+}
+
 struct Axis {
     int kind;   // 0: parallel to the planes (index fixed), 1: linear, 2: nearly parallel
     int fixed;  // voxel index when kind == 0
     int n;      // voxels along the axis
+    int inc;    // 1 if the coordinate grows along the segment
     long long A0, DA;
     double S, D;  // grid-local start / extent
     float sf, df;
@@ -35,7 +51,7 @@ struct Ray {
     Axis ax[3];
     long long amin, amax;
     long long min_units;  // MIN_CHORD_MM in fixed-point units of this segment
-    double len_mm;
+    float len_mm;
     bool empty;
 };
 
@@ -66,10 +82,13 @@ __host__ __device__ __forceinline__ bool voxel_at(const Axis &a, long long al, i
         k = a.fixed;
         return true;
     }
-    float g = fmaf((float)((double)al * (1.0 / FX)), a.df, a.sf);
+    // guess in FP32 from the top 32 of the parameter's 40 fraction bits (no
+    // FP64 on this path); al is inside [amin, amax] within [0, 2^40]
+    const float af = u32_to_f((unsigned)(al >> 8)) * 2.3283064365386963e-10f;  // 2^-32
+    float g = fmaf(af, a.df, a.sf);
     g = fminf(fmaxf(g, -2.0f), (float)a.n + 1.0f);
     int k0 = f2i_rd(g);
-    bool inc = a.D > 0.0;
+    const bool inc = a.inc;
     for (int it = 0; it < 64; ++it) {
         long long lo, hi;
         slab(a, k0, lo, hi);
@@ -95,6 +114,7 @@ __host__ __device__ __forceinline__ void make_axis(Axis &a, double s, double e, 
     a.fixed = 0;
     a.sf = (float)s;
     a.df = (float)a.D;
+    a.inc = a.D > 0.0;
     if (fabs(a.D) < 1e-9) {
         // parallel: a coordinate within 1e-9 voxel of a plane lies on it and
         // belongs to the voxel above
@@ -119,15 +139,16 @@ __host__ __device__ __forceinline__ void make_axis(Axis &a, double s, double e, 
 __host__ __device__ __forceinline__ void make_ray(Ray &r, const Img &im, double px, double py, double pz,
                                          double qx, double qy, double qz) {
     r.empty = false;
-    const double sx = (px - im.ox) / im.dx, ex = (qx - im.ox) / im.dx;
-    const double sy = (py - im.oy) / im.dy, ey = (qy - im.oy) / im.dy;
-    const double sz = (pz - im.oz) / im.dz, ez = (qz - im.oz) / im.dz;
+    const double sx = (px - im.ox) * im.idx, ex = (qx - im.ox) * im.idx;
+    const double sy = (py - im.oy) * im.idy, ey = (qy - im.oy) * im.idy;
+    const double sz = (pz - im.oz) * im.idz, ez = (qz - im.oz) * im.idz;
     make_axis(r.ax[0], sx, ex, im.nx, r.empty);
     make_axis(r.ax[1], sy, ey, im.ny, r.empty);
     make_axis(r.ax[2], sz, ez, im.nz, r.empty);
-    double lx = qx - px, ly = qy - py, lz = qz - pz;
-    r.len_mm = sqrt(lx * lx + ly * ly + lz * lz);
-    r.min_units = (long long)ceil(MIN_CHORD_MM / r.len_mm * FX);
+    // the length only scales the chords (FP32 precision is enough)
+    const float lx = (float)(qx - px), ly = (float)(qy - py), lz = (float)(qz - pz);
+    r.len_mm = sqrtf(lx * lx + ly * ly + lz * lz);
+    r.min_units = (long long)ceilf((float)MIN_CHORD_MM / r.len_mm * (float)FX);
     long long amin = 0, amax = (long long)FX;
     for (int c = 0; c < 3; ++c) {
         const Axis &a = r.ax[c];

@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(SP_THREADS) spread_kernel(
     {
         unsigned char *p = smraw;
         s.red = (double *)p; p += sizeof(double) * 16;
-        s.R1 = (float *)p; p += sizeof(float) * SP_THREADS * Q;
-        s.R2 = (float *)p; p += sizeof(float) * SP_THREADS * Q;
+        s.R1 = (float *)p; p += sizeof(float) * SP_THREADS * (Q + 1);
+        s.R2 = (float *)p; p += sizeof(float) * SP_THREADS * (Q + 1);
         s.accp = (float *)p; p += sizeof(float) * SP_PATS * Q * Q;
         s.wwin = (float *)p; p += sizeof(float) * E * E;
         s.pts = (float *)p; p += sizeof(float) * 2 * NP * 4;
@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(SP_THREADS) spread_kernel(
                 if (r1.valid && r2.valid) {
                     float w1 = 0.0f, w2 = 0.0f;
                     for (int k = 0; k < Q; ++k) {
-                        s.R1[t * Q + k] = r1.q[k];
-                        s.R2[t * Q + k] = r2.q[k];
+                        s.R1[t * (Q + 1) + k] = r1.q[k];  // odd stride: conflict-free
+                        s.R2[t * (Q + 1) + k] = r2.q[k];
                         w1 += r1.q[k];
                         w2 += r2.q[k];
                     }
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(SP_THREADS) spread_kernel(
                     float acc = 0.0f;
                     for (int k = k0; k < k1; ++k) {
                         int sl = s.order[k];
-                        acc = fmaf(s.R1[sl * Q + e1], s.R2[sl * Q + e2], acc);
+                        acc = fmaf(s.R1[sl * (Q + 1) + e1], s.R2[sl * (Q + 1) + e2], acc);
                     }
                     s.accp[P * Q * Q + t] += acc;
                 }
@@ -208,7 +208,7 @@ static size_t spread_smem(const Tab &tb, int Wt, int Wa) {
     int Q = (Wt + 1) * (Wa + 1), E = (2 * Wt + 1) * (2 * Wa + 1);
     int NP = tb.Pt * tb.Pa;
     size_t b = sizeof(double) * 16;
-    b += sizeof(float) * 2 * SP_THREADS * Q;
+    b += sizeof(float) * 2 * SP_THREADS * (Q + 1);
     b += sizeof(float) * SP_PATS * Q * Q;
     b += sizeof(float) * E * E;
     b += sizeof(float) * 2 * NP * 4;

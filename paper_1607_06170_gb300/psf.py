@@ -24,6 +24,7 @@ _TORCH_DT = {PSF_F32: torch.float32, PSF_BF16: torch.bfloat16, PSF_F16: torch.fl
 FUNCTIONS = [
     "psf_strerror", "psf_table_size", "psf_response_build", "psf_bin_spread",
     "psf_lor_set_size", "psf_lor_set_list", "psf_lor_set_classes", "psf_sysmat_rows",
+    "psf_sysmat_rows_set",
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update",
 ]
@@ -71,6 +72,7 @@ _SIGS = {
     "psf_lor_set_classes": (C.c_int, [_P, _P, _P, _P]),
     "psf_sysmat_rows": (C.c_int, [_P, _P, _P, _I64, _P, _I32, _I32, _I32, _P, _P, _P, _P, _I64,
                                   _P, _P]),
+    "psf_sysmat_rows_set": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _P, _P]),
     "psf_matrix_create": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _I32, _P, _P]),
     "psf_matrix_set_spread": (C.c_int, [_P, _P, _P, _I32, _I32, _P]),
     "psf_matrix_destroy": (C.c_int, [_P]),
@@ -226,6 +228,30 @@ def sysmat_rows(sc: dict, im: dict, lors, spread=None, half_t: int = 0, half_a: 
                           dt, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(row_scale), nnz.value,
                           C.byref(nnz), _stream()), "psf_sysmat_rows")
     return row_ptr, col[: nnz.value], val[: nnz.value], row_scale
+
+
+def sysmat_rows_set(sc: dict, im: dict, ls: dict, buffers=None, device="cuda"):
+    """Geometric rows of a structured LOR set (row_ptr, col, val), rows in set
+    order.  buffers=(row_ptr, col, val) of sufficient capacity are filled in
+    one call; otherwise a size query precedes the fill."""
+    s, i, l = scanner(sc), image(im), lor_set(ls)
+    nnz = C.c_int64()
+    L = lib()
+    if buffers is not None:
+        row_ptr, col, val = buffers
+        _ok(L.psf_sysmat_rows_set(C.byref(s), C.byref(i), C.byref(l), _ptr(row_ptr), _ptr(col),
+                                  _ptr(val), col.numel(), C.byref(nnz), _stream()),
+            "psf_sysmat_rows_set")
+        return row_ptr, col[: nnz.value], val[: nnz.value]
+    n, _ = lor_set_size(sc, ls)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=device)
+    _ok(L.psf_sysmat_rows_set(C.byref(s), C.byref(i), C.byref(l), _ptr(row_ptr), None, None, 0,
+                              C.byref(nnz), _stream()), "psf_sysmat_rows_set(size)")
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=device)
+    val = torch.empty(max(nnz.value, 1), dtype=torch.float32, device=device)
+    _ok(L.psf_sysmat_rows_set(C.byref(s), C.byref(i), C.byref(l), _ptr(row_ptr), _ptr(col),
+                              _ptr(val), nnz.value, C.byref(nnz), _stream()), "psf_sysmat_rows_set")
+    return row_ptr, col[: nnz.value], val[: nnz.value]
 
 
 class Matrix:

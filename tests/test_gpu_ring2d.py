@@ -83,6 +83,15 @@ def test_geometric_rows(both):
     assert n > 1000
 
 
+def test_set_rows_equal_list_rows(both, P):
+    name, o, g = both
+    w = I.workload(name)
+    rp, col, val = P.sysmat_rows_set(w["scanner"], w["image"], w["lors"])
+    torch.cuda.synchronize()
+    assert torch.equal(rp, g["G"][0]) and torch.equal(col, g["G"][1])
+    assert torch.equal(val, g["G"][2])
+
+
 def test_psf_rows_and_projectors(both, orc):
     name, o, g = both
     if name != "RING2D":

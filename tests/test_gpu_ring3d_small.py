@@ -85,6 +85,16 @@ def test_geometric_rows(gpu, ref):
     compare_chord_rows((ptr, col, val), ref["G"], ref["nv"])
 
 
+def test_set_rows_equal_list_rows(P, gpu, ref):
+    # the per-transaxial-pair generator must give the very same CSR
+    w = ref["w"]
+    rp, col, val = P.sysmat_rows_set(w["scanner"], w["image"], w["lors"])
+    torch.cuda.synchronize()
+    assert torch.equal(rp, gpu["G"][0])
+    assert torch.equal(col, gpu["G"][1])
+    assert torch.equal(val, gpu["G"][2])
+
+
 def test_factored_projector(gpu, ref, orc):
     w = ref["w"]
     s = w["scanner"]
