@@ -32,7 +32,7 @@ __device__ __forceinline__ void stage_blocks(const Scan &sc, double *cs) {
 }
 
 // Front-face centre of crystal id (mm, FP64).
-__device__ __forceinline__ void face_centre(const Scan &sc, const double *cs, int id, double &x,
+__host__ __device__ __forceinline__ void face_centre(const Scan &sc, const double *cs, int id, double &x,
                                             double &y, double &z) {
     int ring = id / sc.Nt, c = id - ring * sc.Nt;
     int b = c / sc.Nb, i = c - b * sc.Nb;
@@ -420,7 +420,10 @@ struct Cells2D {
     double *xy;       // endpoints (x1, y1, x2, y2)
 };
 
-__device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsigned char *p) {
+// Shared-memory layout, widest fields first so every field is naturally
+// aligned (the 8-byte fields sit at multiples of 8 from a 16-aligned base, the
+// int header at a multiple of 8, the shorts after it).
+__host__ __device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsigned char *p) {
     c.bnd = reinterpret_cast<long long *>(p);
     p += sizeof(long long) * (SET_MAXC + 1);
     c.clip = reinterpret_cast<long long *>(p);
@@ -431,6 +434,8 @@ __device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsigned char
     p += sizeof(Axis);
     c.Y = reinterpret_cast<Axis *>(p);
     p += sizeof(Axis);
+    c.hdr = reinterpret_cast<int *>(p);
+    p += sizeof(int) * 8;
     c.ix = reinterpret_cast<short *>(p);
     p += sizeof(short) * SET_MAXC;
     c.iy = reinterpret_cast<short *>(p);
@@ -441,8 +446,6 @@ __device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsigned char
     p += sizeof(short) * (SET_MAXC + 1);
     c.flag = reinterpret_cast<short *>(p);
     p += sizeof(short) * SET_MAXF;
-    c.hdr = reinterpret_cast<int *>(p);
-    p += sizeof(int) * 8;
     return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
 }
 
@@ -452,7 +455,7 @@ static size_t cells_bytes() {
 }
 
 // One thread: the 2D cells of transaxial pair (a, b).
-__device__ void build_cells(const Scan &sc, const Img &im, const double *cs, int a, int b,
+__host__ __device__ void build_cells(const Scan &sc, const Img &im, const double *cs, int a, int b,
                             Cells2D &c) {
     double px, py, pz, qx, qy, qz;
     face_centre(sc, cs, a, px, py, pz);
@@ -521,7 +524,7 @@ __device__ void build_cells(const Scan &sc, const Img &im, const double *cs, int
 }
 
 // First cell whose interval ends after al / last cell that starts before al.
-__device__ __forceinline__ int first_cell_after(const long long *bnd, int n, long long al) {
+__host__ __device__ __forceinline__ int first_cell_after(const long long *bnd, int n, long long al) {
     int lo = 0, hi = n - 1;  // smallest c with bnd[c+1] > al
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -529,7 +532,7 @@ __device__ __forceinline__ int first_cell_after(const long long *bnd, int n, lon
     }
     return lo;
 }
-__device__ __forceinline__ int last_cell_before(const long long *bnd, int n, long long al) {
+__host__ __device__ __forceinline__ int last_cell_before(const long long *bnd, int n, long long al) {
     int lo = 0, hi = n - 1;  // largest c with bnd[c] < al
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -546,7 +549,7 @@ struct ZRay {
     bool empty;
 };
 
-__device__ __forceinline__ void make_zray(ZRay &r, const Scan &sc, const Img &im,
+__host__ __device__ __forceinline__ void make_zray(ZRay &r, const Scan &sc, const Img &im,
                                           const Cells2D &c, int ra, int rb) {
     const double za = sc.z064 + ra * sc.pa64, zb = sc.z064 + rb * sc.pa64;
     r.empty = c.hdr[0] == 0;
@@ -568,7 +571,7 @@ __device__ __forceinline__ void make_zray(ZRay &r, const Scan &sc, const Img &im
     r.to_mm = len * (float)(1.0 / FX);
 }
 
-__device__ __forceinline__ long long piece(const long long *bnd, int cc, long long zl,
+__host__ __device__ __forceinline__ long long piece(const long long *bnd, int cc, long long zl,
                                            long long zh) {
     long long lo = bnd[cc] > zl ? bnd[cc] : zl, hi = bnd[cc + 1] < zh ? bnd[cc + 1] : zh;
     return hi - lo;
@@ -651,14 +654,14 @@ struct SetCursor {
     bool done;
 };
 
-__device__ __forceinline__ bool set_next_run(const Cells2D &c, SetCursor &s) {
+__host__ __device__ __forceinline__ bool set_next_run(const Cells2D &c, SetCursor &s) {
     // next run of the current slab (false when the slab is exhausted)
     if (s.r == s.r_last) return false;
     s.r += s.rdir;
     return true;
 }
 
-__device__ __forceinline__ void set_start_run(const Cells2D &c, SetCursor &s, bool xinc) {
+__host__ __device__ __forceinline__ void set_start_run(const Cells2D &c, SetCursor &s, bool xinc) {
     int lo = c.rstart[s.r], hi = c.rstart[s.r + 1] - 1;
     lo = lo > s.ca ? lo : s.ca;
     hi = hi < s.cb ? hi : s.cb;
@@ -668,7 +671,7 @@ __device__ __forceinline__ void set_start_run(const Cells2D &c, SetCursor &s, bo
 }
 
 // Position on the next slab with overlapping cells (or done).
-__device__ __forceinline__ void set_next_slab(const Cells2D &c, const ZRay &zr, SetCursor &s,
+__host__ __device__ __forceinline__ void set_next_slab(const Cells2D &c, const ZRay &zr, SetCursor &s,
                                               bool xinc, bool yinc) {
     const int n = c.hdr[0];
     while (++s.iz <= s.z1) {
@@ -690,7 +693,7 @@ __device__ __forceinline__ void set_next_slab(const Cells2D &c, const ZRay &zr, 
 }
 
 // Next stored voxel: returns false when the row is exhausted.
-__device__ __forceinline__ bool set_take(const Cells2D &c, const ZRay &zr, SetCursor &s,
+__host__ __device__ __forceinline__ bool set_take(const Cells2D &c, const ZRay &zr, SetCursor &s,
                                          bool xinc, bool yinc, int &iz, int &cell,
                                          long long &len) {
     while (!s.done) {
