@@ -398,7 +398,8 @@ def run_profile_case(args):
             y = M.forward(x)
             M.back(y)
         if case == "rows_set":
-            P.sysmat_rows_set(s, im, ls, device=dev)
+            # same scanner and image, fan narrowed to +-10 so the capture holds ~3 GB
+            P.sysmat_rows_set(s, im, dict(ls, fan_half=10), device=dev)
         if case in ("rows", "csr"):
             L = P.lor_set_list(s, ls, device=dev)[: 2_000_000].contiguous()
             rp, col, val, _ = P.sysmat_rows(s, im, L)

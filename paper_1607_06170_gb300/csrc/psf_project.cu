@@ -226,6 +226,134 @@ __global__ void __launch_bounds__(ST_T) stencil_kernel(LorSet ls, int Wt, int Wa
     }
 }
 
+// Register-blocked form of the same stencil.  The partner's plane is stored by
+// (ring on a's side, ring difference) so that threads with consecutive ring
+// differences read consecutive words.  Thread (dl, strip) owns the K rows
+// (ra, ra + dl), ra in [strip*K, strip*K + K): along such a diagonal the ring
+// difference, hence the weight of every axial offset pair, is constant.  For
+// each offset difference e = o1 - o2 the partner values the K rows need lie in
+// one plane column (difference dl + e forward, dl - e adjoint) and K + 2*WA
+// consecutive rows; they are loaded once into registers and reused by every
+// offset pair (o1, o1 - e).
+template <bool adjoint, int WA, int K>
+__global__ void __launch_bounds__(ST_T) stencil2_kernel(LorSet ls, int Wt,
+                                                        const float *__restrict__ w,
+                                                        const float *__restrict__ in,
+                                                        float *__restrict__ out) {
+    constexpr int W2a = 2 * WA + 1;
+    extern __shared__ __align__(16) unsigned char raw[];
+    const int Dm = ls.Dm, NR = ls.NR;
+    const int PD = 2 * Dm + 1 + 4 * WA;  // plane columns: differences -Dm-2WA .. Dm+2WA
+    // plane rows: rings -WA .. nstrip*K-1+WA (every strip reads K + 2WA rows)
+    const int PR = (NR + K - 1) / K * K + 2 * WA;
+    const int D0 = Dm + 2 * WA;          // column / weight slot of difference 0
+    const int E = (2 * Wt + 1) * W2a;
+    float *plane = reinterpret_cast<float *>(raw);
+    float *wt = plane + PR * PD;                                   // [PD][W2a][W2a]
+    short2 *rp = reinterpret_cast<short2 *>(wt + PD * W2a * W2a);  // [nrp]
+    int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    for (int j = threadIdx.x; j < ls.nrp; j += ST_T) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rp[j] = make_short2((short)r1, (short)r2);
+    }
+    const int nd = 2 * Dm + 1, nstrip = (NR + K - 1) / K;
+    const int items = nd * nstrip;
+    const int nrp = (int)ls.nrp;
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        int a, b;
+        ls.tp_decode(tp_start, T, &a, &b);
+        const int a0 = a % ls.Nb;
+        const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
+        for (int it0 = 0; it0 < items; it0 += ST_T) {
+            const int item = it0 + threadIdx.x;
+            const bool active = item < items;
+            const int dl = (active ? item % nd : 0) - Dm;  // this thread's ring difference
+            const int r0 = (active ? item / nd : 0) * K;   // first ring of its strip
+            float acc[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = 0.0f;
+            for (int dt = 0; dt < (2 * Wt + 1) * (2 * Wt + 1); ++dt) {
+                const int dt1 = dt / (2 * Wt + 1) - Wt, dt2 = dt % (2 * Wt + 1) - Wt;
+                int pa = adjoint ? a + dt1 : a - dt1, pb = adjoint ? b + dt2 : b - dt2;
+                pa += pa < 0 ? ls.Nt : (pa >= ls.Nt ? -ls.Nt : 0);
+                pb += pb < 0 ? ls.Nt : (pb >= ls.Nt ? -ls.Nt : 0);
+                if (pa == pb) continue;
+                const bool sw = pa > pb;
+                const int c1 = sw ? pb : pa, c2 = sw ? pa : pb;
+                if (!tp_member(ls, c1, c2)) continue;
+                const int64_t prow = (int64_t)tp_index(ls, tp_start, c1, c2) * nrp;
+                __syncthreads();
+                for (int i = threadIdx.x; i < PR * PD; i += ST_T) plane[i] = 0.0f;
+                for (int i = threadIdx.x; i < PD * W2a * W2a; i += ST_T) wt[i] = 0.0f;
+                __syncthreads();
+                for (int j = threadIdx.x; j < nrp; j += ST_T) {
+                    const short2 rr = rp[j];
+                    const int ra = sw ? rr.y : rr.x, rb = sw ? rr.x : rr.y;
+                    plane[(ra + WA) * PD + (rb - ra + D0)] = __ldg(in + prow + j);
+                }
+                const int cls = adjoint ? own_cls
+                                        : tp_index(ls, tp_start, c1 % ls.Nb, c2 - (c1 - c1 % ls.Nb));
+                const bool wsw = adjoint ? false : sw;
+                for (int i = threadIdx.x; i < nd * W2a * W2a; i += ST_T) {
+                    const int d = i / (W2a * W2a) - Dm;
+                    const int L1 = (i / W2a) % W2a, L2 = i % W2a;
+                    const int e_a = (dt1 + Wt) * W2a + L1, e_b = (dt2 + Wt) * W2a + L2;
+                    const int e1 = wsw ? e_b : e_a, e2 = wsw ? e_a : e_b;
+                    const int dc = wsw ? -d : d;
+                    wt[(d + D0) * W2a * W2a + L1 * W2a + L2] =
+                        __ldg(w + ((int64_t)cls * nd + dc + Dm) * E * E + e1 * E + e2);
+                }
+                __syncthreads();
+                if (!active) continue;
+#pragma unroll
+                for (int e = -2 * WA; e <= 2 * WA; ++e) {
+                    // forward: sources at (ra - o1, rb - o2), difference dl + e, weight by it;
+                    // adjoint: targets at (ra + o1, rb + o2), difference dl - e, weight by dl
+                    const int colp = (adjoint ? dl - e : dl + e) + D0;
+                    const float *wrow = wt + (adjoint ? dl + D0 : colp) * W2a * W2a;
+                    float v[K + 2 * WA];
+#pragma unroll
+                    for (int i = 0; i < K + 2 * WA; ++i) {
+                        // v[i] = plane row (r0 + i - WA) + WA
+                        v[i] = plane[(r0 + i) * PD + colp];
+                    }
+#pragma unroll
+                    for (int o1 = -WA; o1 <= WA; ++o1) {
+                        const int o2 = o1 - e;
+                        if (o2 < -WA || o2 > WA) continue;
+                        const float wv = wrow[(o1 + WA) * W2a + (o2 + WA)];
+#pragma unroll
+                        for (int k = 0; k < K; ++k)
+                            acc[k] = fmaf(wv, v[adjoint ? k + o1 + WA : k - o1 + WA], acc[k]);
+                    }
+                }
+            }
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int ra = r0 + k, rb = ra + dl;
+                    if (ra < NR && rb >= 0 && rb < NR)
+                        out[T * nrp + rp_start[ra] + (rb - ls.rp_lo(ra))] = acc[k];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int ST2_K = 8;  // rows per thread in stencil2_kernel
+
+static size_t stencil2_smem_bytes(const LorSet &ls, int Wa) {
+    const int PD = 2 * ls.Dm + 1 + 4 * Wa, W2a = 2 * Wa + 1;
+    const int PR = (ls.NR + ST2_K - 1) / ST2_K * ST2_K + 2 * Wa;
+    return sizeof(float) * (PR * PD + PD * W2a * W2a) + sizeof(short2) * ls.nrp +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 16;
+}
+
 template <typename F>
 static int dispatch_dtype(int dtype, F &&f) {
     if (dtype == PSF_F32) return f((const float *)nullptr);
@@ -257,13 +385,35 @@ static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t
 }
 
 // S (adjoint == false) or S^T on LOR-space vectors of a factored plan.
+template <bool adjoint, int WA>
+static int launch_stencil2(const psf_matrix *m, const float *in, float *out, int grid,
+                           cudaStream_t st) {
+    const size_t shm = stencil2_smem_bytes(m->ls, WA);
+    PSF_TRY(cudaFuncSetAttribute(stencil2_kernel<adjoint, WA, ST2_K>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    stencil2_kernel<adjoint, WA, ST2_K><<<grid, ST_T, shm, st>>>(m->ls, m->Wt, m->cls, in, out);
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
 static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoint,
                    cudaStream_t st) {
-    const size_t shm = stencil_smem_bytes(m->ls, m->Wa);
     int dev = 0, sms = 148;
     PSF_TRY(cudaGetDevice(&dev));
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
+    switch (m->Wa * 2 + (adjoint ? 1 : 0)) {  // register-blocked form for axial windows <= 3
+        case 0: return launch_stencil2<false, 0>(m, in, out, (int)grid, st);
+        case 1: return launch_stencil2<true, 0>(m, in, out, (int)grid, st);
+        case 2: return launch_stencil2<false, 1>(m, in, out, (int)grid, st);
+        case 3: return launch_stencil2<true, 1>(m, in, out, (int)grid, st);
+        case 4: return launch_stencil2<false, 2>(m, in, out, (int)grid, st);
+        case 5: return launch_stencil2<true, 2>(m, in, out, (int)grid, st);
+        case 6: return launch_stencil2<false, 3>(m, in, out, (int)grid, st);
+        case 7: return launch_stencil2<true, 3>(m, in, out, (int)grid, st);
+        default: break;
+    }
+    const size_t shm = stencil_smem_bytes(m->ls, m->Wa);
     if (adjoint) {
         PSF_TRY(cudaFuncSetAttribute(stencil_kernel<true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
@@ -319,7 +469,9 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;
     if (ls.ntp * ls.nrp != m->n_rows) return PSF_EINVAL;
-    if (ls.nrp > ST_T * ST_OUT || stencil_smem_bytes(ls, half_a) > 200 * 1024) return PSF_EINVAL;
+    if (ls.nrp > ST_T * ST_OUT || stencil_smem_bytes(ls, half_a) > 200 * 1024 ||
+        stencil2_smem_bytes(ls, half_a) > 200 * 1024 || ls.NR > 32000)
+        return PSF_EINVAL;
     m->factored = true;
     m->ls = ls;
     m->Wt = half_t;

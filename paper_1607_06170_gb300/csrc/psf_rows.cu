@@ -577,240 +577,205 @@ __host__ __device__ __forceinline__ long long piece(const long long *bnd, int cc
     return hi - lo;
 }
 
-__global__ void __launch_bounds__(SET_T) set_count_kernel(Scan sc, Img im, LorSet ls,
-                                                          int64_t *__restrict__ counts,
-                                                          int *__restrict__ status) {
-    extern __shared__ __align__(16) unsigned char raw[];
+}  // namespace psf
+
+#include "psf_rows_set.cuh"
+
+namespace psf {
+
+// Per CTA: the cells of its current transaxial pair, block trig, set prefix
+// tables and the ring pair of every row offset.
+struct SetSmem {
     Cells2D c;
-    double *cs = reinterpret_cast<double *>(cells_layout(c, raw));
-    int32_t *tp_start = reinterpret_cast<int32_t *>(cs + 2 * sc.R);
-    int32_t *rp_start = tp_start + ls.Nt + 1;
-    short2 *rps = reinterpret_cast<short2 *>(rp_start + ls.NR + 1);
-    stage_blocks(sc, cs);
-    ls.stage_prefix(tp_start, rp_start);
+    double *cs;
+    int32_t *tp_start, *rp_start;
+    short2 *rps;
+    short *s_c, *s_ix, *s_iy;  // voxel-order cell list (fill only)
+};
+
+__device__ __forceinline__ void set_smem_layout(SetSmem &m, unsigned char *raw, const Scan &sc,
+                                                const LorSet &ls) {
+    m.cs = reinterpret_cast<double *>(cells_layout(m.c, raw));
+    m.tp_start = reinterpret_cast<int32_t *>(m.cs + 2 * sc.R);
+    m.rp_start = m.tp_start + ls.Nt + 1;
+    m.rps = reinterpret_cast<short2 *>(m.rp_start + ls.NR + 1);
+    m.s_c = reinterpret_cast<short *>(m.rps + ls.nrp);
+    m.s_ix = m.s_c + SET_MAXC;
+    m.s_iy = m.s_ix + SET_MAXC;
+}
+
+static size_t set_smem(const Scan &sc, const LorSet &ls) {
+    return cells_bytes() + sizeof(double) * 2 * sc.R + sizeof(int32_t) * (ls.Nt + ls.NR + 2) +
+           sizeof(short2) * ls.nrp + sizeof(short) * 3 * SET_MAXC + 64;
+}
+
+__device__ __forceinline__ void set_prologue(SetSmem &m, const Scan &sc, const LorSet &ls) {
+    stage_blocks(sc, m.cs);
+    ls.stage_prefix(m.tp_start, m.rp_start);
     __syncthreads();
     for (int j = threadIdx.x; j < ls.nrp; j += SET_T) {
         int r1, r2;
-        ls.rp_decode(rp_start, j, &r1, &r2);
-        rps[j] = make_short2((short)r1, (short)r2);
+        ls.rp_decode(m.rp_start, j, &r1, &r2);
+        m.rps[j] = make_short2((short)r1, (short)r2);
     }
+}
+
+// K4 (set): one warp per ring pair, lanes over its z slabs.
+__global__ void __launch_bounds__(SET_T, 2) set_count_kernel(Scan sc, Img im, LorSet ls,
+                                                             int64_t *__restrict__ counts,
+                                                             int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    SetSmem m;
+    set_smem_layout(m, raw, sc, ls);
+    set_prologue(m, sc, ls);
+    const Cells2D &c = m.c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nrp = (int)ls.nrp;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
         __syncthreads();
         if (threadIdx.x == 0) {
             int a, b;
-            ls.tp_decode(tp_start, T, &a, &b);
-            build_cells(sc, im, cs, a, b, c);
+            ls.tp_decode(m.tp_start, T, &a, &b);
+            build_cells(sc, im, m.cs, a, b, m.c);
             if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
         }
         __syncthreads();
-        const int n = c.hdr[0], nflag = c.hdr[2];
-        for (int j = threadIdx.x; j < ls.nrp; j += SET_T) {
-            const short2 rr = rps[j];
-            ZRay r;
-            make_zray(r, sc, im, c, rr.x, rr.y);
-            int64_t cnt = 0;
-            if (!r.empty) {
-                int za, zb;
-                bool ok = voxel_at(r.Z, r.amin, za);
-                ok &= voxel_at(r.Z, r.amax - 1, zb);
-                int z0 = za < zb ? za : zb, z1 = za < zb ? zb : za;
-                z0 = z0 < 0 ? 0 : z0;
-                z1 = z1 > im.nz - 1 ? im.nz - 1 : z1;
-                for (int iz = z0; iz <= z1; ++iz) {
-                    long long zl, zh;
-                    slab(r.Z, iz, zl, zh);
-                    zl = zl > r.amin ? zl : r.amin;
-                    zh = zh < r.amax ? zh : r.amax;
-                    if (zh <= zl) continue;
-                    const int ca = first_cell_after(c.bnd, n, zl);
-                    const int cb = last_cell_before(c.bnd, n, zh);
-                    if (cb < ca) continue;
-                    cnt += cb - ca + 1;
-                    if (piece(c.bnd, ca, zl, zh) < r.min_units) --cnt;
-                    if (cb != ca && piece(c.bnd, cb, zl, zh) < r.min_units) --cnt;
-                    if (nflag <= SET_MAXF) {
-                        for (int f = 0; f < nflag; ++f) {
-                            const int cc = c.flag[f];
-                            if (cc > ca && cc < cb && c.bnd[cc + 1] - c.bnd[cc] < r.min_units) --cnt;
-                        }
-                    } else {
-                        for (int cc = ca + 1; cc < cb; ++cc)
-                            if (c.bnd[cc + 1] - c.bnd[cc] < r.min_units) --cnt;
+        for (int base = warp * 32; base < nrp; base += SET_T) {
+            const int j = base + lane, nq = nrp - base < 32 ? nrp - base : 32;
+            ZRay mine;
+            int z0m = 0, z1m = -1;
+            mine.empty = true;
+            if (j < nrp) {
+                make_zray(mine, sc, im, c, m.rps[j].x, m.rps[j].y);
+                zray_slabs(mine, im.nz, z0m, z1m);
+            }
+            long long mycount = 0;
+            for (int q = 0; q < nq; ++q) {
+                ZRay zr;
+                shfl_zray(zr, mine, q);
+                const int z0 = __shfl_sync(0xffffffffu, z0m, q);
+                const int z1 = __shfl_sync(0xffffffffu, z1m, q);
+                long long tot = 0;
+                if (!zr.empty) {
+                    for (int zb = z0; zb <= z1; zb += 32) {
+                        SlabCut s;
+                        s.count = 0;
+                        if (zb + lane <= z1) cut_slab(c, zr, zb + lane, s);
+                        tot += __reduce_add_sync(0xffffffffu, (unsigned)s.count);
                     }
                 }
-                if (!ok) atomicExch(status, PSF_EDEBUG);
+                if (lane == q) mycount = tot;
             }
-            counts[T * ls.nrp + j] = cnt;
+            if (j < nrp) counts[T * nrp + j] = mycount;
         }
     }
 }
 
-// Resumable walk over the voxels of one ring pair in ascending voxel order.
-struct SetCursor {
-    int iz, z1, ca, cb;
-    int r, r_last, rdir;  // run being emitted, last run, step
-    int cc, c_last, cdir;  // cell being emitted, last cell of the run, step
-    long long zl, zh;
-    bool done;
-};
-
-__host__ __device__ __forceinline__ bool set_next_run(const Cells2D &c, SetCursor &s) {
-    // next run of the current slab (false when the slab is exhausted)
-    if (s.r == s.r_last) return false;
-    s.r += s.rdir;
-    return true;
-}
-
-__host__ __device__ __forceinline__ void set_start_run(const Cells2D &c, SetCursor &s, bool xinc) {
-    int lo = c.rstart[s.r], hi = c.rstart[s.r + 1] - 1;
-    lo = lo > s.ca ? lo : s.ca;
-    hi = hi < s.cb ? hi : s.cb;
-    s.cc = xinc ? lo : hi;
-    s.c_last = xinc ? hi : lo;
-    s.cdir = xinc ? 1 : -1;
-}
-
-// Position on the next slab with overlapping cells (or done).
-__host__ __device__ __forceinline__ void set_next_slab(const Cells2D &c, const ZRay &zr, SetCursor &s,
-                                              bool xinc, bool yinc) {
-    const int n = c.hdr[0];
-    while (++s.iz <= s.z1) {
-        slab(zr.Z, s.iz, s.zl, s.zh);
-        s.zl = s.zl > zr.amin ? s.zl : zr.amin;
-        s.zh = s.zh < zr.amax ? s.zh : zr.amax;
-        if (s.zh <= s.zl) continue;
-        s.ca = first_cell_after(c.bnd, n, s.zl);
-        s.cb = last_cell_before(c.bnd, n, s.zh);
-        if (s.cb < s.ca) continue;
-        const int ra = c.run[s.ca], rb = c.run[s.cb];
-        s.r = yinc ? ra : rb;
-        s.r_last = yinc ? rb : ra;
-        s.rdir = yinc ? 1 : -1;
-        set_start_run(c, s, xinc);
-        return;
-    }
-    s.done = true;
-}
-
-// Next stored voxel: returns false when the row is exhausted.
-__host__ __device__ __forceinline__ bool set_take(const Cells2D &c, const ZRay &zr, SetCursor &s,
-                                         bool xinc, bool yinc, int &iz, int &cell,
-                                         long long &len) {
-    while (!s.done) {
-        const int cc = s.cc, izc = s.iz;
-        const long long L = piece(c.bnd, cc, s.zl, s.zh);
-        if (s.cc == s.c_last) {  // advance to the next run, or the next slab
-            if (set_next_run(c, s)) set_start_run(c, s, xinc);
-            else set_next_slab(c, zr, s, xinc, yinc);
-        } else {
-            s.cc += s.cdir;
-        }
-        if (L >= zr.min_units) {
-            iz = izc;
-            cell = cc;
-            len = L;
-            return true;
-        }
-    }
-    return false;
-}
-
-__global__ void __launch_bounds__(SET_T) set_fill_kernel(Scan sc, Img im, LorSet ls,
-                                                         const int64_t *__restrict__ row_ptr,
-                                                         int32_t *__restrict__ col,
-                                                         float *__restrict__ val,
-                                                         int *__restrict__ status) {
+// K6 (set): one warp per ring pair; lanes cut the z slabs, then copy each
+// slab's voxel-order cell ranges to consecutive output slots.
+__global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, LorSet ls,
+                                                            const int64_t *__restrict__ row_ptr,
+                                                            int32_t *__restrict__ col,
+                                                            float *__restrict__ val,
+                                                            int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char raw[];
-    Cells2D c;
-    double *cs = reinterpret_cast<double *>(cells_layout(c, raw));
-    int32_t *tp_start = reinterpret_cast<int32_t *>(cs + 2 * sc.R);
-    int32_t *rp_start = tp_start + ls.Nt + 1;
-    short2 *rps = reinterpret_cast<short2 *>(rp_start + ls.NR + 1);
-    unsigned char *stg = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(rps + ls.nrp) + 15) & ~uintptr_t(15));
+    SetSmem m;
+    set_smem_layout(m, raw, sc, ls);
+    set_prologue(m, sc, ls);
+    const Cells2D &c = m.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t *scol = reinterpret_cast<int32_t *>(stg) + warp * 32 * FILL_PAD;
-    float *sval = reinterpret_cast<float *>(reinterpret_cast<int32_t *>(stg) +
-                                            (SET_T / 32) * 32 * FILL_PAD) +
-                  warp * 32 * FILL_PAD;
-    stage_blocks(sc, cs);
-    ls.stage_prefix(tp_start, rp_start);
-    __syncthreads();
-    for (int j = threadIdx.x; j < ls.nrp; j += SET_T) {
-        int r1, r2;
-        ls.rp_decode(rp_start, j, &r1, &r2);
-        rps[j] = make_short2((short)r1, (short)r2);
-    }
+    const unsigned lt = (1u << lane) - 1u;
+    const int nrp = (int)ls.nrp;
     const int nx = im.nx, nxy = im.nx * im.ny;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
         __syncthreads();
         if (threadIdx.x == 0) {
             int a, b;
-            ls.tp_decode(tp_start, T, &a, &b);
-            build_cells(sc, im, cs, a, b, c);
+            ls.tp_decode(m.tp_start, T, &a, &b);
+            build_cells(sc, im, m.cs, a, b, m.c);
         }
         __syncthreads();
         const bool xinc = c.X->kind == 0 || c.X->inc;
         const bool yinc = c.Y->kind == 0 || c.Y->inc;
-        for (int base = warp * 32; base < ls.nrp; base += SET_T) {
-            const int j = base + lane;
-            ZRay zr;
-            SetCursor s;
-            s.done = true;
-            int64_t pos = 0, end = 0;
-            if (j < ls.nrp) {
-                const short2 rr = rps[j];
-                make_zray(zr, sc, im, c, rr.x, rr.y);
-                pos = row_ptr[T * ls.nrp + j];
-                end = row_ptr[T * ls.nrp + j + 1];
-                if (!zr.empty) {
-                    int za, zb;
-                    voxel_at(zr.Z, zr.amin, za);
-                    voxel_at(zr.Z, zr.amax - 1, zb);
-                    int z0 = za < zb ? za : zb, z1 = za < zb ? zb : za;
-                    s.iz = (z0 < 0 ? 0 : z0) - 1;
-                    s.z1 = z1 > im.nz - 1 ? im.nz - 1 : z1;
-                    s.done = false;
-                    set_next_slab(c, zr, s, xinc, yinc);
-                }
+        for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
+            const int p = sorted_pos(c, cc, xinc, yinc);
+            m.s_c[p] = (short)cc;
+            m.s_ix[p] = c.ix[cc];
+            m.s_iy[p] = c.iy[cc];
+        }
+        __syncthreads();
+        for (int base = warp * 32; base < nrp; base += SET_T) {
+            const int j = base + lane, nq = nrp - base < 32 ? nrp - base : 32;
+            ZRay mine;
+            int z0m = 0, z1m = -1;
+            long long start = 0;
+            mine.empty = true;
+            if (j < nrp) {
+                make_zray(mine, sc, im, c, m.rps[j].x, m.rps[j].y);
+                zray_slabs(mine, im.nz, z0m, z1m);
+                start = row_ptr[T * nrp + j];
             }
-            bool bad = false;
-            while (__any_sync(0xffffffffu, !s.done)) {
-                int cnt = 0;
-                while (cnt < 32 && !s.done) {
-                    int iz, cell;
-                    long long L;
-                    if (!set_take(c, zr, s, xinc, yinc, iz, cell, L)) break;
-                    scol[lane * FILL_PAD + cnt] = iz * nxy + c.iy[cell] * nx + c.ix[cell];
-                    sval[lane * FILL_PAD + cnt] = units_to_f(L) * zr.to_mm;
-                    ++cnt;
-                }
-                if (pos + cnt > end) {
-                    bad = true;
-                    cnt = (int)(end - pos > 0 ? end - pos : 0);
-                }
-                __syncwarp();
-                for (int q = 0; q < 32; ++q) {
-                    const int cq = __shfl_sync(0xffffffffu, cnt, q);
-                    const int64_t pq = __shfl_sync(0xffffffffu, pos, q);
-                    if (lane < cq) {
-                        col[pq + lane] = scol[q * FILL_PAD + lane];
-                        val[pq + lane] = sval[q * FILL_PAD + lane];
+            for (int q = 0; q < nq; ++q) {
+                ZRay zr;
+                shfl_zray(zr, mine, q);
+                const int z0 = __shfl_sync(0xffffffffu, z0m, q);
+                const int z1 = __shfl_sync(0xffffffffu, z1m, q);
+                long long out = __shfl_sync(0xffffffffu, start, q);
+                if (!zr.empty) {
+                    for (int zb = z0; zb <= z1; zb += 32) {
+                        SlabCut s;
+                        s.count = 0;
+                        s.ca = 0;
+                        s.cb = -1;
+                        if (zb + lane <= z1) cut_slab(c, zr, zb + lane, s);
+                        // exclusive scan of the slab counts: output offset of each slab
+                        int inc = s.count;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                            if (lane >= o) inc += t;
+                        }
+                        const int excl = inc - s.count;
+                        const int total = __shfl_sync(0xffffffffu, inc, 31);
+                        const int nsl = z1 - zb + 1 < 32 ? z1 - zb + 1 : 32;
+                        for (int k = 0; k < nsl; ++k) {
+                            const int cnt = __shfl_sync(0xffffffffu, s.count, k);
+                            if (cnt == 0) continue;
+                            const int ca = __shfl_sync(0xffffffffu, s.ca, k);
+                            const int cb = __shfl_sync(0xffffffffu, s.cb, k);
+                            const long long zl = __shfl_sync(0xffffffffu, s.zl, k);
+                            const long long zh = __shfl_sync(0xffffffffu, s.zh, k);
+                            long long pos = out + __shfl_sync(0xffffffffu, excl, k);
+                            const int vz = (zb + k) * nxy;
+                            int lo[3], hi[3];
+                            const int ns = slab_segments(c, ca, cb, xinc, yinc, lo, hi);
+                            for (int g = 0; g < ns; ++g) {
+                                for (int p0 = lo[g]; p0 <= hi[g]; p0 += 32) {
+                                    const int p = p0 + lane;
+                                    long long L = 0;
+                                    int cc = 0;
+                                    if (p <= hi[g]) {
+                                        cc = m.s_c[p];
+                                        L = piece(c.bnd, cc, zl, zh);
+                                    }
+                                    const bool keep = p <= hi[g] && L >= zr.min_units;
+                                    const unsigned msk = __ballot_sync(0xffffffffu, keep);
+                                    if (keep) {
+                                        const long long w = pos + __popc(msk & lt);
+                                        col[w] = vz + m.s_iy[p] * nx + m.s_ix[p];
+                                        val[w] = units_to_f(L) * zr.to_mm;
+                                    }
+                                    pos += __popc(msk);
+                                }
+                            }
+                        }
+                        out += total;
                     }
                 }
-                pos += cnt;
-                __syncwarp();
+                if (lane == 0 && out != row_ptr[T * nrp + base + q + 1])
+                    atomicExch(status, PSF_EDEBUG);
             }
-            if (j < ls.nrp && (bad || pos != end)) atomicExch(status, PSF_EDEBUG);
         }
     }
-}
-
-static size_t set_smem(const Scan &sc, const LorSet &ls, bool fill) {
-    size_t b = cells_bytes() + sizeof(double) * 2 * sc.R + sizeof(int32_t) * (ls.Nt + ls.NR + 2) +
-               sizeof(short2) * ls.nrp + 32;
-    if (fill) b += sizeof(int32_t) * 2 * (SET_T / 32) * 32 * FILL_PAD;
-    return b;
 }
 
 }  // namespace psf
@@ -844,7 +809,7 @@ extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *
     cudaMemsetAsync(status, 0, sizeof(int), st);
     const int grid_max = sm_count() * 4;
     const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
-    const size_t cshm = set_smem(sc, ls, false), fshm = set_smem(sc, ls, true);
+    const size_t cshm = set_smem(sc, ls), fshm = cshm;
     int h_status = 0;
     int64_t nnz = 0;
     rc = PSF_OK;

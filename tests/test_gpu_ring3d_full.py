@@ -1,0 +1,150 @@
+"""GPU parity at the full 3D workload (44.7M LORs, 160 x 160 x 104 voxels) in
+the launch configuration bench.py times, on outputs the oracle can compute
+one by one: the whole response table, sampled class spreads, sampled chord
+rows, sampled forward-projected LORs (each gathered from the oracle's
+per-LOR spreads of up to 2 x 2401 neighbouring LORs), and the dot-product
+identity of the factored projector."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1607_06170_gb300 import inputs as I
+from parity import assert_close, compare_chord_rows
+
+pytestmark = pytest.mark.gpu
+NAME = "RING3D"
+
+
+@pytest.fixture(scope="module")
+def setup(orc):
+    from paper_1607_06170_gb300 import build, psf as P
+
+    build.build()
+    w = I.workload(NAME)
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    T, eta = P.response_build(s, t)
+    C = P.lor_set_classes(s, ls)
+    WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)
+    G = P.sysmat_rows_set(s, im, ls)
+    nv = im["nx"] * im["ny"] * im["nz"]
+    M = P.Matrix(G[0], G[1], G[2], nv).set_spread(s, ls, Wt, Wa, WC)
+    torch.cuda.synchronize()
+    To, eo = orc.table_build(s, t)
+    tp = I.transaxial_pairs(s, ls["fan_half"]).astype(np.int64)
+    rp = I.ring_pairs(s, ls["max_ring_diff"]).astype(np.int64)
+    return dict(w=w, P=P, T=T, eta=eta, C=C, WC=WC, G=G, M=M, To=To, eo=eo, tp=tp, rp=rp, nv=nv)
+
+
+def lor_of(d, rows):
+    nt = I.n_transaxial(d["w"]["scanner"])
+    nrp = len(d["rp"])
+    t = d["tp"][rows // nrp]
+    r = d["rp"][rows % nrp]
+    return np.stack([r[:, 0] * nt + t[:, 0], r[:, 1] * nt + t[:, 1]], 1).astype(np.int32)
+
+
+def test_table_full(setup):
+    d = setup
+    assert_close(d["T"].cpu().numpy(), d["To"], 1e-5, 1e-7, "table")
+    assert_close(d["eta"].cpu().numpy()[..., -1], d["eo"], 1e-6, 1e-12, "eta")
+
+
+def test_sampled_class_spreads(setup, orc):
+    d = setup
+    w = d["w"]
+    Wt, Wa = w["window"]
+    C = d["C"].cpu().numpy()
+    pick = np.random.default_rng(31).choice(len(C), 48, replace=False)
+    Wo = orc.spread(w["scanner"], w["table"], d["To"], C[pick], Wt, Wa)
+    ok = orc.tie_margin(w["scanner"], w["table"], d["To"], C[pick]) >= 1e-5
+    assert ok.sum() >= 40
+    got = d["WC"][torch.from_numpy(pick).cuda()].cpu().numpy()
+    scale = np.abs(Wo).reshape(len(pick), -1).max(1)[:, None, None]
+    assert_close(got[ok], Wo[ok], 1e-5, 1e-12 * scale[ok] + 1e-30, "class spreads")
+
+
+def test_sampled_rows(setup, orc):
+    d = setup
+    w = d["w"]
+    ptr = d["G"][0]
+    n = ptr.numel() - 1
+    rows = np.sort(np.random.default_rng(32).choice(n, 3000, replace=False))
+    L = lor_of(d, rows)
+    ref = orc.rows_geom(w["scanner"], w["image"], L)
+    pr = ptr.cpu().numpy()
+    col, val = d["G"][1], d["G"][2]
+    starts, ends = pr[rows], pr[rows + 1]
+    idx = torch.from_numpy(np.concatenate([np.arange(a, b) for a, b in zip(starts, ends)])).cuda()
+    gcol = col[idx].cpu().numpy()
+    gval = val[idx].cpu().numpy()
+    gptr = np.concatenate([[0], np.cumsum(ends - starts)])
+    compare_chord_rows((gptr, gcol, gval), ref, d["nv"])
+
+
+def _neighbours(d, m_row):
+    """Geometric LORs whose +-3 x +-3 window lands on LOR m_row, with the
+    window entries (e1, e2) of each term."""
+    w = d["w"]
+    s = w["scanner"]
+    nt, nr = I.n_transaxial(s), I.n_rings(s)
+    F, Dm = w["lors"]["fan_half"], w["lors"]["max_ring_diff"]
+    Wt, Wa = w["window"]
+    W2a = 2 * Wa + 1
+    (X, Y), = lor_of(d, np.array([m_row]))
+    tX, rX, tY, rY = X % nt, X // nt, Y % nt, Y // nt
+    terms = []
+    for e1 in range((2 * Wt + 1) * W2a):
+        dt1, da1 = e1 // W2a - Wt, e1 % W2a - Wa
+        for e2 in range((2 * Wt + 1) * W2a):
+            dt2, da2 = e2 // W2a - Wt, e2 % W2a - Wa
+            for t1, r1, t2, r2 in ((tX, rX, tY, rY), (tY, rY, tX, rX)):
+                g1t, g2t = (t1 - dt1) % nt, (t2 - dt2) % nt
+                g1r, g2r = r1 - da1, r2 - da2
+                if not (0 <= g1r < nr and 0 <= g2r < nr) or g1t >= g2t:
+                    continue
+                dd = g2t - g1t
+                if dd < nt // 2 - F or dd > nt // 2 + F or abs(g2r - g1r) > Dm:
+                    continue
+                terms.append((g1r * nt + g1t, g2r * nt + g2t, e1, e2))
+    return terms
+
+
+def test_sampled_forward_outputs(setup, orc):
+    d = setup
+    w = d["w"]
+    s, t, im = w["scanner"], w["table"], w["image"]
+    Wt, Wa = w["window"]
+    x = I.phantom_cylinder(im, 1).reshape(-1)
+    y = d["M"].forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    n = y.size
+    g = np.random.default_rng(33)
+    checked = 0
+    for m_row in g.choice(n, 12, replace=False):
+        terms = _neighbours(d, int(m_row))
+        lors = np.unique(np.array([(a, b) for a, b, _, _ in terms], dtype=np.int32), axis=0)
+        if orc.tie_margin(s, t, d["To"], lors).min() < 1e-5:
+            continue
+        Wg = orc.spread(s, t, d["To"], lors, Wt, Wa)
+        Gg = orc.rows_geom(s, im, lors)
+        p = orc.csr_fwd(Gg, x.astype(np.float64))
+        pos = {(int(a), int(b)): k for k, (a, b) in enumerate(lors)}
+        ref = sum(Wg[pos[(a, b)], e1, e2] * p[pos[(a, b)]] for a, b, e1, e2 in terms)
+        assert y[m_row] == pytest.approx(ref, rel=2e-5, abs=1e-6 * abs(ref) + 1e-12)
+        checked += 1
+        if checked == 3:
+            break
+    assert checked >= 2
+
+
+def test_adjoint_identity_full(setup):
+    d = setup
+    im = d["w"]["image"]
+    M = d["M"]
+    n = d["G"][0].numel() - 1
+    for k in range(2):
+        xk = torch.from_numpy(I.random_image(im, 900 + k).reshape(-1)).cuda()
+        yk = torch.from_numpy(I.random_lor_values(n, 910 + k)).cuda()
+        lhs = torch.dot(M.forward(xk).double(), yk.double()).item()
+        rhs = torch.dot(xk.double(), M.back(yk).double()).item()
+        assert lhs == pytest.approx(rhs, rel=1e-5)
