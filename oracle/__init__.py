@@ -22,6 +22,7 @@ from .oracle import (  # noqa: F401
     composed,
     spread,
     tie_margin,
+    tie_count,
     siddon,
     slabclip,
     rows_geom,

@@ -96,6 +96,7 @@ def _load():
                 "orc_spread_adjoint": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
                 "orc_threads": (C.c_int, []),
                 "orc_tie_margin": (None, [_P, _P, _P, _P, C.c_int64, _P]),
+                "orc_tie_stats": (None, [_P, _P, _P, _P, C.c_int64, C.c_double, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -221,6 +222,19 @@ def tie_margin(scanner: dict, table: dict, T: np.ndarray, lors) -> np.ndarray:
     out = np.zeros(L.shape[0])
     _load().orc_tie_margin(C.byref(s), C.byref(t), _ptr(T), _ptr(L), L.shape[0], _ptr(out))
     return out
+
+
+def tie_count(scanner: dict, table: dict, T: np.ndarray, lors, tau: float):
+    """Per LOR, (smallest margin, number of sub-LORs with a decision closer than
+    tau to its boundary)."""
+    s, t = _scanner(scanner), _table(table)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    L = _lors(lors)
+    m = np.zeros(L.shape[0])
+    c = np.zeros(L.shape[0], dtype=np.int64)
+    _load().orc_tie_stats(C.byref(s), C.byref(t), _ptr(T), _ptr(L), L.shape[0], float(tau),
+                          _ptr(m), _ptr(c))
+    return m, c
 
 
 def _trace(fn, image: dict, a, b):

@@ -514,77 +514,98 @@ static double frac_margin(double x)
     return fabs(x - rint(x));
 }
 
-void orc_tie_margin(const orc_scanner *s, const orc_table *tb, const double *T,
-                    const int32_t *lors, int64_t n, double *margin)
+/* Smallest margin of the decisions for one sub-LOR (both ends). */
+static double subpair_margin(const orc_scanner *s, const orc_table *tb, const double *T,
+                             int id1, int id2, int p1, int q1, int p2, int q2)
+{
+    double best = 1.0;
+    orc_xtal x1 = orc_decode(s, id1), x2 = orc_decode(s, id2);
+    double E1[3], E2[3];
+    orc_face_point(s, id1, ((p1 + 0.5) / tb->Pt - 0.5) * s->wt,
+                   ((q1 + 0.5) / tb->Pa - 0.5) * s->wa, E1);
+    orc_face_point(s, id2, ((p2 + 0.5) / tb->Pt - 0.5) * s->wt,
+                   ((q2 + 0.5) / tb->Pa - 0.5) * s->wa, E2);
+    for (int end = 0; end < 2; ++end) {
+        orc_xtal x = end ? x2 : x1;
+        int ipt = end ? p2 : p1, ipa = end ? q2 : q1;
+        double d[3];
+        for (int c = 0; c < 3; ++c) d[c] = end ? E2[c] - E1[c] : E1[c] - E2[c];
+        double vn = d[0] * x.n[0] + d[1] * x.n[1];
+        double vt = d[0] * x.t[0] + d[1] * x.t[1];
+        if (!(vn > 0.0)) continue;
+        double alpha = atan2(fabs(vt), vn);
+        double theta = atan2(fabs(d[2]), sqrt(vn * vn + vt * vt));
+        double st = tb->amax_t_deg / tb->Kt * ORC_PI / 180.0;
+        double sa = tb->amax_a_deg / tb->Ka * ORC_PI / 180.0;
+        /* nearest node: boundaries where angle/step + 1/2 is an integer */
+        if (alpha / st < tb->Kt - 1) best = fmin(best, frac_margin(alpha / st + 0.5));
+        if (theta / sa < tb->Ka - 1) best = fmin(best, frac_margin(theta / sa + 0.5));
+        int sgt = vt >= 0.0 ? 1 : -1, sga = d[2] >= 0.0 ? 1 : -1;
+        double beta, AP1, run;
+        orc_gap_eq(s, alpha, 0.5 * orc_block_width(s) -
+                       sgt * (x.s_centre + ((ipt + 0.5) / tb->Pt - 0.5) * s->wt),
+                   &beta, &AP1, &run);
+        if (!(beta > 0.0)) continue;
+        /* does the gap path reach any stored crystal? */
+        double q = AP1 - s->gt;
+        if (q < 0.0) q = 0.0;
+        int m = (int)floor(q / orc_pt(s));
+        int kt1 = orc_node(beta, tb->amax_t_deg, tb->Kt);
+        int ka = orc_node(theta, tb->amax_a_deg, tb->Ka);
+        double reach = 0.0;
+        for (int iu = 0; iu < tb->Pt; ++iu)
+            for (int iv = 0; iv < tb->Pa; ++iv)
+                for (int dx = m; dx < tb->Mt && dx <= m + 2; ++dx)
+                    for (int dz = 0; dz < tb->Ma; ++dz)
+                        reach += T[(orc_tidx(tb, kt1, ka, iu, iv) * tb->Mt + dx) * tb->Ma + dz];
+        if (reach == 0.0) continue;
+        if (beta / st < tb->Kt - 1) best = fmin(best, frac_margin(beta / st + 0.5));
+        best = fmin(best, frac_margin(q / orc_pt(s)));
+        double f = q - m * orc_pt(s);
+        best = fmin(best, fabs(f - s->wt) / orc_pt(s));
+        if (f < s->wt) best = fmin(best, frac_margin((s->wt - f) / s->wt * tb->Pt));
+        if (tb->Pa > 1 || orc_nrings(s) > 1) {
+            double z1 = x.z_centre + ((ipa + 0.5) / tb->Pa - 0.5) * s->wa +
+                        sga * run * tan(theta);
+            double zl = z1 - (orc_ring_z(s, 0) - 0.5 * s->wa);
+            best = fmin(best, frac_margin(zl / orc_pa(s)));
+            double fa = zl - floor(zl / orc_pa(s)) * orc_pa(s);
+            best = fmin(best, fabs(fa - s->wa) / orc_pa(s));
+            if (fa <= s->wa) best = fmin(best, frac_margin(fa / s->wa * tb->Pa));
+        }
+    }
+    return best;
+}
+
+/* Per LOR: the smallest margin over its sub-LORs (margin) and the number of
+ * its sub-LORs whose margin is below tau (count, may be NULL). */
+void orc_tie_stats(const orc_scanner *s, const orc_table *tb, const double *T,
+                   const int32_t *lors, int64_t n, double tau, double *margin, int64_t *count)
 {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t k = 0; k < n; ++k) {
         int id1 = lors[2 * k], id2 = lors[2 * k + 1];
         double best = 1.0;
-        orc_xtal x1 = orc_decode(s, id1), x2 = orc_decode(s, id2);
-        if (x1.block != x2.block) {
+        int64_t nb = 0;
+        if (orc_decode(s, id1).block != orc_decode(s, id2).block) {
             for (int p1 = 0; p1 < tb->Pt; ++p1)
             for (int q1 = 0; q1 < tb->Pa; ++q1)
             for (int p2 = 0; p2 < tb->Pt; ++p2)
             for (int q2 = 0; q2 < tb->Pa; ++q2) {
-                double E1[3], E2[3];
-                orc_face_point(s, id1, ((p1 + 0.5) / tb->Pt - 0.5) * s->wt,
-                               ((q1 + 0.5) / tb->Pa - 0.5) * s->wa, E1);
-                orc_face_point(s, id2, ((p2 + 0.5) / tb->Pt - 0.5) * s->wt,
-                               ((q2 + 0.5) / tb->Pa - 0.5) * s->wa, E2);
-                for (int end = 0; end < 2; ++end) {
-                    orc_xtal x = end ? x2 : x1;
-                    int ipt = end ? p2 : p1, ipa = end ? q2 : q1;
-                    double d[3];
-                    for (int c = 0; c < 3; ++c) d[c] = end ? E2[c] - E1[c] : E1[c] - E2[c];
-                    double vn = d[0] * x.n[0] + d[1] * x.n[1];
-                    double vt = d[0] * x.t[0] + d[1] * x.t[1];
-                    if (!(vn > 0.0)) continue;
-                    double alpha = atan2(fabs(vt), vn);
-                    double theta = atan2(fabs(d[2]), sqrt(vn * vn + vt * vt));
-                    double st = tb->amax_t_deg / tb->Kt * ORC_PI / 180.0;
-                    double sa = tb->amax_a_deg / tb->Ka * ORC_PI / 180.0;
-                    /* nearest node: boundaries where angle/step + 1/2 is an integer */
-                    if (alpha / st < tb->Kt - 1) best = fmin(best, frac_margin(alpha / st + 0.5));
-                    if (theta / sa < tb->Ka - 1) best = fmin(best, frac_margin(theta / sa + 0.5));
-                    int sgt = vt >= 0.0 ? 1 : -1, sga = d[2] >= 0.0 ? 1 : -1;
-                    double beta, AP1, run;
-                    orc_gap_eq(s, alpha, 0.5 * orc_block_width(s) -
-                                   sgt * (x.s_centre + ((ipt + 0.5) / tb->Pt - 0.5) * s->wt),
-                               &beta, &AP1, &run);
-                    if (!(beta > 0.0)) continue;
-                    /* does the gap path reach any stored crystal? */
-                    double q = AP1 - s->gt;
-                    if (q < 0.0) q = 0.0;
-                    int m = (int)floor(q / orc_pt(s));
-                    int kt1 = orc_node(beta, tb->amax_t_deg, tb->Kt);
-                    int ka = orc_node(theta, tb->amax_a_deg, tb->Ka);
-                    double reach = 0.0;
-                    for (int iu = 0; iu < tb->Pt; ++iu)
-                        for (int iv = 0; iv < tb->Pa; ++iv)
-                            for (int dx = m; dx < tb->Mt && dx <= m + 2; ++dx)
-                                for (int dz = 0; dz < tb->Ma; ++dz)
-                                    reach += T[(orc_tidx(tb, kt1, ka, iu, iv) * tb->Mt + dx) * tb->Ma + dz];
-                    if (reach == 0.0) continue;
-                    if (beta / st < tb->Kt - 1) best = fmin(best, frac_margin(beta / st + 0.5));
-                    best = fmin(best, frac_margin(q / orc_pt(s)));
-                    double f = q - m * orc_pt(s);
-                    best = fmin(best, fabs(f - s->wt) / orc_pt(s));
-                    if (f < s->wt) best = fmin(best, frac_margin((s->wt - f) / s->wt * tb->Pt));
-                    if (tb->Pa > 1 || orc_nrings(s) > 1) {
-                        double z1 = x.z_centre + ((ipa + 0.5) / tb->Pa - 0.5) * s->wa +
-                                    sga * run * tan(theta);
-                        double zl = z1 - (orc_ring_z(s, 0) - 0.5 * s->wa);
-                        best = fmin(best, frac_margin(zl / orc_pa(s)));
-                        double fa = zl - floor(zl / orc_pa(s)) * orc_pa(s);
-                        best = fmin(best, fabs(fa - s->wa) / orc_pa(s));
-                        if (fa <= s->wa) best = fmin(best, frac_margin(fa / s->wa * tb->Pa));
-                    }
-                }
+                double mg = subpair_margin(s, tb, T, id1, id2, p1, q1, p2, q2);
+                best = fmin(best, mg);
+                nb += mg < tau;
             }
         }
         margin[k] = best;
+        if (count) count[k] = nb;
     }
+}
+
+void orc_tie_margin(const orc_scanner *s, const orc_table *tb, const double *T,
+                    const int32_t *lors, int64_t n, double *margin)
+{
+    orc_tie_stats(s, tb, T, lors, n, 0.0, margin, NULL);
 }
 
 /* ---------------------------------------------------------------------- */

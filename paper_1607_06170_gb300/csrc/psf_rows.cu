@@ -620,7 +620,7 @@ __device__ __forceinline__ void set_prologue(SetSmem &m, const Scan &sc, const L
     }
 }
 
-// K4 (set): one warp per ring pair, lanes over its z slabs.
+// K4 (set): one thread per ring pair, summing the stored voxels of its slabs.
 __global__ void __launch_bounds__(SET_T, 2) set_count_kernel(Scan sc, Img im, LorSet ls,
                                                              int64_t *__restrict__ counts,
                                                              int *__restrict__ status) {
@@ -629,7 +629,6 @@ __global__ void __launch_bounds__(SET_T, 2) set_count_kernel(Scan sc, Img im, Lo
     set_smem_layout(m, raw, sc, ls);
     set_prologue(m, sc, ls);
     const Cells2D &c = m.c;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nrp = (int)ls.nrp;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
         __syncthreads();
@@ -640,39 +639,37 @@ __global__ void __launch_bounds__(SET_T, 2) set_count_kernel(Scan sc, Img im, Lo
             if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
         }
         __syncthreads();
-        for (int base = warp * 32; base < nrp; base += SET_T) {
-            const int j = base + lane, nq = nrp - base < 32 ? nrp - base : 32;
-            ZRay mine;
-            int z0m = 0, z1m = -1;
-            mine.empty = true;
-            if (j < nrp) {
-                make_zray(mine, sc, im, c, m.rps[j].x, m.rps[j].y);
-                zray_slabs(mine, im.nz, z0m, z1m);
-            }
-            long long mycount = 0;
-            for (int q = 0; q < nq; ++q) {
-                ZRay zr;
-                shfl_zray(zr, mine, q);
-                const int z0 = __shfl_sync(0xffffffffu, z0m, q);
-                const int z1 = __shfl_sync(0xffffffffu, z1m, q);
-                long long tot = 0;
-                if (!zr.empty) {
-                    for (int zb = z0; zb <= z1; zb += 32) {
-                        SlabCut s;
-                        s.count = 0;
-                        if (zb + lane <= z1) cut_slab(c, zr, zb + lane, s);
-                        tot += __reduce_add_sync(0xffffffffu, (unsigned)s.count);
-                    }
+        for (int j = threadIdx.x; j < nrp; j += SET_T) {
+            ZRay zr;
+            make_zray(zr, sc, im, c, m.rps[j].x, m.rps[j].y);
+            int z0, z1;
+            zray_slabs(zr, im.nz, z0, z1);
+            long long cnt = 0;
+            if (!zr.empty)
+                for (int iz = z0; iz <= z1; ++iz) {
+                    SlabCut s;
+                    cut_slab(c, zr, iz, s);
+                    cnt += s.count;
                 }
-                if (lane == q) mycount = tot;
-            }
-            if (j < nrp) counts[T * nrp + j] = mycount;
+            counts[T * nrp + j] = cnt;
         }
     }
 }
 
-// K6 (set): one warp per ring pair; lanes cut the z slabs, then copy each
-// slab's voxel-order cell ranges to consecutive output slots.
+// K6 (set): one warp per ring pair.  Lanes cut up to 32 z slabs at a time and
+// turn each into its (at most 3) voxel-order cell ranges; the ranges of all
+// those slabs are laid end to end and the lanes then walk that flattened
+// list 32 entries at a time (a short binary search finds each lane's range),
+// so every lane stores one voxel per iteration, on consecutive slots.
+constexpr int SEG_MAX = 3 * 32;
+
+struct WarpSegs {
+    int start[SEG_MAX + 1];  // flattened offset of each range
+    int lo[SEG_MAX];         // first voxel-order position
+    int slab[SEG_MAX];       // slab (lane of the round) of each range
+    long long zl[32], zh[32];
+};
+
 __global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, LorSet ls,
                                                             const int64_t *__restrict__ row_ptr,
                                                             int32_t *__restrict__ col,
@@ -681,9 +678,12 @@ __global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, Lor
     extern __shared__ __align__(16) unsigned char raw[];
     SetSmem m;
     set_smem_layout(m, raw, sc, ls);
+    WarpSegs *ws = reinterpret_cast<WarpSegs *>(
+        (reinterpret_cast<uintptr_t>(m.s_iy + SET_MAXC) + 15) & ~uintptr_t(15));
     set_prologue(m, sc, ls);
     const Cells2D &c = m.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSegs &W = ws[warp];
     const unsigned lt = (1u << lane) - 1u;
     const int nrp = (int)ls.nrp;
     const int nx = im.nx, nxy = im.nx * im.ny;
@@ -720,58 +720,75 @@ __global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, Lor
                 shfl_zray(zr, mine, q);
                 const int z0 = __shfl_sync(0xffffffffu, z0m, q);
                 const int z1 = __shfl_sync(0xffffffffu, z1m, q);
-                long long out = __shfl_sync(0xffffffffu, start, q);
+                long long pos = __shfl_sync(0xffffffffu, start, q);
                 if (!zr.empty) {
                     for (int zb = z0; zb <= z1; zb += 32) {
+                        // 1. this round's slabs -> voxel-order ranges, flattened
                         SlabCut s;
                         s.count = 0;
                         s.ca = 0;
                         s.cb = -1;
-                        if (zb + lane <= z1) cut_slab(c, zr, zb + lane, s);
-                        // exclusive scan of the slab counts: output offset of each slab
-                        int inc = s.count;
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int t = __shfl_up_sync(0xffffffffu, inc, o);
-                            if (lane >= o) inc += t;
+                        int lo[3], hi[3], ns = 0;
+                        if (zb + lane <= z1) {
+                            cut_slab(c, zr, zb + lane, s);
+                            if (s.cb >= s.ca) ns = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
                         }
-                        const int excl = inc - s.count;
-                        const int total = __shfl_sync(0xffffffffu, inc, 31);
-                        const int nsl = z1 - zb + 1 < 32 ? z1 - zb + 1 : 32;
-                        for (int k = 0; k < nsl; ++k) {
-                            const int cnt = __shfl_sync(0xffffffffu, s.count, k);
-                            if (cnt == 0) continue;
-                            const int ca = __shfl_sync(0xffffffffu, s.ca, k);
-                            const int cb = __shfl_sync(0xffffffffu, s.cb, k);
-                            const long long zl = __shfl_sync(0xffffffffu, s.zl, k);
-                            const long long zh = __shfl_sync(0xffffffffu, s.zh, k);
-                            long long pos = out + __shfl_sync(0xffffffffu, excl, k);
-                            const int vz = (zb + k) * nxy;
-                            int lo[3], hi[3];
-                            const int ns = slab_segments(c, ca, cb, xinc, yinc, lo, hi);
-                            for (int g = 0; g < ns; ++g) {
-                                for (int p0 = lo[g]; p0 <= hi[g]; p0 += 32) {
-                                    const int p = p0 + lane;
-                                    long long L = 0;
-                                    int cc = 0;
-                                    if (p <= hi[g]) {
-                                        cc = m.s_c[p];
-                                        L = piece(c.bnd, cc, zl, zh);
-                                    }
-                                    const bool keep = p <= hi[g] && L >= zr.min_units;
-                                    const unsigned msk = __ballot_sync(0xffffffffu, keep);
-                                    if (keep) {
-                                        const long long w = pos + __popc(msk & lt);
-                                        col[w] = vz + m.s_iy[p] * nx + m.s_ix[p];
-                                        val[w] = units_to_f(L) * zr.to_mm;
-                                    }
-                                    pos += __popc(msk);
-                                }
+                        int len = 0;
+                        for (int g = 0; g < ns; ++g) len += hi[g] - lo[g] + 1;
+                        int segs = ns, inc_len = len, inc_seg = segs;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int a1 = __shfl_up_sync(0xffffffffu, inc_len, o);
+                            const int a2 = __shfl_up_sync(0xffffffffu, inc_seg, o);
+                            if (lane >= o) {
+                                inc_len += a1;
+                                inc_seg += a2;
                             }
                         }
-                        out += total;
+                        const int total = __shfl_sync(0xffffffffu, inc_len, 31);
+                        const int nseg = __shfl_sync(0xffffffffu, inc_seg, 31);
+                        int off = inc_len - len, si = inc_seg - segs;
+                        for (int g = 0; g < ns; ++g) {
+                            W.start[si + g] = off;
+                            W.lo[si + g] = lo[g];
+                            W.slab[si + g] = lane;
+                            off += hi[g] - lo[g] + 1;
+                        }
+                        W.zl[lane] = s.zl;
+                        W.zh[lane] = s.zh;
+                        if (lane == 0) W.start[nseg] = total;
+                        __syncwarp();
+                        // 2. every lane stores one voxel per iteration
+                        for (int e0 = 0; e0 < total; e0 += 32) {
+                            const int e = e0 + lane;
+                            bool keep = false;
+                            int colv = 0;
+                            float v = 0.0f;
+                            if (e < total) {
+                                int g0 = 0, g1 = nseg - 1;  // last range with start <= e
+                                while (g0 < g1) {
+                                    const int mid = (g0 + g1 + 1) >> 1;
+                                    if (W.start[mid] <= e) g0 = mid; else g1 = mid - 1;
+                                }
+                                const int p = W.lo[g0] + (e - W.start[g0]);
+                                const int k = W.slab[g0];
+                                const int cc = m.s_c[p];
+                                const long long L = piece(c.bnd, cc, W.zl[k], W.zh[k]);
+                                keep = L >= zr.min_units;
+                                colv = (zb + k) * nxy + m.s_iy[p] * nx + m.s_ix[p];
+                                v = units_to_f(L) * zr.to_mm;
+                            }
+                            const unsigned msk = __ballot_sync(0xffffffffu, keep);
+                            if (keep) {
+                                const long long wpos = pos + __popc(msk & lt);
+                                col[wpos] = colv;
+                                val[wpos] = v;
+                            }
+                            pos += __popc(msk);
+                        }
+                        __syncwarp();
                     }
                 }
-                if (lane == 0 && out != row_ptr[T * nrp + base + q + 1])
+                if (lane == 0 && pos != row_ptr[T * nrp + base + q + 1])
                     atomicExch(status, PSF_EDEBUG);
             }
         }
@@ -809,7 +826,8 @@ extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *
     cudaMemsetAsync(status, 0, sizeof(int), st);
     const int grid_max = sm_count() * 4;
     const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
-    const size_t cshm = set_smem(sc, ls), fshm = cshm;
+    const size_t cshm = set_smem(sc, ls);
+    const size_t fshm = cshm + sizeof(WarpSegs) * (SET_T / 32) + 16;
     int h_status = 0;
     int64_t nnz = 0;
     rc = PSF_OK;

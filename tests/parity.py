@@ -1,9 +1,12 @@
 """Comparison helpers for the GPU-vs-oracle parity tests.
 
 Tolerances (derivations in the design doc):
-  * response table: |d| <= 1e-5 |ref| + 1e-7 (FP32 box clipping; a box the
-    ray only grazes has a first-interaction probability below 1e-7);
-  * spread: |d| <= 1e-5 |ref| + 1e-12 max|ref| per LOR;
+  * response table: |d| <= 1e-5 |ref| + TABLE_ATOL.  FP32 box bounds and
+    crossing depths carry absolute errors of a few 1e-6 mm, so a path clipped
+    through a crystal corner (tens of micrometres long) has a length error
+    near 2e-5 mm; the probability error is then below mu * 2.3e-5 = 2e-6;
+  * spread: |d| <= 1e-5 |ref| + SPREAD_ATOL_REL * max|ref| per LOR (products of
+    table values inherit the table's absolute floor);
   * chords: voxel sets bit-exact after removing voxels with chord < 1e-6 mm on
     either side, values |d| <= 1e-4 |ref| + 1e-6 mm;
   * PSF rows and projections: |d| <= 1e-4 |ref| + 1e-6 * (row scale).
@@ -11,6 +14,8 @@ Tolerances (derivations in DESIGN.md):
 import numpy as np
 
 SET_THR_MM = 1e-6
+TABLE_ATOL = 2e-6
+SPREAD_ATOL_REL = 1e-6
 
 
 def assert_close(got, ref, rtol, atol, what=""):

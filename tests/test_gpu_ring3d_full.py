@@ -9,7 +9,7 @@ import pytest
 import torch
 
 from paper_1607_06170_gb300 import inputs as I
-from parity import assert_close, compare_chord_rows
+from parity import SPREAD_ATOL_REL, TABLE_ATOL, assert_close, compare_chord_rows
 
 pytestmark = pytest.mark.gpu
 NAME = "RING3D"
@@ -46,7 +46,7 @@ def lor_of(d, rows):
 
 def test_table_full(setup):
     d = setup
-    assert_close(d["T"].cpu().numpy(), d["To"], 1e-5, 1e-7, "table")
+    assert_close(d["T"].cpu().numpy(), d["To"], 1e-5, TABLE_ATOL, "table")
     assert_close(d["eta"].cpu().numpy()[..., -1], d["eo"], 1e-6, 1e-12, "eta")
 
 
@@ -61,7 +61,7 @@ def test_sampled_class_spreads(setup, orc):
     assert ok.sum() >= 40
     got = d["WC"][torch.from_numpy(pick).cuda()].cpu().numpy()
     scale = np.abs(Wo).reshape(len(pick), -1).max(1)[:, None, None]
-    assert_close(got[ok], Wo[ok], 1e-5, 1e-12 * scale[ok] + 1e-30, "class spreads")
+    assert_close(got[ok], Wo[ok], 1e-5, SPREAD_ATOL_REL * scale[ok] + 1e-30, "class spreads")
 
 
 def test_sampled_rows(setup, orc):
@@ -111,30 +111,45 @@ def _neighbours(d, m_row):
 
 
 def test_sampled_forward_outputs(setup, orc):
+    # Each sampled output gathers up to 2 x 2401 neighbouring LORs, each with
+    # 4096 sub-LORs; somewhere among them a rounding decision sits within the
+    # FP32 working precision of a node or lattice boundary, where both sides
+    # of the boundary are correct.  The oracle counts, per neighbour, the
+    # sub-LORs with a decision within 1e-5 of a boundary, and the comparison
+    # allows each such sub-LOR 8x its average share of that neighbour's term.
     d = setup
     w = d["w"]
     s, t, im = w["scanner"], w["table"], w["image"]
     Wt, Wa = w["window"]
+    nsub = (t["n_sub_t"] * t["n_sub_a"]) ** 2
     x = I.phantom_cylinder(im, 1).reshape(-1)
     y = d["M"].forward(torch.from_numpy(x).cuda()).cpu().numpy()
-    n = y.size
     g = np.random.default_rng(33)
+    rows = [int(r) for r in g.choice(y.size, 40, replace=False)]
     checked = 0
-    for m_row in g.choice(n, 12, replace=False):
-        terms = _neighbours(d, int(m_row))
-        lors = np.unique(np.array([(a, b) for a, b, _, _ in terms], dtype=np.int32), axis=0)
-        if orc.tie_margin(s, t, d["To"], lors).min() < 1e-5:
+    for m_row in rows:
+        terms = _neighbours(d, m_row)
+        if not terms:
             continue
+        lors = np.unique(np.array([(a, b) for a, b, _, _ in terms], dtype=np.int32), axis=0)
+        _, namb = orc.tie_count(s, t, d["To"], lors, 1e-5)
         Wg = orc.spread(s, t, d["To"], lors, Wt, Wa)
         Gg = orc.rows_geom(s, im, lors)
         p = orc.csr_fwd(Gg, x.astype(np.float64))
+        if not p.any():
+            continue
         pos = {(int(a), int(b)): k for k, (a, b) in enumerate(lors)}
-        ref = sum(Wg[pos[(a, b)], e1, e2] * p[pos[(a, b)]] for a, b, e1, e2 in terms)
-        assert y[m_row] == pytest.approx(ref, rel=2e-5, abs=1e-6 * abs(ref) + 1e-12)
+        ref, amb = 0.0, 0.0
+        for a, b, e1, e2 in terms:
+            k = pos[(a, b)]
+            term = Wg[k, e1, e2] * p[k]
+            ref += term
+            amb += 8.0 * namb[k] / nsub * abs(term)
+        assert abs(y[m_row] - ref) <= 2e-5 * abs(ref) + amb + 1e-12, (m_row, y[m_row], ref, amb)
         checked += 1
         if checked == 3:
             break
-    assert checked >= 2
+    assert checked == 3
 
 
 def test_adjoint_identity_full(setup):
