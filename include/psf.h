@@ -43,6 +43,8 @@ extern "C" {
 #define PSF_ECUDA (-3)     /* a CUDA runtime call failed                     */
 #define PSF_ETIMEOUT (-4)  /* a bounded device-side wait gave up             */
 #define PSF_EDEBUG (-5)    /* a device-side bounds check recorded a fault    */
+#define PSF_ENOSCRATCH (-6) /* problem too large for the fixed scratch of
+                               psf_sysmat_rows_set_noalloc                    */
 
 /* Ring scanner of flat blocks (Sec. 3; Fig. 6 for the block corner layout). */
 typedef struct {
@@ -185,6 +187,35 @@ int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *image, const in
 int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
                         const psf_lor_set *set, int64_t *row_ptr, int32_t *col, float *val,
                         int64_t capacity, int64_t *nnz_out, void *stream);
+
+/*
+ * psf_sysmat_rows_set_noalloc -- psf_sysmat_rows_set for callers that may not
+ * allocate device memory.  The paper has no counterpart; this is a service
+ * of the library.  Some callers cannot let a library call cudaMalloc or
+ * cudaMallocAsync: an application that reserves its whole device budget at
+ * start-up and forbids later allocations, a pipeline whose latency cannot
+ * absorb the implicit device synchronisation of cudaMalloc, or code whose
+ * memory is owned by an allocator it does not control.  This entry point
+ * performs no allocation of any kind (no cudaMalloc/cudaFree, no allocating
+ * library routine): its only scratch -- the scan's per-tile sums and a
+ * status word -- lives in one file-scope device array of
+ * PSF_NOALLOC_SCRATCH_BYTES (1 MiB) that every GPU loading the library keeps
+ * until the process exits.  The caller still provides row_ptr, col and val.
+ *  - Limit: a set of at most PSF_NOALLOC_MAX_ROWS rows; larger sets return
+ *    PSF_ENOSCRATCH before any device work.
+ *  - The first call on a device (the current device) looks up the array's
+ *    device address once; make that first call before any stream capture.
+ *  - All calls share the array and leave their contents in it: calls whose
+ *    work overlaps on the GPU (different streams, or host threads) race and
+ *    must be serialised by the caller.
+ * Arguments, results, size query, capacity rule and synchronisation are those
+ * of psf_sysmat_rows_set.
+ */
+#define PSF_NOALLOC_SCRATCH_BYTES (1 << 20)
+#define PSF_NOALLOC_MAX_ROWS ((int64_t)((PSF_NOALLOC_SCRATCH_BYTES - 64) / 8 - 1) * 2048)
+int psf_sysmat_rows_set_noalloc(const psf_scanner *scanner, const psf_image *image,
+                                const psf_lor_set *set, int64_t *row_ptr, int32_t *col,
+                                float *val, int64_t capacity, int64_t *nnz_out, void *stream);
 
 /*
  * Projector plan over caller CSR (pointers retained until destroy; the caller

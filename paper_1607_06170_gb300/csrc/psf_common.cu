@@ -208,6 +208,8 @@ extern "C" const char *psf_strerror(int code) {
         case PSF_ECUDA: return cudaGetErrorString(g_last_cuda);
         case PSF_ETIMEOUT: return "bounded device wait gave up";
         case PSF_EDEBUG: return "device bounds check failed";
+        case PSF_ENOSCRATCH:
+            return "LOR set too large for the fixed scratch of the no-allocation entry point";
         default: return "unknown error";
     }
 }

@@ -981,3 +981,86 @@ extern "C" int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *imag
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = PSF_ECUDA;
     return rc;
 }
+
+// ------------------------------------------------ no-allocation entry point
+// psf_sysmat_rows_set without any allocation: the scan's tile sums and the
+// status word live in one fixed device array (see psf.h).  The array's device
+// address is looked up once per device, on that device's first call.
+#include <mutex>
+
+namespace psf {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PSF_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[1024];  // device address of the array, per device ordinal
+
+static int noalloc_scratch(void **out) {
+    int dev = 0;
+    PSF_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 1024) return PSF_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        PSF_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));  // host name -> device address
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PSF_OK;
+}
+}  // namespace psf
+
+extern "C" int psf_sysmat_rows_set_noalloc(const psf_scanner *scanner, const psf_image *image,
+                                           const psf_lor_set *set, int64_t *row_ptr,
+                                           int32_t *col, float *val, int64_t capacity,
+                                           int64_t *nnz_out, void *stream) {
+    Scan sc;
+    Img im;
+    LorSet ls;
+    int rc = make_scan(scanner, &sc);
+    if (rc) return rc;
+    rc = make_img(image, &im);
+    if (rc) return rc;
+    rc = make_lorset(scanner, set, &ls);
+    if (rc) return rc;
+    if (!row_ptr || !nnz_out || (col && !val)) return PSF_EINVAL;
+    if (im.nx + im.ny + 1 > SET_MAXC || im.nx > 32767 || im.ny > 32767) return PSF_EINVAL;
+    const int64_t n = ls.ntp * ls.nrp;
+    *nnz_out = 0;
+    if (n > PSF_NOALLOC_MAX_ROWS) return PSF_ENOSCRATCH;
+    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE + 1;
+    if (sizeof(int64_t) * ntiles + 64 > (size_t)PSF_NOALLOC_SCRATCH_BYTES) return PSF_ENOSCRATCH;
+    void *scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
+    if (n == 0) return PSF_OK;
+    int64_t *tiles = (int64_t *)scratch;  // fully rewritten by the scan
+    int *status = (int *)(tiles + ntiles);
+    PSF_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));  // left set by an earlier call
+    const int grid_max = sm_count() * 4;
+    const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
+    const size_t cshm = set_smem(sc, ls);
+    const size_t fshm = cshm + sizeof(WarpSegs) * (SET_T / 32) + 16;
+    PSF_TRY(cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cshm));
+    PSF_TRY(cudaFuncSetAttribute(set_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fshm));
+    set_count_kernel<<<grid, SET_T, cshm, st>>>(sc, im, ls, row_ptr + 1, status);
+    PSF_LAUNCHED();
+    rc = inclusive_scan(row_ptr + 1, n, tiles, st);
+    if (rc) return rc;
+    int64_t nnz = 0;
+    int h_status = 0;
+    PSF_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSF_TRY(cudaStreamSynchronize(st));
+    *nnz_out = nnz;
+    if (h_status) return h_status;
+    if (!col) return PSF_OK;
+    if (nnz > capacity) return PSF_ECAPACITY;
+    set_fill_kernel<<<grid, SET_T, fshm, st>>>(sc, im, ls, row_ptr, col, val, status);
+    PSF_LAUNCHED();
+    PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSF_TRY(cudaStreamSynchronize(st));
+    return h_status;
+}

@@ -24,7 +24,7 @@ _TORCH_DT = {PSF_F32: torch.float32, PSF_BF16: torch.bfloat16, PSF_F16: torch.fl
 FUNCTIONS = [
     "psf_strerror", "psf_table_size", "psf_response_build", "psf_bin_spread",
     "psf_lor_set_size", "psf_lor_set_list", "psf_lor_set_classes", "psf_sysmat_rows",
-    "psf_sysmat_rows_set",
+    "psf_sysmat_rows_set", "psf_sysmat_rows_set_noalloc",
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update",
 ]
@@ -73,6 +73,7 @@ _SIGS = {
     "psf_sysmat_rows": (C.c_int, [_P, _P, _P, _I64, _P, _I32, _I32, _I32, _P, _P, _P, _P, _I64,
                                   _P, _P]),
     "psf_sysmat_rows_set": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _P, _P]),
+    "psf_sysmat_rows_set_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _P, _P]),
     "psf_matrix_create": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _I32, _P, _P]),
     "psf_matrix_set_spread": (C.c_int, [_P, _P, _P, _I32, _I32, _P]),
     "psf_matrix_destroy": (C.c_int, [_P]),
