@@ -197,11 +197,13 @@ int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
  * absorb the implicit device synchronisation of cudaMalloc, or code whose
  * memory is owned by an allocator it does not control.  This entry point
  * performs no allocation of any kind (no cudaMalloc/cudaFree, no allocating
- * library routine): its only scratch -- the scan's per-tile sums and a
- * status word -- lives in one file-scope device array of
+ * library routine): its only scratch -- the scan's per-tile sums (8 bytes
+ * per 2048 rows), a status word and the ring-pair z-axis table (80 bytes per
+ * ring pair) -- lives in one file-scope device array of
  * PSF_NOALLOC_SCRATCH_BYTES (1 MiB) that every GPU loading the library keeps
  * until the process exits.  The caller still provides row_ptr, col and val.
- *  - Limit: a set of at most PSF_NOALLOC_MAX_ROWS rows; larger sets return
+ *  - Limit: a set of at most PSF_NOALLOC_MAX_ROWS rows whose tile sums and
+ *    ring-pair table fit in the array together; other sets return
  *    PSF_ENOSCRATCH before any device work.
  *  - The first call on a device (the current device) looks up the array's
  *    device address once; make that first call before any stream capture.

@@ -426,8 +426,8 @@ struct Cells2D {
 __host__ __device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsigned char *p) {
     c.bnd = reinterpret_cast<long long *>(p);
     p += sizeof(long long) * (SET_MAXC + 1);
-    c.clip = reinterpret_cast<long long *>(p);
-    p += sizeof(long long) * 2;
+    c.clip = reinterpret_cast<long long *>(p);  // amin, amax, short-cell threshold, -
+    p += sizeof(long long) * 4;
     c.xy = reinterpret_cast<double *>(p);
     p += sizeof(double) * 4;
     c.X = reinterpret_cast<Axis *>(p);
@@ -450,7 +450,7 @@ __host__ __device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsi
 }
 
 static size_t cells_bytes() {
-    return sizeof(long long) * (SET_MAXC + 3) + sizeof(double) * 4 + 2 * sizeof(Axis) +
+    return sizeof(long long) * (SET_MAXC + 5) + sizeof(double) * 4 + 2 * sizeof(Axis) +
            sizeof(short) * (4 * SET_MAXC + 1 + SET_MAXF) + sizeof(int) * 8 + 32;
 }
 
@@ -479,6 +479,7 @@ __host__ __device__ void build_cells(const Scan &sc, const Img &im, const double
     }
     c.clip[0] = amin;
     c.clip[1] = amax;
+    c.clip[2] = 0;
     int n = 0, nruns = 0, nflag = 0;
     bool ok = true;
     if (!empty && amax > amin) {
@@ -491,6 +492,7 @@ __host__ __device__ void build_cells(const Scan &sc, const Img &im, const double
         const float len2 = sqrtf(lx * lx + ly * ly);
         // the 3D threshold is at most the transaxial one (3D segments are longer)
         const long long thr2 = 2 * (long long)ceilf((float)MIN_CHORD_MM / len2 * (float)FX);
+        c.clip[2] = thr2;
         for (int it = 0; it < im.nx + im.ny + 4 && n < SET_MAXC; ++it) {
             long long lo, ex_, ey_;
             if (X.kind == 0) ex_ = FX_BIG; else slab(X, cx, lo, ex_);
@@ -541,36 +543,6 @@ __host__ __device__ __forceinline__ int last_cell_before(const long long *bnd, i
     return lo;
 }
 
-// Per ring pair: the z axis, clip and chord scale of the 3D segment.
-struct ZRay {
-    Axis Z;
-    long long amin, amax, min_units;
-    float to_mm;
-    bool empty;
-};
-
-__host__ __device__ __forceinline__ void make_zray(ZRay &r, const Scan &sc, const Img &im,
-                                          const Cells2D &c, int ra, int rb) {
-    const double za = sc.z064 + ra * sc.pa64, zb = sc.z064 + rb * sc.pa64;
-    r.empty = c.hdr[0] == 0;
-    make_axis(r.Z, (za - im.oz) * im.idz, (zb - im.oz) * im.idz, im.nz, r.empty);
-    long long amin = c.clip[0], amax = c.clip[1];
-    if (r.Z.kind != 0) {
-        long long p = plane_alpha(r.Z, 0), q = plane_alpha(r.Z, im.nz);
-        long long lo = p < q ? p : q, hi = p < q ? q : p;
-        amin = lo > amin ? lo : amin;
-        amax = hi < amax ? hi : amax;
-    }
-    r.amin = amin;
-    r.amax = amax;
-    if (amax <= amin) r.empty = true;
-    const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
-    const float lz = (float)(zb - za);
-    const float len = sqrtf(lx * lx + ly * ly + lz * lz);
-    r.min_units = (long long)ceilf((float)MIN_CHORD_MM / len * (float)FX);
-    r.to_mm = len * (float)(1.0 / FX);
-}
-
 __host__ __device__ __forceinline__ long long piece(const long long *bnd, int cc, long long zl,
                                            long long zh) {
     long long lo = bnd[cc] > zl ? bnd[cc] : zl, hi = bnd[cc + 1] < zh ? bnd[cc + 1] : zh;
@@ -584,93 +556,140 @@ __host__ __device__ __forceinline__ long long piece(const long long *bnd, int cc
 namespace psf {
 
 // Per CTA: the cells of its current transaxial pair, block trig, set prefix
-// tables and the ring pair of every row offset.
+// tables, the cells again in voxel order (their packed x/y voxel, chord and
+// chord as a float), and each warp's work area.
 struct SetSmem {
     Cells2D c;
     double *cs;
+    long long *s_len;   // [SET_MAXC] chord (units) of the cell at each voxel-order position
+    int *s_xy;          // [SET_MAXC] iy * nx + ix, sign bit set for short cells
+    float *s_lenf;      // [SET_MAXC] chord as a float (rounded once)
     int32_t *tp_start, *rp_start;
-    short2 *rps;
-    short *s_c, *s_ix, *s_iy;  // voxel-order cell list (fill only)
+    int *next;          // next ring-pair group of the current transaxial pair
+    SetWarp *w;         // [SET_T / 32]
 };
 
 __device__ __forceinline__ void set_smem_layout(SetSmem &m, unsigned char *raw, const Scan &sc,
                                                 const LorSet &ls) {
     m.cs = reinterpret_cast<double *>(cells_layout(m.c, raw));
-    m.tp_start = reinterpret_cast<int32_t *>(m.cs + 2 * sc.R);
+    m.s_len = reinterpret_cast<long long *>(m.cs + 2 * sc.R);
+    m.s_xy = reinterpret_cast<int *>(m.s_len + SET_MAXC);
+    m.s_lenf = reinterpret_cast<float *>(m.s_xy + SET_MAXC);
+    m.tp_start = reinterpret_cast<int32_t *>(m.s_lenf + SET_MAXC);
     m.rp_start = m.tp_start + ls.Nt + 1;
-    m.rps = reinterpret_cast<short2 *>(m.rp_start + ls.NR + 1);
-    m.s_c = reinterpret_cast<short *>(m.rps + ls.nrp);
-    m.s_ix = m.s_c + SET_MAXC;
-    m.s_iy = m.s_ix + SET_MAXC;
+    m.next = m.rp_start + ls.NR + 1;
+    m.w = reinterpret_cast<SetWarp *>(
+        (reinterpret_cast<uintptr_t>(m.next + 4) + 15) & ~uintptr_t(15));
 }
 
 static size_t set_smem(const Scan &sc, const LorSet &ls) {
-    return cells_bytes() + sizeof(double) * 2 * sc.R + sizeof(int32_t) * (ls.Nt + ls.NR + 2) +
-           sizeof(short2) * ls.nrp + sizeof(short) * 3 * SET_MAXC + 64;
+    return cells_bytes() + sizeof(double) * 2 * sc.R +
+           (sizeof(long long) + sizeof(int) + sizeof(float)) * SET_MAXC +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + sizeof(int) * 4 + 16 +
+           sizeof(SetWarp) * (SET_T / 32) + 64;
 }
 
-__device__ __forceinline__ void set_prologue(SetSmem &m, const Scan &sc, const LorSet &ls) {
-    stage_blocks(sc, m.cs);
-    ls.stage_prefix(m.tp_start, m.rp_start);
+// Ring-pair table of a set: entry j is the z axis of ring pair j's segments.
+__global__ void __launch_bounds__(256) zaxis_kernel(Scan sc, Img im, LorSet ls,
+                                                    ZAx *__restrict__ zt) {
+    extern __shared__ int32_t zpre[];  // [Nt + 1 + NR + 1]
+    ls.stage_prefix(zpre, zpre + ls.Nt + 1);
     __syncthreads();
-    for (int j = threadIdx.x; j < ls.nrp; j += SET_T) {
-        int r1, r2;
-        ls.rp_decode(m.rp_start, j, &r1, &r2);
-        m.rps[j] = make_short2((short)r1, (short)r2);
-    }
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ls.nrp) return;
+    int ra, rb;
+    ls.rp_decode(zpre + ls.Nt + 1, j, &ra, &rb);
+    zaxis_of(sc, im, ra, rb, zt[j]);
 }
 
-// K4 (set): one thread per ring pair, summing the stored voxels of its slabs.
+// Per transaxial pair: one thread builds the 2D cells, then every thread
+// helps write the voxel-order copies.  Returns after the CTA barrier.
+__device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const Img &im,
+                                               const LorSet &ls, int64_t T, int *status) {
+    __syncthreads();  // the previous pair's readers are done
+    const Cells2D &c = m.c;
+    if (threadIdx.x == 0) {
+        int a, b;
+        ls.tp_decode(m.tp_start, T, &a, &b);
+        build_cells(sc, im, m.cs, a, b, m.c);
+        if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
+        *m.next = 0;
+    }
+    __syncthreads();
+    const bool xinc = c.X->kind == 0 || c.X->inc;
+    const bool yinc = c.Y->kind == 0 || c.Y->inc;
+    const long long thr2 = c.clip[2];
+    for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
+        const int p = sorted_pos(c, cc, xinc, yinc);
+        const long long L = c.bnd[cc + 1] - c.bnd[cc];
+        m.s_len[p] = L;
+        m.s_lenf[p] = units_to_f(L);
+        m.s_xy[p] = ((int)c.iy[cc] * im.nx + c.ix[cc]) | (L < thr2 ? (int)0x80000000 : 0);
+    }
+    __syncthreads();
+}
+
+// Next group of 32 ring pairs for this warp (groups handed out in order).
+__device__ __forceinline__ int set_next_group(int *next) {
+    int g = 0;
+    if ((threadIdx.x & 31) == 0) g = atomicAdd(next, 1);
+    return __shfl_sync(0xffffffffu, g, 0);
+}
+
+// K4 (set): a warp takes 32 ring pairs of the CTA's transaxial pair; its
+// lanes cut the z slabs of all of them, 32 slabs at a time, and add each
+// slab's stored voxels to its ring pair's count.
 __global__ void __launch_bounds__(SET_T, 2) set_count_kernel(Scan sc, Img im, LorSet ls,
+                                                             const ZAx *__restrict__ zt,
                                                              int64_t *__restrict__ counts,
                                                              int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char raw[];
     SetSmem m;
     set_smem_layout(m, raw, sc, ls);
-    set_prologue(m, sc, ls);
+    stage_blocks(sc, m.cs);
+    ls.stage_prefix(m.tp_start, m.rp_start);
     const Cells2D &c = m.c;
-    const int nrp = (int)ls.nrp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SetWarp &W = m.w[warp];
+    const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int a, b;
-            ls.tp_decode(m.tp_start, T, &a, &b);
-            build_cells(sc, im, m.cs, a, b, m.c);
-            if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < nrp; j += SET_T) {
-            ZRay zr;
-            make_zray(zr, sc, im, c, m.rps[j].x, m.rps[j].y);
-            int z0, z1;
-            zray_slabs(zr, im.nz, z0, z1);
-            long long cnt = 0;
-            if (!zr.empty)
-                for (int iz = z0; iz <= z1; ++iz) {
-                    SlabCut s;
-                    cut_slab(c, zr, iz, s);
-                    cnt += s.count;
+        set_pair_cells(m, sc, im, ls, T, status);
+        const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
+        for (int g = set_next_group(m.next); g < ngroups; g = set_next_group(m.next)) {
+            const int j = g * 32 + lane;
+            RingPair rp;
+            rp_setup(c, zt, j, nrp, im.nz, lx, ly, rp);
+            W.cnt[lane] = 0;
+            int incl = rp.nsl;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            for (int base = 0; base < total; base += 32) {
+                SlabOf so;
+                slab_of(rp, incl, base + lane, total, so);
+                if (so.q >= 0) {
+                    const SlabCells s = cut_cells(c, so.zl, so.zh, so.minu);
+                    if (s.count) atomicAdd(&W.cnt[so.q], s.count);
                 }
-            counts[T * nrp + j] = cnt;
+            }
+            __syncwarp();
+            if (j < nrp) counts[T * nrp + j] = W.cnt[lane];
+            __syncwarp();
         }
     }
 }
 
-// K6 (set): one warp per ring pair.  Lanes cut up to 32 z slabs at a time and
-// turn each into its (at most 3) voxel-order cell ranges; the ranges of all
-// those slabs are laid end to end and the lanes then walk that flattened
-// list 32 entries at a time (a short binary search finds each lane's range),
-// so every lane stores one voxel per iteration, on consecutive slots.
-constexpr int SEG_MAX = 3 * 32;
-
-struct WarpSegs {
-    int start[SEG_MAX + 1];  // flattened offset of each range
-    int lo[SEG_MAX];         // first voxel-order position
-    int slab[SEG_MAX];       // slab (lane of the round) of each range
-    long long zl[32], zh[32];
-};
-
+// K6 (set): the same walk; each round's slabs become at most three
+// voxel-order ranges each, laid end to end, and the lanes then store that
+// flattened list 32 entries at a time on consecutive slots (a slab's
+// interior cells carry their full 2D chord, only its first and last ray-order
+// cells are cut by the z planes).  The 32 rows of a group are consecutive in
+// the CSR, so the whole group is one contiguous output span.
 __global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, LorSet ls,
+                                                            const ZAx *__restrict__ zt,
                                                             const int64_t *__restrict__ row_ptr,
                                                             int32_t *__restrict__ col,
                                                             float *__restrict__ val,
@@ -678,119 +697,119 @@ __global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, Lor
     extern __shared__ __align__(16) unsigned char raw[];
     SetSmem m;
     set_smem_layout(m, raw, sc, ls);
-    WarpSegs *ws = reinterpret_cast<WarpSegs *>(
-        (reinterpret_cast<uintptr_t>(m.s_iy + SET_MAXC) + 15) & ~uintptr_t(15));
-    set_prologue(m, sc, ls);
+    stage_blocks(sc, m.cs);
+    ls.stage_prefix(m.tp_start, m.rp_start);
     const Cells2D &c = m.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSegs &W = ws[warp];
-    const unsigned lt = (1u << lane) - 1u;
-    const int nrp = (int)ls.nrp;
-    const int nx = im.nx, nxy = im.nx * im.ny;
+    SetWarp &W = m.w[warp];
+    const unsigned lt = (1u << lane) - 1u, le = (2u << lane) - 1u;
+    const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
+    const int nxy = im.nx * im.ny;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int a, b;
-            ls.tp_decode(m.tp_start, T, &a, &b);
-            build_cells(sc, im, m.cs, a, b, m.c);
-        }
-        __syncthreads();
+        set_pair_cells(m, sc, im, ls, T, status);
+        const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
         const bool xinc = c.X->kind == 0 || c.X->inc;
         const bool yinc = c.Y->kind == 0 || c.Y->inc;
-        for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
-            const int p = sorted_pos(c, cc, xinc, yinc);
-            m.s_c[p] = (short)cc;
-            m.s_ix[p] = c.ix[cc];
-            m.s_iy[p] = c.iy[cc];
-        }
-        __syncthreads();
-        for (int base = warp * 32; base < nrp; base += SET_T) {
-            const int j = base + lane, nq = nrp - base < 32 ? nrp - base : 32;
-            ZRay mine;
-            int z0m = 0, z1m = -1;
-            long long start = 0;
-            mine.empty = true;
-            if (j < nrp) {
-                make_zray(mine, sc, im, c, m.rps[j].x, m.rps[j].y);
-                zray_slabs(mine, im.nz, z0m, z1m);
-                start = row_ptr[T * nrp + j];
+        for (int g = set_next_group(m.next); g < ngroups; g = set_next_group(m.next)) {
+            const int j0 = g * 32, j = j0 + lane;
+            const int nq = nrp - j0 < 32 ? nrp - j0 : 32;
+            RingPair rp;
+            rp_setup(c, zt, j, nrp, im.nz, lx, ly, rp);
+            int incl = rp.nsl;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
             }
-            for (int q = 0; q < nq; ++q) {
-                ZRay zr;
-                shfl_zray(zr, mine, q);
-                const int z0 = __shfl_sync(0xffffffffu, z0m, q);
-                const int z1 = __shfl_sync(0xffffffffu, z1m, q);
-                long long pos = __shfl_sync(0xffffffffu, start, q);
-                if (!zr.empty) {
-                    for (int zb = z0; zb <= z1; zb += 32) {
-                        // 1. this round's slabs -> voxel-order ranges, flattened
-                        SlabCut s;
-                        s.count = 0;
-                        s.ca = 0;
-                        s.cb = -1;
-                        int lo[3], hi[3], ns = 0;
-                        if (zb + lane <= z1) {
-                            cut_slab(c, zr, zb + lane, s);
-                            if (s.cb >= s.ca) ns = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
-                        }
-                        int len = 0;
-                        for (int g = 0; g < ns; ++g) len += hi[g] - lo[g] + 1;
-                        int segs = ns, inc_len = len, inc_seg = segs;
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int a1 = __shfl_up_sync(0xffffffffu, inc_len, o);
-                            const int a2 = __shfl_up_sync(0xffffffffu, inc_seg, o);
-                            if (lane >= o) {
-                                inc_len += a1;
-                                inc_seg += a2;
-                            }
-                        }
-                        const int total = __shfl_sync(0xffffffffu, inc_len, 31);
-                        const int nseg = __shfl_sync(0xffffffffu, inc_seg, 31);
-                        int off = inc_len - len, si = inc_seg - segs;
-                        for (int g = 0; g < ns; ++g) {
-                            W.start[si + g] = off;
-                            W.lo[si + g] = lo[g];
-                            W.slab[si + g] = lane;
-                            off += hi[g] - lo[g] + 1;
-                        }
-                        W.zl[lane] = s.zl;
-                        W.zh[lane] = s.zh;
-                        if (lane == 0) W.start[nseg] = total;
-                        __syncwarp();
-                        // 2. every lane stores one voxel per iteration
-                        for (int e0 = 0; e0 < total; e0 += 32) {
-                            const int e = e0 + lane;
-                            bool keep = false;
-                            int colv = 0;
-                            float v = 0.0f;
-                            if (e < total) {
-                                int g0 = 0, g1 = nseg - 1;  // last range with start <= e
-                                while (g0 < g1) {
-                                    const int mid = (g0 + g1 + 1) >> 1;
-                                    if (W.start[mid] <= e) g0 = mid; else g1 = mid - 1;
-                                }
-                                const int p = W.lo[g0] + (e - W.start[g0]);
-                                const int k = W.slab[g0];
-                                const int cc = m.s_c[p];
-                                const long long L = piece(c.bnd, cc, W.zl[k], W.zh[k]);
-                                keep = L >= zr.min_units;
-                                colv = (zb + k) * nxy + m.s_iy[p] * nx + m.s_ix[p];
-                                v = units_to_f(L) * zr.to_mm;
-                            }
-                            const unsigned msk = __ballot_sync(0xffffffffu, keep);
-                            if (keep) {
-                                const long long wpos = pos + __popc(msk & lt);
-                                col[wpos] = colv;
-                                val[wpos] = v;
-                            }
-                            pos += __popc(msk);
-                        }
-                        __syncwarp();
+            const int total_slabs = __shfl_sync(0xffffffffu, incl, 31);
+            long long pos = row_ptr[T * nrp + j0];
+            const long long pend = row_ptr[T * nrp + j0 + nq];  // the group's span ends here
+            for (int base = 0; base < total_slabs; base += 32) {
+                // 1. this round's slabs -> voxel-order ranges, flattened
+                SlabOf so;
+                slab_of(rp, incl, base + lane, total_slabs, so);
+                int lo[3], hi[3], ns = 0;
+                if (so.q >= 0) {
+                    const SlabCells s = cut_cells(c, so.zl, so.zh, so.minu);
+                    if (s.cb >= s.ca) {
+                        ns = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
+                        const long long La = piece(c.bnd, s.ca, so.zl, so.zh);
+                        const long long Lb = piece(c.bnd, s.cb, so.zl, so.zh);
+                        W.sa[lane] = make_int4(so.iz * nxy, sorted_pos(c, s.ca, xinc, yinc),
+                                               sorted_pos(c, s.cb, xinc, yinc),
+                                               (La >= so.minu) | ((Lb >= so.minu) << 1));
+                        W.sf[lane] = make_float4(units_to_f(La) * so.to_mm,
+                                                 units_to_f(Lb) * so.to_mm, so.to_mm, 0.0f);
+                        W.sm[lane] = so.minu;
                     }
                 }
-                if (lane == 0 && pos != row_ptr[T * nrp + base + q + 1])
-                    atomicExch(status, PSF_EDEBUG);
+                int len = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (k < ns) len += hi[k] - lo[k] + 1;
+                int inc_len = len, inc_seg = ns;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int a1 = __shfl_up_sync(0xffffffffu, inc_len, o);
+                    const int a2 = __shfl_up_sync(0xffffffffu, inc_seg, o);
+                    if (lane >= o) {
+                        inc_len += a1;
+                        inc_seg += a2;
+                    }
+                }
+                const int total = __shfl_sync(0xffffffffu, inc_len, 31);
+                const int nseg = __shfl_sync(0xffffffffu, inc_seg, 31);
+                int off = inc_len - len;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (k < ns) {
+                        W.rs[inc_seg - ns + k] = make_int2(off, lo[k] | (lane << 16));
+                        off += hi[k] - lo[k] + 1;
+                    }
+                __syncwarp();
+                // 2. every lane stores one voxel per step; the ranges starting
+                // inside each 32-entry chunk are found with one OR-reduction
+                int gbase = -1;  // range holding the entry before the chunk
+                for (int e0 = 0; e0 < total; e0 += 32) {
+                    const int gq = gbase + 1 + lane;
+                    unsigned bit = 0u;
+                    if (gq < nseg) {
+                        const int st = W.rs[gq].x - e0;
+                        if (st < 32) bit = 1u << st;
+                    }
+                    const unsigned B = __reduce_or_sync(0xffffffffu, bit);
+                    const int e = e0 + lane;
+                    bool keep = false;
+                    int colv = 0;
+                    float v = 0.0f;
+                    if (e < total) {
+                        const int gi = gbase + __popc(B & le);
+                        const int2 R = W.rs[gi];
+                        const int p = (R.y & 0xffff) + (e - R.x), k = R.y >> 16;
+                        const int4 A = W.sa[k];
+                        const int xy = m.s_xy[p];
+                        if (p == A.y) {
+                            v = W.sf[k].x;
+                            keep = A.w & 1;
+                        } else if (p == A.z) {
+                            v = W.sf[k].y;
+                            keep = (A.w >> 1) & 1;
+                        } else {
+                            v = m.s_lenf[p] * W.sf[k].z;
+                            keep = xy >= 0 || m.s_len[p] >= W.sm[k];
+                        }
+                        colv = A.x + (xy & 0x7fffffff);
+                    }
+                    gbase += __popc(B);
+                    const unsigned msk = __ballot_sync(0xffffffffu, keep);
+                    const long long wpos = pos + __popc(msk & lt);
+                    if (keep && wpos < pend) {
+                        col[wpos] = colv;
+                        val[wpos] = v;
+                    }
+                    pos += __popc(msk);
+                }
+                __syncwarp();
             }
+            if (lane == 0 && pos != pend) atomicExch(status, PSF_EDEBUG);
         }
     }
 }
@@ -799,12 +818,12 @@ __global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, Lor
 
 using namespace psf;
 
-extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
-                                   const psf_lor_set *set, int64_t *row_ptr, int32_t *col,
-                                   float *val, int64_t capacity, int64_t *nnz_out, void *stream) {
-    Scan sc;
-    Img im;
-    LorSet ls;
+namespace psf {
+
+// Validated arguments of the set row generator.
+static int set_args(const psf_scanner *scanner, const psf_image *image, const psf_lor_set *set,
+                    const int64_t *row_ptr, const int32_t *col, const float *val,
+                    const int64_t *nnz_out, Scan &sc, Img &im, LorSet &ls) {
     int rc = make_scan(scanner, &sc);
     if (rc) return rc;
     rc = make_img(image, &im);
@@ -813,58 +832,77 @@ extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *
     if (rc) return rc;
     if (!row_ptr || !nnz_out || (col && !val)) return PSF_EINVAL;
     if (im.nx + im.ny + 1 > SET_MAXC || im.nx > 32767 || im.ny > 32767) return PSF_EINVAL;
-    cudaStream_t st = as_stream(stream);
+    return PSF_OK;
+}
+
+// Scratch of the set row generator: scan tile sums, a status word and the
+// ring-pair z-axis table.
+static size_t set_scratch_bytes(const LorSet &ls, int64_t *ntiles_out) {
     const int64_t n = ls.ntp * ls.nrp;
+    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE + 1;
+    *ntiles_out = ntiles;
+    return sizeof(int64_t) * ntiles + 64 + sizeof(ZAx) * ls.nrp;
+}
+
+// Ring-pair table, count, scan, (size check,) fill.  row_ptr[0] is already 0.
+static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t *row_ptr,
+                        int32_t *col, float *val, int64_t capacity, int64_t *nnz_out,
+                        unsigned char *scratch, int64_t ntiles, cudaStream_t st) {
+    const int64_t n = ls.ntp * ls.nrp;
+    int64_t *tiles = reinterpret_cast<int64_t *>(scratch);
+    int *status = reinterpret_cast<int *>(tiles + ntiles);
+    ZAx *zt = reinterpret_cast<ZAx *>(reinterpret_cast<unsigned char *>(status) + 64);
+    PSF_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+    const size_t zshm = sizeof(int32_t) * (ls.Nt + ls.NR + 2);
+    zaxis_kernel<<<(int)((ls.nrp + 255) / 256), 256, zshm, st>>>(sc, im, ls, zt);
+    PSF_LAUNCHED();
+    const int grid_max = sm_count() * 2;
+    const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
+    const size_t shm = set_smem(sc, ls);
+    PSF_TRY(cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
+    PSF_TRY(cudaFuncSetAttribute(set_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
+    set_count_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr + 1, status);
+    PSF_LAUNCHED();
+    int rc = inclusive_scan(row_ptr + 1, n, tiles, st);
+    if (rc) return rc;
+    int64_t nnz = 0;
+    int h_status = 0;
+    PSF_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSF_TRY(cudaStreamSynchronize(st));
+    *nnz_out = nnz;
+    if (h_status) return h_status;
+    if (!col) return PSF_OK;
+    if (nnz > capacity) return PSF_ECAPACITY;
+    set_fill_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr, col, val, status);
+    PSF_LAUNCHED();
+    PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSF_TRY(cudaStreamSynchronize(st));
+    return h_status;
+}
+
+}  // namespace psf
+
+extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
+                                   const psf_lor_set *set, int64_t *row_ptr, int32_t *col,
+                                   float *val, int64_t capacity, int64_t *nnz_out, void *stream) {
+    Scan sc;
+    Img im;
+    LorSet ls;
+    int rc = set_args(scanner, image, set, row_ptr, col, val, nnz_out, sc, im, ls);
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
     *nnz_out = 0;
     PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
-    if (n == 0) return PSF_OK;
-    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE + 1;
+    if (ls.ntp * ls.nrp == 0) return PSF_OK;
+    int64_t ntiles = 0;
+    const size_t bytes = set_scratch_bytes(ls, &ntiles);
     void *scratch = nullptr;
-    PSF_TRY(cudaMallocAsync(&scratch, sizeof(int64_t) * ntiles + 256, st));
-    int64_t *tiles = (int64_t *)scratch;
-    int *status = (int *)(tiles + ntiles);
-    cudaMemsetAsync(status, 0, sizeof(int), st);
-    const int grid_max = sm_count() * 4;
-    const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
-    const size_t cshm = set_smem(sc, ls);
-    const size_t fshm = cshm + sizeof(WarpSegs) * (SET_T / 32) + 16;
-    int h_status = 0;
-    int64_t nnz = 0;
-    rc = PSF_OK;
-    if (cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cshm) != cudaSuccess ||
-        cudaFuncSetAttribute(set_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fshm) != cudaSuccess)
-        rc = PSF_ECUDA;
-    if (!rc) {
-        set_count_kernel<<<grid, SET_T, cshm, st>>>(sc, im, ls, row_ptr + 1, status);
-        if (cudaGetLastError() != cudaSuccess) rc = PSF_ECUDA;
-    }
-    if (!rc) rc = inclusive_scan(row_ptr + 1, n, tiles, st);
-    if (!rc && (cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
-                    cudaSuccess ||
-                cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess))
-        rc = PSF_ECUDA;
-    if (!rc) {
-        *nnz_out = nnz;
-        if (h_status) rc = h_status;
-    }
-    if (!rc && col) {
-        if (nnz > capacity) {
-            rc = PSF_ECAPACITY;
-        } else {
-            set_fill_kernel<<<grid, SET_T, fshm, st>>>(sc, im, ls, row_ptr, col, val, status);
-            if (cudaGetLastError() != cudaSuccess ||
-                cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                rc = PSF_ECUDA;
-            else if (h_status)
-                rc = h_status;
-        }
-    }
+    PSF_TRY(cudaMallocAsync(&scratch, bytes, st));
+    rc = set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
+                      static_cast<unsigned char *>(scratch), ntiles, st);
     cudaFreeAsync(scratch, st);
     return rc;
 }
@@ -1015,52 +1053,20 @@ extern "C" int psf_sysmat_rows_set_noalloc(const psf_scanner *scanner, const psf
     Scan sc;
     Img im;
     LorSet ls;
-    int rc = make_scan(scanner, &sc);
+    int rc = set_args(scanner, image, set, row_ptr, col, val, nnz_out, sc, im, ls);
     if (rc) return rc;
-    rc = make_img(image, &im);
-    if (rc) return rc;
-    rc = make_lorset(scanner, set, &ls);
-    if (rc) return rc;
-    if (!row_ptr || !nnz_out || (col && !val)) return PSF_EINVAL;
-    if (im.nx + im.ny + 1 > SET_MAXC || im.nx > 32767 || im.ny > 32767) return PSF_EINVAL;
-    const int64_t n = ls.ntp * ls.nrp;
     *nnz_out = 0;
-    if (n > PSF_NOALLOC_MAX_ROWS) return PSF_ENOSCRATCH;
-    const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE + 1;
-    if (sizeof(int64_t) * ntiles + 64 > (size_t)PSF_NOALLOC_SCRATCH_BYTES) return PSF_ENOSCRATCH;
+    if (ls.ntp * ls.nrp > PSF_NOALLOC_MAX_ROWS) return PSF_ENOSCRATCH;
+    int64_t ntiles = 0;
+    if (set_scratch_bytes(ls, &ntiles) > (size_t)PSF_NOALLOC_SCRATCH_BYTES) return PSF_ENOSCRATCH;
     void *scratch = nullptr;
     rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     cudaStream_t st = as_stream(stream);
     PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
-    if (n == 0) return PSF_OK;
-    int64_t *tiles = (int64_t *)scratch;  // fully rewritten by the scan
-    int *status = (int *)(tiles + ntiles);
-    PSF_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));  // left set by an earlier call
-    const int grid_max = sm_count() * 4;
-    const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
-    const size_t cshm = set_smem(sc, ls);
-    const size_t fshm = cshm + sizeof(WarpSegs) * (SET_T / 32) + 16;
-    PSF_TRY(cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cshm));
-    PSF_TRY(cudaFuncSetAttribute(set_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fshm));
-    set_count_kernel<<<grid, SET_T, cshm, st>>>(sc, im, ls, row_ptr + 1, status);
-    PSF_LAUNCHED();
-    rc = inclusive_scan(row_ptr + 1, n, tiles, st);
-    if (rc) return rc;
-    int64_t nnz = 0;
-    int h_status = 0;
-    PSF_TRY(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PSF_TRY(cudaStreamSynchronize(st));
-    *nnz_out = nnz;
-    if (h_status) return h_status;
-    if (!col) return PSF_OK;
-    if (nnz > capacity) return PSF_ECAPACITY;
-    set_fill_kernel<<<grid, SET_T, fshm, st>>>(sc, im, ls, row_ptr, col, val, status);
-    PSF_LAUNCHED();
-    PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PSF_TRY(cudaStreamSynchronize(st));
-    return h_status;
+    if (ls.ntp * ls.nrp == 0) return PSF_OK;
+    // tile sums and the ring-pair table are fully rewritten; set_pipeline
+    // clears the status word an earlier call may have left set
+    return set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
+                        static_cast<unsigned char *>(scratch), ntiles, st);
 }

@@ -1,4 +1,4 @@
-// Warp-cooperative emission for the structured-set row generator.
+// Slab walk of the structured-set row generator.
 //
 // The 2D cells of a transaxial pair are kept in ray order (their parameter
 // boundaries are monotone there) and are also addressable in voxel order
@@ -7,7 +7,13 @@
 // out, a ray-order range [ca, cb], are at most three ranges of the voxel-order
 // list (the part of the first run, the whole runs in between, the part of the
 // last run), so a warp can copy them with consecutive lanes on consecutive
-// output slots.  Included by psf_rows.cu (needs Cells2D, ZRay, piece).
+// output slots.
+//
+// A ring pair's z-plane crossings depend only on its two rings (z changes
+// linearly from ring a's plane to ring b's along every segment of the pair),
+// so each ring pair's z axis is computed once per call (ZAx) and combined with
+// the transaxial pair's cells per row.  Included by psf_rows.cu (needs
+// Cells2D, piece, first_cell_after, last_cell_before).
 #pragma once
 
 namespace psf {
@@ -22,112 +28,205 @@ __host__ __device__ __forceinline__ int sorted_pos(const Cells2D &c, int cc, boo
 }
 
 // The cells [ca, cb] as up to three disjoint voxel-order ranges [lo, hi],
-// returned in ascending order.  Returns the number of ranges.
+// returned in ascending order.  Returns the number of ranges.  (Every index
+// is static so the arrays stay in registers.)
+__host__ __device__ __forceinline__ void cswap_range(int lo[3], int hi[3], int i, int j) {
+    if (lo[j] < lo[i]) {
+        int t = lo[i]; lo[i] = lo[j]; lo[j] = t;
+        t = hi[i]; hi[i] = hi[j]; hi[j] = t;
+    }
+}
+
 __host__ __device__ __forceinline__ int slab_segments(const Cells2D &c, int ca, int cb,
                                                       bool xinc, bool yinc, int lo[3],
                                                       int hi[3]) {
     const int n = c.hdr[0];
     const int ra = c.run[ca], rb = c.run[cb];
-    int k = 0;
-    int p0, p1;
+    int p0 = sorted_pos(c, ca, xinc, yinc), p1;
     if (ra == rb) {
-        p0 = sorted_pos(c, ca, xinc, yinc);
         p1 = sorted_pos(c, cb, xinc, yinc);
-        lo[k] = p0 < p1 ? p0 : p1;
-        hi[k] = p0 < p1 ? p1 : p0;
+        lo[0] = p0 < p1 ? p0 : p1;
+        hi[0] = p0 < p1 ? p1 : p0;
         return 1;
     }
-    p0 = sorted_pos(c, ca, xinc, yinc);  // first run: ca .. end of its run
-    p1 = sorted_pos(c, c.rstart[ra + 1] - 1, xinc, yinc);
-    lo[k] = p0 < p1 ? p0 : p1;
-    hi[k] = p0 < p1 ? p1 : p0;
-    ++k;
-    if (rb > ra + 1) {  // whole runs in between: one block in voxel order
-        lo[k] = yinc ? c.rstart[ra + 1] : n - c.rstart[rb];
-        hi[k] = yinc ? c.rstart[rb] - 1 : n - c.rstart[ra + 1] - 1;
-        ++k;
-    }
+    p1 = sorted_pos(c, c.rstart[ra + 1] - 1, xinc, yinc);  // first run: ca .. end of its run
+    lo[0] = p0 < p1 ? p0 : p1;
+    hi[0] = p0 < p1 ? p1 : p0;
     p0 = sorted_pos(c, c.rstart[rb], xinc, yinc);  // last run: its start .. cb
     p1 = sorted_pos(c, cb, xinc, yinc);
-    lo[k] = p0 < p1 ? p0 : p1;
-    hi[k] = p0 < p1 ? p1 : p0;
-    ++k;
-    // the three ranges are disjoint; order them by start
-    for (int i = 1; i < k; ++i)
-        for (int j = i; j > 0 && lo[j] < lo[j - 1]; --j) {
-            int t = lo[j]; lo[j] = lo[j - 1]; lo[j - 1] = t;
-            t = hi[j]; hi[j] = hi[j - 1]; hi[j - 1] = t;
-        }
-    return k;
+    lo[1] = p0 < p1 ? p0 : p1;
+    hi[1] = p0 < p1 ? p1 : p0;
+    if (rb > ra + 1) {  // whole runs in between: one block in voxel order
+        lo[2] = yinc ? c.rstart[ra + 1] : n - c.rstart[rb];
+        hi[2] = yinc ? c.rstart[rb] - 1 : n - c.rstart[ra + 1] - 1;
+        cswap_range(lo, hi, 0, 1);
+        cswap_range(lo, hi, 1, 2);
+        cswap_range(lo, hi, 0, 1);
+        return 3;
+    }
+    cswap_range(lo, hi, 0, 1);
+    return 2;
 }
 
-// Slab iz of a ring pair: parameter interval, overlapping ray-order cells and
-// the number of stored voxels (pieces of at least min_units).
-struct SlabCut {
-    long long zl, zh;
+// Cells [ca, cb] overlapping the (clipped) slab interval [zl, zh) and the
+// number of them that keep a chord of at least minu units.
+struct SlabCells {
     int ca, cb, count;
 };
 
-__host__ __device__ __forceinline__ void cut_slab(const Cells2D &c, const ZRay &zr, int iz,
-                                                  SlabCut &s) {
-    const int n = c.hdr[0], nflag = c.hdr[2];
-    slab(zr.Z, iz, s.zl, s.zh);
-    s.zl = s.zl > zr.amin ? s.zl : zr.amin;
-    s.zh = s.zh < zr.amax ? s.zh : zr.amax;
-    s.count = 0;
+__host__ __device__ __forceinline__ SlabCells cut_cells(const Cells2D &c, long long zl,
+                                                        long long zh, long long minu) {
+    SlabCells s;
     s.ca = 0;
     s.cb = -1;
-    if (s.zh <= s.zl) return;
-    s.ca = first_cell_after(c.bnd, n, s.zl);
-    s.cb = last_cell_before(c.bnd, n, s.zh);
-    if (s.cb < s.ca) return;
+    s.count = 0;
+    const int n = c.hdr[0], nflag = c.hdr[2];
+    if (zh <= zl || n == 0) return s;
+    s.ca = first_cell_after(c.bnd, n, zl);
+    s.cb = last_cell_before(c.bnd, n, zh);
+    if (s.cb < s.ca) return s;
     int cnt = s.cb - s.ca + 1;
-    if (piece(c.bnd, s.ca, s.zl, s.zh) < zr.min_units) --cnt;
-    if (s.cb != s.ca && piece(c.bnd, s.cb, s.zl, s.zh) < zr.min_units) --cnt;
+    if (piece(c.bnd, s.ca, zl, zh) < minu) --cnt;
+    if (s.cb != s.ca && piece(c.bnd, s.cb, zl, zh) < minu) --cnt;
     if (nflag <= SET_MAXF) {
         for (int f = 0; f < nflag; ++f) {
             const int cc = c.flag[f];
-            if (cc > s.ca && cc < s.cb && c.bnd[cc + 1] - c.bnd[cc] < zr.min_units) --cnt;
+            if (cc > s.ca && cc < s.cb && c.bnd[cc + 1] - c.bnd[cc] < minu) --cnt;
         }
     } else {
         for (int cc = s.ca + 1; cc < s.cb; ++cc)
-            if (c.bnd[cc + 1] - c.bnd[cc] < zr.min_units) --cnt;
+            if (c.bnd[cc + 1] - c.bnd[cc] < minu) --cnt;
     }
     s.count = cnt;
+    return s;
 }
 
-// z-slab range of a ring pair's segment
-__host__ __device__ __forceinline__ void zray_slabs(const ZRay &zr, int nz, int &z0, int &z1) {
-    int za = 0, zb = -1;
-    if (!zr.empty) {
-        voxel_at(zr.Z, zr.amin, za);
-        voxel_at(zr.Z, zr.amax - 1, zb);
-        if (za > zb) { int t = za; za = zb; zb = t; }
-        za = za < 0 ? 0 : za;
-        zb = zb > nz - 1 ? nz - 1 : zb;
+// z axis of the segments of ring pair (ra, rb) (same numbers as the per-LOR
+// tracer's make_ray for any transaxial pair).
+struct ZAx {
+    Axis Z;
+    long long lo, hi;  // parameter interval of the grid's z range (kind != 0)
+    float lz;          // axial extent of the segment (mm)
+    int empty;         // parallel to the z planes and outside the grid
+};
+
+__host__ __device__ __forceinline__ void zaxis_of(const Scan &sc, const Img &im, int ra, int rb,
+                                                  ZAx &z) {
+    const double za = sc.z064 + ra * sc.pa64, zb = sc.z064 + rb * sc.pa64;
+    bool empty = false;
+    make_axis(z.Z, (za - im.oz) * im.idz, (zb - im.oz) * im.idz, im.nz, empty);
+    z.lo = 0;
+    z.hi = 0;
+    if (z.Z.kind != 0) {
+        const long long p = plane_alpha(z.Z, 0), q = plane_alpha(z.Z, im.nz);
+        z.lo = p < q ? p : q;
+        z.hi = p < q ? q : p;
     }
-    z0 = za;
-    z1 = zb;
+    z.lz = (float)(zb - za);
+    z.empty = empty;
 }
 
-// Broadcast the ring pair owned by lane `src` to the whole warp.
-__device__ __forceinline__ void shfl_zray(ZRay &d, const ZRay &s, int src) {
-    const unsigned F = 0xffffffffu;
-    d.Z.kind = __shfl_sync(F, s.Z.kind, src);
-    d.Z.fixed = __shfl_sync(F, s.Z.fixed, src);
-    d.Z.n = __shfl_sync(F, s.Z.n, src);
-    d.Z.inc = __shfl_sync(F, s.Z.inc, src);
-    d.Z.A0 = __shfl_sync(F, s.Z.A0, src);
-    d.Z.DA = __shfl_sync(F, s.Z.DA, src);
-    d.Z.S = __shfl_sync(F, s.Z.S, src);
-    d.Z.D = __shfl_sync(F, s.Z.D, src);
-    d.Z.sf = __shfl_sync(F, s.Z.sf, src);
-    d.Z.df = __shfl_sync(F, s.Z.df, src);
-    d.amin = __shfl_sync(F, s.amin, src);
-    d.amax = __shfl_sync(F, s.amax, src);
-    d.min_units = __shfl_sync(F, s.min_units, src);
-    d.to_mm = __shfl_sync(F, s.to_mm, src);
-    d.empty = __shfl_sync(F, (int)s.empty, src);
+// One row (transaxial pair x ring pair): z axis, clipped parameter interval,
+// chord scale and its z-slab range [z0, z0 + nsl).
+struct RingPair {
+    Axis Z;
+    long long amin, amax, minu;
+    float to_mm;
+    int z0, nsl;
+};
+
+__device__ __forceinline__ void rp_setup(const Cells2D &c, const ZAx *__restrict__ zt, int j,
+                                         int nrp, int nz, float lx, float ly, RingPair &r) {
+    r.nsl = 0;
+    r.z0 = 0;
+    r.amin = r.amax = r.minu = 0;
+    r.to_mm = 0.0f;
+    r.Z.kind = 0;
+    r.Z.fixed = 0;
+    r.Z.A0 = r.Z.DA = 0;
+    r.Z.S = r.Z.D = 0.0;
+    if (j >= nrp) return;
+    const ZAx &zx = zt[j];
+    r.Z = zx.Z;
+    bool empty = c.hdr[0] == 0 || zx.empty;
+    long long amin = c.clip[0], amax = c.clip[1];
+    if (zx.Z.kind != 0) {
+        amin = zx.lo > amin ? zx.lo : amin;
+        amax = zx.hi < amax ? zx.hi : amax;
+    }
+    if (amax <= amin) empty = true;
+    const float lz = zx.lz;
+    const float len = sqrtf(lx * lx + ly * ly + lz * lz);
+    r.amin = amin;
+    r.amax = amax;
+    r.minu = (long long)ceilf((float)MIN_CHORD_MM / len * (float)FX);
+    r.to_mm = len * (float)(1.0 / FX);
+    if (empty) return;
+    int za = 0, zb = -1;
+    voxel_at(r.Z, amin, za);
+    voxel_at(r.Z, amax - 1, zb);
+    if (za > zb) { const int t = za; za = zb; zb = t; }
+    za = za < 0 ? 0 : za;
+    zb = zb > nz - 1 ? nz - 1 : zb;
+    r.z0 = za;
+    r.nsl = zb >= za ? zb - za + 1 : 0;
 }
+
+// The slab with flattened index f of a warp's 32 rows (incl: inclusive
+// prefix of the rows' slab counts, held one per lane): its row q (-1 when
+// f >= total), slab iz and clipped parameter interval.  Every lane must call.
+struct SlabOf {
+    int q, iz;
+    long long zl, zh, minu;
+    float to_mm;
+};
+
+__device__ __forceinline__ void slab_of(const RingPair &r, int incl, int f, int total,
+                                        SlabOf &s) {
+    const unsigned F = 0xffffffffu;
+    int q = 0;  // rows whose slabs end at or before f
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(F, incl, q + step - 1);
+        if (v <= f) q += step;
+    }
+    q = q > 31 ? 31 : q;
+    Axis Z;
+    Z.kind = __shfl_sync(F, r.Z.kind, q);
+    Z.fixed = __shfl_sync(F, r.Z.fixed, q);
+    Z.A0 = __shfl_sync(F, r.Z.A0, q);
+    Z.DA = __shfl_sync(F, r.Z.DA, q);
+    Z.S = __shfl_sync(F, r.Z.S, q);
+    Z.D = __shfl_sync(F, r.Z.D, q);
+    const long long amin = __shfl_sync(F, r.amin, q), amax = __shfl_sync(F, r.amax, q);
+    s.minu = __shfl_sync(F, r.minu, q);
+    s.to_mm = __shfl_sync(F, r.to_mm, q);
+    const int z0 = __shfl_sync(F, r.z0, q);
+    const int start = __shfl_sync(F, incl - r.nsl, q);
+    s.q = f < total ? q : -1;
+    s.iz = z0 + (f - start);
+    s.zl = 0;
+    s.zh = 0;
+    if (s.q < 0) return;
+    long long zl, zh;
+    slab(Z, s.iz, zl, zh);
+    s.zl = zl > amin ? zl : amin;
+    s.zh = zh < amax ? zh : amax;
+}
+
+// Per-warp work area of the set kernels.
+constexpr int SEG_MAX = 3 * 32;
+struct SetWarp {
+    int2 rs[SEG_MAX];  // range: flattened start, first voxel-order position | slab lane << 16
+    int4 sa[32];       // slab: z offset, voxel-order positions of its first / last
+                       // ray-order cells, keep bits of those two
+    float4 sf[32];     // slab: chords of those two (mm), mm per unit, -
+    long long sm[32];  // slab: shortest stored chord (units)
+    int cnt[32];       // count kernel: voxels of each row of the group
+};
 
 }  // namespace psf
+
+namespace psf {
+static_assert(sizeof(ZAx) == 80, "the no-allocation entry point documents 80 bytes per ring pair");
+}
