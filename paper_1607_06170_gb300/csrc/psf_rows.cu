@@ -414,7 +414,8 @@ struct Cells2D {
     short *run;      // [n] run (constant iy) of each cell
     short *rstart;   // [nruns + 1] first cell of each run
     short *flag;     // [nflag] cells shorter than twice the transaxial chord threshold
-    int *hdr;        // n, nruns, nflag, xinc, yinc
+    short *tie;      // [ny crossings + 1] parallel build: prefix of x/y plane ties
+    int *hdr;        // n, nruns, nflag, ok; parallel build: crossings and first voxels
     Axis *X, *Y;
     long long *clip;  // amin2, amax2
     double *xy;       // endpoints (x1, y1, x2, y2)
@@ -435,7 +436,7 @@ __host__ __device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsi
     c.Y = reinterpret_cast<Axis *>(p);
     p += sizeof(Axis);
     c.hdr = reinterpret_cast<int *>(p);
-    p += sizeof(int) * 8;
+    p += sizeof(int) * 16;
     c.ix = reinterpret_cast<short *>(p);
     p += sizeof(short) * SET_MAXC;
     c.iy = reinterpret_cast<short *>(p);
@@ -446,17 +447,21 @@ __host__ __device__ __forceinline__ unsigned char *cells_layout(Cells2D &c, unsi
     p += sizeof(short) * (SET_MAXC + 1);
     c.flag = reinterpret_cast<short *>(p);
     p += sizeof(short) * SET_MAXF;
+    c.tie = reinterpret_cast<short *>(p);
+    p += sizeof(short) * (SET_MAXC + 1);
     return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
 }
 
 static size_t cells_bytes() {
     return sizeof(long long) * (SET_MAXC + 5) + sizeof(double) * 4 + 2 * sizeof(Axis) +
-           sizeof(short) * (4 * SET_MAXC + 1 + SET_MAXF) + sizeof(int) * 8 + 32;
+           sizeof(short) * (5 * SET_MAXC + 2 + SET_MAXF) + sizeof(int) * 16 + 32;
 }
 
-// One thread: the 2D cells of transaxial pair (a, b).
-__host__ __device__ void build_cells(const Scan &sc, const Img &im, const double *cs, int a, int b,
-                            Cells2D &c) {
+// Segment of transaxial pair (a, b) in the transaxial plane: endpoints,
+// x/y axes, clipped parameter interval [amin, amax) and the short-cell
+// threshold.  Returns false when the segment misses the grid.
+__host__ __device__ bool cells_setup(const Scan &sc, const Img &im, const double *cs, int a,
+                                     int b, Cells2D &c, long long &amin, long long &amax) {
     double px, py, pz, qx, qy, qz;
     face_centre(sc, cs, a, px, py, pz);
     face_centre(sc, cs, b, qx, qy, qz);
@@ -468,7 +473,8 @@ __host__ __device__ void build_cells(const Scan &sc, const Img &im, const double
     Axis &X = *c.X, &Y = *c.Y;
     make_axis(X, (px - im.ox) * im.idx, (qx - im.ox) * im.idx, im.nx, empty);
     make_axis(Y, (py - im.oy) * im.idy, (qy - im.oy) * im.idy, im.ny, empty);
-    long long amin = 0, amax = (long long)FX;
+    amin = 0;
+    amax = (long long)FX;
     for (int k = 0; k < 2; ++k) {
         const Axis &A = k ? Y : X;
         if (A.kind == 0) continue;
@@ -480,19 +486,30 @@ __host__ __device__ void build_cells(const Scan &sc, const Img &im, const double
     c.clip[0] = amin;
     c.clip[1] = amax;
     c.clip[2] = 0;
+    if (empty || amax <= amin) return false;
+    const float lx = (float)(qx - px), ly = (float)(qy - py);
+    const float len2 = sqrtf(lx * lx + ly * ly);
+    // the 3D threshold is at most the transaxial one (3D segments are longer)
+    c.clip[2] = 2 * (long long)ceilf((float)MIN_CHORD_MM / len2 * (float)FX);
+    return true;
+}
+
+// One thread: the 2D cells of transaxial pair (a, b) by walking the x and y
+// plane crossings in ray order (the reference for the parallel build).
+__host__ __device__ void build_cells(const Scan &sc, const Img &im, const double *cs, int a, int b,
+                            Cells2D &c) {
+    long long amin, amax;
+    const bool live = cells_setup(sc, im, cs, a, b, c, amin, amax);
+    const Axis &X = *c.X, &Y = *c.Y;
     int n = 0, nruns = 0, nflag = 0;
     bool ok = true;
-    if (!empty && amax > amin) {
+    if (live) {
         int cx, cy;
         ok &= voxel_at(X, amin, cx);
         ok &= voxel_at(Y, amin, cy);
         long long cur = amin;
         c.bnd[0] = amin;
-        const float lx = (float)(qx - px), ly = (float)(qy - py);
-        const float len2 = sqrtf(lx * lx + ly * ly);
-        // the 3D threshold is at most the transaxial one (3D segments are longer)
-        const long long thr2 = 2 * (long long)ceilf((float)MIN_CHORD_MM / len2 * (float)FX);
-        c.clip[2] = thr2;
+        const long long thr2 = c.clip[2];
         for (int it = 0; it < im.nx + im.ny + 4 && n < SET_MAXC; ++it) {
             long long lo, ex_, ey_;
             if (X.kind == 0) ex_ = FX_BIG; else slab(X, cx, lo, ex_);
@@ -524,6 +541,127 @@ __host__ __device__ void build_cells(const Scan &sc, const Img &im, const double
     c.hdr[2] = nflag;
     c.hdr[3] = ok;
 }
+
+// Parameter of the i-th plane crossing (i >= 1) along the segment of an axis
+// whose voxel at the start of the clipped interval is k0.
+__host__ __device__ __forceinline__ long long crossing(const Axis &A, int k0, int i) {
+    return plane_alpha(A, A.inc ? k0 + i : k0 + 1 - i);
+}
+
+#ifdef __CUDACC__
+// Every thread of the CTA: the same cells as build_cells, built in parallel.
+// The boundaries are the distinct x and y plane crossings inside the clipped
+// interval in ray order.  Each crossing finds its rank in that order by
+// counting the other axis's crossings before it (an exact voxel lookup at
+// the parameter just below it), and a crossing where an x and a y plane meet
+// (a tie) is counted once, through a prefix count of the tied y crossings.
+// A cell's voxel is the voxel at its start, its run the number of y
+// crossings before it.  Ends with a CTA barrier.
+__device__ void build_cells_par(const Scan &sc, const Img &im, const double *cs, int a, int b,
+                                Cells2D &c) {
+    int *H = c.hdr;
+    const Axis &X = *c.X, &Y = *c.Y;
+    if (threadIdx.x == 0) {
+        long long amin, amax;
+        const bool live = cells_setup(sc, im, cs, a, b, c, amin, amax);
+        int kx0 = 0, ky0 = 0, kx1 = 0, ky1 = 0;
+        bool ok = true;
+        if (live) {
+            ok &= voxel_at(X, amin, kx0);
+            ok &= voxel_at(X, amax - 1, kx1);
+            ok &= voxel_at(Y, amin, ky0);
+            ok &= voxel_at(Y, amax - 1, ky1);
+        }
+        const int nxc = live ? abs(kx1 - kx0) : 0, nyc = live ? abs(ky1 - ky0) : 0;
+        H[0] = live ? 1 + nxc + nyc : 0;  // before ties
+        H[2] = 0;
+        H[3] = ok && 1 + nxc + nyc <= SET_MAXC;
+        H[8] = kx0;
+        H[9] = ky0;
+        H[10] = nxc;
+        H[11] = nyc;
+        H[12] = live && H[3];
+    }
+    __syncthreads();
+    const int kx0 = H[8], ky0 = H[9], nxc = H[10], nyc = H[11];
+    const bool live = H[12];
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (live) {
+        // 1. tie flags of the y crossings
+        for (int j = t + 1; j <= nyc; j += nt) {
+            const long long P = crossing(Y, ky0, j);
+            int v1 = 0, v0 = 0;
+            voxel_at(X, P, v1);
+            voxel_at(X, P - 1, v0);
+            c.tie[j] = v1 != v0;
+        }
+    }
+    __syncthreads();
+    if (live && t < 32) {  // 2. inclusive prefix: tie[m] = tied crossings among y 1..m
+        int carry = 0;
+        for (int base = 1; base <= nyc; base += 32) {
+            const int j = base + t;
+            const int v = j <= nyc ? c.tie[j] : 0;
+            int inc = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (t >= o) inc += u;
+            }
+            if (j <= nyc) c.tie[j] = (short)(carry + inc);
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (t == 0) c.tie[0] = 0;
+    }
+    __syncthreads();
+    if (live) {  // 3. ranks -> boundaries, run starts
+        for (int i = t + 1; i <= nxc; i += nt) {
+            const long long P = crossing(X, kx0, i);
+            int vy = 0;
+            voxel_at(Y, P - 1, vy);
+            const int ylt = abs(vy - ky0);
+            c.bnd[(i - 1) + ylt - c.tie[ylt] + 1] = P;
+        }
+        for (int j = t + 1; j <= nyc; j += nt) {
+            const long long P = crossing(Y, ky0, j);
+            int vx = 0;
+            voxel_at(X, P - 1, vx);
+            const int r = (j - 1) + abs(vx - kx0) - c.tie[j - 1] + 1;
+            c.bnd[r] = P;  // a tie writes the same value as its x crossing
+            c.rstart[j] = (short)r;
+        }
+        if (t == 0) {
+            const int n = 1 + nxc + nyc - c.tie[nyc];
+            c.bnd[0] = c.clip[0];
+            c.bnd[n] = c.clip[1];
+            c.rstart[0] = 0;
+            c.rstart[nyc + 1] = (short)n;
+            H[0] = n;
+            H[1] = nyc + 1;
+        }
+    } else if (t == 0) {
+        H[0] = 0;
+        H[1] = 0;
+        c.rstart[0] = 0;
+    }
+    __syncthreads();
+    const int n = H[0];
+    const long long thr2 = c.clip[2];
+    for (int cc = t; cc < n; cc += nt) {  // 4. cells
+        const long long s0 = c.bnd[cc];
+        int cx = 0, cy = 0;
+        voxel_at(X, s0, cx);
+        voxel_at(Y, s0, cy);
+        c.ix[cc] = (short)(cx < 0 ? 0 : (cx >= im.nx ? im.nx - 1 : cx));
+        c.iy[cc] = (short)(cy < 0 ? 0 : (cy >= im.ny ? im.ny - 1 : cy));
+        c.run[cc] = (short)abs(cy - ky0);
+        if (c.bnd[cc + 1] - s0 < thr2) {
+            const int f = atomicAdd(&H[2], 1);
+            if (f < SET_MAXF) c.flag[f] = (short)cc;
+        }
+    }
+    __syncthreads();
+}
+#endif
 
 // First cell whose interval ends after al / last cell that starts before al.
 __host__ __device__ __forceinline__ int first_cell_after(const long long *bnd, int n, long long al) {
@@ -608,10 +746,10 @@ __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const
                                                const LorSet &ls, int64_t T, int *status) {
     __syncthreads();  // the previous pair's readers are done
     const Cells2D &c = m.c;
+    int a, b;
+    ls.tp_decode(m.tp_start, T, &a, &b);
+    build_cells_par(sc, im, m.cs, a, b, m.c);
     if (threadIdx.x == 0) {
-        int a, b;
-        ls.tp_decode(m.tp_start, T, &a, &b);
-        build_cells(sc, im, m.cs, a, b, m.c);
         if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
         *m.next = 0;
     }

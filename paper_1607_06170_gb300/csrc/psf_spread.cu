@@ -216,6 +216,314 @@ static size_t spread_smem(const Tab &tb, int Wt, int Wa) {
     return b;
 }
 
+
+// K3 with a compile-time window (the common windows).  A warp evaluates 32
+// sub-LORs at a time, one per lane, into warp-private rows of shared memory,
+// then accumulates their outer products r1 (x) r2 with each lane owning a
+// fixed RB x CB block of the Q x Q quadrant-local product.  Sub-LORs with
+// different travel patterns land in different quadrants of the window, so
+// each pattern present in the LOR gets its own register accumulator ("slot");
+// the slot of a sub-LOR is the same for the whole warp at each step, so the
+// choice is a uniform branch.  A pre-pass finds the patterns present; a LOR
+// with more than SQ_SLOTS patterns is done in several passes.  The per-warp
+// accumulators are summed in a fixed order at the end of the LOR (FP32,
+// deterministic), folded into the window, and normalised with FP64 totals.
+constexpr int SQ_SLOTS = 4;
+constexpr int SQ_WARPS = SP_THREADS / 32;
+
+template <int WT, int WA>
+struct SqShape {
+    static constexpr int Q = (WT + 1) * (WA + 1);
+    static constexpr int E = (2 * WT + 1) * (2 * WA + 1);
+    static constexpr int RB = (Q + 7) / 8;  // rows of the product per lane (8 row groups)
+    static constexpr int CB = (Q + 3) / 4;  // columns per lane (4 column groups)
+    // row stride of the staged responses: covers every lane's reads, 16-byte
+    // rows, and an odd number of 16-byte units so 8 lanes storing 16 bytes
+    // each hit distinct banks
+    static constexpr int QR = (8 * RB > 4 * CB ? 8 * RB : 4 * CB);
+    static constexpr int QS = ((QR + 3) / 4) % 2 == 0 ? ((QR + 3) / 4) * 4 + 4 : ((QR + 3) / 4) * 4;
+};
+
+// One staged sub-LOR's operands of a lane: RB entries of r1, CB of r2.
+template <int RB, int CB>
+__device__ __forceinline__ void load_ab(const float *ra, const float *rbp, float (&a)[RB],
+                                        float (&b)[CB]) {
+    if constexpr (RB == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(ra);
+        a[0] = v.x;
+        a[1] = v.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) a[i] = ra[i];
+    }
+    if constexpr (CB == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(rbp);
+        b[0] = v.x;
+        b[1] = v.y;
+        b[2] = v.z;
+        b[3] = v.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < CB; ++j) b[j] = rbp[j];
+    }
+}
+
+// All 32 staged sub-LORs of a warp into one accumulator (same slot).
+template <int RB, int CB, int QS>
+__device__ __forceinline__ void acc_all32(float (&acc)[RB][CB], const float *ra,
+                                          const float *rbp) {
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+        float a[RB], b[CB];
+        load_ab<RB, CB>(ra + k * QS, rbp + k * QS, a, b);
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int j = 0; j < CB; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+}
+
+template <int WT, int WA>
+static size_t spread_q_smem(const Tab &tb) {
+    using S = SqShape<WT, WA>;
+    const int NP = tb.Pt * tb.Pa;
+    size_t b = sizeof(double) * 2 * SQ_WARPS;                       // FP64 partial totals
+    b += sizeof(int) * 20;                                           // pattern mask, slots
+    b += sizeof(float) * SQ_WARPS * 2 * 32 * S::QS;                  // staged responses
+    b += sizeof(float) * S::E * S::E;                                // window
+    b += sizeof(float) * 2 * NP * 4;                                 // sub-position centres
+    b += sizeof(float) * (2 * tb.Kt + tb.Ka);                        // node tangents
+    return b + 64;
+}
+
+template <int WT, int WA>
+__global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
+    Scan sc, Tab tb, const float *__restrict__ T, const double *__restrict__ eta,
+    const int32_t *__restrict__ lors, int64_t n_lors, int norm, float *__restrict__ out) {
+    using S = SqShape<WT, WA>;
+    constexpr int Q = S::Q, E = S::E, RB = S::RB, CB = S::CB, QS = S::QS;
+    constexpr int W2a = 2 * WA + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int NP = tb.Pt * tb.Pa;
+    const int nsub = NP * NP;
+    double *red = reinterpret_cast<double *>(smraw);                 // [2][SQ_WARPS]
+    int *ipat = reinterpret_cast<int *>(red + 2 * SQ_WARPS);        // [0] mask, [1] npat, [4..19] slot pattern
+    float *Rw = reinterpret_cast<float *>(ipat + 20);               // [warps][2][32][QS]
+    float *wwin = Rw + SQ_WARPS * 2 * 32 * QS;                      // [E*E]
+    float *pts = wwin + E * E;                                      // [2][NP][4]
+    float *part = Rw;  // [warps][SQ_SLOTS][Q*Q], reuses the staging rows at the end of a LOR
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float *R1w = Rw + warp * 2 * 32 * QS, *R2w = R1w + 32 * QS;
+    const int rb = lane >> 2, cb = lane & 3;
+    const GapConst gk = make_gapconst(sc, tb, pts + 2 * NP * 4);  // visible after the first barrier
+    for (int k = t; k < SQ_WARPS * 2 * 32 * QS; k += SP_THREADS) Rw[k] = 0.0f;
+    for (int64_t lor = blockIdx.x; lor < n_lors; lor += gridDim.x) {
+        const int id1 = lors[2 * lor], id2 = lors[2 * lor + 1];
+        const int ring1 = id1 / sc.Nt, c1 = id1 - ring1 * sc.Nt;
+        const int ring2 = id2 / sc.Nt, c2 = id2 - ring2 * sc.Nt;
+        const int b1 = c1 / sc.Nb, i1 = c1 - b1 * sc.Nb;
+        const int b2 = c2 / sc.Nb, i2 = c2 - b2 * sc.Nb;
+        float *o = out + lor * (int64_t)E * E;
+        const int nc = sc.Nt * sc.NR;
+        __syncthreads();  // previous LOR's readers of pts / wwin / part are done
+        if (b1 == b2 || id1 < 0 || id2 < 0 || id1 >= nc || id2 >= nc) {
+            for (int k = t; k < E * E; k += SP_THREADS) o[k] = 0.0f;
+            continue;
+        }
+        float sb1, cb1, sb2, cb2;
+        sincospif(2.0f * b1 / sc.R, &sb1, &cb1);
+        sincospif(2.0f * b2 / sc.R, &sb2, &cb2);
+        for (int k = t; k < 2 * NP; k += SP_THREADS) {
+            const int end = k / NP, sp = k - end * NP;
+            const int p = sp / tb.Pa, q = sp - p * tb.Pa;
+            const int i = end ? i2 : i1, ring = end ? ring2 : ring1;
+            const float cbk = end ? cb2 : cb1, sbk = end ? sb2 : sb1;
+            const float se = (i - 0.5f * (sc.Nb - 1)) * sc.pt + ((p + 0.5f) / tb.Pt - 0.5f) * sc.wt;
+            const float ze = sc.z0 + ring * sc.pa + ((q + 0.5f) / tb.Pa - 0.5f) * sc.wa;
+            float *P = pts + k * 4;
+            P[0] = sc.radius * cbk - se * sbk;
+            P[1] = sc.radius * sbk + se * cbk;
+            P[2] = ze;
+            P[3] = se;
+        }
+        for (int k = t; k < E * E; k += SP_THREADS) wwin[k] = 0.0f;
+        if (t == 0) ipat[0] = 0;
+        __syncthreads();
+        // pre-pass: the travel patterns present among the valid sub-LORs
+        unsigned mine = 0;
+        for (int s = t; s < nsub; s += SP_THREADS) {
+            const int s1 = s / NP, s2 = s - s1 * NP;
+            const float *P1 = pts + s1 * 4, *P2 = pts + (NP + s2) * 4;
+            const float dx = P1[0] - P2[0], dy = P1[1] - P2[1], dz = P1[2] - P2[2];
+            float vn1, vt1, vn2, vt2;
+            end_dir(dx, dy, cb1, sb1, vn1, vt1);
+            end_dir(-dx, -dy, cb2, sb2, vn2, vt2);
+            if (vn1 > 0.0f && vn2 > 0.0f)
+                mine |= 1u << (((vt1 >= 0.0f) << 3) | ((dz >= 0.0f) << 2) | ((vt2 >= 0.0f) << 1) |
+                               (-dz >= 0.0f));
+        }
+        mine = __reduce_or_sync(0xffffffffu, mine);
+        if (lane == 0 && mine) atomicOr(ipat, (int)mine);
+        __syncthreads();
+        const unsigned present = (unsigned)ipat[0];
+        const int npat = __popc(present);
+        double sfull = 0.0;
+        for (int pass = 0; pass * SQ_SLOTS < npat; ++pass) {
+            float acc[SQ_SLOTS][RB][CB];
+#pragma unroll
+            for (int a = 0; a < SQ_SLOTS; ++a)
+#pragma unroll
+                for (int i = 0; i < RB; ++i)
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) acc[a][i][j] = 0.0f;
+            for (int base = warp * 32; base < nsub; base += SP_THREADS) {
+                const int s = base + lane;
+                int slot = -1;
+                if (s < nsub) {
+                    const int s1 = s / NP, s2 = s - s1 * NP;
+                    const float *P1 = pts + s1 * 4, *P2 = pts + (NP + s2) * 4;
+                    const float dx = P1[0] - P2[0], dy = P1[1] - P2[1], dz = P1[2] - P2[2];
+                    float vn1, vt1, vn2, vt2;
+                    end_dir(dx, dy, cb1, sb1, vn1, vt1);
+                    end_dir(-dx, -dy, cb2, sb2, vn2, vt2);
+                    if (vn1 > 0.0f && vn2 > 0.0f) {
+                        const int P = ((vt1 >= 0.0f) << 3) | ((dz >= 0.0f) << 2) |
+                                      ((vt2 >= 0.0f) << 1) | (-dz >= 0.0f);
+                        // slot = rank of the pattern among those present
+                        const int sl = __popc(present & ((1u << P) - 1u)) - pass * SQ_SLOTS;
+                        if (sl >= 0 && sl < SQ_SLOTS) {
+                            slot = sl;
+                            QResp<WT, WA> r;
+                            end_resp_q<WT, WA>(sc, tb, gk, T, eta, i1, ring1, s1 / tb.Pa,
+                                               s1 % tb.Pa, P1[3], P1[2], vn1, vt1, dz, r);
+                            const double e1 = r.eta;
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) R1w[lane * QS + k] = r.q[k];
+                            end_resp_q<WT, WA>(sc, tb, gk, T, eta, i2, ring2, s2 / tb.Pa,
+                                               s2 % tb.Pa, P2[3], P2[2], vn2, vt2, -dz, r);
+#pragma unroll
+                            for (int k = 0; k < Q; ++k) R2w[lane * QS + k] = r.q[k];
+                            sfull += e1 * r.eta;
+                        }
+                    }
+                }
+                __syncwarp();
+                const float *ra = R1w + rb * RB, *rbp = R2w + cb * CB;
+                const int s0 = __shfl_sync(0xffffffffu, slot, 0);
+                if (__all_sync(0xffffffffu, slot == s0)) {
+                    // common case: one travel pattern for the whole warp
+                    static_assert(SQ_SLOTS == 4, "one case per slot");
+                    switch (s0) {
+                        case 0: acc_all32<RB, CB, QS>(acc[0], ra, rbp); break;
+                        case 1: acc_all32<RB, CB, QS>(acc[1], ra, rbp); break;
+                        case 2: acc_all32<RB, CB, QS>(acc[2], ra, rbp); break;
+                        case 3: acc_all32<RB, CB, QS>(acc[3], ra, rbp); break;
+                        default: break;
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = 0; k < 32; ++k) {
+                        const int sk = __shfl_sync(0xffffffffu, slot, k);
+                        if (sk < 0) continue;
+                        float a[RB], b[CB];
+                        load_ab<RB, CB>(ra + k * QS, rbp + k * QS, a, b);
+#pragma unroll
+                        for (int sl = 0; sl < SQ_SLOTS; ++sl)
+                            if (sk == sl) {
+#pragma unroll
+                                for (int i = 0; i < RB; ++i)
+#pragma unroll
+                                    for (int j = 0; j < CB; ++j)
+                                        acc[sl][i][j] = fmaf(a[i], b[j], acc[sl][i][j]);
+                            }
+                    }
+                }
+                __syncwarp();
+            }
+            // per-warp accumulators -> part, then fold into the window
+            __syncthreads();
+#pragma unroll
+            for (int sl = 0; sl < SQ_SLOTS; ++sl)
+#pragma unroll
+                for (int i = 0; i < RB; ++i)
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) {
+                        const int e1 = rb * RB + i, e2 = cb * CB + j;
+                        if (e1 < Q && e2 < Q)
+                            part[(warp * SQ_SLOTS + sl) * Q * Q + e1 * Q + e2] = acc[sl][i][j];
+                    }
+            __syncthreads();
+            const int nsl = min(SQ_SLOTS, npat - pass * SQ_SLOTS);
+            for (int wc = t; wc < E * E; wc += SP_THREADS) {
+                const int w1 = wc / E, w2 = wc - w1 * E;
+                const int tx1 = w1 / W2a - WT, tz1 = w1 % W2a - WA;
+                const int tx2 = w2 / W2a - WT, tz2 = w2 % W2a - WA;
+                float v = wwin[wc];
+                int c = 0;
+                for (int P = 0; P < SP_PATS; ++P) {
+                    if (!((present >> P) & 1)) continue;
+                    const int sl = c++ - pass * SQ_SLOTS;
+                    if (sl < 0 || sl >= nsl) continue;
+                    const int g1 = (P >> 3) & 1 ? 1 : -1, a1 = (P >> 2) & 1 ? 1 : -1;
+                    const int g2 = (P >> 1) & 1 ? 1 : -1, a2 = P & 1 ? 1 : -1;
+                    const int x1 = g1 * tx1, z1 = a1 * tz1, x2 = g2 * tx2, z2 = a2 * tz2;
+                    if (x1 < 0 || z1 < 0 || x2 < 0 || z2 < 0) continue;
+                    const int e = (x1 * (WA + 1) + z1) * Q + x2 * (WA + 1) + z2;
+                    float sum = 0.0f;
+#pragma unroll
+                    for (int w = 0; w < SQ_WARPS; ++w) sum += part[(w * SQ_SLOTS + sl) * Q * Q + e];
+                    v += sum;
+                }
+                wwin[wc] = v;
+            }
+            __syncthreads();  // part aliases the staging rows of the next pass
+        }
+        // FP64 totals: sfull over sub-LORs, sw over the accumulated window
+        double swin = 0.0;
+        for (int wc = t; wc < E * E; wc += SP_THREADS) swin += (double)wwin[wc];
+        sfull = warp_sum_d(sfull);
+        swin = warp_sum_d(swin);
+        if (lane == 0) {
+            red[warp] = sfull;
+            red[SQ_WARPS + warp] = swin;
+        }
+        __syncthreads();
+        double sf = 0.0, sw = 0.0;
+#pragma unroll
+        for (int w = 0; w < SQ_WARPS; ++w) {
+            sf += red[w];
+            sw += red[SQ_WARPS + w];
+        }
+        double scale = 1.0 / nsub;                                       // NONE: mean
+        if (norm == PSF_NORM_EFF && sw > 0.0) scale = sf / (sw * nsub);    // total = mean eta1 eta2
+        if (norm == PSF_NORM_UNIT && sw > 0.0) scale = 1.0 / sw;           // total = 1
+        const float fs = (float)scale;
+        for (int k = t; k < E * E; k += SP_THREADS) o[k] = wwin[k] * fs;
+    }
+}
+
+template <int WT, int WA>
+static int launch_spread_q(const Scan &sc, const Tab &tb, const float *T, const double *eta,
+                           const int32_t *lors, int64_t n_lors, int norm, float *out,
+                           cudaStream_t st) {
+    const size_t shm = spread_q_smem<WT, WA>(tb);
+    if (shm > 200 * 1024) return PSF_EINVAL;
+    PSF_TRY(cudaFuncSetAttribute(spread_q_kernel<WT, WA>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    int dev = 0, sms = 148, per_sm = 0;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PSF_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spread_q_kernel<WT, WA>,
+                                                          SP_THREADS, shm));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t cap = (int64_t)sms * per_sm;
+    const int64_t grid = n_lors < cap ? n_lors : cap;
+    spread_q_kernel<WT, WA><<<(int)grid, SP_THREADS, shm, st>>>(sc, tb, T, eta, lors, n_lors,
+                                                                norm, out);
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
 }  // namespace psf
 
 using namespace psf;
@@ -236,6 +544,13 @@ extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *
     if (n_lors == 0) return PSF_OK;
     if (!table || !eta || !lors || !spread) return PSF_EINVAL;
     if (tb.Pt * tb.Pa > 1024) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    if (half_t == 3 && half_a == 3)
+        return launch_spread_q<3, 3>(sc, tb, table, eta, lors, n_lors, norm, spread, st);
+    if (half_t == 3 && half_a == 2)
+        return launch_spread_q<3, 2>(sc, tb, table, eta, lors, n_lors, norm, spread, st);
+    if (half_t == 3 && half_a == 0)
+        return launch_spread_q<3, 0>(sc, tb, table, eta, lors, n_lors, norm, spread, st);
     size_t shm = spread_smem(tb, half_t, half_a);
     if (shm > 200 * 1024) return PSF_EINVAL;
     PSF_TRY(cudaFuncSetAttribute(spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -115,3 +115,15 @@ def test_factored_projector(gpu, ref, orc):
         lhs = torch.dot(M.forward(xk).double(), yk.double()).item()
         rhs = torch.dot(xk.double(), M.back(yk).double()).item()
         assert lhs == pytest.approx(rhs, rel=1e-5)
+
+
+@pytest.mark.parametrize("Wt,Wa", [(2, 1), (1, 3)])
+def test_class_spreads_other_windows(P, gpu, ref, orc, Wt, Wa):
+    """Windows without a compile-time kernel go through the generic one."""
+    w = ref["w"]
+    C = gpu["C"].cpu().numpy()
+    WC = P.bin_spread(w["scanner"], w["table"], gpu["T"], gpu["eta"], gpu["C"], Wt, Wa)
+    Wo = orc.spread(w["scanner"], w["table"], ref["T"], C, Wt, Wa)
+    ok = orc.tie_margin(w["scanner"], w["table"], ref["T"], C) >= 1e-5
+    scale = np.abs(Wo).reshape(len(C), -1).max(1)[:, None, None]
+    assert_close(WC.cpu().numpy()[ok], Wo[ok], 1e-5, 1e-12 * scale[ok] + 1e-30, "class spread")
