@@ -345,6 +345,228 @@ __global__ void __launch_bounds__(ST_T) stencil2_kernel(LorSet ls, int Wt,
     }
 }
 
+// Third form of the same stencil.  One CTA of 128 threads owns one
+// transaxial pair; a thread owns K = 8 rings x M = 2 consecutive ring
+// differences.  Each partner's plane (by ring-difference column, rings
+// contiguous, so the K + 2*WA values of one column are four 16-byte loads) and
+// its weight slice (per column and e = o1 - o2, the o1 entries contiguous) are
+// brought into shared memory by asynchronous copies, two partners deep, so
+// the copies of the next partner overlap the arithmetic of this one.  Every
+// partner writes the same cells, so the padding cells zeroed at the start stay
+// zero.  For one partner column and one of the thread's differences, e is a
+// compile-time constant, so every register index is static.
+constexpr int ST3_T = 128, ST3_K = 8, ST3_M = 2;
+
+struct St3Shape {
+    int nd, nstrip, ndg, items, PRp, ne;
+    int plane_f, w_f, buf_f;  // floats of one partner buffer
+};
+
+__host__ __device__ inline St3Shape st3_shape(const LorSet &ls, int WA) {
+    St3Shape s;
+    s.nd = 2 * ls.Dm + 1;
+    s.nstrip = (ls.NR + ST3_K - 1) / ST3_K;
+    s.ndg = (s.nd + ST3_M - 1) / ST3_M;
+    s.items = s.nstrip * s.ndg;
+    // rows = ring + WA, a strip reads 16 rows from its first; a column stride
+    // of 4 (mod 32) words spreads consecutive columns over the banks
+    s.PRp = s.nstrip * ST3_K + 8;
+    s.PRp += (36 - s.PRp % 32) % 32;
+    s.ne = 4 * WA + 1;
+    s.plane_f = s.nd * s.PRp;
+    s.w_f = s.nd * s.ne * 8;
+    s.buf_f = s.plane_f + s.w_f;
+    return s;
+}
+
+static size_t stencil3_smem_bytes(const LorSet &ls, int WA) {
+    const St3Shape s = st3_shape(ls, WA);
+    return sizeof(float) * 2 * (size_t)s.buf_f + sizeof(short2) * ls.nrp +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 32;
+}
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// Transaxial partner dt of pair (a, b): false if it is not in the set.
+struct St3Partner {
+    int64_t prow;
+    int cls, dt1, dt2;
+    bool sw, wsw;
+};
+
+template <bool adjoint>
+__device__ __forceinline__ bool st3_partner(const LorSet &ls, const int32_t *tp_start, int a,
+                                            int b, int dt, int Wt, int own_cls, St3Partner &P) {
+    P.dt1 = dt / (2 * Wt + 1) - Wt;
+    P.dt2 = dt % (2 * Wt + 1) - Wt;
+    int pa = adjoint ? a + P.dt1 : a - P.dt1, pb = adjoint ? b + P.dt2 : b - P.dt2;
+    pa += pa < 0 ? ls.Nt : (pa >= ls.Nt ? -ls.Nt : 0);
+    pb += pb < 0 ? ls.Nt : (pb >= ls.Nt ? -ls.Nt : 0);
+    if (pa == pb) return false;
+    P.sw = pa > pb;
+    const int c1 = P.sw ? pb : pa, c2 = P.sw ? pa : pb;
+    if (!tp_member(ls, c1, c2)) return false;
+    P.prow = (int64_t)tp_index(ls, tp_start, c1, c2) * ls.nrp;
+    P.cls = adjoint ? own_cls : tp_index(ls, tp_start, c1 % ls.Nb, c2 - (c1 - c1 % ls.Nb));
+    P.wsw = adjoint ? false : P.sw;
+    return true;
+}
+
+template <bool adjoint>
+__device__ __forceinline__ int st3_next(const LorSet &ls, const int32_t *tp_start, int a, int b,
+                                        int dt, int nwin, int Wt, int own_cls, St3Partner &P) {
+    for (; dt < nwin; ++dt)
+        if (st3_partner<adjoint>(ls, tp_start, a, b, dt, Wt, own_cls, P)) return dt;
+    return nwin;
+}
+
+// Issue (without waiting) the copies of one partner into a buffer.
+template <int WA>
+__device__ __forceinline__ void st3_stage(const LorSet &ls, const St3Shape &S, const short2 *rp,
+                                          const St3Partner &P, int Wt,
+                                          const float *__restrict__ w,
+                                          const float *__restrict__ in, float *buf) {
+    constexpr int W2a = 2 * WA + 1, NE = 4 * WA + 1;
+    const int Dm = ls.Dm, nd = S.nd, PRp = S.PRp, nrp = (int)ls.nrp;
+    const int E = (2 * Wt + 1) * W2a;
+    float *plane = buf, *w3 = buf + S.plane_f;
+    for (int j = threadIdx.x; j < nrp; j += ST3_T) {
+        const short2 rr = rp[j];
+        const int ra = P.sw ? rr.y : rr.x, rb = P.sw ? rr.x : rr.y;
+        cp_async4(plane + (rb - ra + Dm) * PRp + (ra + WA), in + P.prow + j);
+    }
+    const float *wc = w + (int64_t)P.cls * nd * E * E;
+    for (int i = threadIdx.x; i < nd * W2a * W2a; i += ST3_T) {
+        const int d = i / (W2a * W2a) - Dm, L1 = (i / W2a) % W2a, L2 = i % W2a;
+        const int e_a = (P.dt1 + Wt) * W2a + L1, e_b = (P.dt2 + Wt) * W2a + L2;
+        const int e1 = P.wsw ? e_b : e_a, e2 = P.wsw ? e_a : e_b;
+        const int dc = P.wsw ? -d : d;
+        cp_async4(w3 + ((d + Dm) * NE + (L1 - L2) + 2 * WA) * 8 + L1,
+                  wc + (int64_t)(dc + Dm) * E * E + e1 * E + e2);
+    }
+    cp_async_commit();
+}
+
+template <bool adjoint, int WA>
+__global__ void __launch_bounds__(ST3_T, 4) stencil3_kernel(LorSet ls, int Wt,
+                                                            const float *__restrict__ w,
+                                                            const float *__restrict__ in,
+                                                            float *__restrict__ out) {
+    constexpr int NE = 4 * WA + 1, K = ST3_K, M = ST3_M;
+    extern __shared__ __align__(16) unsigned char raw[];
+    const St3Shape S = st3_shape(ls, WA);
+    const int Dm = ls.Dm, NR = ls.NR, PRp = S.PRp;
+    const int nwin = (2 * Wt + 1) * (2 * Wt + 1);
+    float *bufs = reinterpret_cast<float *>(raw);  // [2][buf_f]
+    short2 *rp = reinterpret_cast<short2 *>(bufs + 2 * S.buf_f);
+    int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    const int t = threadIdx.x;
+    for (int i = t; i < 2 * S.buf_f; i += ST3_T) bufs[i] = 0.0f;
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    for (int j = t; j < ls.nrp; j += ST3_T) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rp[j] = make_short2((short)r1, (short)r2);
+    }
+    __syncthreads();
+    const int nrp = (int)ls.nrp;
+    const bool active = t < S.items;
+    const int q = active ? t / S.nstrip : 0, strip = active ? t % S.nstrip : 0;
+    const int dl0 = q * M - Dm, r0 = strip * K;
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        int a, b;
+        ls.tp_decode(tp_start, T, &a, &b);
+        const int a0 = a % ls.Nb;
+        const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
+        float acc[M][K];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[m][k] = 0.0f;
+        St3Partner P;
+        int dt = st3_next<adjoint>(ls, tp_start, a, b, 0, nwin, Wt, own_cls, P);
+        if (dt < nwin) st3_stage<WA>(ls, S, rp, P, Wt, w, in, bufs);
+        int cur = 0;
+        while (dt < nwin) {
+            St3Partner Pn;
+            const int nxt = st3_next<adjoint>(ls, tp_start, a, b, dt + 1, nwin, Wt, own_cls, Pn);
+            if (nxt < nwin)
+                st3_stage<WA>(ls, S, rp, Pn, Wt, w, in, bufs + (cur ^ 1) * S.buf_f);
+            else
+                cp_async_commit();  // empty group keeps the count uniform
+            cp_async_wait1();       // this partner's copies (all but the newest group)
+            __syncthreads();
+            if (active) {
+                const float *plane = bufs + cur * S.buf_f, *w3 = plane + S.plane_f;
+#pragma unroll
+                for (int cc = 0; cc < M + 4 * WA; ++cc) {
+                    const int c = dl0 - 2 * WA + cc;  // partner column (ring difference)
+                    if (c < -Dm || c > Dm) continue;
+                    float v[16];
+                    const float4 *pv =
+                        reinterpret_cast<const float4 *>(plane + (c + Dm) * PRp + r0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 f = pv[u];
+                        v[4 * u] = f.x;
+                        v[4 * u + 1] = f.y;
+                        v[4 * u + 2] = f.z;
+                        v[4 * u + 3] = f.w;
+                    }
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        // forward: source difference c = dl + e, weights by c;
+                        // adjoint: target difference c = dl - e, weights by dl
+                        const int e = adjoint ? m + 2 * WA - cc : cc - 2 * WA - m;
+                        if (e < -2 * WA || e > 2 * WA) continue;
+                        const int wd = adjoint ? dl0 + m : c;
+                        if (adjoint && wd > Dm) continue;
+                        const float4 *pw = reinterpret_cast<const float4 *>(
+                            w3 + ((wd + Dm) * NE + e + 2 * WA) * 8);
+                        const float4 w0 = pw[0], w1 = pw[1];
+                        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int o1 = -WA; o1 <= WA; ++o1) {
+                            const int o2 = o1 - e;
+                            if (o2 < -WA || o2 > WA) continue;
+                            const float wgt = wv[o1 + WA];
+#pragma unroll
+                            for (int k = 0; k < K; ++k)
+                                acc[m][k] =
+                                    fmaf(wgt, v[adjoint ? k + o1 + WA : k - o1 + WA], acc[m][k]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();  // this buffer is free for the partner after next
+            cur ^= 1;
+            dt = nxt;
+            P = Pn;
+        }
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int ra = r0 + k, dl = dl0 + m, rb = ra + dl;
+                    if (ra < NR && dl <= Dm && rb >= 0 && rb < NR)
+                        out[T * nrp + rp_start[ra] + (rb - ls.rp_lo(ra))] = acc[m][k];
+                }
+        }
+    }
+}
+
 constexpr int ST2_K = 8;  // rows per thread in stencil2_kernel
 
 static size_t stencil2_smem_bytes(const LorSet &ls, int Wa) {
@@ -396,11 +618,37 @@ static int launch_stencil2(const psf_matrix *m, const float *in, float *out, int
     return PSF_OK;
 }
 
+template <bool adjoint, int WA>
+static int launch_stencil3(const psf_matrix *m, const float *in, float *out, int grid,
+                           cudaStream_t st) {
+    const size_t shm = stencil3_smem_bytes(m->ls, WA);
+    PSF_TRY(cudaFuncSetAttribute(stencil3_kernel<adjoint, WA>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    stencil3_kernel<adjoint, WA><<<grid, ST3_T, shm, st>>>(m->ls, m->Wt, m->cls, in, out);
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
 static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoint,
                    cudaStream_t st) {
     int dev = 0, sms = 148;
     PSF_TRY(cudaGetDevice(&dev));
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const St3Shape s3 = st3_shape(m->ls, m->Wa);
+    if (m->Wa <= 3 && s3.items <= ST3_T && stencil3_smem_bytes(m->ls, m->Wa) <= 110 * 1024) {
+        const int64_t g3 = m->ls.ntp < (int64_t)sms * 4 ? m->ls.ntp : (int64_t)sms * 4;
+        switch (m->Wa * 2 + (adjoint ? 1 : 0)) {
+            case 0: return launch_stencil3<false, 0>(m, in, out, (int)g3, st);
+            case 1: return launch_stencil3<true, 0>(m, in, out, (int)g3, st);
+            case 2: return launch_stencil3<false, 1>(m, in, out, (int)g3, st);
+            case 3: return launch_stencil3<true, 1>(m, in, out, (int)g3, st);
+            case 4: return launch_stencil3<false, 2>(m, in, out, (int)g3, st);
+            case 5: return launch_stencil3<true, 2>(m, in, out, (int)g3, st);
+            case 6: return launch_stencil3<false, 3>(m, in, out, (int)g3, st);
+            case 7: return launch_stencil3<true, 3>(m, in, out, (int)g3, st);
+            default: break;
+        }
+    }
     int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
     switch (m->Wa * 2 + (adjoint ? 1 : 0)) {  // register-blocked form for axial windows <= 3
         case 0: return launch_stencil2<false, 0>(m, in, out, (int)grid, st);
