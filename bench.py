@@ -182,6 +182,83 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def stencil_pairs(s, ls, Wt, Wa):
+    """Exact number of (output LOR, source LOR) products in one application of
+    the spread S over a structured LOR set: transaxial (pair, partner) pairs
+    in the set times axial (ring pair, ring pair) pairs in the set."""
+    import numpy as np
+
+    from paper_1607_06170_gb300 import inputs as I
+
+    nt, F, Dm = I.n_transaxial(s), ls["fan_half"], ls["max_ring_diff"]
+    tp = I.transaxial_pairs(s, F)
+    a, b = tp[:, 0].astype(np.int64), tp[:, 1].astype(np.int64)
+    n_t = 0
+    for d1 in range(-Wt, Wt + 1):
+        for d2 in range(-Wt, Wt + 1):
+            pa, pb = (a - d1) % nt, (b - d2) % nt
+            d = np.abs(pa - pb)
+            n_t += int(((pa != pb) & (d >= nt // 2 - F) & (d <= nt // 2 + F)).sum())
+    nr = I.n_rings(s)
+    ra, rb = np.meshgrid(np.arange(nr), np.arange(nr), indexing="ij")
+    n_a = 0
+    for o1 in range(-Wa, Wa + 1):
+        for o2 in range(-Wa, Wa + 1):
+            sa, sb = ra - o1, rb - o2
+            ok = (np.abs(ra - rb) <= Dm) & (sa >= 0) & (sa < nr) & (sb >= 0) & (sb < nr)
+            n_a += int((ok & (np.abs(sa - sb) <= Dm)).sum())
+    return n_t * n_a
+
+
+# kernel -> (bound, algorithmic work per launch, unit): bytes a launch must move
+# through HBM, or FP32 FLOPs it must execute
+def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
+    if name == "set_fill_kernel":  # writes column + chord, reads row_ptr
+        return "hbm", 8.0 * nnz + 8.0 * n_lors, "GB/s"
+    if name in ("csr_fwd_kernel", "csr_back_kernel"):  # column + value, row_ptr, LOR value, image
+        return "hbm", 8.0 * nnz + 12.0 * n_lors + 4.0 * nv, "GB/s"
+    if name == "spread_q_kernel":  # one FMA per sub-LOR and quadrant entry pair
+        nsub = (t["n_sub_t"] * t["n_sub_a"]) ** 2
+        return "alu", 2.0 * n_cls * nsub * ((Wt + 1) * (Wa + 1)) ** 2, "TFLOP/s"
+    if name.startswith("stencil"):  # one FMA per (output LOR, source LOR) pair
+        return "alu", 2.0 * stencil_pairs(s, ls, Wt, Wa), "TFLOP/s"
+    return None, None, None
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch from the committed ncu capture of this kernel,
+    or None when the kernel's source file has changed since the capture."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[name]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha1(src).hexdigest() != rec["sha1"]:
+        return None
+    return rec["bytes_per_launch"]
+
+
+def roofline(name, ms_per_launch, peaks, clocks, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
+    bound, work, unit = kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv)
+    out = {"kernel": name, "ms_per_launch": ms_per_launch, "bound": bound}
+    if bound is None:
+        return out
+    sm_mhz = float(clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    if bound == "hbm":
+        peak, src = float(peaks.get("hbm_gbs", 6800.0)), "measured" if peaks else "fallback"
+        achieved = work / 1e9 / (ms_per_launch * 1e-3)
+    else:  # FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x sampled SM clock
+        peak, src = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "derived"
+        achieved = work / 1e12 / (ms_per_launch * 1e-3)
+    tr = kernel_traffic(name)
+    out.update({"achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": tr / 1e9 if tr is not None else None, "traffic_unit": "GB",
+                "work_per_launch": work, "peak_source": src})
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -271,6 +348,7 @@ def run_gpu(args):
         torch.distributed.barrier()
     clk = ClockSampler(local)
     clk.start()
+    P.timing_enable(True)  # CUDA events around every library kernel launch
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     stage_ms = {k: [] for k in stages}
@@ -286,6 +364,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     total_ms = t0.elapsed_time(t1)
     clocks = clk.stop()
+    ktimes = P.timing_read()
+    P.timing_enable(False)
     if world > 1:
         tt = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -312,50 +392,36 @@ def run_gpu(args):
            "h2d_bytes_per_step": int(x_host.numel() * 4 + y_host.numel() * 4),
            "d2h_bytes_per_step": int(out_host.numel() * 4)}
 
-    # roofline of the dominant kernel stage
+    # roofline of the dominant kernel: the library kernel with the most device
+    # time per step (CUDA events around each launch, timed region only)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sm_mhz = float(clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0))
-    E = (2 * Wt + 1) * (2 * Wa + 1)
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA TFLOP/s at the sampled clock
-    model = {
-        # algorithmic work per launch (the design doc lists these per unit)
-        "rows": ("hbm", (8.0 * nnz + 24.0 * n_lors) / 1e9, hbm, "GB/s"),
-        "forward": ("hbm", (8.0 * nnz + 12.0 * n_lors) / 1e9, hbm, "GB/s"),
-        "back": ("hbm", (8.0 * nnz + 12.0 * n_lors) / 1e9, hbm, "GB/s"),
-        "sens": ("hbm", (8.0 * nnz + 12.0 * n_lors) / 1e9, hbm, "GB/s"),
-        "spread": ("alu", 2.0 * n_cls * 4096 * 256 / 1e12, alu_peak, "TFLOP/s"),
-    }
-    top = max(med, key=med.get)
-    if top in model:
-        bound, work, peak, unit = model[top]
-        achieved = work / (med[top] * 1e-3)
-        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "kernel_stage": top,
-                "peak_source": "measured" if peaks else "fallback"}
-    else:
-        roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "kernel_stage": top}
-    launches = 1 + 1 + 1 + (1 + 3 + 1) + 2 + 2 + 1 + 2 + 1
+    kern = {k: {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps,
+                "ms_per_launch": ms / n} for k, (n, ms) in ktimes.items()}
+    top = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    roof = roofline(top, kern[top]["ms_per_launch"], peaks, clocks, s, t, ls, Wt, Wa,
+                    n_lors, n_cls, nnz, nv)
+    launches = sum(n for n, _ in ktimes.values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_lors": n_lors, "nnz": nnz, "n_classes": n_cls,
                    "image": [im["nx"], im["ny"], im["nz"]], "voxel_mm": im["dx"],
-                   "l2": "inputs larger than L2 (53 GB matrix regenerated per step)",
+                   "l2": "inputs larger than L2 (%.0f GB matrix regenerated per step)"
+                         % ((8.0 * nnz + 8.0 * n_lors) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "sysmat_nnz_per_s": rows_rate,
         "fwdback_lor_voxel_per_s": fb,
         "stage_ms": med,
+        "kernels": kern,
         "roofline": roof,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": launches * args.steps,
+        "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         r, dt, cores, desc = cpu_sample(48)

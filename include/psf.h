@@ -250,6 +250,22 @@ int psf_em_ratio(const float *y, const float *yhat, float *ratio, int64_t n, voi
 int psf_em_update(float *x, const float *bp, const float *sens, float floor, int64_t n,
                   void *stream);
 
+/*
+ * Kernel timing -- instrumentation of the library, no counterpart in the
+ * paper.  While enabled, every kernel the library launches is bracketed by a
+ * pair of CUDA events recorded on the launching stream, and the device time
+ * between them is accumulated per kernel name.
+ * psf_timing_enable(on): waits for the pending event pairs, clears the
+ *   accumulators and switches recording on (on != 0) or off.
+ * psf_timing_read(i, name, launches, ms): waits for the pending event pairs
+ *   (synchronising with the GPU work they bracket) and returns kernel i of the
+ *   accumulators: its name (valid until the next psf_timing_enable), number of
+ *   launches and total milliseconds.  PSF_EINVAL past the last kernel.
+ * Timing adds two event records per launch; results are unaffected.
+ */
+int psf_timing_enable(int32_t on);
+int psf_timing_read(int32_t index, const char **name, int64_t *launches, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,7 +1,11 @@
 // Validation of the C-ABI descriptions, error strings, structured LOR sets
 // and the MLEM elementwise steps.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "psf_common.cuh"
 #include "psf_lorset.cuh"
@@ -196,9 +200,103 @@ int grid_for(int64_t n, int block) {
     return g < 1 ? 1 : (int)g;
 }
 
+// ---------------------------------------------------------- kernel timing
+namespace {
+struct TimerPending {
+    const char *name;
+    cudaEvent_t a, b;
+};
+struct TimerAcc {
+    std::string name;
+    int64_t launches;
+    double ms;
+};
+std::mutex g_tmu;
+std::atomic<bool> g_ton{false};
+std::vector<TimerPending> g_tpending;
+std::vector<TimerAcc> g_tacc;
+std::vector<cudaEvent_t> g_tpool;
+
+cudaEvent_t pool_event() {
+    if (!g_tpool.empty()) {
+        cudaEvent_t e = g_tpool.back();
+        g_tpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Fold the recorded pairs into the accumulators (caller holds the lock).
+int drain_pending() {
+    int rc = PSF_OK;
+    for (const TimerPending &p : g_tpending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.b) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) {
+            rc = PSF_ECUDA;
+        } else {
+            size_t k = 0;
+            while (k < g_tacc.size() && g_tacc[k].name != p.name) ++k;
+            if (k == g_tacc.size()) g_tacc.push_back({p.name, 0, 0.0});
+            g_tacc[k].launches += 1;
+            g_tacc[k].ms += ms;
+        }
+        g_tpool.push_back(p.a);
+        g_tpool.push_back(p.b);
+    }
+    g_tpending.clear();
+    return rc;
+}
+}  // namespace
+
+bool timing_on() { return g_ton.load(std::memory_order_relaxed); }
+
+cudaEvent_t timing_start(cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    cudaEvent_t e = pool_event();
+    if (e && cudaEventRecord(e, st) != cudaSuccess) {
+        g_tpool.push_back(e);
+        return nullptr;
+    }
+    return e;
+}
+
+void timing_stop(const char *name, cudaStream_t st, cudaEvent_t start) {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    cudaEvent_t e = pool_event();
+    if (!e || cudaEventRecord(e, st) != cudaSuccess) {
+        g_tpool.push_back(start);
+        if (e) g_tpool.push_back(e);
+        return;
+    }
+    g_tpending.push_back({name, start, e});
+}
+
 }  // namespace psf
 
 using namespace psf;
+
+extern "C" int psf_timing_enable(int32_t on) {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    const int rc = drain_pending();
+    g_tacc.clear();
+    g_ton.store(on != 0);
+    return rc;
+}
+
+extern "C" int psf_timing_read(int32_t index, const char **name, int64_t *launches, double *ms) {
+    if (!name || !launches || !ms) return PSF_EINVAL;
+    std::lock_guard<std::mutex> lock(g_tmu);
+    const int rc = drain_pending();
+    if (rc) return rc;
+    if (index < 0 || (size_t)index >= g_tacc.size()) return PSF_EINVAL;
+    *name = g_tacc[index].name.c_str();
+    *launches = g_tacc[index].launches;
+    *ms = g_tacc[index].ms;
+    return PSF_OK;
+}
 
 extern "C" const char *psf_strerror(int code) {
     switch (code) {
@@ -244,7 +342,10 @@ static int lorset_list(const psf_scanner *s, const psf_lor_set *set, int32_t *lo
     int64_t n = classes ? ls.ntp_cls * (2 * ls.Dm + 1) : ls.ntp * ls.nrp;
     if (n == 0) return PSF_OK;
     size_t sh = sizeof(int32_t) * (ls.Nt + ls.NR + 2);
-    lorset_list_kernel<<<grid_for(n, 256), 256, sh, as_stream(stream)>>>(ls, lors, classes);
+    {
+        PSF_TIMED("lorset_list_kernel", as_stream(stream));
+        lorset_list_kernel<<<grid_for(n, 256), 256, sh, as_stream(stream)>>>(ls, lors, classes);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }
@@ -263,7 +364,10 @@ extern "C" int psf_em_ratio(const float *y, const float *yhat, float *ratio, int
                             void *stream) {
     if (n < 0 || (n > 0 && (!y || !yhat || !ratio))) return PSF_EINVAL;
     if (n == 0) return PSF_OK;
-    em_ratio_kernel<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(y, yhat, ratio, n);
+    {
+        PSF_TIMED("em_ratio_kernel", as_stream(stream));
+        em_ratio_kernel<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(y, yhat, ratio, n);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }
@@ -272,7 +376,10 @@ extern "C" int psf_em_update(float *x, const float *bp, const float *sens, float
                              int64_t n, void *stream) {
     if (n < 0 || (n > 0 && (!x || !bp || !sens))) return PSF_EINVAL;
     if (n == 0) return PSF_OK;
-    em_update_kernel<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(x, bp, sens, floor_, n);
+    {
+        PSF_TIMED("em_update_kernel", as_stream(stream));
+        em_update_kernel<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(x, bp, sens, floor_, n);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }

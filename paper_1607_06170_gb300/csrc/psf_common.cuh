@@ -35,6 +35,27 @@ void set_cuda_error(cudaError_t e);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Kernel timing (psf_timing_enable): a scope around one launch records an
+// event before and one after it on the launching stream while timing is on.
+bool timing_on();
+cudaEvent_t timing_start(cudaStream_t st);
+void timing_stop(const char *name, cudaStream_t st, cudaEvent_t start);
+
+struct KTimer {
+    const char *name;
+    cudaStream_t st;
+    cudaEvent_t ev;
+    KTimer(const char *n, cudaStream_t s) : name(n), st(s), ev(nullptr) {
+        if (timing_on()) ev = timing_start(s);
+    }
+    ~KTimer() {
+        if (ev) timing_stop(name, st, ev);
+    }
+    KTimer(const KTimer &) = delete;
+    KTimer &operator=(const KTimer &) = delete;
+};
+#define PSF_TIMED(name, st) ::psf::KTimer psf_ktimer_(name, st)
+
 // Scanner constants as the kernels use them (passed by value).
 struct Scan {
     int R, Nb, Nt, NR;          // blocks, crystals/block, crystals/ring, rings

@@ -587,8 +587,11 @@ static int rows_fwd(const psf_matrix *m, const float *x, float *y, cudaStream_t 
     int grid = grid_for(m->n_rows * 32, PJ_T);
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
-        csr_fwd_kernel<VT><<<grid, PJ_T, 0, st>>>(m->n_rows, m->row_ptr, m->col,
-                                                   (const VT *)m->val, m->row_scale, x, y);
+        {
+            PSF_TIMED("csr_fwd_kernel", st);
+            csr_fwd_kernel<VT><<<grid, PJ_T, 0, st>>>(m->n_rows, m->row_ptr, m->col,
+                                                       (const VT *)m->val, m->row_scale, x, y);
+        }
         PSF_LAUNCHED();
         return PSF_OK;
     });
@@ -599,8 +602,11 @@ static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t
     int grid = grid_for(m->n_rows * 32, PJ_T);
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
-        csr_back_kernel<VT><<<grid, PJ_T, 0, st>>>(m->n_rows, m->row_ptr, m->col,
-                                                    (const VT *)m->val, m->row_scale, y, x);
+        {
+            PSF_TIMED("csr_back_kernel", st);
+            csr_back_kernel<VT><<<grid, PJ_T, 0, st>>>(m->n_rows, m->row_ptr, m->col,
+                                                        (const VT *)m->val, m->row_scale, y, x);
+        }
         PSF_LAUNCHED();
         return PSF_OK;
     });
@@ -613,7 +619,10 @@ static int launch_stencil2(const psf_matrix *m, const float *in, float *out, int
     const size_t shm = stencil2_smem_bytes(m->ls, WA);
     PSF_TRY(cudaFuncSetAttribute(stencil2_kernel<adjoint, WA, ST2_K>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    stencil2_kernel<adjoint, WA, ST2_K><<<grid, ST_T, shm, st>>>(m->ls, m->Wt, m->cls, in, out);
+    {
+        PSF_TIMED(adjoint ? "stencil2_kernel<adjoint>" : "stencil2_kernel<forward>", st);
+        stencil2_kernel<adjoint, WA, ST2_K><<<grid, ST_T, shm, st>>>(m->ls, m->Wt, m->cls, in, out);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }
@@ -624,7 +633,10 @@ static int launch_stencil3(const psf_matrix *m, const float *in, float *out, int
     const size_t shm = stencil3_smem_bytes(m->ls, WA);
     PSF_TRY(cudaFuncSetAttribute(stencil3_kernel<adjoint, WA>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    stencil3_kernel<adjoint, WA><<<grid, ST3_T, shm, st>>>(m->ls, m->Wt, m->cls, in, out);
+    {
+        PSF_TIMED(adjoint ? "stencil3_kernel<adjoint>" : "stencil3_kernel<forward>", st);
+        stencil3_kernel<adjoint, WA><<<grid, ST3_T, shm, st>>>(m->ls, m->Wt, m->cls, in, out);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }
@@ -665,11 +677,17 @@ static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoin
     if (adjoint) {
         PSF_TRY(cudaFuncSetAttribute(stencil_kernel<true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        stencil_kernel<true><<<(int)grid, ST_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, in, out);
+        {
+            PSF_TIMED("stencil_kernel<adjoint>", st);
+            stencil_kernel<true><<<(int)grid, ST_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, in, out);
+        }
     } else {
         PSF_TRY(cudaFuncSetAttribute(stencil_kernel<false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        stencil_kernel<false><<<(int)grid, ST_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, in, out);
+        {
+            PSF_TIMED("stencil_kernel<forward>", st);
+            stencil_kernel<false><<<(int)grid, ST_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, in, out);
+        }
     }
     PSF_LAUNCHED();
     return PSF_OK;

@@ -110,7 +110,10 @@ extern "C" int psf_response_build(const psf_scanner *scanner, const psf_table_de
     if (shm > 48 * 1024)
         PSF_TRY(cudaFuncSetAttribute(response_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)shm));
-    response_kernel<<<(int)blocks, threads, shm, as_stream(stream)>>>(sc, tb, table, eta);
+    {
+        PSF_TIMED("response_kernel", as_stream(stream));
+        response_kernel<<<(int)blocks, threads, shm, as_stream(stream)>>>(sc, tb, table, eta);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }

@@ -217,11 +217,20 @@ __global__ void __launch_bounds__(SCAN_T) scan_apply_kernel(int64_t *__restrict_
 static int inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t st) {
     if (n <= 0) return PSF_OK;
     int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
-    scan_tiles_kernel<<<(unsigned)nt, SCAN_T, 0, st>>>(x, n, tile_sums);
+    {
+        PSF_TIMED("scan_tiles_kernel", st);
+        scan_tiles_kernel<<<(unsigned)nt, SCAN_T, 0, st>>>(x, n, tile_sums);
+    }
     PSF_LAUNCHED();
-    scan_sums_kernel<<<1, SCAN_T, 0, st>>>(tile_sums, nt);
+    {
+        PSF_TIMED("scan_sums_kernel", st);
+        scan_sums_kernel<<<1, SCAN_T, 0, st>>>(tile_sums, nt);
+    }
     PSF_LAUNCHED();
-    scan_apply_kernel<<<(unsigned)nt, SCAN_T, 0, st>>>(x, n, tile_sums);
+    {
+        PSF_TIMED("scan_apply_kernel", st);
+        scan_apply_kernel<<<(unsigned)nt, SCAN_T, 0, st>>>(x, n, tile_sums);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }
@@ -370,7 +379,10 @@ static int geom_rows(const Scan &sc, const Img &im, const int32_t *lors, int64_t
     const size_t shm = sizeof(double) * 2 * sc.R;
     const int grid = sm_count() * 16;
     PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
-    g_count_kernel<<<grid, ROWS_THREADS, shm, st>>>(sc, im, lors, n, row_ptr + 1, status);
+    {
+        PSF_TIMED("g_count_kernel", st);
+        g_count_kernel<<<grid, ROWS_THREADS, shm, st>>>(sc, im, lors, n, row_ptr + 1, status);
+    }
     PSF_LAUNCHED();
     int rc = inclusive_scan(row_ptr + 1, n, tile_sums, st);
     if (rc) return rc;
@@ -388,8 +400,11 @@ static int geom_rows(const Scan &sc, const Img &im, const int32_t *lors, int64_t
                                  (int)fshm));
     int64_t fgrid = (n + FILL_WARPS * 32 - 1) / (FILL_WARPS * 32);
     if (fgrid > (int64_t)sm_count() * 3) fgrid = (int64_t)sm_count() * 3;
-    g_fill_kernel<<<(int)fgrid, FILL_WARPS * 32, fshm, st>>>(sc, im, lors, n, row_ptr, col, val,
-                                                            status);
+    {
+        PSF_TIMED("g_fill_kernel", st);
+        g_fill_kernel<<<(int)fgrid, FILL_WARPS * 32, fshm, st>>>(sc, im, lors, n, row_ptr, col, val,
+                                                                status);
+    }
     PSF_LAUNCHED();
     PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     PSF_TRY(cudaStreamSynchronize(st));
@@ -992,7 +1007,10 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
     ZAx *zt = reinterpret_cast<ZAx *>(reinterpret_cast<unsigned char *>(status) + 64);
     PSF_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     const size_t zshm = sizeof(int32_t) * (ls.Nt + ls.NR + 2);
-    zaxis_kernel<<<(int)((ls.nrp + 255) / 256), 256, zshm, st>>>(sc, im, ls, zt);
+    {
+        PSF_TIMED("zaxis_kernel", st);
+        zaxis_kernel<<<(int)((ls.nrp + 255) / 256), 256, zshm, st>>>(sc, im, ls, zt);
+    }
     PSF_LAUNCHED();
     const int grid_max = sm_count() * 2;
     const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
@@ -1001,7 +1019,10 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
                                  (int)shm));
     PSF_TRY(cudaFuncSetAttribute(set_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)shm));
-    set_count_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr + 1, status);
+    {
+        PSF_TIMED("set_count_kernel", st);
+        set_count_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr + 1, status);
+    }
     PSF_LAUNCHED();
     int rc = inclusive_scan(row_ptr + 1, n, tiles, st);
     if (rc) return rc;
@@ -1014,7 +1035,10 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
     if (h_status) return h_status;
     if (!col) return PSF_OK;
     if (nnz > capacity) return PSF_ECAPACITY;
-    set_fill_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr, col, val, status);
+    {
+        PSF_TIMED("set_fill_kernel", st);
+        set_fill_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr, col, val, status);
+    }
     PSF_LAUNCHED();
     PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     PSF_TRY(cudaStreamSynchronize(st));
@@ -1113,7 +1137,10 @@ extern "C" int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *imag
         rc = geom_rows(sc, im, lors, n_lors, gptr, gcol, gval, gnnz, &gnnz, tiles, status, st);
     if (!rc) {
         cudaMemsetAsync(map, 0xff, sizeof(int32_t) * nc * nc, st);
-        pair_map_kernel<<<grid_for(n_lors, 256), 256, 0, st>>>(lors, n_lors, nc, map);
+        {
+            PSF_TIMED("pair_map_kernel", st);
+            pair_map_kernel<<<grid_for(n_lors, 256), 256, 0, st>>>(lors, n_lors, nc, map);
+        }
         size_t shm = sizeof(float) * nvox + (sizeof(int32_t) + sizeof(float)) * 2 * E * E +
                      sizeof(int) * (MERGE_T / 32 + 2) + sizeof(float) * (MERGE_T / 32) + 16;
         int grid = sm_count() * 4;
@@ -1121,9 +1148,12 @@ extern "C" int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *imag
             using VT = std::remove_pointer_t<decltype(vptr)>;
             PSF_TRY(cudaFuncSetAttribute(merge_kernel<VT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-            merge_kernel<VT><<<grid, MERGE_T, shm, st>>>(
-                pass, sc, nvox, lors, n_lors, map, gptr, gcol, gval, spread, half_t, half_a,
-                pass == 0 ? row_ptr + 1 : row_ptr, col, vptr, row_scale);
+            {
+                PSF_TIMED("merge_kernel", st);
+                merge_kernel<VT><<<grid, MERGE_T, shm, st>>>(
+                    pass, sc, nvox, lors, n_lors, map, gptr, gcol, gval, spread, half_t, half_a,
+                    pass == 0 ? row_ptr + 1 : row_ptr, col, vptr, row_scale);
+            }
             PSF_LAUNCHED();
             return PSF_OK;
         };

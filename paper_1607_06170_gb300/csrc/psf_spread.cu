@@ -518,8 +518,11 @@ static int launch_spread_q(const Scan &sc, const Tab &tb, const float *T, const 
     if (per_sm < 1) per_sm = 1;
     const int64_t cap = (int64_t)sms * per_sm;
     const int64_t grid = n_lors < cap ? n_lors : cap;
-    spread_q_kernel<WT, WA><<<(int)grid, SP_THREADS, shm, st>>>(sc, tb, T, eta, lors, n_lors,
-                                                                norm, out);
+    {
+        PSF_TIMED("spread_q_kernel", st);
+        spread_q_kernel<WT, WA><<<(int)grid, SP_THREADS, shm, st>>>(sc, tb, T, eta, lors, n_lors,
+                                                                    norm, out);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }
@@ -559,8 +562,11 @@ extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *
     PSF_TRY(cudaGetDevice(&dev));
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int64_t grid = n_lors < (int64_t)sms * 8 ? n_lors : (int64_t)sms * 8;
-    spread_kernel<<<(int)grid, SP_THREADS, shm, as_stream(stream)>>>(
-        sc, tb, table, eta, lors, n_lors, half_t, half_a, norm, spread);
+    {
+        PSF_TIMED("spread_kernel", as_stream(stream));
+        spread_kernel<<<(int)grid, SP_THREADS, shm, as_stream(stream)>>>(
+            sc, tb, table, eta, lors, n_lors, half_t, half_a, norm, spread);
+    }
     PSF_LAUNCHED();
     return PSF_OK;
 }

@@ -26,7 +26,7 @@ FUNCTIONS = [
     "psf_lor_set_size", "psf_lor_set_list", "psf_lor_set_classes", "psf_sysmat_rows",
     "psf_sysmat_rows_set", "psf_sysmat_rows_set_noalloc",
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
-    "psf_back", "psf_em_ratio", "psf_em_update",
+    "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
 ]
 
 
@@ -81,6 +81,8 @@ _SIGS = {
     "psf_back": (C.c_int, [_P, _P, _P, _P]),
     "psf_em_ratio": (C.c_int, [_P, _P, _P, _I64, _P]),
     "psf_em_update": (C.c_int, [_P, _P, _P, C.c_float, _I64, _P]),
+    "psf_timing_enable": (C.c_int, [_I32]),
+    "psf_timing_read": (C.c_int, [_I32, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -105,6 +107,22 @@ def lib() -> C.CDLL:
 
 def strerror(code: int) -> str:
     return lib().psf_strerror(int(code)).decode()
+
+
+def timing_enable(on: bool = True):
+    """Clear the kernel-time accumulators and switch event timing on or off."""
+    _ok(lib().psf_timing_enable(1 if on else 0), "psf_timing_enable")
+
+
+def timing_read() -> dict:
+    """{kernel name: (launches, total ms)} accumulated since timing_enable()."""
+    out = {}
+    name, n, ms = C.c_char_p(), C.c_int64(), C.c_double()
+    i = 0
+    while lib().psf_timing_read(i, C.byref(name), C.byref(n), C.byref(ms)) == 0:
+        out[name.value.decode()] = (n.value, ms.value)
+        i += 1
+    return out
 
 
 def _ok(rc: int, where: str):
