@@ -100,14 +100,15 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU leg
-def cpu_sample(n_tclass: int = 2):
+def cpu_sample(n_tclass: int = 2, batch: int = 48):
     """Time the FP64 oracle on a bounded sample of the workload.
 
     The sample is n_tclass transaxial spread classes with all their members:
     every rotation of each class's crystal pair by whole blocks (24) times all
     1,372 ring pairs, and the spreads of those classes for all 31 ring
-    differences.  The oracle builds the table, the spreads (one per class, the
-    same amortisation as the full job), the chord rows, and projects forward and
+    differences.  The oracle builds the table once, then, `batch` classes at a
+    time (bounded host memory), the spreads (one per class, the same
+    amortisation as the full job), the chord rows, and projects forward and
     back with them.  Returns (nnz/s, seconds, threads, description)."""
     import numpy as np
 
@@ -124,33 +125,39 @@ def cpu_sample(n_tclass: int = 2):
     # classes at evenly spaced quantiles of the list (central to oblique chords)
     pick = cls[((np.arange(n_tclass) + 0.5) / n_tclass * len(cls)).astype(int)]
     rp = I.ring_pairs(s, w["lors"]["max_ring_diff"]).astype(np.int64)
-    lors = []
-    for a, b in pick:
-        for k in range(R):
-            ta, tb_ = (a + k * nb) % nt, (b + k * nb) % nt
-            lo, hi = min(ta, tb_), max(ta, tb_)
-            ra_, rb_ = (rp[:, 0], rp[:, 1]) if ta < tb_ else (rp[:, 1], rp[:, 0])
-            lors.append(np.stack([ra_ * nt + lo, rb_ * nt + hi], 1))
-    lors = np.concatenate(lors).astype(np.int32)
     Dm = w["lors"]["max_ring_diff"]
-    reps = []
-    for a, b in pick:
-        for d in range(-Dm, Dm + 1):
-            ra = max(0, -d)
-            reps.append((ra * nt + a, (ra + d) * nt + b))
-    reps = np.array(reps, dtype=np.int32)
     x = I.phantom_cylinder(im, 1).reshape(-1).astype(np.float64)
     nv = x.size
+    n_lors = nnz = n_reps = 0
+    dt = 0.0
     t0 = time.perf_counter()
     T, _ = oracle.table_build(s, t)
-    oracle.spread(s, t, T, reps, Wt, Wa)
-    G = oracle.rows_geom(s, im, lors)
-    y = oracle.csr_fwd(G, x)
-    oracle.csr_back(G, y, nv)
-    dt = time.perf_counter() - t0
-    nnz = int(G[0][-1])
-    desc = (f"{len(lors)} LORs ({n_tclass} transaxial classes x {R} rotations x {len(rp)} ring "
-            f"pairs, {nnz} nnz) + {len(reps)} class spreads + table; rows, forward, back")
+    dt += time.perf_counter() - t0
+    for c0 in range(0, len(pick), batch):
+        lors, reps = [], []
+        for a, b in pick[c0:c0 + batch]:
+            for k in range(R):
+                ta, tb_ = (a + k * nb) % nt, (b + k * nb) % nt
+                lo, hi = min(ta, tb_), max(ta, tb_)
+                ra_, rb_ = (rp[:, 0], rp[:, 1]) if ta < tb_ else (rp[:, 1], rp[:, 0])
+                lors.append(np.stack([ra_ * nt + lo, rb_ * nt + hi], 1))
+            for d in range(-Dm, Dm + 1):
+                ra = max(0, -d)
+                reps.append((ra * nt + a, (ra + d) * nt + b))
+        lors = np.concatenate(lors).astype(np.int32)
+        reps = np.array(reps, dtype=np.int32)
+        t0 = time.perf_counter()
+        oracle.spread(s, t, T, reps, Wt, Wa)
+        G = oracle.rows_geom(s, im, lors)
+        y = oracle.csr_fwd(G, x)
+        oracle.csr_back(G, y, nv)
+        dt += time.perf_counter() - t0
+        n_lors += len(lors)
+        nnz += int(G[0][-1])
+        n_reps += len(reps)
+        del G, y
+    desc = (f"{n_lors} LORs ({n_tclass} transaxial classes x {R} rotations x {len(rp)} ring "
+            f"pairs, {nnz} nnz) + {n_reps} class spreads + table; rows, forward, back")
     return nnz / dt, dt, oracle.threads(), desc
 
 
@@ -424,7 +431,7 @@ def run_gpu(args):
         "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, dt, cores, desc = cpu_sample(48)
+        r, dt, cores, desc = cpu_sample(480)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
     if rank == 0:
