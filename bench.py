@@ -222,7 +222,8 @@ def stencil_pairs(s, ls, Wt, Wa):
 def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
     if name == "set_fill_kernel":  # writes column + chord, reads row_ptr
         return "hbm", 8.0 * nnz + 8.0 * n_lors, "GB/s"
-    if name in ("csr_fwd_kernel", "csr_back_kernel"):  # column + value, row_ptr, LOR value, image
+    if name in ("csr_fwd_kernel", "csr_back_kernel"):
+        # column + value, row_ptr, LOR value, image
         return "hbm", 8.0 * nnz + 12.0 * n_lors + 4.0 * nv, "GB/s"
     if name == "spread_q_kernel":  # one FMA per sub-LOR and quadrant entry pair
         nsub = (t["n_sub_t"] * t["n_sub_a"]) ** 2

@@ -48,6 +48,23 @@ __device__ __forceinline__ float ld_val<__half>(const __half *v, int64_t j) {
 
 constexpr int PJ_T = 256;
 
+// Streamed (read-once) matrix entries: evict-first, so the image keeps L2.
+template <typename VT>
+__device__ __forceinline__ float ld_val_cs(const VT *v, int64_t j);
+template <>
+__device__ __forceinline__ float ld_val_cs<float>(const float *v, int64_t j) { return __ldcs(v + j); }
+template <>
+__device__ __forceinline__ float ld_val_cs<__nv_bfloat16>(const __nv_bfloat16 *v, int64_t j) {
+    return __bfloat162float(v[j]);
+}
+template <>
+__device__ __forceinline__ float ld_val_cs<__half>(const __half *v, int64_t j) {
+    return __half2float(v[j]);
+}
+
+// Warp per row.  A lane issues the column and value loads of up to four of
+// its row entries before the image gathers that depend on them, so a row of
+// up to 128 entries costs one round trip for each.
 template <typename VT>
 __global__ void __launch_bounds__(PJ_T) csr_fwd_kernel(int64_t n, const int64_t *__restrict__ ptr,
                                                       const int32_t *__restrict__ col,
@@ -55,12 +72,25 @@ __global__ void __launch_bounds__(PJ_T) csr_fwd_kernel(int64_t n, const int64_t 
                                                       const float *__restrict__ scale,
                                                       const float *__restrict__ x,
                                                       float *__restrict__ y) {
+    constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     const int64_t wpb = PJ_T / 32;
     for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < n; r += gridDim.x * wpb) {
         const int64_t j0 = ptr[r], j1 = ptr[r + 1];
         float acc = 0.0f;
-        for (int64_t j = j0 + lane; j < j1; j += 32) acc = fmaf(ld_val(val, j), __ldg(x + col[j]), acc);
+        for (int64_t j = j0 + lane; j < j1; j += 32 * U) {
+            int c[U];
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t jj = j + 32 * u;
+                c[u] = jj < j1 ? __ldcs(col + jj) : 0;
+                v[u] = jj < j1 ? ld_val_cs(val, jj) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j + 32 * u < j1) acc = fmaf(v[u], __ldg(x + c[u]), acc);
+        }
         acc = warp_sum_f(acc);
         if (lane == 0) y[r] = scale ? acc * scale[r] : acc;
     }
@@ -80,7 +110,8 @@ __global__ void __launch_bounds__(PJ_T) csr_back_kernel(int64_t n, const int64_t
         if (scale) yr *= scale[r];
         if (yr == 0.0f) continue;
         const int64_t j0 = ptr[r], j1 = ptr[r + 1];
-        for (int64_t j = j0 + lane; j < j1; j += 32) atomicAdd(x + col[j], ld_val(val, j) * yr);
+        for (int64_t j = j0 + lane; j < j1; j += 32)
+            atomicAdd(x + __ldcs(col + j), ld_val_cs(val, j) * yr);
     }
 }
 
