@@ -29,7 +29,9 @@ def assert_close(got, ref, rtol, atol, what=""):
         raise AssertionError(
             f"{what}: {bad.sum()} / {bad.size} outside tolerance; first at {i}: "
             f"got {got.reshape(-1)[i]}, ref {ref.reshape(-1)[i]}")
-    return float(np.max(err / (np.abs(ref) + atol))) if err.size else 0.0
+    den = np.abs(ref) + atol
+    ratio = np.divide(err, den, out=np.zeros_like(err), where=den > 0)  # err is 0 where den is
+    return float(np.max(ratio)) if err.size else 0.0
 
 
 def csr_keys(ptr, col, ncol):
