@@ -237,6 +237,25 @@ int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner, const psf_l
 
 int psf_matrix_destroy(psf_matrix *m);
 
+/*
+ * Launch tuning of the stored-row projectors (batching of rows of uneven
+ * length, no counterpart in the paper).  Times, with CUDA events on `stream`,
+ * a forward and a back projection of all-ones vectors for the grid-stride
+ * kernels and for the persistent work-queue kernels (each warp takes the next
+ * chunk of rows from a counter) at chunk in {1,2,4,8,16,32} rows and
+ * {128,256,512} threads per CTA, and keeps the fastest for psf_forward /
+ * psf_back of this plan.  chunk_out / threads_out (host, may be NULL) receive
+ * the choice (chunk 0: grid-stride kernels).  Synchronises; allocates a
+ * temporary image-sized buffer; call it outside stream capture, after which
+ * the projections of the plan can be captured in a CUDA graph.
+ */
+int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out, void *stream);
+
+/* Set that launch explicitly: chunk 0 selects the grid-stride kernels; chunk
+ * in [1, 2^20] rows per take with threads a multiple of 32 in [32, 1024]
+ * selects the work-queue kernels.  PSF_EINVAL otherwise. */
+int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads);
+
 /* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]). */
 int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream);
 

@@ -29,6 +29,10 @@ struct psf_matrix {
     int Wt, Wa, E;
     const float *cls;
     float *p, *q;  // plan-owned scratch [n_rows]
+    // stored-row projectors: persistent work-queue launch when wq_chunk > 0
+    // (chosen by psf_matrix_autotune), else the grid-stride kernels
+    int wq_chunk, wq_threads;
+    unsigned long long *queue;  // plan-owned row counter
 };
 
 namespace psf {
@@ -113,6 +117,80 @@ __global__ void __launch_bounds__(PJ_T) csr_back_kernel(int64_t n, const int64_t
         for (int64_t j = j0 + lane; j < j1; j += 32)
             atomicAdd(x + __ldcs(col + j), ld_val_cs(val, j) * yr);
     }
+}
+
+// Persistent forms for rows of uneven length: the grid is sized to the
+// resident CTAs and each warp takes the next `chunk` rows from a row counter
+// (the work queue), so long and short rows balance across warps without a
+// launch per batch.  Per row the arithmetic is the grid-stride kernels'.
+template <typename VT>
+__device__ __forceinline__ float csr_row_dot(const int64_t *__restrict__ ptr,
+                                             const int32_t *__restrict__ col,
+                                             const VT *__restrict__ val,
+                                             const float *__restrict__ x, int64_t r, int lane) {
+    constexpr int U = 4;
+    const int64_t j0 = ptr[r], j1 = ptr[r + 1];
+    float acc = 0.0f;
+    for (int64_t j = j0 + lane; j < j1; j += 32 * U) {
+        int c[U];
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t jj = j + 32 * u;
+            c[u] = jj < j1 ? __ldcs(col + jj) : 0;
+            v[u] = jj < j1 ? ld_val_cs(val, jj) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (j + 32 * u < j1) acc = fmaf(v[u], __ldg(x + c[u]), acc);
+    }
+    return warp_sum_f(acc);
+}
+
+__device__ __forceinline__ int64_t wq_take(unsigned long long *queue, int chunk, int lane) {
+    unsigned long long r0 = 0;
+    if (lane == 0) r0 = atomicAdd(queue, (unsigned long long)chunk);
+    return (int64_t)__shfl_sync(0xffffffffu, r0, 0);
+}
+
+template <typename VT>
+__global__ void csr_fwd_wq_kernel(int64_t n, const int64_t *__restrict__ ptr,
+                                  const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                  const float *__restrict__ scale, const float *__restrict__ x,
+                                  float *__restrict__ y, unsigned long long *queue, int chunk) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r0 = wq_take(queue, chunk, lane); r0 < n; r0 = wq_take(queue, chunk, lane)) {
+        const int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
+        for (int64_t r = r0; r < r1; ++r) {
+            const float acc = csr_row_dot(ptr, col, val, x, r, lane);
+            if (lane == 0) y[r] = scale ? acc * scale[r] : acc;
+        }
+    }
+}
+
+template <typename VT>
+__global__ void csr_back_wq_kernel(int64_t n, const int64_t *__restrict__ ptr,
+                                   const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                   const float *__restrict__ scale, const float *__restrict__ y,
+                                   float *__restrict__ x, unsigned long long *queue, int chunk) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r0 = wq_take(queue, chunk, lane); r0 < n; r0 = wq_take(queue, chunk, lane)) {
+        const int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
+        for (int64_t r = r0; r < r1; ++r) {
+            float yr = y[r];
+            if (scale) yr *= scale[r];
+            if (yr == 0.0f) continue;
+            const int64_t j0 = ptr[r], j1 = ptr[r + 1];
+            for (int64_t j = j0 + lane; j < j1; j += 32)
+                atomicAdd(x + __ldcs(col + j), ld_val_cs(val, j) * yr);
+        }
+    }
+}
+
+__global__ void fill_kernel(float *__restrict__ a, float v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
 }
 
 // Tiled S and S^T.  The window of a LOR splits into 49 transaxial offsets
@@ -614,11 +692,34 @@ static int dispatch_dtype(int dtype, F &&f) {
     return f((const __half *)nullptr);
 }
 
-static int rows_fwd(const psf_matrix *m, const float *x, float *y, cudaStream_t st) {
-    int grid = grid_for(m->n_rows * 32, PJ_T);
+// Resident CTAs of a work-queue kernel at `threads` per CTA (whole grid).
+template <typename K>
+static int wq_grid(K kernel, int threads, int *grid) {
+    int dev = 0, sms = 148, per_sm = 0;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PSF_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
+    *grid = sms * (per_sm > 0 ? per_sm : 1);
+    return PSF_OK;
+}
+
+static int rows_fwd_with(const psf_matrix *m, const float *x, float *y, int chunk, int threads,
+                         cudaStream_t st) {
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
-        {
+        if (chunk > 0) {
+            int grid = 0;
+            int rc = wq_grid(csr_fwd_wq_kernel<VT>, threads, &grid);
+            if (rc) return rc;
+            PSF_TRY(cudaMemsetAsync(m->queue, 0, sizeof(unsigned long long), st));
+            {
+                PSF_TIMED("csr_fwd_wq_kernel", st);
+                csr_fwd_wq_kernel<VT><<<grid, threads, 0, st>>>(
+                    m->n_rows, m->row_ptr, m->col, (const VT *)m->val, m->row_scale, x, y,
+                    m->queue, chunk);
+            }
+        } else {
+            const int grid = grid_for(m->n_rows * 32, PJ_T);
             PSF_TIMED("csr_fwd_kernel", st);
             csr_fwd_kernel<VT><<<grid, PJ_T, 0, st>>>(m->n_rows, m->row_ptr, m->col,
                                                        (const VT *)m->val, m->row_scale, x, y);
@@ -628,12 +729,24 @@ static int rows_fwd(const psf_matrix *m, const float *x, float *y, cudaStream_t 
     });
 }
 
-static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t st) {
+static int rows_back_with(const psf_matrix *m, const float *y, float *x, int chunk, int threads,
+                          cudaStream_t st) {
     PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
-    int grid = grid_for(m->n_rows * 32, PJ_T);
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
-        {
+        if (chunk > 0) {
+            int grid = 0;
+            int rc = wq_grid(csr_back_wq_kernel<VT>, threads, &grid);
+            if (rc) return rc;
+            PSF_TRY(cudaMemsetAsync(m->queue + 1, 0, sizeof(unsigned long long), st));
+            {
+                PSF_TIMED("csr_back_wq_kernel", st);
+                csr_back_wq_kernel<VT><<<grid, threads, 0, st>>>(
+                    m->n_rows, m->row_ptr, m->col, (const VT *)m->val, m->row_scale, y, x,
+                    m->queue + 1, chunk);
+            }
+        } else {
+            const int grid = grid_for(m->n_rows * 32, PJ_T);
             PSF_TIMED("csr_back_kernel", st);
             csr_back_kernel<VT><<<grid, PJ_T, 0, st>>>(m->n_rows, m->row_ptr, m->col,
                                                         (const VT *)m->val, m->row_scale, y, x);
@@ -641,6 +754,14 @@ static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t
         PSF_LAUNCHED();
         return PSF_OK;
     });
+}
+
+static int rows_fwd(const psf_matrix *m, const float *x, float *y, cudaStream_t st) {
+    return rows_fwd_with(m, x, y, m->wq_chunk, m->wq_threads, st);
+}
+
+static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t st) {
+    return rows_back_with(m, y, x, m->wq_chunk, m->wq_threads, st);
 }
 
 // S (adjoint == false) or S^T on LOR-space vectors of a factored plan.
@@ -746,10 +867,18 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->row_scale = row_scale;
     m->factored = false;
     m->p = m->q = nullptr;
+    m->wq_chunk = 0;
+    m->wq_threads = 0;
+    m->queue = nullptr;
+    if (cudaMalloc(&m->queue, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        delete m;
+        return PSF_ECUDA;
+    }
     if (n_rows > 0) {
         if (cudaMalloc(&m->p, sizeof(float) * n_rows) != cudaSuccess ||
             cudaMalloc(&m->q, sizeof(float) * n_rows) != cudaSuccess) {
             cudaFree(m->p);
+            cudaFree(m->queue);
             delete m;
             return PSF_ECUDA;
         }
@@ -782,6 +911,7 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
     if (!m) return PSF_EINVAL;
     cudaFree(m->p);
     cudaFree(m->q);
+    cudaFree(m->queue);
     delete m;
     return PSF_OK;
 }
@@ -807,4 +937,72 @@ extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *str
     int rc = stencil(m, y, m->q, true, st);
     if (rc) return rc;
     return rows_back(m, m->q, x, st);
+}
+
+extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out,
+                                   void *stream) {
+    if (!m) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    if (m->n_rows == 0) {
+        m->wq_chunk = 0;
+        m->wq_threads = 0;
+    } else {
+        // candidates: the grid-stride kernels (chunk 0) and the work queue at
+        // every (rows per take, threads per CTA) pair; each is timed on a
+        // forward + back of all-ones vectors, the fastest kept
+        static const int chunks[] = {0, 1, 2, 4, 8, 16, 32};
+        static const int threads[] = {128, 256, 512};
+        float *x = nullptr;
+        PSF_TRY(cudaMallocAsync(&x, sizeof(float) * m->n_cols, st));
+        float *y = m->p, *xb = x;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int rc = PSF_OK;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            rc = PSF_ECUDA;
+        float best = 1e30f;
+        int bc = 0, bt = 0;
+        if (!rc) {
+            fill_kernel<<<grid_for(m->n_cols, 256), 256, 0, st>>>(x, 1.0f, m->n_cols);
+            fill_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(y, 1.0f, m->n_rows);
+            if (cudaGetLastError() != cudaSuccess) rc = PSF_ECUDA;
+        }
+        for (int c : chunks) {
+            for (int t : threads) {
+                if (rc) break;
+                if (c == 0 && t != PJ_T) continue;
+                for (int rep = 0; rep < 3 && !rc; ++rep) {  // first repetition warms up
+                    if (cudaEventRecord(e0, st) != cudaSuccess) rc = PSF_ECUDA;
+                    if (!rc) rc = rows_fwd_with(m, x, y, c, t, st);
+                    if (!rc) rc = rows_back_with(m, y, xb, c, t, st);
+                    float ms = 0.0f;
+                    if (!rc && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                        rc = PSF_ECUDA;
+                    if (!rc && rep > 0 && ms < best) {
+                        best = ms;
+                        bc = c;
+                        bt = t;
+                    }
+                }
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFreeAsync(x, st);
+        if (rc) return rc;
+        m->wq_chunk = bc;
+        m->wq_threads = bt;
+    }
+    if (chunk_out) *chunk_out = m->wq_chunk;
+    if (threads_out) *threads_out = m->wq_threads;
+    return PSF_OK;
+}
+
+extern "C" int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads) {
+    if (!m || chunk < 0 || chunk > (1 << 20)) return PSF_EINVAL;
+    if (chunk > 0 && (threads < 32 || threads > 1024 || threads % 32)) return PSF_EINVAL;
+    m->wq_chunk = chunk;
+    m->wq_threads = chunk > 0 ? threads : 0;
+    return PSF_OK;
 }

@@ -27,6 +27,7 @@ FUNCTIONS = [
     "psf_sysmat_rows_set", "psf_sysmat_rows_set_noalloc",
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
+    "psf_matrix_autotune", "psf_matrix_set_launch",
 ]
 
 
@@ -83,6 +84,8 @@ _SIGS = {
     "psf_em_update": (C.c_int, [_P, _P, _P, C.c_float, _I64, _P]),
     "psf_timing_enable": (C.c_int, [_I32]),
     "psf_timing_read": (C.c_int, [_I32, _P, _P, _P]),
+    "psf_matrix_autotune": (C.c_int, [_P, _P, _P, _P]),
+    "psf_matrix_set_launch": (C.c_int, [_P, _I32, _I32]),
 }
 
 _lock = threading.Lock()
@@ -291,6 +294,22 @@ class Matrix:
         s, l = scanner(sc), lor_set(ls)
         _ok(lib().psf_matrix_set_spread(self._h, C.byref(s), C.byref(l), half_t, half_a,
                                         _ptr(class_spread)), "psf_matrix_set_spread")
+        return self
+
+    def autotune(self):
+        """Pick the stored-row projector launch (work-queue chunk, CTA size)
+        by timing the candidates; returns (chunk, threads), chunk 0 = the
+        grid-stride kernels."""
+        c, t = C.c_int32(), C.c_int32()
+        _ok(lib().psf_matrix_autotune(self._h, C.byref(c), C.byref(t), _stream()),
+            "psf_matrix_autotune")
+        return c.value, t.value
+
+    def set_launch(self, chunk: int, threads: int = 256):
+        """Stored-row projector launch: chunk 0 = grid-stride kernels, else the
+        work-queue kernels taking `chunk` rows per warp."""
+        _ok(lib().psf_matrix_set_launch(self._h, int(chunk), int(threads)),
+            "psf_matrix_set_launch")
         return self
 
     def forward(self, x, out=None):

@@ -31,12 +31,14 @@ def sensitivity(matrix, n_rows: int, device="cuda"):
     return matrix.back(ones)
 
 
-def mlem(matrix, y, iters: int = 10, x0=None, sens=None):
+def mlem(matrix, y, iters: int = 10, x0=None, sens=None, graph: bool = False):
     """MLEM (Sec. 3): sens = A^T 1; x <- x * A^T(y / A x) / sens.
 
     Voxels with sens < 1e-12 * max(sens) are held at zero, and 0/0 in the
     ratio is zero.  All steps are library kernels (psf_forward, psf_em_ratio,
-    psf_back, psf_em_update).
+    psf_back, psf_em_update).  With graph=True the `iters` iterations are
+    captured once in a CUDA graph (after one uncaptured iteration on a copy,
+    which sets up the kernels' launch attributes) and replayed as one launch.
     """
     if sens is None:
         sens = sensitivity(matrix, y.numel(), y.device)
@@ -49,9 +51,22 @@ def mlem(matrix, y, iters: int = 10, x0=None, sens=None):
     yhat = torch.empty_like(y)
     ratio = torch.empty_like(y)
     bp = torch.empty_like(sens)
-    for _ in range(iters):
-        matrix.forward(x, out=yhat)
+
+    def iteration(xi):
+        matrix.forward(xi, out=yhat)
         psf.em_ratio(y, yhat, out=ratio)
         matrix.back(ratio, out=bp)
-        psf.em_update(x, bp, sens, floor)
+        psf.em_update(xi, bp, sens, floor)
+
+    if not graph:
+        for _ in range(iters):
+            iteration(x)
+        return x
+    iteration(x.clone())  # uncaptured warm-up on a scratch copy
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        for _ in range(iters):
+            iteration(x)
+    g.replay()
     return x
