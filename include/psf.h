@@ -244,7 +244,10 @@ int psf_matrix_destroy(psf_matrix *m);
  * kernels and for the persistent work-queue kernels (each warp takes the next
  * chunk of rows from a counter) at chunk in {1,2,4,8,16,32} rows and
  * {128,256,512} threads per CTA, and keeps the fastest for psf_forward /
- * psf_back of this plan.  chunk_out / threads_out (host, may be NULL) receive
+ * psf_back of this plan; for a factored plan it also times the two forms of
+ * the LOR-space spread stencil in each direction on all-ones vectors and keeps
+ * the faster (call it after psf_matrix_set_spread).  chunk_out / threads_out
+ * (host, may be NULL) receive
  * the choice (chunk 0: grid-stride kernels).  Synchronises; allocates a
  * temporary image-sized buffer; call it outside stream capture, after which
  * the projections of the plan can be captured in a CUDA graph.

@@ -33,6 +33,9 @@ struct psf_matrix {
     // (chosen by psf_matrix_autotune), else the grid-stride kernels
     int wq_chunk, wq_threads;
     unsigned long long *queue;  // plan-owned row counter
+    // factored plans: stencil form per direction (0: default order, 3 or 4:
+    // that form), chosen by psf_matrix_autotune
+    int st_form[2];
 };
 
 namespace psf {
@@ -539,8 +542,8 @@ __device__ __forceinline__ int st3_next(const LorSet &ls, const int32_t *tp_star
 }
 
 // Issue (without waiting) the copies of one partner into a buffer.
-template <int WA>
-__device__ __forceinline__ void st3_stage(const LorSet &ls, const St3Shape &S, const short2 *rp,
+template <int WA, class Shape>
+__device__ __forceinline__ void st3_stage(const LorSet &ls, const Shape &S, const short2 *rp,
                                           const St3Partner &P, int Wt,
                                           const float *__restrict__ w,
                                           const float *__restrict__ in, float *buf) {
@@ -548,19 +551,33 @@ __device__ __forceinline__ void st3_stage(const LorSet &ls, const St3Shape &S, c
     const int Dm = ls.Dm, nd = S.nd, PRp = S.PRp, nrp = (int)ls.nrp;
     const int E = (2 * Wt + 1) * W2a;
     float *plane = buf, *w3 = buf + S.plane_f;
-    for (int j = threadIdx.x; j < nrp; j += ST3_T) {
+    for (int j = threadIdx.x; j < nrp; j += blockDim.x) {
         const short2 rr = rp[j];
         const int ra = P.sw ? rr.y : rr.x, rb = P.sw ? rr.x : rr.y;
         cp_async4(plane + (rb - ra + Dm) * PRp + (ra + WA), in + P.prow + j);
     }
+    // weights: one (difference, o1) pair per step, its W2a o2 entries as one
+    // run -- window entry e1 = (dt1 + Wt) W2a + L1 of the end on a's side,
+    // e2 = (dt2 + Wt) W2a + L2 of the other (swapped roles when the partner's
+    // first crystal sits on b's side); slot (d, e = L1 - L2, L1)
+    // (consecutive threads take the index that is contiguous in the class
+    // table, so a warp's copies read runs of consecutive words)
     const float *wc = w + (int64_t)P.cls * nd * E * E;
-    for (int i = threadIdx.x; i < nd * W2a * W2a; i += ST3_T) {
-        const int d = i / (W2a * W2a) - Dm, L1 = (i / W2a) % W2a, L2 = i % W2a;
-        const int e_a = (P.dt1 + Wt) * W2a + L1, e_b = (P.dt2 + Wt) * W2a + L2;
-        const int e1 = P.wsw ? e_b : e_a, e2 = P.wsw ? e_a : e_b;
-        const int dc = P.wsw ? -d : d;
-        cp_async4(w3 + ((d + Dm) * NE + (L1 - L2) + 2 * WA) * 8 + L1,
-                  wc + (int64_t)(dc + Dm) * E * E + e1 * E + e2);
+    const int ea0 = (P.dt1 + Wt) * W2a, eb0 = (P.dt2 + Wt) * W2a;
+    for (int i = threadIdx.x; i < nd * W2a; i += blockDim.x) {
+        const int d = i / W2a - Dm, u = i % W2a;
+        const float *src = wc + (int64_t)((P.wsw ? -d : d) + Dm) * E * E;
+        if (!P.wsw) {  // entry (ea0 + L1) * E + eb0 + L2: thread over L2, run over L1
+            const float *s0 = src + ea0 * E + eb0 + u;
+            float *d0 = w3 + ((d + Dm) * NE - u + 2 * WA) * 8;
+#pragma unroll
+            for (int L1 = 0; L1 < W2a; ++L1) cp_async4(d0 + 9 * L1, s0 + L1 * E);
+        } else {  // entry (eb0 + L2) * E + ea0 + L1: thread over L1, run over L2
+            const float *s0 = src + eb0 * E + ea0 + u;
+            float *d0 = w3 + ((d + Dm) * NE + u + 2 * WA) * 8 + u;
+#pragma unroll
+            for (int L2 = 0; L2 < W2a; ++L2) cp_async4(d0 - 8 * L2, s0 + L2 * E);
+        }
     }
     cp_async_commit();
 }
@@ -659,6 +676,147 @@ __global__ void __launch_bounds__(ST3_T, 4) stencil3_kernel(LorSet ls, int Wt,
                 }
             }
             __syncthreads();  // this buffer is free for the partner after next
+            cur ^= 1;
+            dt = nxt;
+            P = Pn;
+        }
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int ra = r0 + k, dl = dl0 + m, rb = ra + dl;
+                    if (ra < NR && dl <= Dm && rb >= 0 && rb < NR)
+                        out[T * nrp + rp_start[ra] + (rb - ls.rp_lo(ra))] = acc[m][k];
+                }
+        }
+    }
+}
+
+// Fourth form, for fewer distinct shared-memory addresses per warp.  Each
+// half-warp owns one group of M = 8 consecutive ring differences and its 16
+// lanes the strips of K = 4 rings, so a weight load has two addresses per
+// warp (one per half) and a plane load is 8 bytes per lane on consecutive
+// rows; a thread does K x M = 32 products per partner value pair it loads.
+// Staging and the partner walk are those of the third form.
+constexpr int ST4_K = 4, ST4_M = 8;
+
+struct St4Shape {
+    int nd, nstrip, nqg, threads, PRp, ne;
+    int plane_f, w_f, buf_f;
+};
+
+__host__ __device__ inline St4Shape st4_shape(const LorSet &ls, int WA) {
+    St4Shape s;
+    s.nd = 2 * ls.Dm + 1;
+    s.nstrip = (ls.NR + ST4_K - 1) / ST4_K;
+    s.nqg = (s.nd + ST4_M - 1) / ST4_M;
+    s.threads = 32 * ((s.nqg + 1) / 2);
+    s.PRp = s.nstrip * ST4_K + 2 * WA;  // rows = ring + WA; a strip reads K + 2 WA rows
+    s.ne = 4 * WA + 1;
+    s.plane_f = (s.nd * s.PRp + 3) / 4 * 4;
+    s.w_f = s.nd * s.ne * 8;
+    s.buf_f = s.plane_f + s.w_f;
+    return s;
+}
+
+static size_t stencil4_smem_bytes(const LorSet &ls, int WA) {
+    const St4Shape s = st4_shape(ls, WA);
+    return sizeof(float) * 2 * (size_t)s.buf_f + sizeof(short2) * ls.nrp +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 32;
+}
+
+template <bool adjoint, int WA>
+__global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
+                                                        const float *__restrict__ w,
+                                                        const float *__restrict__ in,
+                                                        float *__restrict__ out) {
+    constexpr int NE = 4 * WA + 1, K = ST4_K, M = ST4_M, NV = K + 2 * WA;
+    static_assert(NV % 2 == 0, "8-byte plane loads");
+    extern __shared__ __align__(16) unsigned char raw[];
+    const St4Shape S = st4_shape(ls, WA);
+    const int Dm = ls.Dm, NR = ls.NR, PRp = S.PRp;
+    const int nwin = (2 * Wt + 1) * (2 * Wt + 1);
+    float *bufs = reinterpret_cast<float *>(raw);  // [2][buf_f]
+    short2 *rp = reinterpret_cast<short2 *>(bufs + 2 * S.buf_f);
+    int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    const int t = threadIdx.x, lane = t & 31;
+    for (int i = t; i < 2 * S.buf_f; i += blockDim.x) bufs[i] = 0.0f;
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    for (int j = t; j < ls.nrp; j += blockDim.x) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rp[j] = make_short2((short)r1, (short)r2);
+    }
+    __syncthreads();
+    const int nrp = (int)ls.nrp;
+    const int q = 2 * (t >> 5) + (lane >> 4), strip = lane & 15;
+    const bool active = q < S.nqg && strip < S.nstrip;
+    const int dl0 = q * M - Dm, r0 = strip * K;
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        int a, b;
+        ls.tp_decode(tp_start, T, &a, &b);
+        const int a0 = a % ls.Nb;
+        const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
+        float acc[M][K];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[m][k] = 0.0f;
+        St3Partner P;
+        int dt = st3_next<adjoint>(ls, tp_start, a, b, 0, nwin, Wt, own_cls, P);
+        if (dt < nwin) st3_stage<WA>(ls, S, rp, P, Wt, w, in, bufs);
+        int cur = 0;
+        while (dt < nwin) {
+            St3Partner Pn;
+            const int nxt = st3_next<adjoint>(ls, tp_start, a, b, dt + 1, nwin, Wt, own_cls, Pn);
+            if (nxt < nwin)
+                st3_stage<WA>(ls, S, rp, Pn, Wt, w, in, bufs + (cur ^ 1) * S.buf_f);
+            else
+                cp_async_commit();
+            cp_async_wait1();
+            __syncthreads();
+            if (active) {
+                const float *plane = bufs + cur * S.buf_f, *w3 = plane + S.plane_f;
+#pragma unroll
+                for (int cc = 0; cc < M + 4 * WA; ++cc) {
+                    const int c = dl0 - 2 * WA + cc;  // partner column (ring difference)
+                    if (c < -Dm || c > Dm) continue;
+                    float v[NV];
+                    const float2 *pv =
+                        reinterpret_cast<const float2 *>(plane + (c + Dm) * PRp + r0);
+#pragma unroll
+                    for (int u = 0; u < NV / 2; ++u) {
+                        const float2 f = pv[u];
+                        v[2 * u] = f.x;
+                        v[2 * u + 1] = f.y;
+                    }
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int e = adjoint ? m + 2 * WA - cc : cc - 2 * WA - m;
+                        if (e < -2 * WA || e > 2 * WA) continue;
+                        const int wd = adjoint ? dl0 + m : c;
+                        if (adjoint && wd > Dm) continue;
+                        const float4 *pw = reinterpret_cast<const float4 *>(
+                            w3 + ((wd + Dm) * NE + e + 2 * WA) * 8);
+                        const float4 w0 = pw[0], w1 = pw[1];
+                        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int o1 = -WA; o1 <= WA; ++o1) {
+                            const int o2 = o1 - e;
+                            if (o2 < -WA || o2 > WA) continue;
+                            const float wgt = wv[o1 + WA];
+#pragma unroll
+                            for (int k = 0; k < K; ++k)
+                                acc[m][k] =
+                                    fmaf(wgt, v[adjoint ? k + o1 + WA : k - o1 + WA], acc[m][k]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
             cur ^= 1;
             dt = nxt;
             P = Pn;
@@ -780,6 +938,28 @@ static int launch_stencil2(const psf_matrix *m, const float *in, float *out, int
 }
 
 template <bool adjoint, int WA>
+static int launch_stencil4(const psf_matrix *m, const float *in, float *out, cudaStream_t st) {
+    const St4Shape s4 = st4_shape(m->ls, WA);
+    const size_t shm = stencil4_smem_bytes(m->ls, WA);
+    PSF_TRY(cudaFuncSetAttribute(stencil4_kernel<adjoint, WA>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    int dev = 0, sms = 148, per_sm = 0;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PSF_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil4_kernel<adjoint, WA>,
+                                                          s4.threads, shm));
+    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(m->ls.ntp < cap ? m->ls.ntp : cap);
+    {
+        PSF_TIMED(adjoint ? "stencil4_kernel<adjoint>" : "stencil4_kernel<forward>", st);
+        stencil4_kernel<adjoint, WA><<<grid, s4.threads, shm, st>>>(m->ls, m->Wt, m->cls, in,
+                                                                    out);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
+template <bool adjoint, int WA>
 static int launch_stencil3(const psf_matrix *m, const float *in, float *out, int grid,
                            cudaStream_t st) {
     const size_t shm = stencil3_smem_bytes(m->ls, WA);
@@ -793,13 +973,39 @@ static int launch_stencil3(const psf_matrix *m, const float *in, float *out, int
     return PSF_OK;
 }
 
+static bool stencil4_ok(const LorSet &ls, int Wa) {
+    const St4Shape s4 = st4_shape(ls, Wa);
+    return Wa <= 3 && s4.nstrip <= 16 && s4.threads <= 256 &&
+           stencil4_smem_bytes(ls, Wa) <= 110 * 1024;
+}
+
+static bool stencil3_ok(const LorSet &ls, int Wa) {
+    const St3Shape s3 = st3_shape(ls, Wa);
+    return Wa <= 3 && s3.items <= ST3_T && stencil3_smem_bytes(ls, Wa) <= 110 * 1024;
+}
+
 static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoint,
                    cudaStream_t st) {
     int dev = 0, sms = 148;
     PSF_TRY(cudaGetDevice(&dev));
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const St3Shape s3 = st3_shape(m->ls, m->Wa);
-    if (m->Wa <= 3 && s3.items <= ST3_T && stencil3_smem_bytes(m->ls, m->Wa) <= 110 * 1024) {
+    const int form = m->st_form[adjoint ? 1 : 0];
+    const bool ok4 = stencil4_ok(m->ls, m->Wa), ok3 = stencil3_ok(m->ls, m->Wa);
+    const bool use4 = ok4 && (form != 3 || !ok3), use3 = !use4 && ok3;
+    if (use4) {
+        switch (m->Wa * 2 + (adjoint ? 1 : 0)) {
+            case 0: return launch_stencil4<false, 0>(m, in, out, st);
+            case 1: return launch_stencil4<true, 0>(m, in, out, st);
+            case 2: return launch_stencil4<false, 1>(m, in, out, st);
+            case 3: return launch_stencil4<true, 1>(m, in, out, st);
+            case 4: return launch_stencil4<false, 2>(m, in, out, st);
+            case 5: return launch_stencil4<true, 2>(m, in, out, st);
+            case 6: return launch_stencil4<false, 3>(m, in, out, st);
+            case 7: return launch_stencil4<true, 3>(m, in, out, st);
+            default: break;
+        }
+    }
+    if (use3) {
         const int64_t g3 = m->ls.ntp < (int64_t)sms * 4 ? m->ls.ntp : (int64_t)sms * 4;
         switch (m->Wa * 2 + (adjoint ? 1 : 0)) {
             case 0: return launch_stencil3<false, 0>(m, in, out, (int)g3, st);
@@ -870,6 +1076,7 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->wq_chunk = 0;
     m->wq_threads = 0;
     m->queue = nullptr;
+    m->st_form[0] = m->st_form[1] = 0;
     if (cudaMalloc(&m->queue, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         delete m;
         return PSF_ECUDA;
@@ -993,6 +1200,36 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
         if (rc) return rc;
         m->wq_chunk = bc;
         m->wq_threads = bt;
+        if (m->factored && stencil3_ok(m->ls, m->Wa) && stencil4_ok(m->ls, m->Wa)) {
+            // stencil form per direction: both timed on all-ones LOR vectors
+            cudaEvent_t f0 = nullptr, f1 = nullptr;
+            if (cudaEventCreate(&f0) != cudaSuccess || cudaEventCreate(&f1) != cudaSuccess)
+                rc = PSF_ECUDA;
+            for (int dir = 0; dir < 2 && !rc; ++dir) {
+                float best_ms = 1e30f;
+                int best_form = 0;
+                for (int form = 3; form <= 4 && !rc; ++form) {
+                    m->st_form[dir] = form;
+                    for (int rep = 0; rep < 2 && !rc; ++rep) {
+                        float ms = 0.0f;
+                        if (cudaEventRecord(f0, st) != cudaSuccess) rc = PSF_ECUDA;
+                        if (!rc) rc = stencil(m, m->p, m->q, dir == 1, st);
+                        if (!rc && (cudaEventRecord(f1, st) != cudaSuccess ||
+                                    cudaEventSynchronize(f1) != cudaSuccess ||
+                                    cudaEventElapsedTime(&ms, f0, f1) != cudaSuccess))
+                            rc = PSF_ECUDA;
+                        if (!rc && rep > 0 && ms < best_ms) {
+                            best_ms = ms;
+                            best_form = form;
+                        }
+                    }
+                }
+                m->st_form[dir] = best_form;
+            }
+            if (f0) cudaEventDestroy(f0);
+            if (f1) cudaEventDestroy(f1);
+            if (rc) return rc;
+        }
     }
     if (chunk_out) *chunk_out = m->wq_chunk;
     if (threads_out) *threads_out = m->wq_threads;

@@ -792,7 +792,7 @@ __device__ __forceinline__ int set_next_group(int *next) {
 // K4 (set): a warp takes 32 ring pairs of the CTA's transaxial pair; its
 // lanes cut the z slabs of all of them, 32 slabs at a time, and add each
 // slab's stored voxels to its ring pair's count.
-__global__ void __launch_bounds__(SET_T, 2) set_count_kernel(Scan sc, Img im, LorSet ls,
+__global__ void __launch_bounds__(SET_T, 3) set_count_kernel(Scan sc, Img im, LorSet ls,
                                                              const ZAx *__restrict__ zt,
                                                              int64_t *__restrict__ counts,
                                                              int *__restrict__ status) {
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(SET_T, 2) set_count_kernel(Scan sc, Img im, Lo
 // interior cells carry their full 2D chord, only its first and last ray-order
 // cells are cut by the z planes).  The 32 rows of a group are consecutive in
 // the CSR, so the whole group is one contiguous output span.
-__global__ void __launch_bounds__(SET_T, 2) set_fill_kernel(Scan sc, Img im, LorSet ls,
+__global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, LorSet ls,
                                                             const ZAx *__restrict__ zt,
                                                             const int64_t *__restrict__ row_ptr,
                                                             int32_t *__restrict__ col,
@@ -1012,7 +1012,7 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
         zaxis_kernel<<<(int)((ls.nrp + 255) / 256), 256, zshm, st>>>(sc, im, ls, zt);
     }
     PSF_LAUNCHED();
-    const int grid_max = sm_count() * 2;
+    const int grid_max = sm_count() * 3;  // resident CTAs (launch bounds 3 per SM)
     const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
     const size_t shm = set_smem(sc, ls);
     PSF_TRY(cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
