@@ -239,24 +239,27 @@ int psf_matrix_destroy(psf_matrix *m);
 
 /*
  * Launch tuning of the stored-row projectors (batching of rows of uneven
- * length, no counterpart in the paper).  Times, with CUDA events on `stream`,
- * a forward and a back projection of all-ones vectors for the grid-stride
- * kernels and for the persistent work-queue kernels (each warp takes the next
- * chunk of rows from a counter) at chunk in {1,2,4,8,16,32} rows and
- * {128,256,512} threads per CTA, and keeps the fastest for psf_forward /
- * psf_back of this plan; for a factored plan it also times the two forms of
- * the LOR-space spread stencil in each direction on all-ones vectors and keeps
- * the faster (call it after psf_matrix_set_spread).  chunk_out / threads_out
- * (host, may be NULL) receive
- * the choice (chunk 0: grid-stride kernels).  Synchronises; allocates a
- * temporary image-sized buffer; call it outside stream capture, after which
- * the projections of the plan can be captured in a CUDA graph.
+ * length, no counterpart in the paper).  For each direction it times, with
+ * CUDA events on `stream`, the grid-stride kernels, the persistent work-queue
+ * kernels (each warp takes the next chunk of rows from a counter) at chunk in
+ * {1,2,4,8,16,32} rows and {128,256,512} threads per CTA and, for the forward
+ * projection of FP32 rows, streaming tiles (64 rows per CTA, entries loaded
+ * 16 bytes at a time independently of row boundaries), on all-ones vectors,
+ * and keeps the fastest for psf_forward / psf_back of this plan; for a
+ * factored plan it also times the two forms of the LOR-space spread stencil
+ * in each direction and keeps the faster (call it after
+ * psf_matrix_set_spread).  chunk_out / threads_out: host arrays of 2
+ * (forward, back), may be NULL; chunk -1 = streaming tiles, 0 = grid-stride,
+ * > 0 = work queue.  Synchronises; allocates a temporary image-sized buffer;
+ * call it outside stream capture, after which the projections of the plan can
+ * be captured in a CUDA graph.
  */
 int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out, void *stream);
 
-/* Set that launch explicitly: chunk 0 selects the grid-stride kernels; chunk
- * in [1, 2^20] rows per take with threads a multiple of 32 in [32, 1024]
- * selects the work-queue kernels.  PSF_EINVAL otherwise. */
+/* Set that launch explicitly for both directions: chunk 0 selects the
+ * grid-stride kernels; chunk in [1, 2^20] rows per take with threads a
+ * multiple of 32 in [32, 1024] the work-queue kernels; chunk -1 (FP32 rows
+ * only) the streaming forward (back: grid-stride).  PSF_EINVAL otherwise. */
 int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads);
 
 /* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]). */

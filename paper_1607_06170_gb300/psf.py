@@ -284,6 +284,7 @@ class Matrix:
         self._keep = [row_ptr, col, val, row_scale]
         self.n_rows = row_ptr.shape[0] - 1
         self.n_cols = int(n_cols)
+        self.dtype_name = {PSF_F32: "f32", PSF_BF16: "bf16", PSF_F16: "f16"}[dt]
         self._h = C.c_void_p()
         _ok(lib().psf_matrix_create(C.byref(self._h), self.n_rows, self.n_cols, _ptr(row_ptr),
                                     _ptr(col), _ptr(val), dt, _ptr(row_scale), _stream()),
@@ -297,13 +298,12 @@ class Matrix:
         return self
 
     def autotune(self):
-        """Pick the stored-row projector launch (work-queue chunk, CTA size)
-        by timing the candidates; returns (chunk, threads), chunk 0 = the
-        grid-stride kernels."""
-        c, t = C.c_int32(), C.c_int32()
-        _ok(lib().psf_matrix_autotune(self._h, C.byref(c), C.byref(t), _stream()),
-            "psf_matrix_autotune")
-        return c.value, t.value
+        """Pick the stored-row projector launches by timing the candidates;
+        returns ((chunk, threads) forward, (chunk, threads) back): chunk -1 =
+        streaming tiles, 0 = grid-stride kernels, > 0 = work queue."""
+        c, t = (C.c_int32 * 2)(), (C.c_int32 * 2)()
+        _ok(lib().psf_matrix_autotune(self._h, c, t, _stream()), "psf_matrix_autotune")
+        return (c[0], t[0]), (c[1], t[1])
 
     def set_launch(self, chunk: int, threads: int = 256):
         """Stored-row projector launch: chunk 0 = grid-stride kernels, else the
