@@ -31,7 +31,8 @@ struct psf_matrix {
     float *p, *q;  // plan-owned scratch [n_rows]
     // stored-row projectors: persistent work-queue launch when wq_chunk > 0
     // (chosen by psf_matrix_autotune), else the grid-stride kernels
-    int wq_chunk, wq_threads;
+    int wq_chunk, wq_threads;     // back projection (and forward unless fwd_chunk set)
+    int fwd_chunk, fwd_threads;   // forward: -1 streaming tiles, 0 grid-stride, > 0 queue
     unsigned long long *queue;  // plan-owned row counter
     // factored plans: stencil form per direction (0: default order, 3 or 4:
     // that form), chosen by psf_matrix_autotune
@@ -103,6 +104,16 @@ __global__ void __launch_bounds__(PJ_T) csr_fwd_kernel(int64_t n, const int64_t 
     }
 }
 
+// Scatter of one row into the image by a warp (FP32 atomics in L2).
+template <typename VT>
+__device__ __forceinline__ void csr_row_scatter(const int32_t *__restrict__ col,
+                                                const VT *__restrict__ val, int64_t j0,
+                                                int64_t j1, float yr, float *__restrict__ x,
+                                                int lane) {
+    for (int64_t j = j0 + lane; j < j1; j += 32)
+        atomicAdd(x + __ldcs(col + j), ld_val_cs(val, j) * yr);
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(PJ_T) csr_back_kernel(int64_t n, const int64_t *__restrict__ ptr,
                                                        const int32_t *__restrict__ col,
@@ -116,9 +127,7 @@ __global__ void __launch_bounds__(PJ_T) csr_back_kernel(int64_t n, const int64_t
         float yr = y[r];
         if (scale) yr *= scale[r];
         if (yr == 0.0f) continue;
-        const int64_t j0 = ptr[r], j1 = ptr[r + 1];
-        for (int64_t j = j0 + lane; j < j1; j += 32)
-            atomicAdd(x + __ldcs(col + j), ld_val_cs(val, j) * yr);
+        csr_row_scatter(col, val, ptr[r], ptr[r + 1], yr, x, lane);
     }
 }
 
@@ -183,10 +192,66 @@ __global__ void csr_back_wq_kernel(int64_t n, const int64_t *__restrict__ ptr,
             float yr = y[r];
             if (scale) yr *= scale[r];
             if (yr == 0.0f) continue;
-            const int64_t j0 = ptr[r], j1 = ptr[r + 1];
-            for (int64_t j = j0 + lane; j < j1; j += 32)
-                atomicAdd(x + __ldcs(col + j), ld_val_cs(val, j) * yr);
+            csr_row_scatter(col, val, ptr[r], ptr[r + 1], yr, x, lane);
         }
+    }
+}
+
+// Streaming form of y = A x for FP32 rows: a CTA takes a tile of CS_ROWS
+// consecutive rows and streams their entries with 16-byte loads, four
+// entries per thread per step regardless of where rows begin, so the loads
+// of a whole step are in flight at once.  The products go to shared memory
+// and each warp then adds the part of its rows that lies in the step (a
+// fixed order, so the result is deterministic).
+constexpr int CS_T = 256, CS_ROWS = 64, CS_STEP = CS_T * 4;
+
+__global__ void __launch_bounds__(CS_T) csr_fwd_stream_kernel(
+    int64_t n, const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y) {
+    __shared__ int64_t rp[CS_ROWS + 1];
+    __shared__ __align__(16) float prod[CS_STEP];
+    __shared__ float racc[CS_ROWS];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t ntile = (n + CS_ROWS - 1) / CS_ROWS;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t r0 = tile * CS_ROWS;
+        const int nr = n - r0 < CS_ROWS ? (int)(n - r0) : CS_ROWS;
+        __syncthreads();  // the previous tile's readers are done
+        for (int i = t; i <= nr; i += CS_T) rp[i] = ptr[r0 + i];
+        for (int i = t; i < CS_ROWS; i += CS_T) racc[i] = 0.0f;
+        __syncthreads();
+        const int64_t j0 = rp[0], j1 = rp[nr];
+        for (int64_t base = j0 & ~(int64_t)3; base < j1; base += CS_STEP) {
+            const int64_t jj = base + 4 * t;
+            float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (jj >= j0 && jj + 3 < j1) {
+                const int4 c = __ldcs(reinterpret_cast<const int4 *>(col + jj));
+                const float4 v = __ldcs(reinterpret_cast<const float4 *>(val + jj));
+                p[0] = v.x * __ldg(x + c.x);
+                p[1] = v.y * __ldg(x + c.y);
+                p[2] = v.z * __ldg(x + c.z);
+                p[3] = v.w * __ldg(x + c.w);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (jj + u >= j0 && jj + u < j1)
+                        p[u] = __ldcs(val + jj + u) * __ldg(x + __ldcs(col + jj + u));
+            }
+            reinterpret_cast<float4 *>(prod)[t] = make_float4(p[0], p[1], p[2], p[3]);
+            __syncthreads();
+            const int64_t s1 = base + CS_STEP;
+            for (int r = warp; r < nr; r += CS_T / 32) {
+                const int64_t a = rp[r] > base ? rp[r] : base;
+                const int64_t b = rp[r + 1] < s1 ? rp[r + 1] : s1;
+                if (a >= b) continue;
+                float acc = 0.0f;
+                for (int64_t j = a + lane; j < b; j += 32) acc += prod[j - base];
+                acc = warp_sum_f(acc);
+                if (lane == 0) racc[r] += acc;
+            }
+            __syncthreads();
+        }
+        for (int i = t; i < nr; i += CS_T) y[r0 + i] = racc[i];
     }
 }
 
@@ -863,6 +928,21 @@ static int wq_grid(K kernel, int threads, int *grid) {
 
 static int rows_fwd_with(const psf_matrix *m, const float *x, float *y, int chunk, int threads,
                          cudaStream_t st) {
+    if (chunk < 0) {  // streaming tiles (FP32 rows without a scale)
+        if (m->dtype != PSF_F32) return PSF_EINVAL;
+        int dev = 0, sms = 148;
+        PSF_TRY(cudaGetDevice(&dev));
+        PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t ntile = (m->n_rows + CS_ROWS - 1) / CS_ROWS;
+        const int grid = (int)(ntile < (int64_t)sms * 8 ? ntile : (int64_t)sms * 8);
+        {
+            PSF_TIMED("csr_fwd_stream_kernel", st);
+            csr_fwd_stream_kernel<<<grid, CS_T, 0, st>>>(m->n_rows, m->row_ptr, m->col,
+                                                         (const float *)m->val, x, y);
+        }
+        PSF_LAUNCHED();
+        return PSF_OK;
+    }
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
         if (chunk > 0) {
@@ -890,6 +970,7 @@ static int rows_fwd_with(const psf_matrix *m, const float *x, float *y, int chun
 static int rows_back_with(const psf_matrix *m, const float *y, float *x, int chunk, int threads,
                           cudaStream_t st) {
     PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
+    if (chunk < 0) chunk = 0;  // the streaming form is forward only
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
         if (chunk > 0) {
@@ -915,7 +996,7 @@ static int rows_back_with(const psf_matrix *m, const float *y, float *x, int chu
 }
 
 static int rows_fwd(const psf_matrix *m, const float *x, float *y, cudaStream_t st) {
-    return rows_fwd_with(m, x, y, m->wq_chunk, m->wq_threads, st);
+    return rows_fwd_with(m, x, y, m->fwd_chunk, m->fwd_threads, st);
 }
 
 static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t st) {
@@ -1075,6 +1156,8 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->p = m->q = nullptr;
     m->wq_chunk = 0;
     m->wq_threads = 0;
+    m->fwd_chunk = 0;
+    m->fwd_threads = 0;
     m->queue = nullptr;
     m->st_form[0] = m->st_form[1] = 0;
     if (cudaMalloc(&m->queue, 2 * sizeof(unsigned long long)) != cudaSuccess) {
@@ -1151,55 +1234,64 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
     if (!m) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (m->n_rows == 0) {
-        m->wq_chunk = 0;
-        m->wq_threads = 0;
+        m->wq_chunk = m->wq_threads = m->fwd_chunk = m->fwd_threads = 0;
     } else {
-        // candidates: the grid-stride kernels (chunk 0) and the work queue at
-        // every (rows per take, threads per CTA) pair; each is timed on a
-        // forward + back of all-ones vectors, the fastest kept
-        static const int chunks[] = {0, 1, 2, 4, 8, 16, 32};
+        // candidates per direction: the grid-stride kernels (chunk 0), the work
+        // queue at every (rows per take, threads per CTA) pair and, forward with
+        // FP32 rows, the streaming tiles (chunk -1); each timed with CUDA events
+        // on all-ones vectors (one warm-up, best of two), the fastest kept
+        static const int chunks[] = {-1, 0, 1, 2, 4, 8, 16, 32};
         static const int threads[] = {128, 256, 512};
         float *x = nullptr;
         PSF_TRY(cudaMallocAsync(&x, sizeof(float) * m->n_cols, st));
-        float *y = m->p, *xb = x;
+        float *y = m->p;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         int rc = PSF_OK;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
             rc = PSF_ECUDA;
-        float best = 1e30f;
-        int bc = 0, bt = 0;
         if (!rc) {
             fill_kernel<<<grid_for(m->n_cols, 256), 256, 0, st>>>(x, 1.0f, m->n_cols);
             fill_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(y, 1.0f, m->n_rows);
             if (cudaGetLastError() != cudaSuccess) rc = PSF_ECUDA;
         }
-        for (int c : chunks) {
-            for (int t : threads) {
-                if (rc) break;
-                if (c == 0 && t != PJ_T) continue;
-                for (int rep = 0; rep < 3 && !rc; ++rep) {  // first repetition warms up
-                    if (cudaEventRecord(e0, st) != cudaSuccess) rc = PSF_ECUDA;
-                    if (!rc) rc = rows_fwd_with(m, x, y, c, t, st);
-                    if (!rc) rc = rows_back_with(m, y, xb, c, t, st);
-                    float ms = 0.0f;
-                    if (!rc && (cudaEventRecord(e1, st) != cudaSuccess ||
-                                cudaEventSynchronize(e1) != cudaSuccess ||
-                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                        rc = PSF_ECUDA;
-                    if (!rc && rep > 0 && ms < best) {
-                        best = ms;
-                        bc = c;
-                        bt = t;
+        for (int dir = 0; dir < 2 && !rc; ++dir) {
+            float best = 1e30f;
+            int bc = 0, bt = 0;
+            for (int c : chunks) {
+                if (c < 0 && (dir == 1 || m->dtype != PSF_F32)) continue;
+                for (int t : threads) {
+                    if (rc) break;
+                    if (c <= 0 && t != PJ_T) continue;
+                    for (int rep = 0; rep < 3 && !rc; ++rep) {
+                        if (cudaEventRecord(e0, st) != cudaSuccess) rc = PSF_ECUDA;
+                        if (!rc)
+                            rc = dir == 0 ? rows_fwd_with(m, x, y, c, t, st)
+                                          : rows_back_with(m, y, x, c, t, st);
+                        float ms = 0.0f;
+                        if (!rc && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                    cudaEventSynchronize(e1) != cudaSuccess ||
+                                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                            rc = PSF_ECUDA;
+                        if (!rc && rep > 0 && ms < best) {
+                            best = ms;
+                            bc = c;
+                            bt = c > 0 ? t : 0;
+                        }
                     }
                 }
+            }
+            if (dir == 0) {
+                m->fwd_chunk = bc;
+                m->fwd_threads = bt;
+            } else {
+                m->wq_chunk = bc;
+                m->wq_threads = bt;
             }
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         cudaFreeAsync(x, st);
         if (rc) return rc;
-        m->wq_chunk = bc;
-        m->wq_threads = bt;
         if (m->factored && stencil3_ok(m->ls, m->Wa) && stencil4_ok(m->ls, m->Wa)) {
             // stencil form per direction: both timed on all-ones LOR vectors
             cudaEvent_t f0 = nullptr, f1 = nullptr;
@@ -1231,15 +1323,24 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
             if (rc) return rc;
         }
     }
-    if (chunk_out) *chunk_out = m->wq_chunk;
-    if (threads_out) *threads_out = m->wq_threads;
+    if (chunk_out) {
+        chunk_out[0] = m->fwd_chunk;
+        chunk_out[1] = m->wq_chunk;
+    }
+    if (threads_out) {
+        threads_out[0] = m->fwd_threads;
+        threads_out[1] = m->wq_threads;
+    }
     return PSF_OK;
 }
 
 extern "C" int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads) {
-    if (!m || chunk < 0 || chunk > (1 << 20)) return PSF_EINVAL;
+    if (!m || chunk < -1 || chunk > (1 << 20)) return PSF_EINVAL;
     if (chunk > 0 && (threads < 32 || threads > 1024 || threads % 32)) return PSF_EINVAL;
-    m->wq_chunk = chunk;
+    if (chunk < 0 && m->dtype != PSF_F32) return PSF_EINVAL;
+    m->fwd_chunk = chunk;
+    m->fwd_threads = chunk > 0 ? threads : 0;
+    m->wq_chunk = chunk > 0 ? chunk : 0;
     m->wq_threads = chunk > 0 ? threads : 0;
     return PSF_OK;
 }
