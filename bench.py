@@ -320,8 +320,7 @@ def run_gpu(args):
         mark("rows", 1)
         M.set_spread(s, ls, Wt, Wa, WC)
         mark("sens", 0)
-        ones = torch.ones(n_lors, dtype=torch.float32, device=dev)
-        sens = M.back(ones)
+        sens = M.sensitivity(device=dev)
         mark("sens", 1)
         mark("forward", 0)
         yh = M.forward(x_in)

@@ -262,6 +262,15 @@ int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out,
  * only) the streaming forward (back: grid-stride).  PSF_EINVAL otherwise. */
 int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads);
 
+/*
+ * x = A^T 1, the sensitivity image of MLEM (Sec. 3), x (device float
+ * [n_cols], overwritten).  For a factored plan S^T 1 is formed from the class
+ * spreads' window sums over in-set measured LORs (the all-ones input needs no
+ * stencil), then G^T is applied; for stored rows it is psf_back of ones.
+ * Equal to psf_back(m, ones) up to FP32 summation order.
+ */
+int psf_sensitivity(const psf_matrix *m, float *x, void *stream);
+
 /* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]). */
 int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream);
 

@@ -899,6 +899,96 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
     }
 }
 
+// S^T 1 for the sensitivity image A^T 1 = G^T (S^T 1).  With an all-ones
+// input the adjoint stencil's value at source LOR g is the sum of g's window
+// weights over the window entries whose measured LOR is in the set:
+//   q[g] = sum_{partner dt in set} sum_{(o1,o2): target rings in set}
+//          W_{class(g)}[d][(dt1,o1)][(dt2,o2)],   d = g's ring difference.
+// Per transaxial pair the partner sums C[d][o1][o2] = sum_{dt in set} W[...]
+// are formed once (shared memory), then each ring pair adds the C entries of
+// its in-set targets: 31 x 49 x 49 + 1372 x 49 additions per pair instead of
+// the stencil's 1372 x 2401 products.
+constexpr int SS_T = 128;
+
+__global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, int Wa,
+                                                           const float *__restrict__ w,
+                                                           float *__restrict__ q) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, nd = 2 * ls.Dm + 1;
+    const int nwin = (2 * Wt + 1) * (2 * Wt + 1), NR = ls.NR, Dm = ls.Dm;
+    float *C = reinterpret_cast<float *>(raw);                     // [nd][W2a][W2a]
+    short2 *rp = reinterpret_cast<short2 *>(C + nd * W2a * W2a);   // [nrp]
+    int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    unsigned long long *mask = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(rp_start + ls.NR + 1) + 7) & ~uintptr_t(7));
+    const int t = threadIdx.x;
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    for (int j = t; j < ls.nrp; j += SS_T) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rp[j] = make_short2((short)r1, (short)r2);
+    }
+    const int nrp = (int)ls.nrp;
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        __syncthreads();
+        int a, b;
+        ls.tp_decode(tp_start, T, &a, &b);
+        if (t == 0) {  // partners in the set (one bit per window offset pair)
+            unsigned long long mk[2] = {0ull, 0ull};
+            for (int dt = 0; dt < nwin && dt < 128; ++dt) {
+                int pa = a + dt / (2 * Wt + 1) - Wt, pb = b + dt % (2 * Wt + 1) - Wt;
+                pa += pa < 0 ? ls.Nt : (pa >= ls.Nt ? -ls.Nt : 0);
+                pb += pb < 0 ? ls.Nt : (pb >= ls.Nt ? -ls.Nt : 0);
+                if (pa != pb && tp_member(ls, pa < pb ? pa : pb, pa < pb ? pb : pa))
+                    mk[dt >> 6] |= 1ull << (dt & 63);
+            }
+            mask[0] = mk[0];
+            mask[1] = mk[1];
+        }
+        __syncthreads();
+        const unsigned long long m0 = mask[0], m1 = mask[1];
+        const int a0 = a % ls.Nb;
+        const int64_t cls = tp_index(ls, tp_start, a0, b - (a - a0));
+        const float *wc = w + cls * nd * E * E;
+        for (int i = t; i < nd * W2a * W2a; i += SS_T) {
+            const int d = i / (W2a * W2a), L1 = (i / W2a) % W2a, L2 = i % W2a;
+            const float *wd = wc + (int64_t)d * E * E + L1 * E + L2;
+            float acc = 0.0f;
+            for (int dt = 0; dt < nwin; ++dt) {
+                if (!(((dt < 64 ? m0 >> dt : m1 >> (dt - 64)) & 1ull))) continue;
+                const int dt1 = dt / (2 * Wt + 1), dt2 = dt % (2 * Wt + 1);
+                acc += __ldg(wd + dt1 * W2a * E + dt2 * W2a);
+            }
+            C[i] = acc;
+        }
+        __syncthreads();
+        for (int j = t; j < nrp; j += SS_T) {
+            const short2 rr = rp[j];
+            const int ra = rr.x, rb = rr.y, d = rb - ra;
+            const float *Cd = C + (d + Dm) * W2a * W2a;
+            float acc = 0.0f;
+            for (int L1 = 0; L1 < W2a; ++L1) {
+                const int ta = ra + L1 - Wa;
+                if (ta < 0 || ta >= NR) continue;
+                for (int L2 = 0; L2 < W2a; ++L2) {
+                    const int tb = rb + L2 - Wa;
+                    if (tb < 0 || tb >= NR || tb - ta > Dm || ta - tb > Dm) continue;
+                    acc += Cd[L1 * W2a + L2];
+                }
+            }
+            q[T * nrp + j] = acc;
+        }
+    }
+}
+
+static size_t sens_smem_bytes(const LorSet &ls, int Wa) {
+    const int W2a = 2 * Wa + 1, nd = 2 * ls.Dm + 1;
+    return sizeof(float) * nd * W2a * W2a + sizeof(short2) * ls.nrp +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 8 + 2 * sizeof(unsigned long long) + 16;
+}
+
 constexpr int ST2_K = 8;  // rows per thread in stencil2_kernel
 
 static size_t stencil2_smem_bytes(const LorSet &ls, int Wa) {
@@ -1343,4 +1433,36 @@ extern "C" int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threa
     m->wq_chunk = chunk > 0 ? chunk : 0;
     m->wq_threads = chunk > 0 ? threads : 0;
     return PSF_OK;
+}
+
+extern "C" int psf_sensitivity(const psf_matrix *m, float *x, void *stream) {
+    if (!m || !x) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    if (m->n_rows == 0) {
+        PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
+        return PSF_OK;
+    }
+    if (!m->factored) {  // stored rows: A^T of an all-ones vector
+        {
+            PSF_TIMED("fill_kernel", st);
+            fill_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(m->p, 1.0f, m->n_rows);
+        }
+        PSF_LAUNCHED();
+        return rows_back(m, m->p, x, st);
+    }
+    const int nwin = (2 * m->Wt + 1) * (2 * m->Wt + 1);
+    const size_t shm = sens_smem_bytes(m->ls, m->Wa);
+    if (nwin > 128 || shm > 200 * 1024) return PSF_EINVAL;
+    PSF_TRY(cudaFuncSetAttribute(sens_spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
+    {
+        PSF_TIMED("sens_spread_kernel", st);
+        sens_spread_kernel<<<(int)grid, SS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, m->q);
+    }
+    PSF_LAUNCHED();
+    return rows_back(m, m->q, x, st);
 }

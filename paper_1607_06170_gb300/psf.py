@@ -27,7 +27,7 @@ FUNCTIONS = [
     "psf_sysmat_rows_set", "psf_sysmat_rows_set_noalloc",
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
-    "psf_matrix_autotune", "psf_matrix_set_launch",
+    "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity",
 ]
 
 
@@ -86,6 +86,7 @@ _SIGS = {
     "psf_timing_read": (C.c_int, [_I32, _P, _P, _P]),
     "psf_matrix_autotune": (C.c_int, [_P, _P, _P, _P]),
     "psf_matrix_set_launch": (C.c_int, [_P, _I32, _I32]),
+    "psf_sensitivity": (C.c_int, [_P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -316,6 +317,13 @@ class Matrix:
         if out is None:
             out = torch.empty(self.n_rows, dtype=torch.float32, device=x.device)
         _ok(lib().psf_forward(self._h, _ptr(x), _ptr(out), _stream()), "psf_forward")
+        return out
+
+    def sensitivity(self, out=None, device="cuda"):
+        """A^T 1 (psf_sensitivity)."""
+        if out is None:
+            out = torch.empty(self.n_cols, dtype=torch.float32, device=device)
+        _ok(lib().psf_sensitivity(self._h, _ptr(out), _stream()), "psf_sensitivity")
         return out
 
     def back(self, y, out=None):

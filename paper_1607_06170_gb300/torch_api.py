@@ -27,8 +27,9 @@ def project(x, matrix):
 
 
 def sensitivity(matrix, n_rows: int, device="cuda"):
-    ones = torch.ones(n_rows, dtype=torch.float32, device=device)
-    return matrix.back(ones)
+    """A^T 1 through psf_sensitivity (n_rows kept for the call's signature)."""
+    del n_rows
+    return matrix.sensitivity(device=device)
 
 
 def mlem(matrix, y, iters: int = 10, x0=None, sens=None, graph: bool = False):

@@ -163,3 +163,11 @@ def test_adjoint_identity_full(setup):
         lhs = torch.dot(M.forward(xk).double(), yk.double()).item()
         rhs = torch.dot(xk.double(), M.back(yk).double()).item()
         assert lhs == pytest.approx(rhs, rel=1e-5)
+
+
+def test_sensitivity_full(setup):
+    """At full size: psf_sensitivity against the back-projection of ones."""
+    M = setup["M"]
+    sens = M.sensitivity()
+    back1 = M.back(torch.ones(M.n_rows, device="cuda"))
+    torch.testing.assert_close(sens, back1, rtol=1e-5, atol=1e-6 * back1.abs().max().item())

@@ -127,3 +127,18 @@ def test_class_spreads_other_windows(P, gpu, ref, orc, Wt, Wa):
     ok = orc.tie_margin(w["scanner"], w["table"], ref["T"], C) >= 1e-5
     scale = np.abs(Wo).reshape(len(C), -1).max(1)[:, None, None]
     assert_close(WC.cpu().numpy()[ok], Wo[ok], 1e-5, 1e-12 * scale[ok] + 1e-30, "class spread")
+
+
+def test_sensitivity(gpu, ref, orc):
+    """psf_sensitivity (window sums for S^T 1) equals A^T 1 of the oracle and
+    the GPU back-projection of ones."""
+    w = ref["w"]
+    Wt, Wa = w["window"]
+    M = gpu["M"]
+    sens = M.sensitivity().cpu().numpy()
+    back1 = M.back(torch.ones(M.n_rows, device="cuda")).cpu().numpy()
+    ones = np.ones(len(ref["L"]))
+    so = orc.csr_back(ref["G"], orc.spread_adjoint(w["scanner"], ref["L"], ref["W"], Wt, Wa, ones),
+                      ref["nv"])
+    assert_close(sens, so, 2e-5, 1e-6 * so.max(), "sensitivity vs oracle")
+    assert_close(sens, back1, 1e-5, 1e-6 * back1.max(), "sensitivity vs back(1)")
