@@ -44,6 +44,21 @@ def dist_info():
     return rank, world, local
 
 
+def job_rate(total_ms: float, units_per_rank: float, device) -> tuple:
+    """Whole-job throughput of replicas: the slowest rank's time (max over
+    ranks) and the units all ranks processed divided by it.  Single process:
+    the local time."""
+    import torch
+
+    world = 1
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        world = torch.distributed.get_world_size()
+        tt = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = tt.item()
+    return total_ms, world * units_per_rank / (total_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
@@ -374,12 +389,8 @@ def run_gpu(args):
     clocks = clk.stop()
     ktimes = P.timing_read()
     P.timing_enable(False)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = tt.item()
+    total_ms, value = job_rate(total_ms, nnz * args.steps, dev)
     ms_step = total_ms / args.steps
-    value = world * nnz * args.steps / (total_ms * 1e-3)
     med = {k: statistics.median(v) for k, v in stage_ms.items()}
     rows_rate = nnz / (med["rows"] * 1e-3)
     fb = 2 * nnz / ((med["forward"] + med["back"]) * 1e-3)
