@@ -6,7 +6,9 @@ Tolerances (derivations in DESIGN.md):
     through a crystal corner (tens of micrometres long) has a length error
     near 2e-5 mm; the probability error is then below mu * 2.3e-5 = 2e-6;
   * spread: |d| <= 1e-5 |ref| + SPREAD_ATOL_REL * max|ref| per LOR (products of
-    table values inherit the table's absolute floor);
+    table values inherit the table's absolute floor, and FP32 sums of
+    products leave a residue near 1e-7 of the largest term where the exact
+    sum cancels to zero);
   * chords: voxel sets bit-exact after removing voxels with chord < 1e-6 mm on
     either side, values |d| <= 1e-4 |ref| + 1e-6 mm;
   * PSF rows and projections: |d| <= 1e-4 |ref| + 1e-6 * (row scale).
