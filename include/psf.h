@@ -271,6 +271,17 @@ int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads);
  */
 int psf_sensitivity(const psf_matrix *m, float *x, void *stream);
 
+/*
+ * x = A^T y and sens = A^T 1 (both device float [n_cols], overwritten) with one
+ * pass over the stored rows: each entry adds its two products to an
+ * interleaved image pair with one 8-byte atomic.  MLEM's first iteration
+ * needs both (an initial image of ones gives the same forward projection as
+ * ones on the voxels the scanner sees, because the other voxels' columns are
+ * zero).  Results equal psf_back and psf_sensitivity up to FP32 summation
+ * order.
+ */
+int psf_back_sens(const psf_matrix *m, const float *y, float *x, float *sens, void *stream);
+
 /* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]). */
 int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream);
 

@@ -37,6 +37,7 @@ struct psf_matrix {
     // factored plans: stencil form per direction (0: default order, 3 or 4:
     // that form), chosen by psf_matrix_autotune
     int st_form[2];
+    float2 *img2;  // plan-owned [n_cols]: the image pair of psf_back_sens
 };
 
 namespace psf {
@@ -252,6 +253,50 @@ __global__ void __launch_bounds__(CS_T) csr_fwd_stream_kernel(
             __syncthreads();
         }
         for (int i = t; i < nr; i += CS_T) y[r0 + i] = racc[i];
+    }
+}
+
+// Two back-projections in one pass over the rows: x2[v] += val * (ya[r], yb[r])
+// with one 8-byte vector atomic per entry into the interleaved image pair.
+// Rows are taken grid-stride (queue == nullptr) or from the work queue.
+template <typename VT>
+__global__ void csr_back_pair_kernel(int64_t n, const int64_t *__restrict__ ptr,
+                                     const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                     const float *__restrict__ scale,
+                                     const float *__restrict__ ya, const float *__restrict__ yb,
+                                     float2 *__restrict__ x2, unsigned long long *queue,
+                                     int chunk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpg = (int64_t)gridDim.x * (blockDim.x / 32);
+    int64_t r0 = queue ? wq_take(queue, chunk, lane)
+                       : (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int step = queue ? chunk : 1;
+    while (r0 < n) {
+        const int64_t r1 = r0 + step < n ? r0 + step : n;
+        for (int64_t r = r0; r < r1; ++r) {
+            float a = ya[r], b = yb[r];
+            if (scale) {
+                a *= scale[r];
+                b *= scale[r];
+            }
+            if (a == 0.0f && b == 0.0f) continue;
+            const int64_t j0 = ptr[r], j1 = ptr[r + 1];
+            for (int64_t j = j0 + lane; j < j1; j += 32) {
+                const float v = ld_val_cs(val, j);
+                atomicAdd(x2 + __ldcs(col + j), make_float2(v * a, v * b));
+            }
+        }
+        r0 = queue ? wq_take(queue, chunk, lane) : r0 + wpg;
+    }
+}
+
+__global__ void split_pair_kernel(const float2 *__restrict__ x2, float *__restrict__ xa,
+                                  float *__restrict__ xb, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = x2[i];
+        xa[i] = v.x;
+        xb[i] = v.y;
     }
 }
 
@@ -1250,7 +1295,13 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->fwd_threads = 0;
     m->queue = nullptr;
     m->st_form[0] = m->st_form[1] = 0;
+    m->img2 = nullptr;
     if (cudaMalloc(&m->queue, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        delete m;
+        return PSF_ECUDA;
+    }
+    if (cudaMalloc(&m->img2, sizeof(float2) * n_cols) != cudaSuccess) {
+        cudaFree(m->queue);
         delete m;
         return PSF_ECUDA;
     }
@@ -1259,6 +1310,7 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
             cudaMalloc(&m->q, sizeof(float) * n_rows) != cudaSuccess) {
             cudaFree(m->p);
             cudaFree(m->queue);
+            cudaFree(m->img2);
             delete m;
             return PSF_ECUDA;
         }
@@ -1292,6 +1344,7 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
     cudaFree(m->p);
     cudaFree(m->q);
     cudaFree(m->queue);
+    cudaFree(m->img2);
     delete m;
     return PSF_OK;
 }
@@ -1465,4 +1518,72 @@ extern "C" int psf_sensitivity(const psf_matrix *m, float *x, void *stream) {
     }
     PSF_LAUNCHED();
     return rows_back(m, m->q, x, st);
+}
+
+// x = A^T y and sens = A^T 1 with one pass over the stored rows.
+extern "C" int psf_back_sens(const psf_matrix *m, const float *y, float *x, float *sens,
+                             void *stream) {
+    if (!m || !y || !x || !sens) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    if (m->n_rows == 0) {
+        PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
+        PSF_TRY(cudaMemsetAsync(sens, 0, sizeof(float) * m->n_cols, st));
+        return PSF_OK;
+    }
+    const float *qa, *qb;  // LOR-space inputs of G^T: S^T 1 and S^T y (or 1 and y)
+    if (m->factored) {
+        const int nwin = (2 * m->Wt + 1) * (2 * m->Wt + 1);
+        const size_t shm = sens_smem_bytes(m->ls, m->Wa);
+        if (nwin > 128 || shm > 200 * 1024) return PSF_EINVAL;
+        PSF_TRY(cudaFuncSetAttribute(sens_spread_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        int dev = 0, sms = 148;
+        PSF_TRY(cudaGetDevice(&dev));
+        PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
+        {
+            PSF_TIMED("sens_spread_kernel", st);
+            sens_spread_kernel<<<(int)grid, SS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, m->p);
+        }
+        PSF_LAUNCHED();
+        int rc = stencil(m, y, m->q, true, st);
+        if (rc) return rc;
+        qa = m->p;
+        qb = m->q;
+    } else {
+        {
+            PSF_TIMED("fill_kernel", st);
+            fill_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(m->p, 1.0f, m->n_rows);
+        }
+        PSF_LAUNCHED();
+        qa = m->p;
+        qb = y;
+    }
+    PSF_TRY(cudaMemsetAsync(m->img2, 0, sizeof(float2) * m->n_cols, st));
+    const int chunk = m->wq_chunk > 0 ? m->wq_chunk : 0;
+    const int threads = chunk > 0 ? m->wq_threads : PJ_T;
+    int rc = dispatch_dtype(m->dtype, [&](auto tag) -> int {
+        using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+        int grid = grid_for(m->n_rows * 32, PJ_T);
+        if (chunk > 0) {
+            int r = wq_grid(csr_back_pair_kernel<VT>, threads, &grid);
+            if (r) return r;
+            PSF_TRY(cudaMemsetAsync(m->queue + 1, 0, sizeof(unsigned long long), st));
+        }
+        {
+            PSF_TIMED("csr_back_pair_kernel", st);
+            csr_back_pair_kernel<VT><<<grid, threads, 0, st>>>(
+                m->n_rows, m->row_ptr, m->col, (const VT *)m->val, m->row_scale, qa, qb, m->img2,
+                chunk > 0 ? m->queue + 1 : nullptr, chunk);
+        }
+        PSF_LAUNCHED();
+        return PSF_OK;
+    });
+    if (rc) return rc;
+    {
+        PSF_TIMED("split_pair_kernel", st);
+        split_pair_kernel<<<grid_for(m->n_cols, 256), 256, 0, st>>>(m->img2, sens, x, m->n_cols);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
 }

@@ -27,7 +27,7 @@ FUNCTIONS = [
     "psf_sysmat_rows_set", "psf_sysmat_rows_set_noalloc",
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
-    "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity",
+    "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
 ]
 
 
@@ -87,6 +87,7 @@ _SIGS = {
     "psf_matrix_autotune": (C.c_int, [_P, _P, _P, _P]),
     "psf_matrix_set_launch": (C.c_int, [_P, _I32, _I32]),
     "psf_sensitivity": (C.c_int, [_P, _P, _P]),
+    "psf_back_sens": (C.c_int, [_P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -325,6 +326,16 @@ class Matrix:
             out = torch.empty(self.n_cols, dtype=torch.float32, device=device)
         _ok(lib().psf_sensitivity(self._h, _ptr(out), _stream()), "psf_sensitivity")
         return out
+
+    def back_sens(self, y, out=None, sens=None):
+        """(A^T y, A^T 1) with one pass over the rows (psf_back_sens)."""
+        if out is None:
+            out = torch.empty(self.n_cols, dtype=torch.float32, device=y.device)
+        if sens is None:
+            sens = torch.empty(self.n_cols, dtype=torch.float32, device=y.device)
+        _ok(lib().psf_back_sens(self._h, _ptr(y), _ptr(out), _ptr(sens), _stream()),
+            "psf_back_sens")
+        return out, sens
 
     def back(self, y, out=None):
         if out is None:

@@ -41,17 +41,30 @@ def mlem(matrix, y, iters: int = 10, x0=None, sens=None, graph: bool = False):
     captured once in a CUDA graph (after one uncaptured iteration on a copy,
     which sets up the kernels' launch attributes) and replayed as one launch.
     """
-    if sens is None:
-        sens = sensitivity(matrix, y.numel(), y.device)
-    floor = 1e-12 * float(sens.max())
-    if x0 is None:
-        x = torch.ones_like(sens)
-        psf.em_update(x, sens, sens, floor)  # 1 on voxels the scanner sees, 0 elsewhere
-    else:
-        x = x0.clone()
     yhat = torch.empty_like(y)
     ratio = torch.empty_like(y)
-    bp = torch.empty_like(sens)
+    if sens is None and x0 is None and iters > 0:
+        # first iteration from an image of ones: its forward projection equals
+        # that of ones on the voxels the scanner sees (the others' columns are
+        # zero), so sens = A^T 1 comes with the first back-projection
+        # (psf_back_sens, one pass over the rows)
+        x = torch.ones(matrix.n_cols, dtype=torch.float32, device=y.device)
+        matrix.forward(x, out=yhat)
+        psf.em_ratio(y, yhat, out=ratio)
+        bp, sens = matrix.back_sens(ratio)
+        floor = 1e-12 * float(sens.max())
+        psf.em_update(x, bp, sens, floor)
+        iters -= 1
+    else:
+        if sens is None:
+            sens = sensitivity(matrix, y.numel(), y.device)
+        floor = 1e-12 * float(sens.max())
+        if x0 is None:
+            x = torch.ones_like(sens)
+            psf.em_update(x, sens, sens, floor)  # 1 on voxels the scanner sees, 0 elsewhere
+        else:
+            x = x0.clone()
+        bp = torch.empty_like(sens)
 
     def iteration(xi):
         matrix.forward(xi, out=yhat)
@@ -62,6 +75,8 @@ def mlem(matrix, y, iters: int = 10, x0=None, sens=None, graph: bool = False):
     if not graph:
         for _ in range(iters):
             iteration(x)
+        return x
+    if iters == 0:
         return x
     iteration(x.clone())  # uncaptured warm-up on a scratch copy
     torch.cuda.synchronize()

@@ -144,3 +144,20 @@ def test_projectors_and_mlem(P, orc):
     xo = orc.mlem(lambda v: A @ v, lambda q: A.T @ q, yo, o["nv"], 10)
     rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
     assert rel < 1e-4, rel
+
+
+def test_back_sens_stored_rows(P):
+    """Stored-row plans: one pass gives A^T y and A^T 1."""
+    w = I.workload("RING2D")
+    s, t, im = w["scanner"], w["table"], w["image"]
+    Wt, Wa = w["window"]
+    T, eta = P.response_build(s, t)
+    L = torch.from_numpy(I.workload_lors(w)).cuda()
+    Wg = P.bin_spread(s, t, T, eta, L, Wt, Wa)
+    ptr, col, val, _ = P.sysmat_rows(s, im, L, Wg, Wt, Wa)
+    M = P.Matrix(ptr, col, val, im["nx"] * im["ny"] * im["nz"])
+    r = torch.from_numpy(I.random_lor_values(M.n_rows, 909)).cuda()
+    x, sens = M.back_sens(r)
+    torch.testing.assert_close(x, M.back(r), rtol=1e-5, atol=1e-6 * x.abs().max().item())
+    ones = torch.ones(M.n_rows, device="cuda")
+    torch.testing.assert_close(sens, M.back(ones), rtol=1e-5, atol=1e-6 * sens.abs().max().item())

@@ -144,3 +144,13 @@ def test_sensitivity(gpu, ref, orc):
                       ref["nv"])
     assert_close(sens, so, 2e-5, 1e-6 * so.max(), "sensitivity vs oracle")
     assert_close(sens, back1, 1e-5, 1e-6 * back1.max(), "sensitivity vs back(1)")
+
+
+def test_back_sens_pair(gpu):
+    """psf_back_sens gives psf_back and psf_sensitivity in one pass."""
+    M = gpu["M"]
+    r = torch.from_numpy(I.random_lor_values(M.n_rows, 808)).cuda()
+    x, sens = M.back_sens(r)
+    torch.testing.assert_close(x, M.back(r), rtol=1e-5, atol=1e-6 * x.abs().max().item())
+    s1 = M.sensitivity()
+    torch.testing.assert_close(sens, s1, rtol=1e-5, atol=1e-6 * s1.abs().max().item())
