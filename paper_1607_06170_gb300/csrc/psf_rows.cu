@@ -8,6 +8,7 @@
 // LOR, every geometric LOR whose spread window lands on it, accumulates their
 // weighted rows densely in shared memory in a fixed order, and compacts the
 // non-zeros in ascending voxel order (count pass, scan, fill pass).
+#include <cstring>
 #include <type_traits>
 
 #include <cuda_bf16.h>
@@ -555,6 +556,7 @@ __host__ __device__ void build_cells(const Scan &sc, const Img &im, const double
     c.hdr[1] = nruns;
     c.hdr[2] = nflag;
     c.hdr[3] = ok;
+    c.hdr[13] = float_bits(n > 0 ? (float)n / (float)(c.bnd[n] - c.bnd[0]) : 0.0f);
 }
 
 // Parameter of the i-th plane crossing (i >= 1) along the segment of an axis
@@ -652,10 +654,12 @@ __device__ void build_cells_par(const Scan &sc, const Img &im, const double *cs,
             c.rstart[nyc + 1] = (short)n;
             H[0] = n;
             H[1] = nyc + 1;
+            H[13] = __float_as_int((float)n / (float)(c.clip[1] - c.clip[0]));
         }
     } else if (t == 0) {
         H[0] = 0;
         H[1] = 0;
+        H[13] = 0;
         c.rstart[0] = 0;
     }
     __syncthreads();

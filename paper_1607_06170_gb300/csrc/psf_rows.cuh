@@ -11,6 +11,8 @@
 // (z slab, then y row, then x), which is the CSR column order.
 #pragma once
 
+#include <cstring>
+
 #include "psf_common.cuh"
 
 namespace psf {
@@ -31,6 +33,26 @@ __host__ __device__ __forceinline__ float u32_to_f(unsigned v) {
 __host__ __device__ __forceinline__ float units_to_f(long long v) {
     const unsigned hi = (unsigned)(v >> 24), lo = (unsigned)(v & ((1 << 24) - 1));
     return fmaf(u32_to_f(hi), 16777216.0f, u32_to_f(lo));
+}
+
+// Bit copies between float and int (host and device).
+__host__ __device__ __forceinline__ float bits_float(int v) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(v);
+#else
+    float f;
+    memcpy(&f, &v, sizeof f);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ int float_bits(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_int(f);
+#else
+    int v;
+    memcpy(&v, &f, sizeof v);
+    return v;
+#endif
 }
 
 struct Axis {

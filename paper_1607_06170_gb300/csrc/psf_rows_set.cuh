@@ -68,6 +68,27 @@ __host__ __device__ __forceinline__ int slab_segments(const Cells2D &c, int ca, 
     return 2;
 }
 
+// The cell holding parameter al (bnd[c] <= al < bnd[c+1], al in [bnd[0],
+// bnd[n])).  The boundaries are the union of two arithmetic progressions
+// (the x and the y plane crossings), so the index is within two of
+// proportional to al: a guess from the proportion, a few steps along the
+// list, and the binary search if the steps do not settle.
+__host__ __device__ __forceinline__ int cell_at(const long long *bnd, int n, long long al,
+                                                float per_unit) {
+    int g = (int)((float)(al - bnd[0]) * per_unit);
+    g = g < 0 ? 0 : (g > n - 1 ? n - 1 : g);
+    for (int it = 0; it < 6; ++it) {
+        if (bnd[g + 1] <= al) {
+            ++g;
+        } else if (bnd[g] > al) {
+            --g;
+        } else {
+            return g;
+        }
+    }
+    return first_cell_after(bnd, n, al);
+}
+
 // Cells [ca, cb] overlapping the (clipped) slab interval [zl, zh) and the
 // number of them that keep a chord of at least minu units.
 struct SlabCells {
@@ -82,8 +103,10 @@ __host__ __device__ __forceinline__ SlabCells cut_cells(const Cells2D &c, long l
     s.count = 0;
     const int n = c.hdr[0], nflag = c.hdr[2];
     if (zh <= zl || n == 0) return s;
-    s.ca = first_cell_after(c.bnd, n, zl);
-    s.cb = last_cell_before(c.bnd, n, zh);
+    // parameters are integers: the last cell starting before zh holds zh - 1
+    const float per_unit = bits_float(c.hdr[13]);
+    s.ca = cell_at(c.bnd, n, zl, per_unit);
+    s.cb = cell_at(c.bnd, n, zh - 1, per_unit);
     if (s.cb < s.ca) return s;
     int cnt = s.cb - s.ca + 1;
     if (piece(c.bnd, s.ca, zl, zh) < minu) --cnt;
