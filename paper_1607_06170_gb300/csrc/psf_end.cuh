@@ -115,8 +115,9 @@ __device__ __forceinline__ void end_dir(float dx, float dy, float cb, float sb, 
 // the node lookup by tangents: the nearest node of an angle a in [0, pi/2)
 // is the number of node boundaries (j + 1/2) * step (j = 0 .. K-2) at or
 // below a, and a >= b  <=>  opposite >= adjacent * tan(b) for a positive
-// adjacent side, so the lookups need no arctangent.  tanB holds the alpha
-// boundaries of the block1 angle beta = alpha - 2 pi/R.
+// adjacent side, so the lookups need no exact arctangent (an approximate one
+// only picks where the count starts).  tanB holds the alpha boundaries of the
+// block1 angle beta = alpha - 2 pi/R.
 struct GapConst {
     float c2, s2, t2;     // cos, sin, tan of the angle between neighbouring block normals
     float ipt, ipa, iwt, iwa;
@@ -153,13 +154,28 @@ __device__ __forceinline__ GapConst make_gapconst(const Scan &sc, const Tab &tb,
     return k;
 }
 
-// Number of entries j < K - 1 of the ascending table with adj * tab[j] <= opp.
-__device__ __forceinline__ int node_by_tan(const float *tab, int K, float opp, float adj) {
-    int k = 0;
-    if (K > 1)
-        for (int step = 1 << (31 - __clz(K - 1)); step >= 1; step >>= 1)
-            if (k + step <= K - 1 && adj * tab[k + step - 1] <= opp) k += step;
+// Number of entries j < K - 1 of the ascending table with adj * tab[j] <= opp
+// (adj > 0), found by stepping from a starting guess k0: the predicate is
+// monotone in j, so the count is the k at which it turns from true to false,
+// whatever k0 was (a good guess only saves steps).
+__device__ __forceinline__ int node_by_tan(const float *tab, int K, float opp, float adj,
+                                           int k0) {
+    int k = k0 < 0 ? 0 : (k0 > K - 1 ? K - 1 : k0);
+    while (k < K - 1 && adj * tab[k] <= opp) ++k;
+    while (k > 0 && adj * tab[k - 1] > opp) --k;
     return k;
+}
+
+// Arctangent of y / x for x > 0, y >= 0, good to about 1.5e-3 rad: the
+// quadratic approximation on [0, 1] of Rajan, Wang, Inkol and Joyal
+// ("Efficient approximations for the arctangent function", IEEE Signal
+// Processing Magazine, 2006), reflected about pi/4 above it.  It only seeds
+// node_by_tan, so its error costs steps, never a different node.
+__device__ __forceinline__ float atan_seed(float y, float x) {
+    const bool above = y > x;
+    const float r = above ? __fdividef(x, y) : __fdividef(y, x);
+    const float a = r * (0.78539816f - (r - 1.0f) * (0.2447f + 0.0663f * r));
+    return above ? 1.57079633f - a : a;
 }
 
 // The response of end_response() with a compile-time window: the quadrant
@@ -193,10 +209,15 @@ __device__ __forceinline__ void end_resp_q(const Scan &sc, const Tab &tb, const 
     const float h = h2 * ih;
     const int iu = sgt > 0 ? p : tb.Pt - 1 - p;
     const int iv = sga > 0 ? q : tb.Pa - 1 - q;
-    const int kt = node_by_tan(k.tanT, tb.Kt, avt, vn);
-    const int ka = node_by_tan(k.tanA, tb.Ka, adz, h);
+    // nearest nodes: count of node boundaries (j + 1/2) * step at or below
+    // the angle, seeded from the approximate angle
+    const float alpha = atan_seed(avt, vn);
+    const int kt = node_by_tan(k.tanT, tb.Kt, avt, vn, f2i_rd(fmaf(alpha, tb.inv_dt, 0.5f)));
+    const int ka = node_by_tan(k.tanA, tb.Ka, adz, h,
+                               f2i_rd(fmaf(atan_seed(adz, h), tb.inv_da, 0.5f)));
     const int MM = tb.Mt * tb.Ma;
-    const int64_t ent = table_entry(tb, kt, ka, iu, iv);
+    // table offsets fit 32 bits (the descriptor holds at most 2^28 values)
+    const int ent = ((kt * tb.Ka + ka) * tb.Pt + iu) * tb.Pa + iv;
     const float *Tb = T + ent * MM;
     const int edge = sgt > 0 ? sc.Nb - 1 - i : i;  // crystals of block0 beyond the entry one
     const int nx0 = min(edge, tb.Mt - 1);
@@ -244,20 +265,25 @@ __device__ __forceinline__ void end_resp_q(const Scan &sc, const Tab &tb, const 
             v1 = 0.0f;
         }
         const int iv1 = max(min(f2i_rd(v1 * tb.Pa), tb.Pa - 1), 0);
-        const int kt1 = node_by_tan(k.tanB, tb.Kt, avt, vn);
-        const int64_t ent1 = table_entry(tb, kt1, ka, iu1, iv1);
+        const int kt1 = node_by_tan(k.tanB, tb.Kt, avt, vn,
+                                    f2i_rd(fmaf(alpha - sc.two_pi_R, tb.inv_dt, 0.5f)));
+        const int ent1 = ((kt1 * tb.Ka + ka) * tb.Pt + iu1) * tb.Pa + iv1;
         const float *T1 = T + ent1 * MM;
         const double *E1 = eta + ent1 * (tb.Mt + 1);
         e += ldg(E1 + min(m + 1 + sc.Nb, tb.Mt)) - ldg(E1 + min(m + 1, tb.Mt));
         const int dzq0 = sga * (k1 - ring);
+        // block1 crystals enter the window only from an entry crystal within
+        // WT of the block edge (the same for every sub-LOR of the LOR)
+        if (edge < WT) {
 #pragma unroll
-        for (int X = 0; X <= WT; ++X) {
-            const int j = X - edge - 1, x = m + 1 + j;  // block1 crystal j, table column x
-            if (j < 0 || j >= sc.Nb || x >= tb.Mt) continue;
+            for (int X = 0; X <= WT; ++X) {
+                const int j = X - edge - 1, x = m + 1 + j;  // block1 crystal j, table column x
+                if (j < 0 || j >= sc.Nb || x >= tb.Mt) continue;
 #pragma unroll
-            for (int Z = 0; Z <= WA; ++Z) {
-                const int z = Z - dzq0;
-                if (z >= 0 && z < tb.Ma) r.q[X * W1 + Z] += ldg(T1 + x * tb.Ma + z);
+                for (int Z = 0; Z <= WA; ++Z) {
+                    const int z = Z - dzq0;
+                    if (z >= 0 && z < tb.Ma) r.q[X * W1 + Z] += ldg(T1 + x * tb.Ma + z);
+                }
             }
         }
     }

@@ -283,6 +283,19 @@ __device__ __forceinline__ void acc_all32(float (&acc)[RB][CB], const float *ra,
     }
 }
 
+// A response into its staging row (16-byte aligned when Q is a multiple of 4).
+template <int Q>
+__device__ __forceinline__ void stage_row(float *dst, const float (&q)[Q]) {
+    if constexpr (Q % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < Q; k += 4)
+            *reinterpret_cast<float4 *>(dst + k) = make_float4(q[k], q[k + 1], q[k + 2], q[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) dst[k] = q[k];
+    }
+}
+
 template <int WT, int WA>
 static size_t spread_q_smem(const Tab &tb) {
     using S = SqShape<WT, WA>;
@@ -309,13 +322,16 @@ __global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
     double *red = reinterpret_cast<double *>(smraw);                 // [2][SQ_WARPS]
     int *ipat = reinterpret_cast<int *>(red + 2 * SQ_WARPS);        // [0] mask, [1] npat, [4..19] slot pattern
     float *Rw = reinterpret_cast<float *>(ipat + 20);               // [warps][2][32][QS]
-    float *wwin = Rw + SQ_WARPS * 2 * 32 * QS;                      // [E*E]
-    float *pts = wwin + E * E;                                      // [2][NP][4]
+    float *pts = Rw + SQ_WARPS * 2 * 32 * QS;                       // [2][NP][4]
+    float *wwin = pts + 2 * NP * 4;                                 // [E*E]
     float *part = Rw;  // [warps][SQ_SLOTS][Q*Q], reuses the staging rows at the end of a LOR
+    static_assert(SQ_WARPS * SQ_SLOTS * Q * Q <= SQ_WARPS * 2 * 32 * QS, "part fits the staging rows");
+    static_assert(QS % 4 == 0 && (2 * 8 * SQ_WARPS + 4 * 20) % 16 == 0,
+                  "staging rows and sub-position centres start 16-byte aligned");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     float *R1w = Rw + warp * 2 * 32 * QS, *R2w = R1w + 32 * QS;
     const int rb = lane >> 2, cb = lane & 3;
-    const GapConst gk = make_gapconst(sc, tb, pts + 2 * NP * 4);  // visible after the first barrier
+    const GapConst gk = make_gapconst(sc, tb, wwin + E * E);  // visible after the first barrier
     for (int k = t; k < SQ_WARPS * 2 * 32 * QS; k += SP_THREADS) Rw[k] = 0.0f;
     for (int64_t lor = blockIdx.x; lor < n_lors; lor += gridDim.x) {
         const int id1 = lors[2 * lor], id2 = lors[2 * lor + 1];
@@ -340,11 +356,8 @@ __global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
             const float cbk = end ? cb2 : cb1, sbk = end ? sb2 : sb1;
             const float se = (i - 0.5f * (sc.Nb - 1)) * sc.pt + ((p + 0.5f) / tb.Pt - 0.5f) * sc.wt;
             const float ze = sc.z0 + ring * sc.pa + ((q + 0.5f) / tb.Pa - 0.5f) * sc.wa;
-            float *P = pts + k * 4;
-            P[0] = sc.radius * cbk - se * sbk;
-            P[1] = sc.radius * sbk + se * cbk;
-            P[2] = ze;
-            P[3] = se;
+            reinterpret_cast<float4 *>(pts)[k] =
+                make_float4(sc.radius * cbk - se * sbk, sc.radius * sbk + se * cbk, ze, se);
         }
         for (int k = t; k < E * E; k += SP_THREADS) wwin[k] = 0.0f;
         if (t == 0) ipat[0] = 0;
@@ -353,8 +366,9 @@ __global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
         unsigned mine = 0;
         for (int s = t; s < nsub; s += SP_THREADS) {
             const int s1 = s / NP, s2 = s - s1 * NP;
-            const float *P1 = pts + s1 * 4, *P2 = pts + (NP + s2) * 4;
-            const float dx = P1[0] - P2[0], dy = P1[1] - P2[1], dz = P1[2] - P2[2];
+            const float4 P1 = reinterpret_cast<const float4 *>(pts)[s1];
+            const float4 P2 = reinterpret_cast<const float4 *>(pts)[NP + s2];
+            const float dx = P1.x - P2.x, dy = P1.y - P2.y, dz = P1.z - P2.z;
             float vn1, vt1, vn2, vt2;
             end_dir(dx, dy, cb1, sb1, vn1, vt1);
             end_dir(-dx, -dy, cb2, sb2, vn2, vt2);
@@ -381,8 +395,9 @@ __global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
                 int slot = -1;
                 if (s < nsub) {
                     const int s1 = s / NP, s2 = s - s1 * NP;
-                    const float *P1 = pts + s1 * 4, *P2 = pts + (NP + s2) * 4;
-                    const float dx = P1[0] - P2[0], dy = P1[1] - P2[1], dz = P1[2] - P2[2];
+                    const float4 P1 = reinterpret_cast<const float4 *>(pts)[s1];
+                    const float4 P2 = reinterpret_cast<const float4 *>(pts)[NP + s2];
+                    const float dx = P1.x - P2.x, dy = P1.y - P2.y, dz = P1.z - P2.z;
                     float vn1, vt1, vn2, vt2;
                     end_dir(dx, dy, cb1, sb1, vn1, vt1);
                     end_dir(-dx, -dy, cb2, sb2, vn2, vt2);
@@ -395,14 +410,12 @@ __global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
                             slot = sl;
                             QResp<WT, WA> r;
                             end_resp_q<WT, WA>(sc, tb, gk, T, eta, i1, ring1, s1 / tb.Pa,
-                                               s1 % tb.Pa, P1[3], P1[2], vn1, vt1, dz, r);
+                                               s1 % tb.Pa, P1.w, P1.z, vn1, vt1, dz, r);
                             const double e1 = r.eta;
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) R1w[lane * QS + k] = r.q[k];
+                            stage_row<Q>(R1w + lane * QS, r.q);
                             end_resp_q<WT, WA>(sc, tb, gk, T, eta, i2, ring2, s2 / tb.Pa,
-                                               s2 % tb.Pa, P2[3], P2[2], vn2, vt2, -dz, r);
-#pragma unroll
-                            for (int k = 0; k < Q; ++k) R2w[lane * QS + k] = r.q[k];
+                                               s2 % tb.Pa, P2.w, P2.z, vn2, vt2, -dz, r);
+                            stage_row<Q>(R2w + lane * QS, r.q);
                             sfull += e1 * r.eta;
                         }
                     }
@@ -454,29 +467,28 @@ __global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
                     }
             __syncthreads();
             const int nsl = min(SQ_SLOTS, npat - pass * SQ_SLOTS);
-            for (int wc = t; wc < E * E; wc += SP_THREADS) {
-                const int w1 = wc / E, w2 = wc - w1 * E;
-                const int tx1 = w1 / W2a - WT, tz1 = w1 % W2a - WA;
-                const int tx2 = w2 / W2a - WT, tz2 = w2 % W2a - WA;
-                float v = wwin[wc];
-                int c = 0;
-                for (int P = 0; P < SP_PATS; ++P) {
-                    if (!((present >> P) & 1)) continue;
-                    const int sl = c++ - pass * SQ_SLOTS;
-                    if (sl < 0 || sl >= nsl) continue;
-                    const int g1 = (P >> 3) & 1 ? 1 : -1, a1 = (P >> 2) & 1 ? 1 : -1;
-                    const int g2 = (P >> 1) & 1 ? 1 : -1, a2 = P & 1 ? 1 : -1;
-                    const int x1 = g1 * tx1, z1 = a1 * tz1, x2 = g2 * tx2, z2 = a2 * tz2;
-                    if (x1 < 0 || z1 < 0 || x2 < 0 || z2 < 0) continue;
-                    const int e = (x1 * (WA + 1) + z1) * Q + x2 * (WA + 1) + z2;
+            // fold slot by slot, in pattern order: within one pattern the
+            // quadrant-to-window map is one-to-one, so no two threads meet
+            unsigned rest = present;
+            for (int c = 0; c < pass * SQ_SLOTS; ++c) rest &= rest - 1u;
+            for (int sl = 0; sl < nsl; ++sl) {
+                const int P = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                const int g1 = (P >> 3) & 1 ? 1 : -1, a1 = (P >> 2) & 1 ? 1 : -1;
+                const int g2 = (P >> 1) & 1 ? 1 : -1, a2 = P & 1 ? 1 : -1;
+                for (int e = t; e < Q * Q; e += SP_THREADS) {
+                    const int e1 = e / Q, e2 = e - e1 * Q;
+                    const int x1 = e1 / (WA + 1), z1 = e1 - x1 * (WA + 1);
+                    const int x2 = e2 / (WA + 1), z2 = e2 - x2 * (WA + 1);
+                    const int w1 = (g1 * x1 + WT) * W2a + (a1 * z1 + WA);
+                    const int w2 = (g2 * x2 + WT) * W2a + (a2 * z2 + WA);
                     float sum = 0.0f;
 #pragma unroll
                     for (int w = 0; w < SQ_WARPS; ++w) sum += part[(w * SQ_SLOTS + sl) * Q * Q + e];
-                    v += sum;
+                    wwin[w1 * E + w2] += sum;
                 }
-                wwin[wc] = v;
+                __syncthreads();  // the next slot may meet these entries; part aliases the staging rows
             }
-            __syncthreads();  // part aliases the staging rows of the next pass
         }
         // FP64 totals: sfull over sub-LORs, sw over the accumulated window
         double swin = 0.0;
