@@ -223,12 +223,15 @@ static size_t spread_smem(const Tab &tb, int Wt, int Wa) {
 // fixed RB x CB block of the Q x Q quadrant-local product.  Sub-LORs with
 // different travel patterns land in different quadrants of the window, so
 // each pattern present in the LOR gets its own register accumulator ("slot");
-// the slot of a sub-LOR is the same for the whole warp at each step, so the
-// choice is a uniform branch.  A pre-pass finds the patterns present; a LOR
-// with more than SQ_SLOTS patterns is done in several passes.  The per-warp
-// accumulators are summed in a fixed order at the end of the LOR (FP32,
-// deterministic), folded into the window, and normalised with FP64 totals.
-constexpr int SQ_SLOTS = 4;
+// a pre-pass finds the patterns present and a LOR with more than SQ_SLOTS
+// patterns is done in several passes, each evaluating the responses of only
+// its patterns' sub-LORs.  The per-warp accumulators are summed in a fixed
+// order at the end of each pass (FP32, deterministic), folded into the window,
+// and normalised with FP64 totals.  One slot (a pass per pattern) leaves the
+// registers for three CTAs per SM, which hides more latency than the extra
+// passes over the sub-LOR directions cost (22.1 ms against 24.2 ms with four
+// slots at two CTAs per SM, 3D ring classes).
+constexpr int SQ_SLOTS = 1;
 constexpr int SQ_WARPS = SP_THREADS / 32;
 
 template <int WT, int WA>
@@ -310,7 +313,7 @@ static size_t spread_q_smem(const Tab &tb) {
 }
 
 template <int WT, int WA>
-__global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
+__global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
     Scan sc, Tab tb, const float *__restrict__ T, const double *__restrict__ eta,
     const int32_t *__restrict__ lors, int64_t n_lors, int norm, float *__restrict__ out) {
     using S = SqShape<WT, WA>;
@@ -425,14 +428,9 @@ __global__ void __launch_bounds__(SP_THREADS, 2) spread_q_kernel(
                 const int s0 = __shfl_sync(0xffffffffu, slot, 0);
                 if (__all_sync(0xffffffffu, slot == s0)) {
                     // common case: one travel pattern for the whole warp
-                    static_assert(SQ_SLOTS == 4, "one case per slot");
-                    switch (s0) {
-                        case 0: acc_all32<RB, CB, QS>(acc[0], ra, rbp); break;
-                        case 1: acc_all32<RB, CB, QS>(acc[1], ra, rbp); break;
-                        case 2: acc_all32<RB, CB, QS>(acc[2], ra, rbp); break;
-                        case 3: acc_all32<RB, CB, QS>(acc[3], ra, rbp); break;
-                        default: break;
-                    }
+#pragma unroll
+                    for (int sl = 0; sl < SQ_SLOTS; ++sl)
+                        if (s0 == sl) acc_all32<RB, CB, QS>(acc[sl], ra, rbp);
                 } else {
 #pragma unroll 4
                     for (int k = 0; k < 32; ++k) {
