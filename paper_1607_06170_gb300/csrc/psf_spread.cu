@@ -219,8 +219,9 @@ static size_t spread_smem(const Tab &tb, int Wt, int Wa) {
 
 // K3 with a compile-time window (the common windows).  A warp evaluates 32
 // sub-LORs at a time, one per lane, into warp-private rows of shared memory,
-// then accumulates their outer products r1 (x) r2 with each lane owning a
-// fixed RB x CB block of the Q x Q quadrant-local product.  Sub-LORs with
+// then accumulates their outer products r1 (x) r2: each half-warp takes every
+// other staged sub-LOR, its 16 lanes owning fixed RB x CB blocks of the Q x Q
+// quadrant-local product (two shared-memory reads per 16 FMA).  Sub-LORs with
 // different travel patterns land in different quadrants of the window, so
 // each pattern present in the LOR gets its own register accumulator ("slot");
 // a pre-pass finds the patterns present and a LOR with more than SQ_SLOTS
@@ -241,47 +242,60 @@ template <int WT, int WA>
 struct SqShape {
     static constexpr int Q = (WT + 1) * (WA + 1);
     static constexpr int E = (2 * WT + 1) * (2 * WA + 1);
-    static constexpr int RB = (Q + 7) / 8;  // rows of the product per lane (8 row groups)
-    static constexpr int CB = (Q + 3) / 4;  // columns per lane (4 column groups)
+    // each half-warp covers the Q x Q product with its 16 lanes, lane (rb, cb)
+    // owning rows rb*RB.. and columns cb*CB.. of it; the two halves take
+    // alternate staged sub-LORs and are summed at the end of a pass
+    static constexpr int RB = (Q + 3) / 4;
+    static constexpr int CB = (Q + 3) / 4;
     // row stride of the staged responses: covers every lane's reads, 16-byte
     // rows, and an odd number of 16-byte units so 8 lanes storing 16 bytes
-    // each hit distinct banks
-    static constexpr int QR = (8 * RB > 4 * CB ? 8 * RB : 4 * CB);
+    // each hit distinct banks; then rows r and r + 4 (the two halves' rows at
+    // one step) lie 16 banks apart
+    static constexpr int QR = 4 * RB;
     static constexpr int QS = ((QR + 3) / 4) % 2 == 0 ? ((QR + 3) / 4) * 4 + 4 : ((QR + 3) / 4) * 4;
+    static_assert((4 * QS) % 32 == 16 || QR <= 8, "halves' rows 16 banks apart");
 };
 
 // One staged sub-LOR's operands of a lane: RB entries of r1, CB of r2.
-template <int RB, int CB>
-__device__ __forceinline__ void load_ab(const float *ra, const float *rbp, float (&a)[RB],
-                                        float (&b)[CB]) {
-    if constexpr (RB == 2) {
-        const float2 v = *reinterpret_cast<const float2 *>(ra);
-        a[0] = v.x;
-        a[1] = v.y;
+template <int N>
+__device__ __forceinline__ void load_n(const float *p, float (&v)[N]) {
+    if constexpr (N == 4) {
+        const float4 w = *reinterpret_cast<const float4 *>(p);
+        v[0] = w.x;
+        v[1] = w.y;
+        v[2] = w.z;
+        v[3] = w.w;
+    } else if constexpr (N == 2) {
+        const float2 w = *reinterpret_cast<const float2 *>(p);
+        v[0] = w.x;
+        v[1] = w.y;
     } else {
 #pragma unroll
-        for (int i = 0; i < RB; ++i) a[i] = ra[i];
-    }
-    if constexpr (CB == 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(rbp);
-        b[0] = v.x;
-        b[1] = v.y;
-        b[2] = v.z;
-        b[3] = v.w;
-    } else {
-#pragma unroll
-        for (int j = 0; j < CB; ++j) b[j] = rbp[j];
+        for (int i = 0; i < N; ++i) v[i] = p[i];
     }
 }
 
-// All 32 staged sub-LORs of a warp into one accumulator (same slot).
+template <int RB, int CB>
+__device__ __forceinline__ void load_ab(const float *ra, const float *rbp, float (&a)[RB],
+                                        float (&b)[CB]) {
+    load_n<RB>(ra, a);
+    load_n<CB>(rbp, b);
+}
+
+// Staged row of a half-warp at step k (0..15): the halves take rows r and
+// r + 4 of each group of eight.
+__device__ __forceinline__ int half_row(int k, int h) { return ((k >> 2) << 3) + (k & 3) + (h << 2); }
+
+// All 32 staged sub-LORs of a warp into one accumulator (same slot): each
+// half-warp takes 16 of them.
 template <int RB, int CB, int QS>
 __device__ __forceinline__ void acc_all32(float (&acc)[RB][CB], const float *ra,
-                                          const float *rbp) {
+                                          const float *rbp, int h) {
 #pragma unroll 8
-    for (int k = 0; k < 32; ++k) {
+    for (int k = 0; k < 16; ++k) {
         float a[RB], b[CB];
-        load_ab<RB, CB>(ra + k * QS, rbp + k * QS, a, b);
+        const int row = half_row(k, h);
+        load_ab<RB, CB>(ra + row * QS, rbp + row * QS, a, b);
 #pragma unroll
         for (int i = 0; i < RB; ++i)
 #pragma unroll
@@ -336,7 +350,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
                   "staging rows and sub-position centres start 16-byte aligned");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     float *R1w = Rw + warp * 2 * 32 * QS, *R2w = R1w + 32 * QS;
-    const int rb = lane >> 2, cb = lane & 3;
+    const int hw = lane >> 4, rb = (lane >> 2) & 3, cb = lane & 3;
     const GapConst gk = make_gapconst(sc, tb, wwin + E * E);  // visible after the first barrier
     for (int k = t; k < SQ_WARPS * 2 * 32 * QS; k += SP_THREADS) Rw[k] = 0.0f;
     for (int64_t lor = blockIdx.x; lor < n_lors; lor += gridDim.x) {
@@ -440,14 +454,15 @@ __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
                     // common case: one travel pattern for the whole warp
 #pragma unroll
                     for (int sl = 0; sl < SQ_SLOTS; ++sl)
-                        if (s0 == sl) acc_all32<RB, CB, QS>(acc[sl], ra, rbp);
+                        if (s0 == sl) acc_all32<RB, CB, QS>(acc[sl], ra, rbp, hw);
                 } else {
 #pragma unroll 4
-                    for (int k = 0; k < 32; ++k) {
-                        const int sk = __shfl_sync(0xffffffffu, slot, k);
+                    for (int k = 0; k < 16; ++k) {
+                        const int row = half_row(k, hw);
+                        const int sk = __shfl_sync(0xffffffffu, slot, row);
                         if (sk < 0) continue;
                         float a[RB], b[CB];
-                        load_ab<RB, CB>(ra + k * QS, rbp + k * QS, a, b);
+                        load_ab<RB, CB>(ra + row * QS, rbp + row * QS, a, b);
 #pragma unroll
                         for (int sl = 0; sl < SQ_SLOTS; ++sl)
                             if (sk == sl) {
@@ -461,18 +476,28 @@ __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
                 }
                 __syncwarp();
             }
-            // per-warp accumulators -> part, then fold into the window
-            __syncthreads();
+            // per-warp accumulators (the two halves summed) -> part, then fold
+            // into the window
 #pragma unroll
             for (int sl = 0; sl < SQ_SLOTS; ++sl)
 #pragma unroll
                 for (int i = 0; i < RB; ++i)
 #pragma unroll
-                    for (int j = 0; j < CB; ++j) {
-                        const int e1 = rb * RB + i, e2 = cb * CB + j;
-                        if (e1 < Q && e2 < Q)
-                            part[(warp * SQ_SLOTS + sl) * Q * Q + e1 * Q + e2] = acc[sl][i][j];
-                    }
+                    for (int j = 0; j < CB; ++j)
+                        acc[sl][i][j] += __shfl_xor_sync(0xffffffffu, acc[sl][i][j], 16);
+            __syncthreads();
+            if (hw == 0) {
+#pragma unroll
+                for (int sl = 0; sl < SQ_SLOTS; ++sl)
+#pragma unroll
+                    for (int i = 0; i < RB; ++i)
+#pragma unroll
+                        for (int j = 0; j < CB; ++j) {
+                            const int e1 = rb * RB + i, e2 = cb * CB + j;
+                            if (e1 < Q && e2 < Q)
+                                part[(warp * SQ_SLOTS + sl) * Q * Q + e1 * Q + e2] = acc[sl][i][j];
+                        }
+            }
             __syncthreads();
             const int nsl = min(SQ_SLOTS, npat - pass * SQ_SLOTS);
             // fold slot by slot, in pattern order: within one pattern the
