@@ -804,12 +804,15 @@ __global__ void __launch_bounds__(ST3_T, 4) stencil3_kernel(LorSet ls, int Wt,
 }
 
 // Fourth form, for fewer distinct shared-memory addresses per warp.  Each
-// half-warp owns one group of M = 8 consecutive ring differences and its 16
+// half-warp owns one group of M = 4 consecutive ring differences and its 16
 // lanes the strips of K = 4 rings, so a weight load has two addresses per
 // warp (one per half) and a plane load is 8 bytes per lane on consecutive
-// rows; a thread does K x M = 32 products per partner value pair it loads.
-// Staging and the partner walk are those of the third form.
-constexpr int ST4_K = 4, ST4_M = 8;
+// rows; a thread does K x M = 16 products per partner value pair it loads.
+// (M = 4 gives 128-thread CTAs, twice the warps per SM of M = 8 at the same
+// shared memory: 12.5 / 13.3 ms against 15.4 / 17.0 ms forward / adjoint on
+// the 3D ring; M = 2 14.0 / 14.2 ms.)  Staging and the partner walk are those
+// of the third form.
+constexpr int ST4_K = 4, ST4_M = 4;
 
 struct St4Shape {
     int nd, nstrip, nqg, threads, PRp, ne;
