@@ -250,12 +250,15 @@ def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
 
 def kernel_traffic(name):
     """DRAM bytes per launch from the committed ncu capture of this kernel,
-    or None when the kernel's source file has changed since the capture."""
+    or None when one of the kernel's source files (the record's "source", a
+    path or a list of paths; sha1 of their concatenated bytes) has changed
+    since the capture."""
     import hashlib
 
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[name]
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        srcs = rec["source"] if isinstance(rec["source"], list) else [rec["source"]]
+        src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in srcs)
     except (OSError, ValueError, KeyError):
         return None
     if hashlib.sha1(src).hexdigest() != rec["sha1"]:
@@ -486,7 +489,8 @@ def run_profile_case(args):
             M.back(y)
         if case == "rows_set":
             # same scanner and image, fan narrowed to +-10 so the capture holds ~3 GB
-            P.sysmat_rows_set(s, im, dict(ls, fan_half=10), device=dev)
+            rows_set = P.sysmat_rows_set(s, im, dict(ls, fan_half=10), device=dev)
+            info = {"rows": rows_set[0].numel() - 1, "nnz": rows_set[1].numel()}
         if case in ("rows", "csr"):
             L = P.lor_set_list(s, ls, device=dev)[: 2_000_000].contiguous()
             rp, col, val, _ = P.sysmat_rows(s, im, L)
@@ -495,7 +499,7 @@ def run_profile_case(args):
                 y = M.forward(torch.rand(nv, device=dev))
                 M.back(y)
         torch.cuda.synchronize()
-    print(json.dumps({"profile_case": case, "ok": True}))
+    print(json.dumps({"profile_case": case, "ok": True, **(info if case == "rows_set" else {})}))
 
 
 def main():
