@@ -38,6 +38,10 @@ struct psf_matrix {
     // that form), chosen by psf_matrix_autotune
     int st_form[2];
     float2 *img2;  // plan-owned [n_cols]: the image pair of psf_back_sens
+    // factored plans: per spread class, its window weights summed over all
+    // transaxial partners (plan-owned, sized at psf_matrix_set_spread)
+    float *csum;
+    int64_t csum_n;
 };
 
 namespace psf {
@@ -958,12 +962,37 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
 // the stencil's 1372 x 2401 products.
 constexpr int SS_T = 128;
 
+// Per spread class c: C_c[d][o1][o2] summed over all 49 transaxial partners
+// (the partner sums of a transaxial pair whose partners are all in the set,
+// which is every pair but those near the edge of the fan).
+__global__ void __launch_bounds__(SS_T) sens_class_kernel(LorSet ls, int Wt, int Wa,
+                                                          const float *__restrict__ w,
+                                                          float *__restrict__ csum) {
+    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, nd = 2 * ls.Dm + 1;
+    const int nwin = (2 * Wt + 1) * (2 * Wt + 1), nsum = nd * W2a * W2a;
+    for (int64_t c = blockIdx.x; c < ls.ntp_cls; c += gridDim.x) {
+        const float *wc = w + c * nd * E * E;
+        for (int i = threadIdx.x; i < nsum; i += SS_T) {
+            const int d = i / (W2a * W2a), L1 = (i / W2a) % W2a, L2 = i % W2a;
+            const float *wd = wc + (int64_t)d * E * E + L1 * E + L2;
+            float acc = 0.0f;
+            for (int dt = 0; dt < nwin; ++dt) {
+                const int dt1 = dt / (2 * Wt + 1), dt2 = dt % (2 * Wt + 1);
+                acc += __ldg(wd + dt1 * W2a * E + dt2 * W2a);
+            }
+            csum[c * nsum + i] = acc;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, int Wa,
                                                            const float *__restrict__ w,
+                                                           const float *__restrict__ csum,
                                                            float *__restrict__ q) {
     extern __shared__ __align__(16) unsigned char raw[];
     const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, nd = 2 * ls.Dm + 1;
     const int nwin = (2 * Wt + 1) * (2 * Wt + 1), NR = ls.NR, Dm = ls.Dm;
+    const int nsum = nd * W2a * W2a;
     float *C = reinterpret_cast<float *>(raw);                     // [nd][W2a][W2a]
     short2 *rp = reinterpret_cast<short2 *>(C + nd * W2a * W2a);   // [nrp]
     int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
@@ -999,17 +1028,23 @@ __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, in
         const unsigned long long m0 = mask[0], m1 = mask[1];
         const int a0 = a % ls.Nb;
         const int64_t cls = tp_index(ls, tp_start, a0, b - (a - a0));
-        const float *wc = w + cls * nd * E * E;
-        for (int i = t; i < nd * W2a * W2a; i += SS_T) {
-            const int d = i / (W2a * W2a), L1 = (i / W2a) % W2a, L2 = i % W2a;
-            const float *wd = wc + (int64_t)d * E * E + L1 * E + L2;
-            float acc = 0.0f;
-            for (int dt = 0; dt < nwin; ++dt) {
-                if (!(((dt < 64 ? m0 >> dt : m1 >> (dt - 64)) & 1ull))) continue;
-                const int dt1 = dt / (2 * Wt + 1), dt2 = dt % (2 * Wt + 1);
-                acc += __ldg(wd + dt1 * W2a * E + dt2 * W2a);
+        if (__popcll(m0) + __popcll(m1) == nwin) {
+            // every partner in the set: the class's sums (the same additions
+            // in the same order)
+            for (int i = t; i < nsum; i += SS_T) C[i] = __ldg(csum + cls * nsum + i);
+        } else {
+            const float *wc = w + cls * nd * E * E;
+            for (int i = t; i < nsum; i += SS_T) {
+                const int d = i / (W2a * W2a), L1 = (i / W2a) % W2a, L2 = i % W2a;
+                const float *wd = wc + (int64_t)d * E * E + L1 * E + L2;
+                float acc = 0.0f;
+                for (int dt = 0; dt < nwin; ++dt) {
+                    if (!(((dt < 64 ? m0 >> dt : m1 >> (dt - 64)) & 1ull))) continue;
+                    const int dt1 = dt / (2 * Wt + 1), dt2 = dt % (2 * Wt + 1);
+                    acc += __ldg(wd + dt1 * W2a * E + dt2 * W2a);
+                }
+                C[i] = acc;
             }
-            C[i] = acc;
         }
         __syncthreads();
         for (int j = t; j < nrp; j += SS_T) {
@@ -1299,6 +1334,8 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->queue = nullptr;
     m->st_form[0] = m->st_form[1] = 0;
     m->img2 = nullptr;
+    m->csum = nullptr;
+    m->csum_n = 0;
     if (cudaMalloc(&m->queue, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         delete m;
         return PSF_ECUDA;
@@ -1333,6 +1370,14 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
     if (ls.nrp > ST_T * ST_OUT || stencil_smem_bytes(ls, half_a) > 200 * 1024 ||
         stencil2_smem_bytes(ls, half_a) > 200 * 1024 || ls.NR > 32000)
         return PSF_EINVAL;
+    const int64_t need = ls.ntp_cls * (2 * ls.Dm + 1) * (2 * half_a + 1) * (2 * half_a + 1);
+    if (need > m->csum_n) {  // grows only: a plan reused over calls allocates once
+        cudaFree(m->csum);
+        m->csum = nullptr;
+        m->csum_n = 0;
+        PSF_TRY(cudaMalloc(&m->csum, sizeof(float) * need));
+        m->csum_n = need;
+    }
     m->factored = true;
     m->ls = ls;
     m->Wt = half_t;
@@ -1348,6 +1393,7 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
     cudaFree(m->q);
     cudaFree(m->queue);
     cudaFree(m->img2);
+    cudaFree(m->csum);
     delete m;
     return PSF_OK;
 }
@@ -1491,6 +1537,37 @@ extern "C" int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threa
     return PSF_OK;
 }
 
+namespace psf {
+
+// S^T 1 of a factored plan into out [n_rows]: the per-class partner sums, then
+// the per-pair window sums.
+static int sens_spread(const psf_matrix *m, float *out, cudaStream_t st) {
+    const int nwin = (2 * m->Wt + 1) * (2 * m->Wt + 1);
+    const size_t shm = sens_smem_bytes(m->ls, m->Wa);
+    if (nwin > 128 || shm > 200 * 1024 || !m->csum) return PSF_EINVAL;
+    PSF_TRY(cudaFuncSetAttribute(sens_spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t cgrid = m->ls.ntp_cls < (int64_t)sms * 8 ? m->ls.ntp_cls : (int64_t)sms * 8;
+    {
+        PSF_TIMED("sens_class_kernel", st);
+        sens_class_kernel<<<(int)cgrid, SS_T, 0, st>>>(m->ls, m->Wt, m->Wa, m->cls, m->csum);
+    }
+    PSF_LAUNCHED();
+    const int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
+    {
+        PSF_TIMED("sens_spread_kernel", st);
+        sens_spread_kernel<<<(int)grid, SS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, m->csum,
+                                                         out);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
+}  // namespace psf
+
 extern "C" int psf_sensitivity(const psf_matrix *m, float *x, void *stream) {
     if (!m || !x) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
@@ -1506,20 +1583,8 @@ extern "C" int psf_sensitivity(const psf_matrix *m, float *x, void *stream) {
         PSF_LAUNCHED();
         return rows_back(m, m->p, x, st);
     }
-    const int nwin = (2 * m->Wt + 1) * (2 * m->Wt + 1);
-    const size_t shm = sens_smem_bytes(m->ls, m->Wa);
-    if (nwin > 128 || shm > 200 * 1024) return PSF_EINVAL;
-    PSF_TRY(cudaFuncSetAttribute(sens_spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shm));
-    int dev = 0, sms = 148;
-    PSF_TRY(cudaGetDevice(&dev));
-    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
-    {
-        PSF_TIMED("sens_spread_kernel", st);
-        sens_spread_kernel<<<(int)grid, SS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, m->q);
-    }
-    PSF_LAUNCHED();
+    const int rc = sens_spread(m, m->q, st);
+    if (rc) return rc;
     return rows_back(m, m->q, x, st);
 }
 
@@ -1535,21 +1600,9 @@ extern "C" int psf_back_sens(const psf_matrix *m, const float *y, float *x, floa
     }
     const float *qa, *qb;  // LOR-space inputs of G^T: S^T 1 and S^T y (or 1 and y)
     if (m->factored) {
-        const int nwin = (2 * m->Wt + 1) * (2 * m->Wt + 1);
-        const size_t shm = sens_smem_bytes(m->ls, m->Wa);
-        if (nwin > 128 || shm > 200 * 1024) return PSF_EINVAL;
-        PSF_TRY(cudaFuncSetAttribute(sens_spread_kernel,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        int dev = 0, sms = 148;
-        PSF_TRY(cudaGetDevice(&dev));
-        PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
-        {
-            PSF_TIMED("sens_spread_kernel", st);
-            sens_spread_kernel<<<(int)grid, SS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->cls, m->p);
-        }
-        PSF_LAUNCHED();
-        int rc = stencil(m, y, m->q, true, st);
+        int rc = sens_spread(m, m->p, st);
+        if (rc) return rc;
+        rc = stencil(m, y, m->q, true, st);
         if (rc) return rc;
         qa = m->p;
         qb = m->q;
