@@ -21,6 +21,7 @@ from .oracle import (  # noqa: F401
     table_build,
     composed,
     spread,
+    spread_topn,
     tie_margin,
     tie_count,
     siddon,

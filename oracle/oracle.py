@@ -94,6 +94,7 @@ def _load():
                 "orc_csr_back": (None, [C.c_int64, _P, _P, _P, _P, C.c_int64, _P]),
                 "orc_spread_apply": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
                 "orc_spread_adjoint": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
+                "orc_spread_topn": (None, [C.c_int64, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
                 "orc_threads": (C.c_int, []),
                 "orc_tie_margin": (None, [_P, _P, _P, _P, C.c_int64, _P]),
                 "orc_tie_stats": (None, [_P, _P, _P, _P, C.c_int64, C.c_double, _P, _P]),
@@ -350,6 +351,21 @@ def spread_adjoint(scanner: dict, lors, w: np.ndarray, Wt: int, Wa: int, r: np.n
     _load().orc_spread_adjoint(C.byref(s), L.shape[0], _ptr(L), _ptr(w), int(Wt), int(Wa),
                                _ptr(pair_row_map(scanner, L)), _ptr(r), _ptr(q))
     return q
+
+
+def spread_topn(w: np.ndarray, Wt: int, Wa: int, N: int):
+    """Top-N truncation of each LOR's spread (n x E x E): the truncated,
+    rescaled weights (same shape) and the kept window indices in rank order
+    (n x N int32)."""
+    E = (2 * Wt + 1) * (2 * Wa + 1)
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, E * E)
+    n = w.shape[0]
+    if not 1 <= N <= E * E:
+        raise ValueError("N must be in 1 .. window size")
+    out = np.zeros_like(w)
+    idx = np.zeros((n, N), dtype=np.int32)
+    _load().orc_spread_topn(n, _ptr(w), int(Wt), int(Wa), int(N), _ptr(out), _ptr(idx))
+    return out.reshape(n, E, E), idx
 
 
 def mlem(fwd, back, y: np.ndarray, nvox: int, iters: int, x0=None):

@@ -24,6 +24,8 @@
  *   orc_siddon          pinned (axis-aligned chords, brute slab-clip tracer)
  *   orc_rows_psf        pinned (definition A = S G checked on scatter identity)
  *   orc_csr_fwd / back  pinned (dot-product identity, MLEM count identity)
+ *   orc_spread_topn     pinned (N = whole window is the identity, sum rule,
+ *                       ranking against a brute-force order, tie rules)
  *   agreement of the analytic response with GATE: parity unpinned (the
  *   paper's response curves, Figs. 2-5, are not in the text).
  */
@@ -936,6 +938,75 @@ void orc_spread_adjoint(const orc_scanner *s, int64_t n, const int32_t *lors,
             }
         q[g] = acc;
     }
+}
+
+/*
+ * Top-N truncation of each LOR's spread (Sec. 4.3 and Table 3: the extended
+ * bins are kept in descending order of their proportion, up to N of them).
+ * Readings where the paper is silent:
+ *   - the N entries are taken over the LOR's whole window (both ends'
+ *     transaxial and axial offsets), since here the window, not a per-angle
+ *     bin list, holds the extended bins;
+ *   - entries rank by weight (a negative weight ranks as 0); equal weights
+ *     rank the entry with the smaller offset |dt1|+|da1|+|dt2|+|da2| first,
+ *     then the lower window index e1*E + e2;
+ *   - the kept weights are rescaled so that they sum to the untruncated
+ *     window's total (the LOR's detection efficiency is kept); a LOR whose
+ *     kept weights sum to 0 keeps them unscaled.
+ * The ranking compares the given values exactly, so FP32-representable
+ * inputs rank as they do in FP32.  w, out: n x E*E; idx: n x N window
+ * indices in rank order.
+ */
+static int orc_topn_E, orc_topn_W2a, orc_topn_Wt, orc_topn_Wa;
+static const double *orc_topn_w;
+
+static int orc_topn_dist(int e)
+{
+    int E = orc_topn_E, W2a = orc_topn_W2a;
+    int e1 = e / E, e2 = e % E;
+    int dt1 = e1 / W2a - orc_topn_Wt, da1 = e1 % W2a - orc_topn_Wa;
+    int dt2 = e2 / W2a - orc_topn_Wt, da2 = e2 % W2a - orc_topn_Wa;
+    return abs(dt1) + abs(da1) + abs(dt2) + abs(da2);
+}
+
+/* qsort order: rank 0 first (larger weight, then smaller offset, then lower index) */
+static int orc_topn_cmp(const void *pa, const void *pb)
+{
+    int a = *(const int *)pa, b = *(const int *)pb;
+    double wa = orc_topn_w[a] > 0.0 ? orc_topn_w[a] : 0.0;
+    double wb = orc_topn_w[b] > 0.0 ? orc_topn_w[b] : 0.0;
+    if (wa != wb) return wa > wb ? -1 : 1;
+    int da = orc_topn_dist(a), db = orc_topn_dist(b);
+    if (da != db) return da < db ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+void orc_spread_topn(int64_t n, const double *w, int Wt, int Wa, int N, double *out,
+                     int32_t *idx)
+{
+    const int E = (2 * Wt + 1) * (2 * Wa + 1), EE = E * E;
+    int *order = (int *)malloc(sizeof(int) * EE);
+    orc_topn_E = E;
+    orc_topn_W2a = 2 * Wa + 1;
+    orc_topn_Wt = Wt;
+    orc_topn_Wa = Wa;
+    for (int64_t g = 0; g < n; ++g) {
+        const double *wg = w + (size_t)g * EE;
+        double *og = out + (size_t)g * EE;
+        for (int e = 0; e < EE; ++e) order[e] = e;
+        orc_topn_w = wg;
+        qsort(order, EE, sizeof(int), orc_topn_cmp);
+        double all = 0.0, kept = 0.0;
+        for (int e = 0; e < EE; ++e) all += wg[e];
+        for (int k = 0; k < N; ++k) kept += wg[order[k]];
+        double scale = kept != 0.0 ? all / kept : 1.0;
+        memset(og, 0, sizeof(double) * EE);
+        for (int k = 0; k < N; ++k) {
+            og[order[k]] = wg[order[k]] * scale;
+            idx[(size_t)g * N + k] = order[k];
+        }
+    }
+    free(order);
 }
 
 /* Number of OpenMP threads the oracle runs with (for the baseline record). */
