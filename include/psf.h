@@ -136,6 +136,22 @@ int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *desc, const
                    const double *eta, const int32_t *lors, int64_t n_lors, int32_t half_t,
                    int32_t half_a, int32_t norm, float *spread, void *stream);
 
+/*
+ * Top-N truncation of spreads (Sec. 4.3, Table 3: the extended bins kept in
+ * descending order of proportion, up to N).  For each of n_lors spreads
+ * (device float [n_lors][E][E], E = (2 half_t + 1)(2 half_a + 1), e.g. the
+ * output of psf_bin_spread) the window entries are ranked by weight -- a
+ * negative weight ranks as 0; equal weights rank the smaller offset
+ * |dt1|+|da1|+|dt2|+|da2| first, then the lower window index e1*E + e2 (the
+ * paper gives no tie rule) -- and the first n_keep are written in rank order:
+ * idx (device int32 [n_lors][n_keep], window index e1*E + e2) and w (device
+ * float [n_lors][n_keep]), the kept weights scaled so that they sum to the
+ * untruncated window's total (unscaled when the kept weights sum to 0).
+ * 1 <= n_keep <= min(64, E*E) and E*E <= 2432, else PSF_EINVAL.
+ */
+int psf_spread_topn(const float *spread, int64_t n_lors, int32_t half_t, int32_t half_a,
+                    int32_t n_keep, int32_t *idx, float *w, void *stream);
+
 /* Number of LORs of a structured set, and of its spread classes (one per
  * transaxial pair with a < nt_block times ring difference; every LOR of the
  * set has the spread of its class by the ring's rotation and axial
@@ -235,6 +251,16 @@ int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_cols, const in
 int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner, const psf_lor_set *set,
                           int32_t half_t, int32_t half_a, const float *class_spread);
 
+/* The same factored form with top-N class spreads (the output of
+ * psf_spread_topn on the class spreads: idx int32 and w float, device
+ * [n_classes][n_keep], kept by pointer): S applies only each class's kept
+ * entries.  S^T gathers in rank order; S scatters with FP32 atomics (the
+ * last bits of a sum may vary between runs).  Replaces a previous
+ * psf_matrix_set_spread, and vice versa. */
+int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scanner,
+                               const psf_lor_set *set, int32_t half_t, int32_t half_a,
+                               int32_t n_keep, const int32_t *idx, const float *w);
+
 int psf_matrix_destroy(psf_matrix *m);
 
 /*
@@ -242,12 +268,12 @@ int psf_matrix_destroy(psf_matrix *m);
  * length, no counterpart in the paper).  For each direction it times, with
  * CUDA events on `stream`, the grid-stride kernels, the persistent work-queue
  * kernels (each warp takes the next chunk of rows from a counter) at chunk in
- * {1,2,4,8,16,32} rows and {128,256,512} threads per CTA and, for the forward
+ * {1,2,4,...,128} rows and {128,256,512} threads per CTA and, for the forward
  * projection of FP32 rows, streaming tiles (64 rows per CTA, entries loaded
  * 16 bytes at a time independently of row boundaries), on all-ones vectors,
  * and keeps the fastest for psf_forward / psf_back of this plan; for a
- * factored plan it also times the two forms of the LOR-space spread stencil
- * in each direction and keeps the faster (call it after
+ * factored plan with full-window spreads it also times the two forms of the
+ * LOR-space spread stencil in each direction and keeps the faster (call it after
  * psf_matrix_set_spread).  chunk_out / threads_out: host arrays of 2
  * (forward, back), may be NULL; chunk -1 = streaming tiles, 0 = grid-stride,
  * > 0 = work queue.  Synchronises; allocates a temporary image-sized buffer;

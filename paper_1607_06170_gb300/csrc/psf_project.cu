@@ -42,6 +42,11 @@ struct psf_matrix {
     // transaxial partners (plan-owned, sized at psf_matrix_set_spread)
     float *csum;
     int64_t csum_n;
+    // factored plans with top-N spreads (psf_matrix_set_spread_topn): the
+    // kept window entries and weights of each class, N per class
+    int topn;
+    const int32_t *tidx;
+    const float *tw;
 };
 
 namespace psf {
@@ -1066,6 +1071,105 @@ __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, in
     }
 }
 
+// Top-N spreads (psf_matrix_set_spread_topn): S and S^T with each class's
+// kept window entries as sparse taps.  Forward: every source LOR g adds
+// w_k p[g] to the measured LOR that kept entry k of its class lands on
+// (several sources meet in one target: FP32 atomics, so the order of the
+// additions, and the last bits of a sum, vary between runs); adjoint:
+// q[g] = sum_k w_k r[m_k], a gather in rank order.  A window entry lands on
+// the crystal pair (a + dt1, ra + da1), (b + dt2, rb + da2), transaxial
+// indices wrapping around the ring; pairs outside the set, off the rings or
+// of one crystal with itself are dropped, as in the dense stencil.
+constexpr int TS_T = 256;
+
+template <bool adjoint>
+__global__ void __launch_bounds__(TS_T) topn_s_kernel(LorSet ls, int Wt, int Wa, int N,
+                                                      const int32_t *__restrict__ tidx,
+                                                      const float *__restrict__ tw,
+                                                      const float *__restrict__ in,
+                                                      float *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    int32_t *tp_start = reinterpret_cast<int32_t *>(raw);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    short2 *rp = reinterpret_cast<short2 *>(rp_start + ls.NR + 1);
+    const int t = threadIdx.x;
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    for (int j = t; j < ls.nrp; j += TS_T) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rp[j] = make_short2((short)r1, (short)r2);
+    }
+    __syncthreads();
+    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, Nt = ls.Nt, NR = ls.NR;
+    const int64_t n = ls.ntp * ls.nrp;
+    for (int64_t g = (int64_t)blockIdx.x * TS_T + t; g < n; g += (int64_t)gridDim.x * TS_T) {
+        const int64_t T = g / ls.nrp;
+        const int j = (int)(g - T * ls.nrp);
+        float pg = 0.0f;
+        if (!adjoint) {
+            pg = in[g];
+            if (pg == 0.0f) continue;
+        }
+        int a, b;
+        ls.tp_decode(tp_start, T, &a, &b);
+        const short2 r2 = rp[j];
+        const int ra = r2.x, rb = r2.y;
+        const int64_t cls = ls.class_of(tp_start, a, b, ra, rb);
+        const int32_t *ik = tidx + cls * N;
+        const float *wk = tw + cls * N;
+        float acc = 0.0f;
+        for (int k = 0; k < N; ++k) {
+            const float w = __ldg(wk + k);
+            if (w == 0.0f) continue;
+            const int e = __ldg(ik + k);
+            const int e1 = e / E, e2 = e - e1 * E;
+            const int qa = ra + e1 % W2a - Wa, qb = rb + e2 % W2a - Wa;
+            if (qa < 0 || qa >= NR || qb < 0 || qb >= NR) continue;
+            int pa = a + e1 / W2a - Wt, pb = b + e2 / W2a - Wt;
+            pa += pa < 0 ? Nt : (pa >= Nt ? -Nt : 0);
+            pb += pb < 0 ? Nt : (pb >= Nt ? -Nt : 0);
+            const bool sw = pa > pb;
+            const int A = sw ? pb : pa, B = sw ? pa : pb, RA = sw ? qb : qa, RB = sw ? qa : qb;
+            if (!ls.member(A, B, RA, RB)) continue;
+            const int64_t m = ls.row_of(tp_start, rp_start, A, B, RA, RB);
+            if (adjoint)
+                acc = fmaf(w, __ldg(in + m), acc);
+            else
+                atomicAdd(out + m, w * pg);
+        }
+        if (adjoint) out[g] = acc;
+    }
+}
+
+static int topn_s(const psf_matrix *m, const float *in, float *out, bool adjoint,
+                  cudaStream_t st) {
+    const size_t shm = sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2) + sizeof(short2) * m->ls.nrp + 16;
+    if (shm > 200 * 1024) return PSF_EINVAL;
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t n = m->ls.ntp * m->ls.nrp;
+    const int64_t need = (n + TS_T - 1) / TS_T;
+    const int grid = (int)(need < (int64_t)sms * 8 ? need : (int64_t)sms * 8);
+    if (adjoint) {
+        PSF_TRY(cudaFuncSetAttribute(topn_s_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        PSF_TIMED("topn_s_kernel<adjoint>", st);
+        topn_s_kernel<true><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
+                                                      m->tw, in, out);
+    } else {
+        PSF_TRY(cudaMemsetAsync(out, 0, sizeof(float) * n, st));
+        PSF_TRY(cudaFuncSetAttribute(topn_s_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        PSF_TIMED("topn_s_kernel<forward>", st);
+        topn_s_kernel<false><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
+                                                       m->tw, in, out);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
 static size_t sens_smem_bytes(const LorSet &ls, int Wa) {
     const int W2a = 2 * Wa + 1, nd = 2 * ls.Dm + 1;
     return sizeof(float) * nd * W2a * W2a + sizeof(short2) * ls.nrp +
@@ -1240,6 +1344,7 @@ static bool stencil3_ok(const LorSet &ls, int Wa) {
 
 static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoint,
                    cudaStream_t st) {
+    if (m->topn > 0) return topn_s(m, in, out, adjoint, st);
     int dev = 0, sms = 148;
     PSF_TRY(cudaGetDevice(&dev));
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1336,6 +1441,9 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->img2 = nullptr;
     m->csum = nullptr;
     m->csum_n = 0;
+    m->topn = 0;
+    m->tidx = nullptr;
+    m->tw = nullptr;
     if (cudaMalloc(&m->queue, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         delete m;
         return PSF_ECUDA;
@@ -1384,6 +1492,31 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
     m->Wa = half_a;
     m->E = (2 * half_t + 1) * (2 * half_a + 1);
     m->cls = class_spread;
+    m->topn = 0;
+    m->tidx = nullptr;
+    m->tw = nullptr;
+    return PSF_OK;
+}
+
+extern "C" int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scanner,
+                                          const psf_lor_set *set, int32_t half_t, int32_t half_a,
+                                          int32_t n_keep, const int32_t *idx, const float *w) {
+    if (!m || !idx || !w || half_t < 0 || half_a < 0) return PSF_EINVAL;
+    const int64_t E = (2 * (int64_t)half_t + 1) * (2 * (int64_t)half_a + 1);
+    if (n_keep < 1 || n_keep > E * E) return PSF_EINVAL;
+    LorSet ls;
+    int rc = make_lorset(scanner, set, &ls);
+    if (rc) return rc;
+    if (ls.ntp * ls.nrp != m->n_rows || ls.NR > 32000 || half_t >= ls.Nt) return PSF_EINVAL;
+    m->factored = true;
+    m->ls = ls;
+    m->Wt = half_t;
+    m->Wa = half_a;
+    m->E = (int)E;
+    m->cls = nullptr;
+    m->topn = n_keep;
+    m->tidx = idx;
+    m->tw = w;
     return PSF_OK;
 }
 
@@ -1432,7 +1565,7 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
         // queue at every (rows per take, threads per CTA) pair and, forward with
         // FP32 rows, the streaming tiles (chunk -1); each timed with CUDA events
         // on all-ones vectors (one warm-up, best of two), the fastest kept
-        static const int chunks[] = {-1, 0, 1, 2, 4, 8, 16, 32};
+        static const int chunks[] = {-1, 0, 1, 2, 4, 8, 16, 32, 64, 128};
         static const int threads[] = {128, 256, 512};
         float *x = nullptr;
         PSF_TRY(cudaMallocAsync(&x, sizeof(float) * m->n_cols, st));
@@ -1484,7 +1617,8 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
         if (e1) cudaEventDestroy(e1);
         cudaFreeAsync(x, st);
         if (rc) return rc;
-        if (m->factored && stencil3_ok(m->ls, m->Wa) && stencil4_ok(m->ls, m->Wa)) {
+        if (m->factored && m->topn == 0 && stencil3_ok(m->ls, m->Wa) &&
+            stencil4_ok(m->ls, m->Wa)) {
             // stencil form per direction: both timed on all-ones LOR vectors
             cudaEvent_t f0 = nullptr, f1 = nullptr;
             if (cudaEventCreate(&f0) != cudaSuccess || cudaEventCreate(&f1) != cudaSuccess)
@@ -1542,6 +1676,15 @@ namespace psf {
 // S^T 1 of a factored plan into out [n_rows]: the per-class partner sums, then
 // the per-pair window sums.
 static int sens_spread(const psf_matrix *m, float *out, cudaStream_t st) {
+    if (m->topn > 0) {  // S^T of an all-ones LOR vector, in the plan's other scratch
+        float *ones = out == m->p ? m->q : m->p;
+        {
+            PSF_TIMED("fill_kernel", st);
+            fill_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(ones, 1.0f, m->n_rows);
+        }
+        PSF_LAUNCHED();
+        return topn_s(m, ones, out, true, st);
+    }
     const int nwin = (2 * m->Wt + 1) * (2 * m->Wt + 1);
     const size_t shm = sens_smem_bytes(m->ls, m->Wa);
     if (nwin > 128 || shm > 200 * 1024 || !m->csum) return PSF_EINVAL;

@@ -28,6 +28,7 @@ FUNCTIONS = [
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
+    "psf_spread_topn", "psf_matrix_set_spread_topn",
 ]
 
 
@@ -88,6 +89,8 @@ _SIGS = {
     "psf_matrix_set_launch": (C.c_int, [_P, _I32, _I32]),
     "psf_sensitivity": (C.c_int, [_P, _P, _P]),
     "psf_back_sens": (C.c_int, [_P, _P, _P, _P, _P]),
+    "psf_spread_topn": (C.c_int, [_P, _I64, _I32, _I32, _I32, _P, _P, _P]),
+    "psf_matrix_set_spread_topn": (C.c_int, [_P, _P, _P, _I32, _I32, _I32, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -196,6 +199,17 @@ def bin_spread(sc: dict, tb: dict, T, eta, lors, half_t: int, half_a: int,
     return out
 
 
+def spread_topn(spread, half_t: int, half_a: int, n_keep: int):
+    """Top-N truncation of spreads [n, E, E] (psf_spread_topn): kept window
+    indices int32 [n, n_keep] in rank order and their rescaled weights."""
+    n = spread.shape[0]
+    idx = torch.empty((n, n_keep), dtype=torch.int32, device=spread.device)
+    w = torch.empty((n, n_keep), dtype=torch.float32, device=spread.device)
+    _ok(lib().psf_spread_topn(_ptr(spread), n, half_t, half_a, n_keep, _ptr(idx), _ptr(w),
+                              _stream()), "psf_spread_topn")
+    return idx, w
+
+
 def lor_set_size(sc: dict, ls: dict):
     s, l = scanner(sc), lor_set(ls)
     n, k = C.c_int64(), C.c_int64()
@@ -297,6 +311,15 @@ class Matrix:
         s, l = scanner(sc), lor_set(ls)
         _ok(lib().psf_matrix_set_spread(self._h, C.byref(s), C.byref(l), half_t, half_a,
                                         _ptr(class_spread)), "psf_matrix_set_spread")
+        return self
+
+    def set_spread_topn(self, sc: dict, ls: dict, half_t: int, half_a: int, idx, w):
+        """Factored form with top-N class spreads (outputs of spread_topn)."""
+        self._spread = (idx, w)  # the plan keeps the pointers; keep the tensors alive
+        s, l = scanner(sc), lor_set(ls)
+        _ok(lib().psf_matrix_set_spread_topn(self._h, C.byref(s), C.byref(l), half_t, half_a,
+                                             idx.shape[1], _ptr(idx), _ptr(w)),
+            "psf_matrix_set_spread_topn")
         return self
 
     def autotune(self):
