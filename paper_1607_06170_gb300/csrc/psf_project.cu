@@ -1076,23 +1076,31 @@ __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, in
 // w_k p[g] to the measured LOR that kept entry k of its class lands on
 // (several sources meet in one target: FP32 atomics, so the order of the
 // additions, and the last bits of a sum, vary between runs); adjoint:
-// q[g] = sum_k w_k r[m_k], a gather in rank order.  A window entry lands on
+// q[g] = sum_k w_k r[m_k], a gather in rank order (in == NULL: r = 1, the
+// sensitivity's S^T 1, with no reads).  A window entry lands on
 // the crystal pair (a + dt1, ra + da1), (b + dt2, rb + da2), transaxial
 // indices wrapping around the ring; pairs outside the set, off the rings or
 // of one crystal with itself are dropped, as in the dense stencil.
-constexpr int TS_T = 256;
+constexpr int TS_T = 256, TS_G = 8;
 
 template <bool adjoint>
-__global__ void __launch_bounds__(TS_T) topn_s_kernel(LorSet ls, int Wt, int Wa, int N,
+__global__ void __launch_bounds__(TS_T, 4) topn_s_kernel(LorSet ls, int Wt, int Wa, int N,
                                                       const int32_t *__restrict__ tidx,
                                                       const float *__restrict__ tw,
                                                       const float *__restrict__ in,
                                                       float *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char raw[];
-    int32_t *tp_start = reinterpret_cast<int32_t *>(raw);
+    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, Nt = ls.Nt, NR = ls.NR;
+    char4 *dec = reinterpret_cast<char4 *>(raw);  // [E*E] window index -> (dt1, da1, dt2, da2)
+    int32_t *tp_start = reinterpret_cast<int32_t *>(dec + E * E);
     int32_t *rp_start = tp_start + ls.Nt + 1;
     short2 *rp = reinterpret_cast<short2 *>(rp_start + ls.NR + 1);
     const int t = threadIdx.x;
+    for (int e = t; e < E * E; e += TS_T) {
+        const int e1 = e / E, e2 = e - e1 * E;
+        dec[e] = make_char4((signed char)(e1 / W2a - Wt), (signed char)(e1 % W2a - Wa),
+                            (signed char)(e2 / W2a - Wt), (signed char)(e2 % W2a - Wa));
+    }
     ls.stage_prefix(tp_start, rp_start);
     __syncthreads();
     for (int j = t; j < ls.nrp; j += TS_T) {
@@ -1101,7 +1109,6 @@ __global__ void __launch_bounds__(TS_T) topn_s_kernel(LorSet ls, int Wt, int Wa,
         rp[j] = make_short2((short)r1, (short)r2);
     }
     __syncthreads();
-    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, Nt = ls.Nt, NR = ls.NR;
     const int64_t n = ls.ntp * ls.nrp;
     for (int64_t g = (int64_t)blockIdx.x * TS_T + t; g < n; g += (int64_t)gridDim.x * TS_T) {
         const int64_t T = g / ls.nrp;
@@ -1119,24 +1126,43 @@ __global__ void __launch_bounds__(TS_T) topn_s_kernel(LorSet ls, int Wt, int Wa,
         const int32_t *ik = tidx + cls * N;
         const float *wk = tw + cls * N;
         float acc = 0.0f;
-        for (int k = 0; k < N; ++k) {
-            const float w = __ldg(wk + k);
-            if (w == 0.0f) continue;
-            const int e = __ldg(ik + k);
-            const int e1 = e / E, e2 = e - e1 * E;
-            const int qa = ra + e1 % W2a - Wa, qb = rb + e2 % W2a - Wa;
-            if (qa < 0 || qa >= NR || qb < 0 || qb >= NR) continue;
-            int pa = a + e1 / W2a - Wt, pb = b + e2 / W2a - Wt;
-            pa += pa < 0 ? Nt : (pa >= Nt ? -Nt : 0);
-            pb += pb < 0 ? Nt : (pb >= Nt ? -Nt : 0);
-            const bool sw = pa > pb;
-            const int A = sw ? pb : pa, B = sw ? pa : pb, RA = sw ? qb : qa, RB = sw ? qa : qb;
-            if (!ls.member(A, B, RA, RB)) continue;
-            const int64_t m = ls.row_of(tp_start, rp_start, A, B, RA, RB);
-            if (adjoint)
-                acc = fmaf(w, __ldg(in + m), acc);
-            else
-                atomicAdd(out + m, w * pg);
+        // taps in groups of TS_G: the targets first, then their reads or
+        // atomics, so a group's memory operations are in flight together
+        for (int k0 = 0; k0 < N; k0 += TS_G) {
+            int64_t m[TS_G];
+            float wv[TS_G];
+#pragma unroll
+            for (int u = 0; u < TS_G; ++u) {
+                m[u] = -1;
+                wv[u] = 0.0f;
+                const int k = k0 + u;
+                if (k >= N) continue;
+                const float w = __ldg(wk + k);
+                if (w == 0.0f) continue;
+                const char4 o = dec[__ldg(ik + k)];
+                const int qa = ra + o.y, qb = rb + o.w;
+                if (qa < 0 || qa >= NR || qb < 0 || qb >= NR) continue;
+                int pa = a + o.x, pb = b + o.z;
+                pa += pa < 0 ? Nt : (pa >= Nt ? -Nt : 0);
+                pb += pb < 0 ? Nt : (pb >= Nt ? -Nt : 0);
+                const bool sw = pa > pb;
+                const int A = sw ? pb : pa, B = sw ? pa : pb, RA = sw ? qb : qa, RB = sw ? qa : qb;
+                if (!ls.member(A, B, RA, RB)) continue;
+                m[u] = ls.row_of(tp_start, rp_start, A, B, RA, RB);
+                wv[u] = w;
+            }
+            if (adjoint) {
+                float v[TS_G];
+#pragma unroll
+                for (int u = 0; u < TS_G; ++u)
+                    v[u] = m[u] >= 0 ? (in ? __ldg(in + m[u]) : 1.0f) : 0.0f;
+#pragma unroll
+                for (int u = 0; u < TS_G; ++u) acc = fmaf(wv[u], v[u], acc);
+            } else {
+#pragma unroll
+                for (int u = 0; u < TS_G; ++u)
+                    if (m[u] >= 0) atomicAdd(out + m[u], wv[u] * pg);
+            }
         }
         if (adjoint) out[g] = acc;
     }
@@ -1144,7 +1170,8 @@ __global__ void __launch_bounds__(TS_T) topn_s_kernel(LorSet ls, int Wt, int Wa,
 
 static int topn_s(const psf_matrix *m, const float *in, float *out, bool adjoint,
                   cudaStream_t st) {
-    const size_t shm = sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2) + sizeof(short2) * m->ls.nrp + 16;
+    const size_t shm = sizeof(char4) * (size_t)m->E * m->E + sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2) +
+                       sizeof(short2) * m->ls.nrp + 16;
     if (shm > 200 * 1024) return PSF_EINVAL;
     int dev = 0, sms = 148;
     PSF_TRY(cudaGetDevice(&dev));
@@ -1501,7 +1528,8 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
 extern "C" int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scanner,
                                           const psf_lor_set *set, int32_t half_t, int32_t half_a,
                                           int32_t n_keep, const int32_t *idx, const float *w) {
-    if (!m || !idx || !w || half_t < 0 || half_a < 0) return PSF_EINVAL;
+    if (!m || !idx || !w || half_t < 0 || half_a < 0 || half_t > 127 || half_a > 127)
+        return PSF_EINVAL;
     const int64_t E = (2 * (int64_t)half_t + 1) * (2 * (int64_t)half_a + 1);
     if (n_keep < 1 || n_keep > E * E) return PSF_EINVAL;
     LorSet ls;
@@ -1676,15 +1704,7 @@ namespace psf {
 // S^T 1 of a factored plan into out [n_rows]: the per-class partner sums, then
 // the per-pair window sums.
 static int sens_spread(const psf_matrix *m, float *out, cudaStream_t st) {
-    if (m->topn > 0) {  // S^T of an all-ones LOR vector, in the plan's other scratch
-        float *ones = out == m->p ? m->q : m->p;
-        {
-            PSF_TIMED("fill_kernel", st);
-            fill_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(ones, 1.0f, m->n_rows);
-        }
-        PSF_LAUNCHED();
-        return topn_s(m, ones, out, true, st);
-    }
+    if (m->topn > 0) return topn_s(m, nullptr, out, true, st);  // S^T 1: no input reads
     const int nwin = (2 * m->Wt + 1) * (2 * m->Wt + 1);
     const size_t shm = sens_smem_bytes(m->ls, m->Wa);
     if (nwin > 128 || shm > 200 * 1024 || !m->csum) return PSF_EINVAL;
