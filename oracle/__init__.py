@@ -35,6 +35,7 @@ from .oracle import (  # noqa: F401
     spread_apply,
     spread_adjoint,
     mlem,
+    listmode_osem,
     poisson_loglik,
     poisson_grad,
     NORM_NONE,

@@ -386,6 +386,34 @@ def mlem(fwd, back, y: np.ndarray, nvox: int, iters: int, x0=None):
     return x
 
 
+def listmode_osem(fwd, back, event_rows: np.ndarray, n_lors: int, n_subsets: int, iters: int,
+                  x0=None):
+    """List-mode OSEM (the next step named in Sec. 5; subsets of events as
+    the OSEM subsets of Sec. 3), event by event: the events are split into
+    n_subsets consecutive subsets and for each subset
+        x_j <- x_j / (s_j / n_subsets) * sum_{e in subset} a_ej / sum_k a_ek x_k,
+    s = A^T 1, the per-event terms a_e / (a_e x) gathered one event at a time
+    into LOR space and back-projected once.  Events with row -1 (not in the
+    set) or a zero forward projection contribute nothing; voxels with
+    s < 1e-12 max(s) are held at 0."""
+    rows = np.asarray(event_rows, dtype=np.int64)
+    sens = back(np.ones(n_lors))
+    live = sens >= 1e-12 * sens.max()
+    x = np.where(live, 1.0, 0.0) if x0 is None else np.array(x0, dtype=np.float64)
+    n_ev = rows.shape[0]
+    bounds = [n_ev * j // n_subsets for j in range(n_subsets + 1)]
+    for _ in range(iters):
+        for j in range(n_subsets):
+            yh = fwd(x)
+            r = np.zeros(n_lors)
+            for m in rows[bounds[j]:bounds[j + 1]]:
+                if m >= 0 and yh[m] > 0:
+                    r[m] += 1.0 / yh[m]
+            bp = back(r)
+            x = np.where(live, x * bp / np.where(live, sens / n_subsets, 1.0), 0.0)
+    return x
+
+
 def poisson_loglik(fwd, y: np.ndarray, x: np.ndarray) -> float:
     """L(x) = sum y log(Ax) - Ax (the log y! term dropped)."""
     yh = fwd(x)

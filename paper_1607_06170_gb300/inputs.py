@@ -118,6 +118,27 @@ WORKLOADS = {
         window=(3, 0),
         lors=dict(fan_half=31, max_ring_diff=0),
     ),
+    # list-mode OSEM: the 3D ring with 8 block rings (104 crystal rings), three
+    # uniform spheres of equal concentration, subsets of events
+    "RING3D_LM": dict(
+        index=4,
+        scanner=scanner(24, 13, 13, 8, 1.9, 1.9, 10.0, 0.3, 0.3, 130.0, 0.3, 0.087),
+        table=table(32, 8, 8, 8, 16, 6, 72.0, 16.0),
+        image=image(200, 200, 208, 0.8, 0.8, 0.8),
+        window=(3, 3),
+        lors=dict(fan_half=104, max_ring_diff=15),
+        listmode=dict(events=10_000_000, subset_events=1_000_000, radii_mm=(5.0, 10.0, 20.0),
+                      n_keep=5),
+    ),
+    "RING3D_SMALL_LM": dict(
+        index=12,
+        scanner=scanner(12, 4, 4, 2, 1.9, 1.9, 10.0, 0.3, 0.3, 30.0, 0.3, 0.087),
+        table=table(13, 4, 4, 4, 16, 8, 65.0, 36.0),
+        image=image(24, 24, 16, 1.5, 1.5, 1.1),
+        window=(3, 2),
+        lors=dict(fan_half=10, max_ring_diff=3),
+        listmode=dict(events=20_000, subset_events=5_000, radii_mm=(2.0, 3.0, 4.0), n_keep=5),
+    ),
     "RING3D_GRAD": dict(
         index=3,
         scanner=scanner(24, 13, 13, 4, 1.9, 1.9, 10.0, 0.3, 0.3, 130.0, 0.3, 0.087),
@@ -170,6 +191,109 @@ def lor_list(s: dict, fan_half: int, max_ring_diff: int) -> np.ndarray:
     a = (rp[None, :, 0] * nt + tp[:, None, 0]).reshape(-1)
     b = (rp[None, :, 1] * nt + tp[:, None, 1]).reshape(-1)
     return np.stack([a, b], 1).astype(np.int32)
+
+
+def _crystal_hits(s: dict, p, d):
+    """Crystal reached by rays from points p along directions d (torch [M, 3]
+    float64): the front-face plane of the block the ray leaves the ring
+    polygon through, the crystal under the hit point (transaxial pitch, rings
+    on a uniform axial pitch centred on z = 0).  Returns (transaxial index,
+    ring, ok) with ok False where the hit point falls off the crystal faces
+    (block corners, gaps, beyond the rings)."""
+    import torch
+
+    R, nb = s["n_blocks"], s["nt_block"]
+    nr = n_rings(s)
+    pt = s["xtal_w_t"] + s["gap_t"]
+    pa = s["xtal_w_a"] + s["gap_a"]
+    # the exit through the circumscribed circle picks the block up to one
+    # neighbour; the nearest of those three face planes is the polygon's exit
+    rc = s["radius"] / math.cos(math.pi / R)
+    dxy, pxy = d[:, :2], p[:, :2]
+    aa = (dxy * dxy).sum(1)
+    bb = (pxy * dxy).sum(1)
+    cc = (pxy * pxy).sum(1) - rc * rc
+    tc = (-bb + torch.sqrt(torch.clamp(bb * bb - aa * cc, min=0.0))) / aa
+    e = pxy + tc[:, None] * dxy
+    b0 = torch.round(torch.atan2(e[:, 1], e[:, 0]) / (2 * math.pi / R)).long()
+    cand = (b0[:, None] + torch.tensor([-1, 0, 1], device=p.device)[None, :]) % R   # [M, 3]
+    phi = (2 * math.pi / R) * cand.double()
+    dn = dxy[:, :1] * torch.cos(phi) + dxy[:, 1:] * torch.sin(phi)
+    pn = pxy[:, :1] * torch.cos(phi) + pxy[:, 1:] * torch.sin(phi)
+    t = torch.where(dn > 1e-12, (s["radius"] - pn) / torch.where(dn > 1e-12, dn, 1.0),
+                    torch.full_like(dn, math.inf))
+    tm, j = torch.min(t, 1)
+    blk = cand.gather(1, j[:, None])[:, 0]
+    h = p + torch.where(torch.isfinite(tm), tm, 0.0)[:, None] * d
+    pb = (2 * math.pi / R) * blk.double()
+    st = -h[:, 0] * torch.sin(pb) + h[:, 1] * torch.cos(pb)
+    u = st / pt + 0.5 * (nb - 1)                                    # crystal centres at integers
+    i = torch.round(u).long()
+    ok = torch.isfinite(tm) & ((u - i).abs() * pt <= 0.5 * s["xtal_w_t"]) & (i >= 0) & (i < nb)
+    v = h[:, 2] / pa + 0.5 * (nr - 1)
+    r = torch.round(v).long()
+    ok &= ((v - r).abs() * pa <= 0.5 * s["xtal_w_a"]) & (r >= 0) & (r < nr)
+    return blk * nb + i, r, ok
+
+
+def listmode_events(w: dict, n: int, k: int, device="cpu"):
+    """Coincidence events as crystal-id pairs (torch int32 [n, 2] on `device`,
+    id = ring * Nt + transaxial index; the first crystal is the one with the
+    smaller transaxial index) from three uniform spheres of equal
+    concentration (radii w["listmode"]["radii_mm"], seeded centres inside the
+    image), emitted back to back in isotropic directions.  A pair is redrawn
+    when a photon misses the crystal faces or the pair is outside the LOR set
+    (fan, ring difference).  Directions are drawn uniformly in the band of
+    axial direction cosines that can reach an accepted pair (a redraw of the
+    rest).  Seeded per device type (torch generators)."""
+    import torch
+
+    s, im, ls = w["scanner"], w["image"], w["lors"]
+    gen = torch.Generator(device=device).manual_seed(SEED + k)
+    radii = torch.tensor(w["listmode"]["radii_mm"], dtype=torch.float64, device=device)
+    nt, nr = n_transaxial(s), n_rings(s)
+    F, Dm = ls["fan_half"], ls["max_ring_diff"]
+    half_xy = 0.5 * min(im["nx"] * im["dx"], im["ny"] * im["dy"])
+    half_z = 0.5 * min(im["nz"] * im["dz"], nr * (s["xtal_w_a"] + s["gap_a"]))
+    g = rng(k)  # sphere centres from the numpy stream (identical on every device)
+    cen = []
+    for rs in w["listmode"]["radii_mm"]:
+        rho = g.uniform(0.0, max(0.0, 0.8 * half_xy - rs))
+        ang = g.uniform(0.0, 2 * np.pi)
+        zz = max(0.0, 0.8 * half_z - rs)
+        cen.append((rho * np.cos(ang), rho * np.sin(ang), g.uniform(-zz, zz)))
+    centres = torch.tensor(cen, dtype=torch.float64, device=device)
+    prob = radii ** 3 / (radii ** 3).sum()
+    # largest axial slope of an accepted pair: Dm + 1 ring pitches over the shortest chord
+    pa = s["xtal_w_a"] + s["gap_a"]
+    chord = 2 * s["radius"] * math.sin(math.pi * (nt // 2 - F) / nt)
+    slope = 1.25 * (Dm + 1) * pa / chord
+    cmax = min(1.0, slope / math.sqrt(1 + slope * slope))
+    out, have = [], 0
+    f64 = dict(dtype=torch.float64, device=device, generator=gen)
+    while have < n:
+        m = max(6 * (n - have), 4096)
+        sph = torch.multinomial(prob, m, replacement=True, generator=gen)
+        dirs = torch.randn((m, 3), **f64)
+        dirs /= dirs.norm(dim=1, keepdim=True)
+        rad = radii[sph] * torch.rand(m, **f64) ** (1.0 / 3.0)
+        p = centres[sph] + rad[:, None] * dirs
+        cz = (2 * torch.rand(m, **f64) - 1) * cmax
+        az = 2 * math.pi * torch.rand(m, **f64)
+        sz = torch.sqrt(1.0 - cz * cz)
+        d = torch.stack([sz * torch.cos(az), sz * torch.sin(az), cz], 1)
+        c1, r1, ok1 = _crystal_hits(s, p, d)
+        c2, r2, ok2 = _crystal_hits(s, p, -d)
+        swap = c1 > c2
+        a, b = torch.where(swap, c2, c1), torch.where(swap, c1, c2)
+        ra, rb = torch.where(swap, r2, r1), torch.where(swap, r1, r2)
+        dd = b - a
+        ok = ok1 & ok2 & (a != b) & (dd >= nt // 2 - F) & (dd <= nt // 2 + F) & (
+            (rb - ra).abs() <= Dm)
+        ev = torch.stack([ra * nt + a, rb * nt + b], 1)[ok][: n - have]
+        out.append(ev)
+        have += ev.shape[0]
+    return torch.cat(out).to(torch.int32)
 
 
 def workload_lors(w: dict) -> np.ndarray:
