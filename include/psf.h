@@ -152,6 +152,22 @@ int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *desc, const
 int psf_spread_topn(const float *spread, int64_t n_lors, int32_t half_t, int32_t half_a,
                     int32_t n_keep, int32_t *idx, float *w, void *stream);
 
+/*
+ * List-mode data (the next step the paper names in Sec. 5; events stand for
+ * the histogram organisation of Sec. 4, Table 1).  psf_event_rows writes the
+ * row of each event's crystal pair (device int32 [n_events][2] crystal ids, in
+ * either order) in the structured set, or -1 when the pair is not in it
+ * (device int64 [n_events]).  psf_histogram overwrites counts (device float
+ * [n_rows]) with weight times the number of events per row (rows < 0 or
+ * >= n_rows are skipped).  With weight = the number of subsets, one OSEM
+ * sub-iteration over a subset of events is the MLEM update of the set's
+ * projector on those counts: x <- x * A^T(c / A x) / A^T 1.
+ */
+int psf_event_rows(const psf_scanner *scanner, const psf_lor_set *set, const int32_t *events,
+                   int64_t n_events, int64_t *rows, void *stream);
+int psf_histogram(const int64_t *rows, int64_t n_events, float weight, float *counts,
+                  int64_t n_rows, void *stream);
+
 /* Number of LORs of a structured set, and of its spread classes (one per
  * transaxial pair with a < nt_block times ring difference; every LOR of the
  * set has the spread of its class by the ring's rotation and axial
@@ -313,6 +329,15 @@ int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream);
 
 /* x = A^T y (overwrite). */
 int psf_back(const psf_matrix *m, const float *y, float *x, void *stream);
+
+/* y = A x on the rows with mask != 0 (mask: device float [n_rows],
+ * non-negative, e.g. a subset's counts); every other entry of y is 0.  Only
+ * the stored rows that reach a masked row are evaluated (for a factored plan:
+ * the sources with S^T mask != 0), so a subset of list-mode events costs in
+ * proportion to the LORs it touches.  Uses the plan's scratch; rows of the
+ * plan < 2^31. */
+int psf_forward_masked(const psf_matrix *m, const float *x, const float *mask, float *y,
+                       void *stream);
 
 /* MLEM steps (Sec. 3): ratio[i] = y[i] / yhat[i] (0 where yhat[i] <= 0). */
 int psf_em_ratio(const float *y, const float *yhat, float *ratio, int64_t n, void *stream);

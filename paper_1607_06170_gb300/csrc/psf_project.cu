@@ -207,6 +207,46 @@ __global__ void csr_back_wq_kernel(int64_t n, const int64_t *__restrict__ ptr,
     }
 }
 
+// Masked forward (psf_forward_masked): the rows with a nonzero mask are
+// listed (warp-aggregated appends; the list's order does not matter, each
+// row's dot product is computed alone), then one warp per listed row.
+__global__ void mask_rows_kernel(const float *__restrict__ mask, int64_t n,
+                                 int32_t *__restrict__ list, unsigned long long *count) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = base + lane;
+        const bool on = r < n && mask[r] != 0.0f;
+        const unsigned b = __ballot_sync(0xffffffffu, on);
+        unsigned long long at = 0;
+        if (lane == 0 && b) at = atomicAdd(count, (unsigned long long)__popc(b));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (on) list[at + __popc(b & ((1u << lane) - 1u))] = (int32_t)r;
+    }
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(PJ_T) csr_fwd_list_kernel(
+    const int32_t *__restrict__ list, const unsigned long long *count,
+    const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const VT *__restrict__ val,
+    const float *__restrict__ scale, const float *__restrict__ x, float *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nl = (int64_t)*count;
+    const int64_t wpb = PJ_T / 32;
+    for (int64_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nl; i += gridDim.x * wpb) {
+        const int64_t r = list[i];
+        const float acc = csr_row_dot(ptr, col, val, x, r, lane);
+        if (lane == 0) y[r] = scale ? acc * scale[r] : acc;
+    }
+}
+
+__global__ void keep_masked_kernel(const float *__restrict__ mask, float *__restrict__ y,
+                                   int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (mask[i] == 0.0f) y[i] = 0.0f;
+}
+
 // Streaming form of y = A x for FP32 rows: a CTA takes a tile of CS_ROWS
 // consecutive rows and streams their entries with 16-byte loads, four
 // entries per thread per step regardless of where rows begin, so the loads
@@ -1567,6 +1607,60 @@ extern "C" int psf_forward(const psf_matrix *m, const float *x, float *y, void *
     int rc = rows_fwd(m, x, m->p, st);
     if (rc) return rc;
     return stencil(m, m->p, y, false, st);
+}
+
+namespace psf {
+
+// y = G x on the rows with mask != 0 only (the others 0); list: int32
+// scratch of n_rows entries.
+static int rows_fwd_masked(const psf_matrix *m, const float *x, const float *mask, float *y,
+                           int32_t *list, cudaStream_t st) {
+    PSF_TRY(cudaMemsetAsync(m->queue, 0, sizeof(unsigned long long), st));
+    {
+        PSF_TIMED("mask_rows_kernel", st);
+        mask_rows_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(mask, m->n_rows, list,
+                                                                    m->queue);
+    }
+    PSF_LAUNCHED();
+    PSF_TRY(cudaMemsetAsync(y, 0, sizeof(float) * m->n_rows, st));
+    return dispatch_dtype(m->dtype, [&](auto tag) -> int {
+        using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+        int dev = 0, sms = 148;
+        PSF_TRY(cudaGetDevice(&dev));
+        PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        {
+            PSF_TIMED("csr_fwd_list_kernel", st);
+            csr_fwd_list_kernel<VT><<<sms * 8, PJ_T, 0, st>>>(list, m->queue, m->row_ptr, m->col,
+                                                              (const VT *)m->val, m->row_scale,
+                                                              x, y);
+        }
+        PSF_LAUNCHED();
+        return PSF_OK;
+    });
+}
+
+}  // namespace psf
+
+extern "C" int psf_forward_masked(const psf_matrix *m, const float *x, const float *mask,
+                                  float *y, void *stream) {
+    if (!m || !x || !mask || !y) return PSF_EINVAL;
+    if (m->n_rows == 0) return PSF_OK;
+    if (m->n_rows > INT32_MAX) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    if (!m->factored) return rows_fwd_masked(m, x, mask, y, reinterpret_cast<int32_t *>(m->p), st);
+    // sources feeding a masked measured LOR: S^T of the (non-negative) mask
+    int rc = stencil(m, mask, m->q, true, st);
+    if (rc) return rc;
+    rc = rows_fwd_masked(m, x, m->q, m->p, reinterpret_cast<int32_t *>(y), st);
+    if (rc) return rc;
+    rc = stencil(m, m->p, y, false, st);
+    if (rc) return rc;
+    {
+        PSF_TIMED("keep_masked_kernel", st);
+        keep_masked_kernel<<<grid_for(m->n_rows, 256), 256, 0, st>>>(mask, y, m->n_rows);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
 }
 
 extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *stream) {

@@ -28,7 +28,8 @@ FUNCTIONS = [
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
-    "psf_spread_topn", "psf_matrix_set_spread_topn",
+    "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
+    "psf_forward_masked",
 ]
 
 
@@ -91,6 +92,9 @@ _SIGS = {
     "psf_back_sens": (C.c_int, [_P, _P, _P, _P, _P]),
     "psf_spread_topn": (C.c_int, [_P, _I64, _I32, _I32, _I32, _P, _P, _P]),
     "psf_matrix_set_spread_topn": (C.c_int, [_P, _P, _P, _I32, _I32, _I32, _P, _P]),
+    "psf_event_rows": (C.c_int, [_P, _P, _P, _I64, _P, _P]),
+    "psf_histogram": (C.c_int, [_P, _I64, C.c_float, _P, _I64, _P]),
+    "psf_forward_masked": (C.c_int, [_P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -208,6 +212,23 @@ def spread_topn(spread, half_t: int, half_a: int, n_keep: int):
     _ok(lib().psf_spread_topn(_ptr(spread), n, half_t, half_a, n_keep, _ptr(idx), _ptr(w),
                               _stream()), "psf_spread_topn")
     return idx, w
+
+
+def event_rows(sc: dict, ls: dict, events):
+    """Row of each event (int32 [n, 2] crystal ids) in the set, -1 outside."""
+    s, l = scanner(sc), lor_set(ls)
+    rows = torch.empty(events.shape[0], dtype=torch.int64, device=events.device)
+    _ok(lib().psf_event_rows(C.byref(s), C.byref(l), _ptr(events), events.shape[0], _ptr(rows),
+                             _stream()), "psf_event_rows")
+    return rows
+
+
+def histogram(rows, n_rows: int, weight: float = 1.0, out=None):
+    """weight x events per row (float [n_rows])."""
+    out = torch.empty(n_rows, dtype=torch.float32, device=rows.device) if out is None else out
+    _ok(lib().psf_histogram(_ptr(rows), rows.numel(), float(weight), _ptr(out), n_rows,
+                            _stream()), "psf_histogram")
+    return out
 
 
 def lor_set_size(sc: dict, ls: dict):
@@ -341,6 +362,14 @@ class Matrix:
         if out is None:
             out = torch.empty(self.n_rows, dtype=torch.float32, device=x.device)
         _ok(lib().psf_forward(self._h, _ptr(x), _ptr(out), _stream()), "psf_forward")
+        return out
+
+    def forward_masked(self, x, mask, out=None):
+        """A x on the rows with mask != 0, 0 elsewhere (psf_forward_masked)."""
+        if out is None:
+            out = torch.empty(self.n_rows, dtype=torch.float32, device=x.device)
+        _ok(lib().psf_forward_masked(self._h, _ptr(x), _ptr(mask), _ptr(out), _stream()),
+            "psf_forward_masked")
         return out
 
     def sensitivity(self, out=None, device="cuda"):

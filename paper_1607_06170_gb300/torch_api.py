@@ -86,3 +86,38 @@ def mlem(matrix, y, iters: int = 10, x0=None, sens=None, graph: bool = False):
             iteration(x)
     g.replay()
     return x
+
+
+def listmode_osem(matrix, rows, n_subsets: int, iters: int = 1, x0=None, sens=None):
+    """List-mode OSEM over events (the next step named in Sec. 5, with the
+    subsets of Sec. 3): the events (their set rows, psf_event_rows) are split
+    into n_subsets consecutive subsets, and each sub-iteration is
+      x <- x * sum_{e in subset} A_e^T / (A_e x) / (A^T 1 / n_subsets),
+    formed as the MLEM update on the subset's counts weighted by n_subsets
+    (psf_histogram, psf_forward_masked -- the projection only on the LORs the
+    subset's events hit --, psf_em_ratio, psf_back, psf_em_update).
+    Voxels with sens < 1e-12 * max(sens) are held at zero."""
+    n_ev = rows.numel()
+    if sens is None:
+        sens = matrix.sensitivity(device=rows.device)
+    floor = 1e-12 * float(sens.max())
+    if x0 is None:
+        x = torch.ones_like(sens)
+        psf.em_update(x, sens, sens, floor)  # 1 on voxels the scanner sees
+    else:
+        x = x0.clone()
+    counts = torch.empty(matrix.n_rows, dtype=torch.float32, device=rows.device)
+    yhat = torch.empty_like(counts)
+    ratio = torch.empty_like(counts)
+    bp = torch.empty_like(sens)
+    bounds = [n_ev * j // n_subsets for j in range(n_subsets + 1)]
+    for _ in range(iters):
+        for j in range(n_subsets):
+            psf.histogram(rows[bounds[j]:bounds[j + 1]], matrix.n_rows, float(n_subsets),
+                          out=counts)
+            matrix.forward_masked(x, counts, out=yhat)
+            psf.em_ratio(counts, yhat, out=ratio)
+            matrix.back(ratio, out=bp)
+            psf.em_update(x, bp, sens, floor)
+    return x
+
