@@ -22,6 +22,8 @@ from .oracle import (  # noqa: F401
     composed,
     spread,
     spread_topn,
+    sino_index,
+    lor_normal,
     tie_margin,
     tie_count,
     siddon,

@@ -95,6 +95,8 @@ def _load():
                 "orc_spread_apply": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
                 "orc_spread_adjoint": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
                 "orc_spread_topn": (None, [C.c_int64, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
+                "orc_sino_index": (None, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+                "orc_lor_normal": (None, [_P, C.c_int, C.c_int, _P, _P]),
                 "orc_threads": (C.c_int, []),
                 "orc_tie_margin": (None, [_P, _P, _P, _P, C.c_int64, _P]),
                 "orc_tie_stats": (None, [_P, _P, _P, _P, C.c_int64, C.c_double, _P, _P]),
@@ -351,6 +353,28 @@ def spread_adjoint(scanner: dict, lors, w: np.ndarray, Wt: int, Wa: int, r: np.n
     _load().orc_spread_adjoint(C.byref(s), L.shape[0], _ptr(L), _ptr(w), int(Wt), int(Wa),
                                _ptr(pair_row_map(scanner, L)), _ptr(r), _ptr(q))
     return q
+
+
+def sino_index(scanner: dict, pairs, fan_half: int):
+    """(view, bin) of each transaxial pair (a, b), a < b (int [n, 2])."""
+    sc = _scanner(scanner)
+    P = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    out = np.zeros((P.shape[0], 2), dtype=np.int64)
+    v, b = C.c_int(), C.c_int()
+    f = _load().orc_sino_index
+    for k, (a, bb) in enumerate(P):
+        f(C.byref(sc), int(a), int(bb), int(fan_half), C.byref(v), C.byref(b))
+        out[k] = (v.value, b.value)
+    return out
+
+
+def lor_normal(scanner: dict, a: int, b: int):
+    """(phi in [0, pi), signed axis distance) of the line joining the face
+    centres of transaxial crystals a and b."""
+    sc = _scanner(scanner)
+    ph, d = C.c_double(), C.c_double()
+    _load().orc_lor_normal(C.byref(sc), int(a), int(b), C.byref(ph), C.byref(d))
+    return ph.value, d.value
 
 
 def spread_topn(w: np.ndarray, Wt: int, Wa: int, N: int):

@@ -26,6 +26,8 @@
  *   orc_csr_fwd / back  pinned (dot-product identity, MLEM count identity)
  *   orc_spread_topn     pinned (N = whole window is the identity, sum rule,
  *                       ranking against a brute-force order, tie rules)
+ *   orc_sino_index      pinned (one to one onto views x bins; bins ordered by
+ *                       the geometric offset within a view, views by angle)
  *   agreement of the analytic response with GATE: parity unpinned (the
  *   paper's response curves, Figs. 2-5, are not in the text).
  */
@@ -1007,6 +1009,48 @@ void orc_spread_topn(int64_t n, const double *w, int Wt, int Wa, int N, double *
         }
     }
     free(order);
+}
+
+/*
+ * Sinogram indexing of the histogram organisation (Sec. 4, Table 1: 192
+ * angles x 199 bins per angle for 384 crystals per ring).  Reading (the
+ * paper gives only the sizes): the ideal-ring convention.  For the pair of
+ * transaxial indices a < b with d = b - a within F of N/2, u = a + b:
+ *   view = (u mod N) / 2          (two adjacent sums per view: interleaving)
+ *   bin  = sg * (d - N/2) + F,    sg = +1 if u < N, else -1
+ * which maps the (2F+1) N/2 pairs one to one onto views x bins.
+ */
+void orc_sino_index(const orc_scanner *s, int a, int b, int F, int *view, int *bin)
+{
+    int N = orc_nt(s), u = a + b, d = b - a;
+    *view = (u % N) / 2;
+    *bin = (u < N ? 1 : -1) * (d - N / 2) + F;
+}
+
+/* Normal angle phi in [0, pi) and signed distance from the axis of the
+ * transaxial line joining the face centres of crystals a and b (ring 0). */
+void orc_lor_normal(const orc_scanner *s, int a, int b, double *phi, double *dist)
+{
+    double A[3], B[3];
+    orc_face_point(s, a, 0.0, 0.0, A);
+    orc_face_point(s, b, 0.0, 0.0, B);
+    double tx = B[0] - A[0], ty = B[1] - A[1];
+    double nx = ty, ny = -tx, L = sqrt(nx * nx + ny * ny);
+    nx /= L;
+    ny /= L;
+    double ph = atan2(ny, nx);
+    if (ph < 0.0) {
+        ph += ORC_PI;
+        nx = -nx;
+        ny = -ny;
+    }
+    if (ph >= ORC_PI) {
+        ph -= ORC_PI;
+        nx = -nx;
+        ny = -ny;
+    }
+    *phi = ph;
+    *dist = A[0] * nx + A[1] * ny;
 }
 
 /* Number of OpenMP threads the oracle runs with (for the baseline record). */

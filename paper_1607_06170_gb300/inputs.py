@@ -139,6 +139,19 @@ WORKLOADS = {
         lors=dict(fan_half=10, max_ring_diff=3),
         listmode=dict(events=20_000, subset_events=5_000, radii_mm=(2.0, 3.0, 4.0), n_keep=5),
     ),
+    # the paper's scanner (Sec. 4): 2 rings of 24 modules of 16 x 16 crystals of 2 x 2 x 10 mm
+    # on a 2 mm pitch (384 crystals per crystal ring, 32 rings); the radius is not given (125 mm
+    # reading); the histogram organisation of Table 1: 192 angles x 199 bins per ring pair,
+    # direct and cross planes (ring difference <= 1, 63 slices of 1 mm), 380 x 380 x 63 image
+    "EPLUS260": dict(
+        index=5,
+        scanner=scanner(24, 16, 16, 2, 2.0, 2.0, 10.0, 0.0, 0.0, 125.0, 0.0, 0.087),
+        table=table(32, 2, 8, 8, 16, 4, 60.0, 4.0),
+        image=image(380, 380, 63, 0.5, 0.5, 1.0),
+        window=(3, 1),
+        lors=dict(fan_half=99, max_ring_diff=1),
+        sino=dict(views=192, bins=199),
+    ),
     "RING3D_GRAD": dict(
         index=3,
         scanner=scanner(24, 13, 13, 4, 1.9, 1.9, 10.0, 0.3, 0.3, 130.0, 0.3, 0.087),
