@@ -168,6 +168,16 @@ int psf_event_rows(const psf_scanner *scanner, const psf_lor_set *set, const int
 int psf_histogram(const int64_t *rows, int64_t n_events, float weight, float *counts,
                   int64_t n_rows, void *stream);
 
+/* Sinogram view and bin (device int32 [ntp] each) of every transaxial pair of
+ * the set, in set order -- the histogram organisation of Sec. 4, Table 1 (192
+ * angles x 199 bins for 384 crystals per ring and fan 99).  Ideal-ring reading:
+ * u = a + b, view = (u mod Nt) / 2, bin = sg (b - a - Nt/2) + fan_half with
+ * sg = +1 for u < Nt, else -1; one to one onto Nt/2 views x (2 fan_half + 1)
+ * bins.  Row of LOR (transaxial pair T, ring pair j) = T * n_ring_pairs + j.
+ * PSF_EINVAL for an odd Nt or fan_half >= Nt/2. */
+int psf_sino_bins(const psf_scanner *scanner, const psf_lor_set *set, int32_t *view,
+                  int32_t *bin, void *stream);
+
 /* Number of LORs of a structured set, and of its spread classes (one per
  * transaxial pair with a < nt_block times ring difference; every LOR of the
  * set has the spread of its class by the ring's rotation and axial

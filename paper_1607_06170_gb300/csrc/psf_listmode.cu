@@ -45,9 +45,45 @@ __global__ void __launch_bounds__(LM_T) histogram_kernel(const int64_t *__restri
     }
 }
 
+// Sinogram view and bin of every transaxial pair of the set (the histogram
+// organisation of Sec. 4, Table 1), ideal-ring convention: u = a + b,
+// view = (u mod Nt) / 2, bin = sg (b - a - Nt/2) + F, sg = +1 if u < Nt else -1.
+__global__ void __launch_bounds__(LM_T) sino_bins_kernel(LorSet ls, int32_t *__restrict__ view,
+                                                         int32_t *__restrict__ bin) {
+    extern __shared__ int32_t sb_pre[];  // tp_start [Nt + 1], rp_start [NR + 1]
+    ls.stage_prefix(sb_pre, sb_pre + ls.Nt + 1);
+    __syncthreads();
+    for (int64_t T = (int64_t)blockIdx.x * LM_T + threadIdx.x; T < ls.ntp;
+         T += (int64_t)gridDim.x * LM_T) {
+        int a, b;
+        ls.tp_decode(sb_pre, T, &a, &b);
+        const int u = a + b, d = b - a;
+        view[T] = (u % ls.Nt) / 2;
+        bin[T] = (u < ls.Nt ? 1 : -1) * (d - ls.Nt / 2) + ls.F;
+    }
+}
+
 }  // namespace psf
 
 using namespace psf;
+
+extern "C" int psf_sino_bins(const psf_scanner *scanner, const psf_lor_set *set, int32_t *view,
+                             int32_t *bin, void *stream) {
+    LorSet ls;
+    int rc = make_lorset(scanner, set, &ls);
+    if (rc) return rc;
+    if (ls.Nt % 2 || ls.F > ls.Nt / 2 - 1) return PSF_EINVAL;
+    if (ls.ntp == 0) return PSF_OK;
+    if (!view || !bin) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const size_t shm = sizeof(int32_t) * (ls.Nt + ls.NR + 2);
+    {
+        PSF_TIMED("sino_bins_kernel", st);
+        sino_bins_kernel<<<grid_for(ls.ntp, LM_T), LM_T, shm, st>>>(ls, view, bin);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
 
 extern "C" int psf_event_rows(const psf_scanner *scanner, const psf_lor_set *set,
                               const int32_t *events, int64_t n_events, int64_t *rows,

@@ -29,7 +29,7 @@ FUNCTIONS = [
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
-    "psf_forward_masked",
+    "psf_forward_masked", "psf_sino_bins",
 ]
 
 
@@ -95,6 +95,7 @@ _SIGS = {
     "psf_event_rows": (C.c_int, [_P, _P, _P, _I64, _P, _P]),
     "psf_histogram": (C.c_int, [_P, _I64, C.c_float, _P, _I64, _P]),
     "psf_forward_masked": (C.c_int, [_P, _P, _P, _P, _P]),
+    "psf_sino_bins": (C.c_int, [_P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -221,6 +222,25 @@ def event_rows(sc: dict, ls: dict, events):
     _ok(lib().psf_event_rows(C.byref(s), C.byref(l), _ptr(events), events.shape[0], _ptr(rows),
                              _stream()), "psf_event_rows")
     return rows
+
+
+def sino_bins(sc: dict, ls: dict, device="cuda"):
+    """Sinogram (view, bin) of every transaxial pair of the set (int32 [ntp] each)."""
+    s, l = scanner(sc), lor_set(ls)
+    n, _ = lor_set_size(sc, ls)
+    ntp = n // len_ring_pairs(sc, ls)
+    view = torch.empty(ntp, dtype=torch.int32, device=device)
+    bins = torch.empty(ntp, dtype=torch.int32, device=device)
+    _ok(lib().psf_sino_bins(C.byref(s), C.byref(l), _ptr(view), _ptr(bins), _stream()),
+        "psf_sino_bins")
+    return view, bins
+
+
+def len_ring_pairs(sc: dict, ls: dict) -> int:
+    """Ordered ring pairs of the set (|ra - rb| <= max_ring_diff)."""
+    nr = sc["na_block"] * sc["n_block_rings"]
+    d = ls["max_ring_diff"]
+    return sum(min(nr - 1, r + d) - max(0, r - d) + 1 for r in range(nr))
 
 
 def histogram(rows, n_rows: int, weight: float = 1.0, out=None):
