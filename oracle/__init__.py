@@ -23,6 +23,7 @@ from .oracle import (  # noqa: F401
     spread,
     spread_topn,
     sino_index,
+    voxel_homog,
     lor_normal,
     tie_margin,
     tie_count,

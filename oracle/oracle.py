@@ -96,6 +96,8 @@ def _load():
                 "orc_spread_adjoint": (None, [_P, C.c_int64, _P, _P, C.c_int, C.c_int, _P, _P, _P]),
                 "orc_spread_topn": (None, [C.c_int64, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
                 "orc_sino_index": (None, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+                "orc_voxel_homog": (None, [_P, _P, _P, _P, C.c_int, C.c_int, _P, C.c_int64, _P,
+                                           _P]),
                 "orc_lor_normal": (None, [_P, C.c_int, C.c_int, _P, _P]),
                 "orc_threads": (C.c_int, []),
                 "orc_tie_margin": (None, [_P, _P, _P, _P, C.c_int64, _P]),
@@ -353,6 +355,21 @@ def spread_adjoint(scanner: dict, lors, w: np.ndarray, Wt: int, Wa: int, r: np.n
     _load().orc_spread_adjoint(C.byref(s), L.shape[0], _ptr(L), _ptr(w), int(Wt), int(Wa),
                                _ptr(pair_row_map(scanner, L)), _ptr(r), _ptr(q))
     return q
+
+
+def voxel_homog(scanner: dict, table: dict, T: np.ndarray, image: dict, lors, k: int, Wt: int):
+    """Voxel-driven homogenization of a planar scanner (Sec. 2.3 Eq. 11-12):
+    the dense matrix A (n_lors x nvox, rows of the LOR list) from k lines per
+    pixel centre, and each pixel's smallest decision margin."""
+    s, tb, im = _scanner(scanner), _table(table), _image(image)
+    L = _lors(lors)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    nvox = int(image["nx"]) * int(image["ny"])
+    A = np.zeros((L.shape[0], nvox))
+    margin = np.zeros(nvox)
+    _load().orc_voxel_homog(C.byref(s), C.byref(tb), _ptr(T), C.byref(im), int(k), int(Wt),
+                            _ptr(pair_row_map(scanner, L)), L.shape[0], _ptr(A), _ptr(margin))
+    return A, margin
 
 
 def sino_index(scanner: dict, pairs, fan_half: int):

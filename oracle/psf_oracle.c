@@ -28,6 +28,8 @@
  *                       ranking against a brute-force order, tie rules)
  *   orc_sino_index      pinned (one to one onto views x bins; bins ordered by
  *                       the geometric offset within a view, views by angle)
+ *   orc_voxel_homog     pinned (column sums against the composed efficiencies,
+ *                       quarter-turn symmetry, centre pixel)
  *   agreement of the analytic response with GATE: parity unpinned (the
  *   paper's response curves, Figs. 2-5, are not in the text).
  */
@@ -518,67 +520,73 @@ static double frac_margin(double x)
     return fabs(x - rint(x));
 }
 
+/* Smallest margin of the response decisions of one end: crystal x entered at
+ * sub-position (ipt, ipa) travelling along d (out of the ring). */
+static double end_margin(const orc_scanner *s, const orc_table *tb, const double *T,
+                         orc_xtal x, int ipt, int ipa, const double d[3])
+{
+    double best = 1.0;
+    double vn = d[0] * x.n[0] + d[1] * x.n[1];
+    double vt = d[0] * x.t[0] + d[1] * x.t[1];
+    if (!(vn > 0.0)) return best;
+    double alpha = atan2(fabs(vt), vn);
+    double theta = atan2(fabs(d[2]), sqrt(vn * vn + vt * vt));
+    double st = tb->amax_t_deg / tb->Kt * ORC_PI / 180.0;
+    double sa = tb->amax_a_deg / tb->Ka * ORC_PI / 180.0;
+    /* nearest node: boundaries where angle/step + 1/2 is an integer */
+    if (alpha / st < tb->Kt - 1) best = fmin(best, frac_margin(alpha / st + 0.5));
+    if (theta / sa < tb->Ka - 1) best = fmin(best, frac_margin(theta / sa + 0.5));
+    int sgt = vt >= 0.0 ? 1 : -1, sga = d[2] >= 0.0 ? 1 : -1;
+    double beta, AP1, run;
+    orc_gap_eq(s, alpha, 0.5 * orc_block_width(s) -
+                   sgt * (x.s_centre + ((ipt + 0.5) / tb->Pt - 0.5) * s->wt),
+               &beta, &AP1, &run);
+    if (!(beta > 0.0)) return best;
+    /* does the gap path reach any stored crystal? */
+    double q = AP1 - s->gt;
+    if (q < 0.0) q = 0.0;
+    int m = (int)floor(q / orc_pt(s));
+    int kt1 = orc_node(beta, tb->amax_t_deg, tb->Kt);
+    int ka = orc_node(theta, tb->amax_a_deg, tb->Ka);
+    double reach = 0.0;
+    for (int iu = 0; iu < tb->Pt; ++iu)
+        for (int iv = 0; iv < tb->Pa; ++iv)
+            for (int dx = m; dx < tb->Mt && dx <= m + 2; ++dx)
+                for (int dz = 0; dz < tb->Ma; ++dz)
+                    reach += T[(orc_tidx(tb, kt1, ka, iu, iv) * tb->Mt + dx) * tb->Ma + dz];
+    if (reach == 0.0) return best;
+    if (beta / st < tb->Kt - 1) best = fmin(best, frac_margin(beta / st + 0.5));
+    best = fmin(best, frac_margin(q / orc_pt(s)));
+    double f = q - m * orc_pt(s);
+    best = fmin(best, fabs(f - s->wt) / orc_pt(s));
+    if (f < s->wt) best = fmin(best, frac_margin((s->wt - f) / s->wt * tb->Pt));
+    if (tb->Pa > 1 || orc_nrings(s) > 1) {
+        double z1 = x.z_centre + ((ipa + 0.5) / tb->Pa - 0.5) * s->wa +
+                    sga * run * tan(theta);
+        double zl = z1 - (orc_ring_z(s, 0) - 0.5 * s->wa);
+        best = fmin(best, frac_margin(zl / orc_pa(s)));
+        double fa = zl - floor(zl / orc_pa(s)) * orc_pa(s);
+        best = fmin(best, fabs(fa - s->wa) / orc_pa(s));
+        if (fa <= s->wa) best = fmin(best, frac_margin(fa / s->wa * tb->Pa));
+    }
+    return best;
+}
+
 /* Smallest margin of the decisions for one sub-LOR (both ends). */
 static double subpair_margin(const orc_scanner *s, const orc_table *tb, const double *T,
                              int id1, int id2, int p1, int q1, int p2, int q2)
 {
-    double best = 1.0;
     orc_xtal x1 = orc_decode(s, id1), x2 = orc_decode(s, id2);
-    double E1[3], E2[3];
+    double E1[3], E2[3], d1[3], d2[3];
     orc_face_point(s, id1, ((p1 + 0.5) / tb->Pt - 0.5) * s->wt,
                    ((q1 + 0.5) / tb->Pa - 0.5) * s->wa, E1);
     orc_face_point(s, id2, ((p2 + 0.5) / tb->Pt - 0.5) * s->wt,
                    ((q2 + 0.5) / tb->Pa - 0.5) * s->wa, E2);
-    for (int end = 0; end < 2; ++end) {
-        orc_xtal x = end ? x2 : x1;
-        int ipt = end ? p2 : p1, ipa = end ? q2 : q1;
-        double d[3];
-        for (int c = 0; c < 3; ++c) d[c] = end ? E2[c] - E1[c] : E1[c] - E2[c];
-        double vn = d[0] * x.n[0] + d[1] * x.n[1];
-        double vt = d[0] * x.t[0] + d[1] * x.t[1];
-        if (!(vn > 0.0)) continue;
-        double alpha = atan2(fabs(vt), vn);
-        double theta = atan2(fabs(d[2]), sqrt(vn * vn + vt * vt));
-        double st = tb->amax_t_deg / tb->Kt * ORC_PI / 180.0;
-        double sa = tb->amax_a_deg / tb->Ka * ORC_PI / 180.0;
-        /* nearest node: boundaries where angle/step + 1/2 is an integer */
-        if (alpha / st < tb->Kt - 1) best = fmin(best, frac_margin(alpha / st + 0.5));
-        if (theta / sa < tb->Ka - 1) best = fmin(best, frac_margin(theta / sa + 0.5));
-        int sgt = vt >= 0.0 ? 1 : -1, sga = d[2] >= 0.0 ? 1 : -1;
-        double beta, AP1, run;
-        orc_gap_eq(s, alpha, 0.5 * orc_block_width(s) -
-                       sgt * (x.s_centre + ((ipt + 0.5) / tb->Pt - 0.5) * s->wt),
-                   &beta, &AP1, &run);
-        if (!(beta > 0.0)) continue;
-        /* does the gap path reach any stored crystal? */
-        double q = AP1 - s->gt;
-        if (q < 0.0) q = 0.0;
-        int m = (int)floor(q / orc_pt(s));
-        int kt1 = orc_node(beta, tb->amax_t_deg, tb->Kt);
-        int ka = orc_node(theta, tb->amax_a_deg, tb->Ka);
-        double reach = 0.0;
-        for (int iu = 0; iu < tb->Pt; ++iu)
-            for (int iv = 0; iv < tb->Pa; ++iv)
-                for (int dx = m; dx < tb->Mt && dx <= m + 2; ++dx)
-                    for (int dz = 0; dz < tb->Ma; ++dz)
-                        reach += T[(orc_tidx(tb, kt1, ka, iu, iv) * tb->Mt + dx) * tb->Ma + dz];
-        if (reach == 0.0) continue;
-        if (beta / st < tb->Kt - 1) best = fmin(best, frac_margin(beta / st + 0.5));
-        best = fmin(best, frac_margin(q / orc_pt(s)));
-        double f = q - m * orc_pt(s);
-        best = fmin(best, fabs(f - s->wt) / orc_pt(s));
-        if (f < s->wt) best = fmin(best, frac_margin((s->wt - f) / s->wt * tb->Pt));
-        if (tb->Pa > 1 || orc_nrings(s) > 1) {
-            double z1 = x.z_centre + ((ipa + 0.5) / tb->Pa - 0.5) * s->wa +
-                        sga * run * tan(theta);
-            double zl = z1 - (orc_ring_z(s, 0) - 0.5 * s->wa);
-            best = fmin(best, frac_margin(zl / orc_pa(s)));
-            double fa = zl - floor(zl / orc_pa(s)) * orc_pa(s);
-            best = fmin(best, fabs(fa - s->wa) / orc_pa(s));
-            if (fa <= s->wa) best = fmin(best, frac_margin(fa / s->wa * tb->Pa));
-        }
+    for (int c = 0; c < 3; ++c) {
+        d1[c] = E1[c] - E2[c];
+        d2[c] = -d1[c];
     }
-    return best;
+    return fmin(end_margin(s, tb, T, x1, p1, q1, d1), end_margin(s, tb, T, x2, p2, q2, d2));
 }
 
 /* Per LOR: the smallest margin over its sub-LORs (margin) and the number of
@@ -1051,6 +1059,129 @@ void orc_lor_normal(const orc_scanner *s, int a, int b, double *phi, double *dis
     }
     *phi = ph;
     *dist = A[0] * nx + A[1] * ny;
+}
+
+/*
+ * Voxel-driven homogenization (Sec. 2.3, Eq. 11-12, Figs. 7-8): the paper's
+ * own generator, for a planar (single crystal ring) scanner.  A point source
+ * at each pixel centre emits k lines, theta_i = pi i / k (Eq. 11), with equal
+ * proportion 1/k.  Each line reaches a crystal at both ends: the block whose
+ * front-face plane it leaves the ring polygon through, the crystal under the
+ * hit point; a hit in an inter-crystal gap or off the faces gives nothing (the
+ * paper: a gamma through the gap has proportion zero).  The photon enters
+ * that crystal at the sub-position cell of the face holding the hit point
+ * (cells of width wt / Pt counted from the -tangent edge; a hit on a cell
+ * boundary is shared half and half by the two cells, which keeps the
+ * scanner's mirror symmetry), and the
+ * single-photon responses of the two ends (orc_composed: block0 and the gap
+ * path to block1) give the detected pair (c1 + d1, c2 + d2) the proportion
+ * rho1[d1] rho2[d2] (Eq. 10, summed as Eq. 12), over the +-Wt window.
+ *   A[m][v] = (1/k) sum_i sum_{d1,d2 -> pair m} rho1[d1] rho2[d2]
+ * dense (nrows x nvox, rows by pair_row).  margin[v]: the smallest distance,
+ * over the lines of pixel v, of a response decision to its boundary -- the
+ * node and gap-path decisions of end_margin, in their own spacings (the cell
+ * decision is exact by the sharing rule).
+ */
+
+/* Entries of the ray from c along d into the crystal faces: the block whose
+ * face plane the ray leaves the ring polygon through, the crystal and
+ * sub-position cell under the hit point, with weight 1; a hit within 1e-9
+ * cell of a cell boundary lies on it and is shared half and half by the two
+ * cells (the neighbouring crystal's edge cell at a crystal edge with no gap;
+ * nothing past a block edge or into a gap).  Returns the number of entries
+ * (0..2) written to id/ipt/wgt. */
+static int orc_ray_entry(const orc_scanner *s, const orc_table *tb, const double c[3],
+                         const double d[3], int id[2], int ipt[2], double wgt[2])
+{
+    int best = -1;
+    double tmin = 1e300;
+    for (int b = 0; b < s->R; ++b) {
+        double phi = 2.0 * ORC_PI * b / s->R;
+        double dn = d[0] * cos(phi) + d[1] * sin(phi);
+        if (!(dn > 1e-15)) continue;
+        double t = (s->radius - (c[0] * cos(phi) + c[1] * sin(phi))) / dn;
+        if (t > 0.0 && t < tmin) {
+            tmin = t;
+            best = b;
+        }
+    }
+    if (best < 0) return 0;
+    double phi = 2.0 * ORC_PI * best / s->R;
+    double hx = c[0] + tmin * d[0], hy = c[1] + tmin * d[1];
+    double st = -hx * sin(phi) + hy * cos(phi);  /* tangential coordinate on the face */
+    /* position in sub-position cells of the face lattice: crystal i spans
+     * cells [i * Pp, i * Pp + Pt) with Pp = Pt * pitch / width cells per pitch */
+    double Pp = tb->Pt * orc_pt(s) / s->wt;
+    double u = (st + 0.5 * orc_block_width(s)) / s->wt * tb->Pt;
+    int on = fabs(u - rint(u)) < 1e-9;
+    if (on) u = rint(u);
+    int n = 0;
+    for (int side = 0; side < (on ? 2 : 1); ++side) {
+        double uu = on ? u - 0.5 + side : u;  /* the cell below / above a boundary */
+        int i = (int)floor(uu / Pp);
+        if (i < 0 || i >= s->Nb) continue;
+        double cell = uu - i * Pp;
+        if (cell >= tb->Pt) continue;  /* in the gap after crystal i */
+        id[n] = best * s->Nb + i;
+        ipt[n] = (int)floor(cell);
+        wgt[n] = on ? 0.5 : 1.0;
+        ++n;
+    }
+    return n;
+}
+
+void orc_voxel_homog(const orc_scanner *s, const orc_table *tb, const double *T,
+                     const orc_image *im, int k, int Wt, const int64_t *pair_row,
+                     int64_t nrows, double *A, double *margin)
+{
+    const int64_t nvox = (int64_t)im->nx * im->ny;
+    const int64_t Nc = (int64_t)orc_nt(s) * orc_nrings(s);
+    const int cap = 4 * (tb->Mt * tb->Ma) + 16;
+    memset(A, 0, sizeof(double) * nrows * nvox);
+#pragma omp parallel
+    {
+        orc_entry *r1 = (orc_entry *)malloc(sizeof(orc_entry) * cap);
+        orc_entry *r2 = (orc_entry *)malloc(sizeof(orc_entry) * cap);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t v = 0; v < nvox; ++v) {
+            int ix = (int)(v % im->nx), iy = (int)(v / im->nx);
+            double c[3] = {im->ox + (ix + 0.5) * im->dx, im->oy + (iy + 0.5) * im->dy,
+                           orc_ring_z(s, 0)};
+            double mg = 1.0;
+            for (int i = 0; i < k; ++i) {
+                double th = ORC_PI * i / k;
+                double d1[3] = {cos(th), sin(th), 0.0}, d2[3] = {-d1[0], -d1[1], 0.0};
+                int ia[2], ib[2], pa[2], pb[2];
+                double wa[2], wb[2];
+                int na = orc_ray_entry(s, tb, c, d1, ia, pa, wa);
+                int nb = orc_ray_entry(s, tb, c, d2, ib, pb, wb);
+                for (int ea = 0; ea < na; ++ea)
+                for (int eb = 0; eb < nb; ++eb) {
+                    orc_xtal x1 = orc_decode(s, ia[ea]), x2 = orc_decode(s, ib[eb]);
+                    if (x1.block == x2.block) continue;
+                    mg = fmin(mg, end_margin(s, tb, T, x1, pa[ea], 0, d1));
+                    mg = fmin(mg, end_margin(s, tb, T, x2, pb[eb], 0, d2));
+                    double e1, e2, wl = wa[ea] * wb[eb] / k;
+                    int n1 = orc_composed(s, tb, T, ia[ea], pa[ea], 0, d1, r1, cap, &e1);
+                    int n2 = orc_composed(s, tb, T, ib[eb], pb[eb], 0, d2, r2, cap, &e2);
+                    for (int a = 0; a < n1; ++a) {
+                        if (abs(r1[a].dt) > Wt || r1[a].da != 0) continue;
+                        int X = ((x1.ct + r1[a].dt) % orc_nt(s) + orc_nt(s)) % orc_nt(s);
+                        for (int b = 0; b < n2; ++b) {
+                            if (abs(r2[b].dt) > Wt || r2[b].da != 0) continue;
+                            int Y = ((x2.ct + r2[b].dt) % orc_nt(s) + orc_nt(s)) % orc_nt(s);
+                            if (X == Y) continue;
+                            int64_t m = pair_row[(int64_t)X * Nc + Y];
+                            if (m >= 0) A[m * nvox + v] += r1[a].val * r2[b].val * wl;
+                        }
+                    }
+                }
+            }
+            margin[v] = mg;
+        }
+        free(r1);
+        free(r2);
+    }
 }
 
 /* Number of OpenMP threads the oracle runs with (for the baseline record). */
