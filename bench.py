@@ -493,13 +493,63 @@ def run_profile_case(args):
             info = {"rows": rows_set[0].numel() - 1, "nnz": rows_set[1].numel()}
         if case in ("rows", "csr"):
             L = P.lor_set_list(s, ls, device=dev)[: 2_000_000].contiguous()
-            rp, col, val, _ = P.sysmat_rows(s, im, L)
             if case == "csr":
                 M = P.Matrix(rp, col, val, nv)
                 y = M.forward(torch.rand(nv, device=dev))
                 M.back(y)
         torch.cuda.synchronize()
     print(json.dumps({"profile_case": case, "ok": True, **(info if case == "rows_set" else {})}))
+
+
+VH_K = (60, 240, 960, 3840, 15360)
+
+
+def run_voxel_homog(args):
+    """The paper's voxel-driven generator (Sec. 2.3, Eq. 11-12) on the planar
+    ring: the dense matrix from k lines per pixel for growing k (the
+    k-convergence the paper describes), its generation time, the relative
+    change of the disc phantom's projection against the largest k, and the
+    projection's correlation with the LOR-driven A = S G of the library.
+    Prints one JSON object."""
+    import torch
+
+    from paper_1607_06170_gb300 import build as B
+    from paper_1607_06170_gb300 import inputs as I
+    from paper_1607_06170_gb300 import psf as P
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    w = I.workload("RING2D")
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    nv = im["nx"] * im["ny"]
+    x = torch.from_numpy(I.phantom_discs(im, 0).reshape(-1)).to(dev)
+    T, eta = P.response_build(s, t, device=dev)
+    L = P.lor_set_list(s, ls, device=dev)
+    WL = P.bin_spread(s, t, T, eta, L, Wt, Wa)
+    ptr, col2, val2, _ = P.sysmat_rows(s, im, L, WL, Wt, Wa)
+    y_lor = P.Matrix(ptr, col2, val2, nv).forward(x).double()
+    st = torch.cuda.current_stream()
+    rows, proj = [], {}
+    for k in VH_K:
+        P.voxel_homog(s, t, T, eta, im, ls, k, Wt)  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        A = P.voxel_homog(s, t, T, eta, im, ls, k, Wt)
+        b.record(st)
+        torch.cuda.synchronize()
+        y = (A.double() @ x.double())
+        proj[k] = y
+        c = float(torch.corrcoef(torch.stack([y, y_lor]))[0, 1])
+        rows.append({"k": k, "ms": a.elapsed_time(b), "lines_per_s": nv * k / (a.elapsed_time(b) * 1e-3),
+                     "corr_with_lor_driven": c})
+        del A
+    ref = proj[VH_K[-1]]
+    for r in rows:
+        r["proj_rel_change_vs_kmax"] = float(torch.linalg.norm(proj[r["k"]] - ref) / torch.linalg.norm(ref))
+    print(json.dumps({"voxel_homog": "RING2D", "n_lors": int(L.shape[0]), "pixels": nv,
+                      "window_t": Wt, "rows": rows}))
 
 
 PAPER_ITERATION_S = 43.0  # Table 2: one PSF reconstruction iteration on the paper's GPU
@@ -745,6 +795,8 @@ def main():
                     help="time one list-mode OSEM iteration on the 104-ring workload")
     ap.add_argument("--eplus", action="store_true",
                     help="matrix generation and one MLEM iteration on the paper's scanner")
+    ap.add_argument("--voxel-homog", action="store_true",
+                    help="the voxel-driven generator's k-convergence on the planar ring")
     args = ap.parse_args()
     if args.topn_table:
         run_topn_table(args)
@@ -754,6 +806,9 @@ def main():
         return
     if args.eplus:
         run_eplus(args)
+        return
+    if args.voxel_homog:
+        run_voxel_homog(args)
         return
     if args.profile_case:
         run_profile_case(args)

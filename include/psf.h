@@ -178,6 +178,25 @@ int psf_histogram(const int64_t *rows, int64_t n_events, float weight, float *co
 int psf_sino_bins(const psf_scanner *scanner, const psf_lor_set *set, int32_t *view,
                   int32_t *bin, void *stream);
 
+/*
+ * Voxel-driven homogenization (Sec. 2.3, Eq. 11-12, Figs. 7-8): the paper's own
+ * generator of the PSF matrix, for a planar scanner (one crystal ring, an image
+ * of one slice).  A point source at each pixel centre emits k lines at
+ * theta_i = pi i / k with proportion 1/k each; each line enters a crystal face
+ * at both ends (the crystal and sub-position cell under the hit point; a hit in
+ * a gap or off the faces gives nothing; a hit on a cell boundary is shared half
+ * and half by the two cells -- a reading, the paper is silent), and the
+ * detected pair (c1 + d1, c2 + d2), |d| <= half_t, receives rho1[d1] rho2[d2] / k
+ * from the two single-photon responses (table, eta: psf_response_build; the
+ * gap path of Eq. 2, 4, 5 included).  A: device float [n_lors][nx*ny], dense,
+ * rows in set order (pairs outside the set are dropped), overwritten.
+ * PSF_EINVAL unless the set has one crystal ring, image nz = 1, k >= 1,
+ * n_lors <= 16384 and n_lors * nx * ny <= 2^31.
+ */
+int psf_voxel_homog(const psf_scanner *scanner, const psf_table_desc *desc, const float *table,
+                    const double *eta, const psf_image *image, const psf_lor_set *set, int32_t k,
+                    int32_t half_t, float *A, void *stream);
+
 /* Number of LORs of a structured set, and of its spread classes (one per
  * transaxial pair with a < nt_block times ring difference; every LOR of the
  * set has the spread of its class by the ring's rotation and axial

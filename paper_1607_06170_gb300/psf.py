@@ -29,7 +29,7 @@ FUNCTIONS = [
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
-    "psf_forward_masked", "psf_sino_bins",
+    "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog",
 ]
 
 
@@ -96,6 +96,7 @@ _SIGS = {
     "psf_histogram": (C.c_int, [_P, _I64, C.c_float, _P, _I64, _P]),
     "psf_forward_masked": (C.c_int, [_P, _P, _P, _P, _P]),
     "psf_sino_bins": (C.c_int, [_P, _P, _P, _P, _P]),
+    "psf_voxel_homog": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -222,6 +223,19 @@ def event_rows(sc: dict, ls: dict, events):
     _ok(lib().psf_event_rows(C.byref(s), C.byref(l), _ptr(events), events.shape[0], _ptr(rows),
                              _stream()), "psf_event_rows")
     return rows
+
+
+def voxel_homog(sc: dict, tb: dict, T, eta, im: dict, ls: dict, k: int, half_t: int,
+                out=None):
+    """Voxel-driven homogenization matrix (dense [n_lors, nx*ny], psf_voxel_homog)."""
+    s, t, i, l = scanner(sc), table_desc(tb), image(im), lor_set(ls)
+    n, _ = lor_set_size(sc, ls)
+    if out is None:
+        out = torch.empty((n, im["nx"] * im["ny"]), dtype=torch.float32, device=T.device)
+    _ok(lib().psf_voxel_homog(C.byref(s), C.byref(t), _ptr(T), _ptr(eta), C.byref(i),
+                              C.byref(l), int(k), int(half_t), _ptr(out), _stream()),
+        "psf_voxel_homog")
+    return out
 
 
 def sino_bins(sc: dict, ls: dict, device="cuda"):
