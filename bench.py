@@ -493,10 +493,13 @@ def run_profile_case(args):
             info = {"rows": rows_set[0].numel() - 1, "nnz": rows_set[1].numel()}
         if case in ("rows", "csr"):
             L = P.lor_set_list(s, ls, device=dev)[: 2_000_000].contiguous()
+            rp, col, val, _ = P.sysmat_rows(s, im, L)
             if case == "csr":
                 M = P.Matrix(rp, col, val, nv)
+                M.set_launch(32, 512)  # the work-queue launch the bench step's autotuner picks
                 y = M.forward(torch.rand(nv, device=dev))
                 M.back(y)
+                M.back_sens(y)
         torch.cuda.synchronize()
     print(json.dumps({"profile_case": case, "ok": True, **(info if case == "rows_set" else {})}))
 
