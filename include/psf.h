@@ -353,10 +353,13 @@ int psf_sensitivity(const psf_matrix *m, float *x, void *stream);
  */
 int psf_back_sens(const psf_matrix *m, const float *y, float *x, float *sens, void *stream);
 
-/* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]). */
+/* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]).
+ * A plan with no rows returns PSF_OK at once (y may then be NULL). */
 int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream);
 
-/* x = A^T y (overwrite). */
+/* x = A^T y (overwrite); with no rows x is zeroed (y may then be NULL).  The
+ * same holds for the LOR-space arguments of psf_back_sens and
+ * psf_forward_masked. */
 int psf_back(const psf_matrix *m, const float *y, float *x, void *stream);
 
 /* y = A x on the rows with mask != 0 (mask: device float [n_rows],

@@ -151,20 +151,23 @@ __device__ __forceinline__ float csr_row_dot(const int64_t *__restrict__ ptr,
                                              const VT *__restrict__ val,
                                              const float *__restrict__ x, int64_t r, int lane) {
     constexpr int U = 4;
-    const int64_t j0 = ptr[r], j1 = ptr[r + 1];
+    const int64_t j0 = ptr[r];
+    const int nr = (int)(ptr[r + 1] - j0);
+    const int32_t *cr = col + j0;
+    const VT *vr = val + j0;
     float acc = 0.0f;
-    for (int64_t j = j0 + lane; j < j1; j += 32 * U) {
+    for (int j = lane; j < nr; j += 32 * U) {
         int c[U];
         float v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t jj = j + 32 * u;
-            c[u] = jj < j1 ? __ldcs(col + jj) : 0;
-            v[u] = jj < j1 ? ld_val_cs(val, jj) : 0.0f;
+            const int jj = j + 32 * u;
+            c[u] = jj < nr ? __ldcs(cr + jj) : 0;
+            v[u] = jj < nr ? ld_val_cs(vr, jj) : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (j + 32 * u < j1) acc = fmaf(v[u], __ldg(x + c[u]), acc);
+            if (j + 32 * u < nr) acc = fmaf(v[u], __ldg(x + c[u]), acc);
     }
     return warp_sum_f(acc);
 }
@@ -329,10 +332,23 @@ __global__ void csr_back_pair_kernel(int64_t n, const int64_t *__restrict__ ptr,
                 b *= scale[r];
             }
             if (a == 0.0f && b == 0.0f) continue;
-            const int64_t j0 = ptr[r], j1 = ptr[r + 1];
-            for (int64_t j = j0 + lane; j < j1; j += 32) {
-                const float v = ld_val_cs(val, j);
-                atomicAdd(x2 + __ldcs(col + j), make_float2(v * a, v * b));
+            const int64_t j0 = ptr[r];
+            const int nr = (int)(ptr[r + 1] - j0);
+            const int32_t *cr = col + j0;
+            const VT *vr = val + j0;
+            constexpr int U = 4;
+            for (int j = lane; j < nr; j += 32 * U) {
+                int c[U];
+                float v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int jj = j + 32 * u;
+                    c[u] = jj < nr ? __ldcs(cr + jj) : -1;
+                    v[u] = jj < nr ? ld_val_cs(vr, jj) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (c[u] >= 0) atomicAdd(x2 + c[u], make_float2(v[u] * a, v[u] * b));
             }
         }
         r0 = queue ? wq_take(queue, chunk, lane) : r0 + wpg;
@@ -1600,8 +1616,9 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
 }
 
 extern "C" int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream) {
-    if (!m || !x || !y) return PSF_EINVAL;
-    if (m->n_rows == 0) return PSF_OK;
+    if (!m || !x) return PSF_EINVAL;
+    if (m->n_rows == 0) return PSF_OK;  // y has no entries (may be NULL)
+    if (!y) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (!m->factored) return rows_fwd(m, x, y, st);
     int rc = rows_fwd(m, x, m->p, st);
@@ -1643,8 +1660,9 @@ static int rows_fwd_masked(const psf_matrix *m, const float *x, const float *mas
 
 extern "C" int psf_forward_masked(const psf_matrix *m, const float *x, const float *mask,
                                   float *y, void *stream) {
-    if (!m || !x || !mask || !y) return PSF_EINVAL;
-    if (m->n_rows == 0) return PSF_OK;
+    if (!m || !x) return PSF_EINVAL;
+    if (m->n_rows == 0) return PSF_OK;  // mask and y have no entries (may be NULL)
+    if (!mask || !y) return PSF_EINVAL;
     if (m->n_rows > INT32_MAX) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (!m->factored) return rows_fwd_masked(m, x, mask, y, reinterpret_cast<int32_t *>(m->p), st);
@@ -1664,12 +1682,13 @@ extern "C" int psf_forward_masked(const psf_matrix *m, const float *x, const flo
 }
 
 extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *stream) {
-    if (!m || !x || !y) return PSF_EINVAL;
+    if (!m || !x) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
-    if (m->n_rows == 0) {
+    if (m->n_rows == 0) {  // y has no entries (may be NULL)
         PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
         return PSF_OK;
     }
+    if (!y) return PSF_EINVAL;
     if (!m->factored) return rows_back(m, y, x, st);
     int rc = stencil(m, y, m->q, true, st);
     if (rc) return rc;
@@ -1848,13 +1867,14 @@ extern "C" int psf_sensitivity(const psf_matrix *m, float *x, void *stream) {
 // x = A^T y and sens = A^T 1 with one pass over the stored rows.
 extern "C" int psf_back_sens(const psf_matrix *m, const float *y, float *x, float *sens,
                              void *stream) {
-    if (!m || !y || !x || !sens) return PSF_EINVAL;
+    if (!m || !x || !sens) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
-    if (m->n_rows == 0) {
+    if (m->n_rows == 0) {  // y has no entries (may be NULL)
         PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
         PSF_TRY(cudaMemsetAsync(sens, 0, sizeof(float) * m->n_cols, st));
         return PSF_OK;
     }
+    if (!y) return PSF_EINVAL;
     const float *qa, *qb;  // LOR-space inputs of G^T: S^T 1 and S^T y (or 1 and y)
     if (m->factored) {
         int rc = sens_spread(m, m->p, st);

@@ -1,0 +1,119 @@
+"""Edge cases of the library on the GPU: empty inputs, invalid arguments,
+degenerate and invalid LORs, rows of very uneven length."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1607_06170_gb300 import inputs as I
+from parity import assert_close, compare_chord_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1607_06170_gb300 import build, psf
+
+    build.build()
+    return psf
+
+
+@pytest.fixture(scope="module")
+def ring2d(P):
+    w = I.workload("RING2D")
+    T, eta = P.response_build(w["scanner"], w["table"])
+    return dict(w=w, T=T, eta=eta, nv=w["image"]["nx"] * w["image"]["ny"])
+
+
+def test_empty_inputs(P, ring2d):
+    w = ring2d["w"]
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    L0 = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    W0 = P.bin_spread(s, t, ring2d["T"], ring2d["eta"], L0, Wt, Wa)
+    assert W0.shape == (0, 2 * Wt + 1, 2 * Wt + 1)
+    rp, col, val, _ = P.sysmat_rows(s, im, L0)
+    assert rp.cpu().tolist() == [0] and col.numel() == 0
+    M = P.Matrix(rp, col, val, ring2d["nv"])
+    x = torch.rand(ring2d["nv"], device="cuda")
+    assert M.forward(x).numel() == 0
+    assert torch.count_nonzero(M.back(torch.zeros(0, device="cuda"))) == 0
+    assert torch.count_nonzero(M.sensitivity()) == 0
+    rows = P.event_rows(s, ls, L0)
+    assert rows.numel() == 0
+    assert torch.count_nonzero(P.histogram(rows, 10, 1.0)) == 0
+
+
+def test_invalid_arguments_raise(P, ring2d):
+    from paper_1607_06170_gb300.psf import PSFError
+
+    w = ring2d["w"]
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    L = torch.from_numpy(I.workload_lors(w)[1000:1008]).cuda()  # chords across the image
+    with pytest.raises(PSFError):  # quadrant (half_t + 1)(half_a + 1) above 16
+        P.bin_spread(s, t, ring2d["T"], ring2d["eta"], L, 15, 1)
+    with pytest.raises(PSFError):  # geometric rows are FP32 only
+        P.sysmat_rows(s, im, L, dtype="bf16")
+    with pytest.raises(PSFError):  # the voxel-driven generator is planar
+        w3 = I.workload("RING3D_SMALL")
+        T3, e3 = P.response_build(w3["scanner"], w3["table"])
+        P.voxel_homog(w3["scanner"], w3["table"], T3, e3, w3["image"], w3["lors"], 8, 1)
+    with pytest.raises(PSFError):  # sinogram indexing needs an even ring
+        P.sino_bins(dict(s, n_blocks=9, nt_block=7), dict(fan_half=20, max_ring_diff=0))
+    # capacity below the row count: PSF_ECAPACITY and the required size
+    lib = P.lib()
+    rp = torch.empty(L.shape[0] + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(4, dtype=torch.int32, device="cuda")
+    val = torch.empty(4, dtype=torch.float32, device="cuda")
+    nnz = C.c_int64()
+    rc = lib.psf_sysmat_rows(C.byref(P.scanner(s)), C.byref(P.image(im)), P._ptr(L), L.shape[0],
+                             None, 0, 0, 0, P._ptr(rp), P._ptr(col), P._ptr(val), None, 4,
+                             C.byref(nnz), P._stream())
+    torch.cuda.synchronize()
+    assert rc == -2 and nnz.value > 4  # PSF_ECAPACITY
+
+
+def test_invalid_and_degenerate_lors(P, ring2d, orc):
+    """Invalid crystal ids and pairs of one crystal give empty rows and zero
+    spreads; a pair inside one block (its chord runs along the block face) has
+    no spread and, outside the image, no chords; valid LORs next to them are
+    unaffected."""
+    w = ring2d["w"]
+    s, t, im = w["scanner"], w["table"], w["image"]
+    Wt, Wa = w["window"]
+    good = I.workload_lors(w)[[0, 500, 1500]]
+    bad = np.array([[-1, 5], [3, 3], [2, 900], [0, 3]], dtype=np.int32)  # [0, 3]: one block
+    L = np.concatenate([good, bad]).astype(np.int32)
+    Lt = torch.from_numpy(L).cuda()
+    W = P.bin_spread(s, t, ring2d["T"], ring2d["eta"], Lt, Wt, Wa).cpu().numpy()
+    assert np.all(W[3:] == 0.0)
+    To, _ = orc.table_build(s, t)
+    Wo = orc.spread(s, t, To, good, Wt, Wa)
+    assert_close(W[:3], Wo, 1e-5, 1e-6 * np.abs(Wo).max(), "spreads beside invalid LORs")
+    rp, col, val, _ = P.sysmat_rows(s, im, Lt)
+    rp = rp.cpu().numpy()
+    assert np.all(np.diff(rp)[3:] == 0)
+    compare_chord_rows((rp[:4], col.cpu().numpy()[: rp[3]], val.cpu().numpy()[: rp[3]]),
+                       orc.rows_geom(s, im, good), ring2d["nv"])
+
+
+def test_uneven_rows_every_launch(P, ring2d):
+    """The planar ring's rows run from empty (LORs that miss the image) to
+    about 90 voxels; every projector launch gives the same projections."""
+    w = ring2d["w"]
+    s, im = w["scanner"], w["image"]
+    Lt = torch.from_numpy(I.workload_lors(w)).cuda()
+    rp, col, val, _ = P.sysmat_rows(s, im, Lt)
+    lens = torch.diff(rp).cpu().numpy()
+    assert lens.min() == 0 and lens.max() > 60
+    M = P.Matrix(rp, col, val, ring2d["nv"])
+    x = torch.from_numpy(I.phantom_discs(im, 0).reshape(-1)).cuda()
+    y = torch.from_numpy(I.random_lor_values(M.n_rows, 5)).cuda()
+    M.set_launch(0)
+    f0, b0 = M.forward(x), M.back(y)
+    for chunk, threads in [(1, 128), (7, 256), (128, 512), (-1, 256)]:
+        M.set_launch(chunk, threads)
+        torch.testing.assert_close(M.forward(x), f0, rtol=1e-6, atol=1e-6 * f0.abs().max().item())
+        torch.testing.assert_close(M.back(y), b0, rtol=1e-5, atol=1e-6 * b0.abs().max().item())
