@@ -942,17 +942,15 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                         const int2 R = W.rs[gi];
                         const int p = (R.y & 0xffff) + (e - R.x), k = R.y >> 16;
                         const int4 A = W.sa[k];
+                        const float4 F = W.sf[k];
                         const int xy = m.s_xy[p];
-                        if (p == A.y) {
-                            v = W.sf[k].x;
-                            keep = A.w & 1;
-                        } else if (p == A.z) {
-                            v = W.sf[k].y;
-                            keep = (A.w >> 1) & 1;
-                        } else {
-                            v = m.s_lenf[p] * W.sf[k].z;
-                            keep = xy >= 0 || m.s_len[p] >= W.sm[k];
-                        }
+                        const float lf = m.s_lenf[p];
+                        // end cells take their cut chord and keep bit; interior
+                        // cells their 2D chord, kept unless flagged short
+                        const bool isa = p == A.y, isb = p == A.z;
+                        v = isa ? F.x : (isb ? F.y : lf * F.z);
+                        keep = isa ? (A.w & 1) : (isb ? ((A.w >> 1) & 1) : xy >= 0);
+                        if (xy < 0 && !isa && !isb) keep = m.s_len[p] >= W.sm[k];  // rare
                         colv = A.x + (xy & 0x7fffffff);
                     }
                     gbase += __popc(B);
