@@ -415,6 +415,66 @@ def run_gpu(args):
            "h2d_bytes_per_step": int(x_host.numel() * 4 + y_host.numel() * 4),
            "d2h_bytes_per_step": int(out_host.numel() * 4)}
 
+    # the plain FP32 GPU form of the same step (outside the timed region): the
+    # per-LOR tracer instead of the structured-set generator, grid-stride CSR
+    # projectors, the plain one-output-per-thread stencil, and the sensitivity
+    # as a separate back-projection of ones; same spread kernel
+    Mp = P.Matrix(row_ptr, col, val, nv)
+    plain_stages = ["table", "classes", "spread", "rows", "forward", "ratio", "back", "sens",
+                    "update"]
+    pev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for k in plain_stages}
+
+    def plain_step(x_in, y_in):
+        def mark(k, i):
+            pev[k][i].record(st)
+
+        mark("table", 0)
+        T, eta = P.response_build(s, t, device=dev)
+        mark("table", 1)
+        mark("classes", 0)
+        C = P.lor_set_classes(s, ls, device=dev)
+        mark("classes", 1)
+        mark("spread", 0)
+        WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)
+        mark("spread", 1)
+        mark("rows", 0)
+        P.sysmat_rows(s, im, L, buffers=(row_ptr, col, val, None))
+        mark("rows", 1)
+        Mp.set_spread(s, ls, Wt, Wa, WC).set_launch(0).set_stencil_form(1)
+        mark("forward", 0)
+        yh = Mp.forward(x_in)
+        mark("forward", 1)
+        mark("ratio", 0)
+        r = P.em_ratio(y_in, yh)
+        mark("ratio", 1)
+        mark("back", 0)
+        bp = Mp.back(r)
+        mark("back", 1)
+        mark("sens", 0)
+        sens = Mp.back(torch.ones_like(r))
+        mark("sens", 1)
+        mark("update", 0)
+        x_out = x_in.clone()
+        P.em_update(x_out, bp, sens, 1e-12)
+        mark("update", 1)
+        return x_out
+
+    plain_step(x, y_meas)  # warm-up
+    torch.cuda.synchronize()
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pa.record(st)
+    plain_step(x, y_meas)
+    pb.record(st)
+    torch.cuda.synchronize()
+    plain_ms = pa.elapsed_time(pb)
+    plain = {"ms_per_step": plain_ms, "value": nnz / (plain_ms * 1e-3), "unit": UNIT,
+             "speedup": plain_ms / ms_step,
+             "stage_ms": {k: pev[k][0].elapsed_time(pev[k][1]) for k in plain_stages},
+             "form": "per-LOR tracer rows, grid-stride CSR projectors, plain stencil, "
+                     "sensitivity as a back-projection of ones; same spread kernel"}
+    del Mp
+
     # roofline of the dominant kernel: the library kernel with the most device
     # time per step (CUDA events around each launch, timed region only)
     peaks = {}
@@ -444,6 +504,7 @@ def run_gpu(args):
         "roofline": roof,
         "clocks": clocks,
         "e2e": e2e,
+        "plain_fp32": plain,
         "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -333,6 +333,13 @@ int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out,
  * only) the streaming forward (back: grid-stride).  PSF_EINVAL otherwise. */
 int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads);
 
+/* Stencil form of a factored plan, both directions (no counterpart in the
+ * paper): 0 the default (the fastest form that fits, or the autotuner's
+ * choice), 1 the plain one-output-per-thread stencil, 2 the register-blocked
+ * form, 3 and 4 the cp.async-staged forms (used when they fit).  For
+ * comparisons against the plain forms; PSF_EINVAL outside 0..4. */
+int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form);
+
 /*
  * x = A^T 1, the sensitivity image of MLEM (Sec. 3), x (device float
  * [n_cols], overwritten).  For a factored plan S^T 1 is formed from the class

@@ -1433,7 +1433,8 @@ static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoin
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int form = m->st_form[adjoint ? 1 : 0];
     const bool ok4 = stencil4_ok(m->ls, m->Wa), ok3 = stencil3_ok(m->ls, m->Wa);
-    const bool use4 = ok4 && (form != 3 || !ok3), use3 = !use4 && ok3;
+    const bool use4 = form != 1 && form != 2 && ok4 && (form != 3 || !ok3);
+    const bool use3 = form != 1 && form != 2 && !use4 && ok3;
     if (use4) {
         switch (m->Wa * 2 + (adjoint ? 1 : 0)) {
             case 0: return launch_stencil4<false, 0>(m, in, out, st);
@@ -1462,6 +1463,7 @@ static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoin
         }
     }
     int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
+    if (form != 1)
     switch (m->Wa * 2 + (adjoint ? 1 : 0)) {  // register-blocked form for axial windows <= 3
         case 0: return launch_stencil2<false, 0>(m, in, out, (int)grid, st);
         case 1: return launch_stencil2<true, 0>(m, in, out, (int)grid, st);
@@ -1798,6 +1800,12 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
         threads_out[0] = m->fwd_threads;
         threads_out[1] = m->wq_threads;
     }
+    return PSF_OK;
+}
+
+extern "C" int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form) {
+    if (!m || form < 0 || form > 4) return PSF_EINVAL;
+    m->st_form[0] = m->st_form[1] = form;
     return PSF_OK;
 }
 

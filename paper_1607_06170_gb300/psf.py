@@ -29,7 +29,7 @@ FUNCTIONS = [
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
-    "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog",
+    "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
 ]
 
 
@@ -97,6 +97,7 @@ _SIGS = {
     "psf_forward_masked": (C.c_int, [_P, _P, _P, _P, _P]),
     "psf_sino_bins": (C.c_int, [_P, _P, _P, _P, _P]),
     "psf_voxel_homog": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
+    "psf_matrix_set_stencil_form": (C.c_int, [_P, _I32]),
 }
 
 _lock = threading.Lock()
@@ -390,6 +391,11 @@ class Matrix:
         work-queue kernels taking `chunk` rows per warp."""
         _ok(lib().psf_matrix_set_launch(self._h, int(chunk), int(threads)),
             "psf_matrix_set_launch")
+        return self
+
+    def set_stencil_form(self, form: int):
+        """Stencil form of a factored plan (0 default, 1 plain, 2 register-blocked, 3, 4)."""
+        _ok(lib().psf_matrix_set_stencil_form(self._h, int(form)), "psf_matrix_set_stencil_form")
         return self
 
     def forward(self, x, out=None):
