@@ -719,9 +719,8 @@ def run_listmode(args):
     rows = P.event_rows(s, ls, events)
     del events
     T, eta = P.response_build(s, t, device=dev)
-    WC = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
-    idx, wk = P.spread_topn(WC, Wt, Wa, lm["n_keep"])
-    del WC
+    WCf = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+    idx, wk = P.spread_topn(WCf, Wt, Wa, lm["n_keep"])
     st = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -748,7 +747,20 @@ def run_listmode(args):
     kt = P.timing_read()
     P.timing_enable(False)
     clocks = clk.stop()
+    # the same iteration with the full 49 x 49 window (the dense stencil)
+    Mf = P.Matrix(rp, col, val, nv).set_spread(s, ls, Wt, Wa, WCf)
+    Mf.autotune()
+    sens_f = Mf.sensitivity()
+    listmode_osem(Mf, rows[: lm["subset_events"]].contiguous(), 1, 1, sens=sens_f)
+    torch.cuda.synchronize()
+    a.record(st)
+    listmode_osem(Mf, rows, n_sub, 1, sens=sens_f)
+    b.record(st)
+    torch.cuda.synchronize()
+    ms_full = a.elapsed_time(b)
+    del Mf
     print(json.dumps({
+        "full_window": {"iteration_ms": ms_full, "events_per_s": lm["events"] / (ms_full * 1e-3)},
         "listmode": "RING3D_LM", "events": lm["events"], "subsets": n_sub,
         "n_keep": lm["n_keep"], "n_lors": int(rp.numel() - 1), "nnz": nnz,
         "image": [im["nx"], im["ny"], im["nz"]], "iteration_ms": ms,

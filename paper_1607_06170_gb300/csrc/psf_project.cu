@@ -873,6 +873,7 @@ __global__ void __launch_bounds__(ST3_T, 4) stencil3_kernel(LorSet ls, int Wt,
 // lanes the strips of K = 4 rings, so a weight load has two addresses per
 // warp (one per half) and a plane load is 8 bytes per lane on consecutive
 // rows; a thread does K x M = 16 products per partner value pair it loads.
+// Scanners of 65 to 128 rings use whole warps per group (32 strips).
 // (M = 4 gives 128-thread CTAs, twice the warps per SM of M = 8 at the same
 // shared memory: 12.5 / 13.3 ms against 15.4 / 17.0 ms forward / adjoint on
 // the 3D ring; M = 2 14.0 / 14.2 ms.)  Staging and the partner walk are those
@@ -881,6 +882,7 @@ constexpr int ST4_K = 4, ST4_M = 4;
 
 struct St4Shape {
     int nd, nstrip, nqg, threads, PRp, ne;
+    int lpg_log;  // lanes per difference group: 16 (up to 64 rings) or 32 (up to 128)
     int plane_f, w_f, buf_f;
 };
 
@@ -889,7 +891,9 @@ __host__ __device__ inline St4Shape st4_shape(const LorSet &ls, int WA) {
     s.nd = 2 * ls.Dm + 1;
     s.nstrip = (ls.NR + ST4_K - 1) / ST4_K;
     s.nqg = (s.nd + ST4_M - 1) / ST4_M;
-    s.threads = 32 * ((s.nqg + 1) / 2);
+    s.lpg_log = s.nstrip <= 16 ? 4 : 5;
+    const int gpw = 32 >> s.lpg_log;  // groups per warp
+    s.threads = 32 * ((s.nqg + gpw - 1) / gpw);
     s.PRp = s.nstrip * ST4_K + 2 * WA;  // rows = ring + WA; a strip reads K + 2 WA rows
     s.ne = 4 * WA + 1;
     s.plane_f = (s.nd * s.PRp + 3) / 4 * 4;
@@ -930,7 +934,8 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
     }
     __syncthreads();
     const int nrp = (int)ls.nrp;
-    const int q = 2 * (t >> 5) + (lane >> 4), strip = lane & 15;
+    const int q = ((t >> 5) << (5 - S.lpg_log)) + (lane >> S.lpg_log),
+              strip = lane & ((1 << S.lpg_log) - 1);
     const bool active = q < S.nqg && strip < S.nstrip;
     const int dl0 = q * M - Dm, r0 = strip * K;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
@@ -1416,8 +1421,15 @@ static int launch_stencil3(const psf_matrix *m, const float *in, float *out, int
 
 static bool stencil4_ok(const LorSet &ls, int Wa) {
     const St4Shape s4 = st4_shape(ls, Wa);
-    return Wa <= 3 && s4.nstrip <= 16 && s4.threads <= 256 &&
+    return Wa <= 3 && s4.nstrip <= 32 && s4.threads <= 256 &&
            stencil4_smem_bytes(ls, Wa) <= 110 * 1024;
+}
+
+// The plain and register-blocked stencil forms: one CTA holds all ring pairs of
+// a transaxial pair.
+static bool plain_stencil_ok(const LorSet &ls, int Wa) {
+    return ls.nrp <= ST_T * ST_OUT && stencil_smem_bytes(ls, Wa) <= 200 * 1024 &&
+           stencil2_smem_bytes(ls, Wa) <= 200 * 1024;
 }
 
 static bool stencil3_ok(const LorSet &ls, int Wa) {
@@ -1463,6 +1475,7 @@ static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoin
         }
     }
     int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
+    if (!plain_stencil_ok(m->ls, m->Wa)) return PSF_EINVAL;  // sets beyond the plain forms' size
     if (form != 1)
     switch (m->Wa * 2 + (adjoint ? 1 : 0)) {  // register-blocked form for axial windows <= 3
         case 0: return launch_stencil2<false, 0>(m, in, out, (int)grid, st);
@@ -1560,8 +1573,7 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;
     if (ls.ntp * ls.nrp != m->n_rows) return PSF_EINVAL;
-    if (ls.nrp > ST_T * ST_OUT || stencil_smem_bytes(ls, half_a) > 200 * 1024 ||
-        stencil2_smem_bytes(ls, half_a) > 200 * 1024 || ls.NR > 32000)
+    if (!(plain_stencil_ok(ls, half_a) || stencil4_ok(ls, half_a)) || ls.NR > 32000)
         return PSF_EINVAL;
     const int64_t need = ls.ntp_cls * (2 * ls.Dm + 1) * (2 * half_a + 1) * (2 * half_a + 1);
     if (need > m->csum_n) {  // grows only: a plan reused over calls allocates once

@@ -110,6 +110,16 @@ WORKLOADS = {
         window=(3, 2),
         lors=dict(fan_half=10, max_ring_diff=3),
     ),
+    # RING3D_SMALL's blocks stacked 18 high (72 crystal rings): a set whose
+    # ring-pair plane needs whole-warp groups in the factored stencil
+    "RING3D_TALL": dict(
+        index=13,
+        scanner=scanner(12, 4, 4, 18, 1.9, 1.9, 10.0, 0.3, 0.3, 30.0, 0.3, 0.087),
+        table=table(13, 4, 4, 4, 16, 8, 65.0, 36.0),
+        image=image(24, 24, 144, 1.5, 1.5, 1.1),
+        window=(3, 2),
+        lors=dict(fan_half=2, max_ring_diff=1),
+    ),
     "RING2D_ELLIPSES": dict(
         index=2,
         scanner=_RING2D_SCANNER,

@@ -154,3 +154,32 @@ def test_back_sens_pair(gpu):
     torch.testing.assert_close(x, M.back(r), rtol=1e-5, atol=1e-6 * x.abs().max().item())
     s1 = M.sensitivity()
     torch.testing.assert_close(sens, s1, rtol=1e-5, atol=1e-6 * s1.abs().max().item())
+
+
+def test_factored_projector_tall_scanner(P, orc):
+    """A set of 72 crystal rings (ring strips beyond one half-warp: the factored
+    stencil takes whole warps per difference group) against the oracle."""
+    w = I.workload("RING3D_TALL")
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    nv = im["nx"] * im["ny"] * im["nz"]
+    To, _ = orc.table_build(s, t)
+    L = I.workload_lors(w)
+    Wo = orc.spread(s, t, To, L, Wt, Wa)
+    Go = orc.rows_geom(s, im, L)
+    T, eta = P.response_build(s, t)
+    WC = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls), Wt, Wa)
+    G = P.sysmat_rows_set(s, im, ls)
+    M = P.Matrix(G[0], G[1], G[2], nv).set_spread(s, ls, Wt, Wa, WC)
+    x = I.random_image(im, 640).reshape(-1)
+    y = M.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    yo = orc.spread_apply(s, L, Wo, Wt, Wa, orc.csr_fwd(Go, x))
+    assert_close(y, yo, 2e-5, 1e-6 * yo.max(), "factored forward, 72 rings")
+    r = I.random_lor_values(len(L), 641)
+    b = M.back(torch.from_numpy(r).cuda()).cpu().numpy()
+    bo = orc.csr_back(Go, orc.spread_adjoint(s, L, Wo, Wt, Wa, r), nv)
+    assert_close(b, bo, 2e-5, 1e-6 * bo.max(), "factored back, 72 rings")
+    # the same through the plain stencil form
+    M.set_stencil_form(1)
+    torch.testing.assert_close(M.forward(torch.from_numpy(x).cuda()).cpu(), torch.from_numpy(y),
+                               rtol=1e-5, atol=1e-6 * float(abs(y).max()))
