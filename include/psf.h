@@ -315,13 +315,21 @@ int psf_matrix_destroy(psf_matrix *m);
  * kernels (each warp takes the next chunk of rows from a counter) at chunk in
  * {1,2,4,...,128} rows and {128,256,512} threads per CTA and, for the forward
  * projection of FP32 rows, streaming tiles (64 rows per CTA, entries loaded
- * 16 bytes at a time independently of row boundaries), on all-ones vectors,
- * and keeps the fastest for psf_forward / psf_back of this plan; for a
+ * 16 bytes at a time independently of row boundaries) and the bulk-staged
+ * kernels (FP32 rows with 16-byte aligned column and value arrays: chunks of
+ * 4096 entries brought into shared memory by cp.async.bulk copies completing
+ * on an mbarrier, one chunk ahead; each chunk owns the rows that start in it),
+ * on all-ones vectors, and keeps the fastest for psf_forward / psf_back of
+ * this plan; the pair back-projection of psf_back_sens takes the faster of
+ * the back launch and the bulk-staged kernel (psf_back keeps launches that
+ * skip rows with y = 0, which a bulk-staged pass cannot); for a
  * factored plan with full-window spreads it also times the two forms of the
  * LOR-space spread stencil in each direction and keeps the faster (call it after
  * psf_matrix_set_spread).  chunk_out / threads_out: host arrays of 2
- * (forward, back), may be NULL; chunk -1 = streaming tiles, 0 = grid-stride,
- * > 0 = work queue.  Synchronises; allocates a temporary image-sized buffer;
+ * (forward, back), may be NULL; chunk -2 = bulk-staged, -1 = streaming tiles,
+ * 0 = grid-stride, > 0 = work queue.  Synchronises; allocates a temporary
+ * image-sized buffer and, for the bulk-staged forms, a plan-owned table of 8
+ * bytes per 4096 entries;
  * call it outside stream capture, after which the projections of the plan can
  * be captured in a CUDA graph.
  */
@@ -330,8 +338,16 @@ int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out,
 /* Set that launch explicitly for both directions: chunk 0 selects the
  * grid-stride kernels; chunk in [1, 2^20] rows per take with threads a
  * multiple of 32 in [32, 1024] the work-queue kernels; chunk -1 (FP32 rows
- * only) the streaming forward (back: grid-stride).  PSF_EINVAL otherwise. */
+ * only) the streaming forward (back: grid-stride); chunk -2 (FP32 rows,
+ * 16-byte aligned arrays, at least one entry; synchronises the default
+ * stream once to build its table) the bulk-staged kernels in every
+ * direction.  PSF_EINVAL otherwise. */
 int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads);
+
+/* Device status of the plan's bounded waits: synchronises `stream`, returns
+ * PSF_OK, or PSF_ETIMEOUT when a bulk-staged kernel gave up waiting for a
+ * copy since the last call (its outputs are then incomplete), and clears it. */
+int psf_matrix_check(const psf_matrix *m, void *stream);
 
 /* Stencil form of a factored plan, both directions (no counterpart in the
  * paper): 0 the default (the fastest form that fits, or the autotuner's

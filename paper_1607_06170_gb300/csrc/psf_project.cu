@@ -47,6 +47,14 @@ struct psf_matrix {
     int topn;
     const int32_t *tidx;
     const float *tw;
+    // bulk-staged projector forms (launch form -2, FP32 rows): the first row
+    // of each BK_CAP-entry chunk (plan-owned, built on first use), and the
+    // form of the pair back-projection of psf_back_sens (-2 bulk, else the
+    // back projection's launch)
+    int64_t *bk_first;
+    int64_t bk_nch, bk_nnz;
+    int pair_form;
+    int *status;  // plan-owned device status word (PSF_ETIMEOUT from a bounded wait)
 };
 
 namespace psf {
@@ -353,6 +361,314 @@ __global__ void csr_back_pair_kernel(int64_t n, const int64_t *__restrict__ ptr,
         }
         r0 = queue ? wq_take(queue, chunk, lane) : r0 + wpg;
     }
+}
+
+// Bulk-staged forms of the FP32 projectors (launch form -2).  The entry
+// arrays are cut into fixed chunks of BK_CAP entries; a CTA takes chunks
+// grid-stride and one of its threads brings each chunk's columns and values
+// into shared memory with two cp.async.bulk copies that complete on an
+// mbarrier, one chunk ahead of the one being used (two stages), so the HBM
+// stream runs independently of the image gathers and atomics.  A chunk owns
+// the rows that start in it (first_row, a plan-owned table); entries of its
+// rows that lie past the chunk, or in the ragged tail after the last whole 16
+// bytes, are read from global memory.
+constexpr int BK_T = 256, BK_CAP = 4096;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Global -> shared bulk copy completing on `bar`, marked evict-first in L2 (the
+// entries are read once; the image they gather from or add into stays in L2).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for a phase of the barrier; false after about 2^31 cycles (about a
+// second at the SM clock).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+
+struct BkStage {
+    int32_t *col;
+    float *val;
+    uint64_t *bar;
+};
+
+__device__ __forceinline__ BkStage bk_stage(unsigned char *raw, int s) {
+    BkStage g;
+    g.col = reinterpret_cast<int32_t *>(raw) + s * BK_CAP;
+    g.val = reinterpret_cast<float *>(raw + sizeof(int32_t) * 2 * BK_CAP) + s * BK_CAP;
+    g.bar = reinterpret_cast<uint64_t *>(raw + (sizeof(int32_t) + sizeof(float)) * 2 * BK_CAP) + s;
+    return g;
+}
+
+// Entries of chunk c copied to shared memory (a multiple of 4).
+__device__ __forceinline__ int bk_copied(int64_t c, int64_t nnz) {
+    const int64_t ne = nnz - c * BK_CAP;
+    return (int)((ne < BK_CAP ? ne : BK_CAP) & ~(int64_t)3);
+}
+
+__device__ __forceinline__ void bk_issue(int64_t c, int64_t nnz, const int32_t *col,
+                                         const float *val, const BkStage &g) {
+    const uint32_t bytes = (uint32_t)bk_copied(c, nnz) * 4u;
+    mbar_expect(g.bar, 2u * bytes);
+    if (bytes) {
+        bulk_g2s(g.col, col + c * BK_CAP, bytes, g.bar);
+        bulk_g2s(g.val, val + c * BK_CAP, bytes, g.bar);
+    }
+}
+
+__device__ __forceinline__ void bk_rows(const int64_t *__restrict__ first_row, int64_t c,
+                                        int64_t nch, int64_t n, int64_t &r0, int64_t &r1) {
+    r0 = c < nch ? first_row[c] : 0;
+    r1 = c + 1 < nch ? first_row[c + 1] : (c < nch ? n : 0);
+}
+
+// After a wait gave up: record it, wait (bounded) for the copies still in
+// flight into this CTA's stages, return.
+__device__ __forceinline__ void bk_give_up(unsigned char *raw, int it, bool next_issued,
+                                           int *status) {
+    if (threadIdx.x == 0) {
+        atomicExch(status, PSF_ETIMEOUT);
+        mbar_wait(bk_stage(raw, it & 1).bar, (it >> 1) & 1);
+        if (next_issued) mbar_wait(bk_stage(raw, (it + 1) & 1).bar, ((it + 1) >> 1) & 1);
+    }
+}
+
+// End of a row's staged part, chunk-local: min(b - j0, copied), at least 0.
+__device__ __forceinline__ int bk_local_end(int64_t b, int64_t j0, int copied) {
+    const int64_t e = b - j0;
+    return e < copied ? (e > 0 ? (int)e : 0) : copied;
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void bk_add(float *x, float2 *x2, int c, float v, float qa, float qb) {
+    if (PAIR)
+        atomicAdd(x2 + c, make_float2(v * qa, v * qb));
+    else
+        atomicAdd(x + c, v * qa);
+}
+
+__global__ void __launch_bounds__(BK_T) csr_fwd_bulk_kernel(
+    int64_t n, int64_t nnz, int64_t nch, const int64_t *__restrict__ first_row,
+    const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y,
+    int *status) {
+    extern __shared__ __align__(128) unsigned char bk_raw[];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NW = BK_T / 32, PER_T = BK_CAP / BK_T;
+    if (t == 0) {
+        mbar_init(bk_stage(bk_raw, 0).bar);
+        mbar_init(bk_stage(bk_raw, 1).bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t c = blockIdx.x;
+    if (t == 0 && c < nch) bk_issue(c, nnz, col, val, bk_stage(bk_raw, 0));
+    int64_t r0, r1;
+    bk_rows(first_row, c, nch, n, r0, r1);
+    for (int it = 0; c < nch; ++it, c += gridDim.x) {
+        const BkStage g = bk_stage(bk_raw, it & 1);
+        const int64_t cn = c + gridDim.x;
+        if (t == 0 && cn < nch) bk_issue(cn, nnz, col, val, bk_stage(bk_raw, (it + 1) & 1));
+        int64_t nr0, nr1;
+        bk_rows(first_row, cn, nch, n, nr0, nr1);
+        // extents of this warp's first 32 rows (rows r0 + warp + NW i)
+        const int64_t rr = r0 + warp + (int64_t)NW * lane;
+        int64_t pa = 0, pb = 0;
+        if (rr < r1) {
+            pa = ptr[rr];
+            pb = ptr[rr + 1];
+        }
+        const bool ok = mbar_wait(g.bar, (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            bk_give_up(bk_raw, it, cn < nch, status);
+            return;
+        }
+        const int64_t j0 = c * BK_CAP;
+        const int copied = bk_copied(c, nnz);
+        // products of the staged entries, in place
+        int ci[PER_T];
+#pragma unroll
+        for (int k = 0; k < PER_T; ++k) ci[k] = t + k * BK_T < copied ? g.col[t + k * BK_T] : -1;
+        float xv[PER_T];
+#pragma unroll
+        for (int k = 0; k < PER_T; ++k) xv[k] = ci[k] >= 0 ? __ldg(x + ci[k]) : 0.0f;
+#pragma unroll
+        for (int k = 0; k < PER_T; ++k)
+            if (ci[k] >= 0) g.val[t + k * BK_T] *= xv[k];
+        __syncthreads();
+        // rows in batches of 32 per warp (lane k: row r0 + warp + NW (32 batch + k));
+        // empty rows are written by their lanes, the others one at a time
+        for (int64_t bb = r0 + warp; bb < r1; bb += 32 * NW) {
+            const int64_t rl = bb + (int64_t)NW * lane;
+            if (bb != r0 + warp) {
+                pa = pb = 0;
+                if (rl < r1) {
+                    pa = ptr[rl];
+                    pb = ptr[rl + 1];
+                }
+            }
+            // rows of at most 32 entries: summed by their own lane
+            if (rl < r1 && pb - pa <= 32) {
+                float acc = 0.0f;
+                const int la = (int)(pa - j0), lb = bk_local_end(pb, j0, copied);
+                for (int l = la; l < lb; ++l) acc += g.val[l];
+                for (int64_t j = j0 + lb > pa ? j0 + lb : pa; j < pb; ++j)
+                    acc += __ldg(val + j) * __ldg(x + __ldg(col + j));
+                y[rl] = acc;
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, rl < r1 && pb - pa > 32);
+            while (todo) {
+                const int i = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t a = __shfl_sync(0xffffffffu, pa, i);
+                const int64_t b = __shfl_sync(0xffffffffu, pb, i);
+                float acc = 0.0f;
+                const int la = (int)(a - j0), lb = bk_local_end(b, j0, copied);
+                for (int l = la + lane; l < lb; l += 32) acc += g.val[l];
+                for (int64_t j = (j0 + lb > a ? j0 + lb : a) + lane; j < b; j += 32)
+                    acc += __ldg(val + j) * __ldg(x + __ldg(col + j));
+                acc = warp_sum_f(acc);
+                if (lane == 0) y[bb + (int64_t)NW * i] = acc;
+            }
+        }
+        // the products were generic-proxy writes into a stage the next bulk
+        // copy overwrites
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        r0 = nr0;
+        r1 = nr1;
+    }
+}
+
+// x += A^T y (PAIR: x2 += A^T (ya, yb) into the interleaved pair), rows of a
+// chunk one per warp, entries from the staged chunk.
+template <bool PAIR>
+__global__ void __launch_bounds__(BK_T) csr_back_bulk_kernel(
+    int64_t n, int64_t nnz, int64_t nch, const int64_t *__restrict__ first_row,
+    const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ ya, const float *__restrict__ yb,
+    float *__restrict__ x, float2 *__restrict__ x2, int *status) {
+    extern __shared__ __align__(128) unsigned char bk_raw[];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NW = BK_T / 32;
+    if (t == 0) {
+        mbar_init(bk_stage(bk_raw, 0).bar);
+        mbar_init(bk_stage(bk_raw, 1).bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t c = blockIdx.x;
+    if (t == 0 && c < nch) bk_issue(c, nnz, col, val, bk_stage(bk_raw, 0));
+    int64_t r0, r1;
+    bk_rows(first_row, c, nch, n, r0, r1);
+    for (int it = 0; c < nch; ++it, c += gridDim.x) {
+        const BkStage g = bk_stage(bk_raw, it & 1);
+        const int64_t cn = c + gridDim.x;
+        if (t == 0 && cn < nch) bk_issue(cn, nnz, col, val, bk_stage(bk_raw, (it + 1) & 1));
+        int64_t nr0, nr1;
+        bk_rows(first_row, cn, nch, n, nr0, nr1);
+        const int64_t rr = r0 + warp + (int64_t)NW * lane;
+        int64_t pa = 0, pb = 0;
+        float wa = 0.0f, wb = 0.0f;
+        if (rr < r1) {
+            pa = ptr[rr];
+            pb = ptr[rr + 1];
+            wa = ya[rr];
+            if (PAIR) wb = yb[rr];
+        }
+        const bool ok = mbar_wait(g.bar, (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+            bk_give_up(bk_raw, it, cn < nch, status);
+            return;
+        }
+        const int64_t j0 = c * BK_CAP;
+        const int copied = bk_copied(c, nnz);
+        for (int64_t bb = r0 + warp; bb < r1; bb += 32 * NW) {
+            const int64_t rl = bb + (int64_t)NW * lane;
+            if (bb != r0 + warp) {
+                pa = pb = 0;
+                wa = wb = 0.0f;
+                if (rl < r1) {
+                    pa = ptr[rl];
+                    pb = ptr[rl + 1];
+                    wa = ya[rl];
+                    if (PAIR) wb = yb[rl];
+                }
+            }
+            const bool live = rl < r1 && (wa != 0.0f || wb != 0.0f);
+            // rows of at most 32 entries: added by their own lane
+            if (live && pb - pa <= 32) {
+                const int la = (int)(pa - j0), lb = bk_local_end(pb, j0, copied);
+                for (int l = la; l < lb; ++l) bk_add<PAIR>(x, x2, g.col[l], g.val[l], wa, wb);
+                for (int64_t j = j0 + lb > pa ? j0 + lb : pa; j < pb; ++j)
+                    bk_add<PAIR>(x, x2, __ldg(col + j), __ldg(val + j), wa, wb);
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, live && pb - pa > 32);
+            while (todo) {
+                const int i = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t a = __shfl_sync(0xffffffffu, pa, i);
+                const int64_t b = __shfl_sync(0xffffffffu, pb, i);
+                const float qa = __shfl_sync(0xffffffffu, wa, i);
+                const float qb = PAIR ? __shfl_sync(0xffffffffu, wb, i) : 0.0f;
+                const int la = (int)(a - j0), lb = bk_local_end(b, j0, copied);
+                for (int l = la + lane; l < lb; l += 32)
+                    bk_add<PAIR>(x, x2, g.col[l], g.val[l], qa, qb);
+                for (int64_t j = (j0 + lb > a ? j0 + lb : a) + lane; j < b; j += 32)
+                    bk_add<PAIR>(x, x2, __ldg(col + j), __ldg(val + j), qa, qb);
+            }
+        }
+        __syncthreads();
+        r0 = nr0;
+        r1 = nr1;
+    }
+}
+
+// first_row[c] = the first row r in [0, n] with ptr[r] >= c * BK_CAP.
+__global__ void bk_first_row_kernel(const int64_t *__restrict__ ptr, int64_t n, int64_t nch,
+                                    int64_t *__restrict__ first_row) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nch) return;
+    const int64_t key = c * BK_CAP;
+    int64_t lo = 0, hi = n;  // ptr[n] = nnz > key
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (ptr[mid] >= key)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    first_row[c] = lo;
 }
 
 __global__ void split_pair_kernel(const float2 *__restrict__ x2, float *__restrict__ xa,
@@ -1291,8 +1607,68 @@ static int wq_grid(K kernel, int threads, int *grid) {
     return PSF_OK;
 }
 
+// Grid and shared memory of the bulk-staged kernels: the resident CTAs.
+template <typename K>
+static int bk_launch_shape(K kernel, int64_t nch, int *grid, size_t *shm) {
+    *shm = (sizeof(int32_t) + sizeof(float)) * 2 * BK_CAP + 2 * sizeof(uint64_t);
+    PSF_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*shm));
+    int dev = 0, sms = 148, per_sm = 0;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PSF_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BK_T, *shm));
+    const int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    *grid = (int)(nch < g ? nch : g);
+    return PSF_OK;
+}
+
+// The chunk table of the bulk-staged forms (FP32 rows, 16-byte aligned
+// column and value arrays, at least one entry); PSF_EINVAL when they do not
+// apply.  Synchronises on the first call.
+static int bk_table(psf_matrix *m, cudaStream_t st) {
+    if (m->bk_first) return PSF_OK;
+    if (m->dtype != PSF_F32 || m->n_rows == 0) return PSF_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(m->col) & 15) || (reinterpret_cast<uintptr_t>(m->val) & 15))
+        return PSF_EINVAL;
+    int64_t nnz = 0;
+    PSF_TRY(cudaMemcpyAsync(&nnz, m->row_ptr + m->n_rows, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            st));
+    PSF_TRY(cudaStreamSynchronize(st));
+    if (nnz <= 0) return PSF_EINVAL;
+    const int64_t nch = (nnz + BK_CAP - 1) / BK_CAP;
+    int64_t *fr = nullptr;
+    PSF_TRY(cudaMalloc(&fr, sizeof(int64_t) * nch));
+    {
+        PSF_TIMED("bk_first_row_kernel", st);
+        bk_first_row_kernel<<<(int)((nch + 255) / 256), 256, 0, st>>>(m->row_ptr, m->n_rows, nch,
+                                                                      fr);
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaFree(fr);
+        return PSF_ECUDA;
+    }
+    m->bk_first = fr;
+    m->bk_nch = nch;
+    m->bk_nnz = nnz;
+    return PSF_OK;
+}
+
 static int rows_fwd_with(const psf_matrix *m, const float *x, float *y, int chunk, int threads,
                          cudaStream_t st) {
+    if (chunk == -2) {  // bulk-staged chunks
+        if (!m->bk_first) return PSF_EINVAL;
+        int grid = 0;
+        size_t shm = 0;
+        int rc = bk_launch_shape(csr_fwd_bulk_kernel, m->bk_nch, &grid, &shm);
+        if (rc) return rc;
+        {
+            PSF_TIMED("csr_fwd_bulk_kernel", st);
+            csr_fwd_bulk_kernel<<<grid, BK_T, shm, st>>>(m->n_rows, m->bk_nnz, m->bk_nch,
+                                                         m->bk_first, m->row_ptr, m->col,
+                                                         (const float *)m->val, x, y, m->status);
+        }
+        PSF_LAUNCHED();
+        return PSF_OK;
+    }
     if (chunk < 0) {  // streaming tiles (FP32 rows without a scale)
         if (m->dtype != PSF_F32) return PSF_EINVAL;
         int dev = 0, sms = 148;
@@ -1335,6 +1711,21 @@ static int rows_fwd_with(const psf_matrix *m, const float *x, float *y, int chun
 static int rows_back_with(const psf_matrix *m, const float *y, float *x, int chunk, int threads,
                           cudaStream_t st) {
     PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
+    if (chunk == -2) {  // bulk-staged chunks
+        if (!m->bk_first) return PSF_EINVAL;
+        int grid = 0;
+        size_t shm = 0;
+        int rc = bk_launch_shape(csr_back_bulk_kernel<false>, m->bk_nch, &grid, &shm);
+        if (rc) return rc;
+        {
+            PSF_TIMED("csr_back_bulk_kernel", st);
+            csr_back_bulk_kernel<false><<<grid, BK_T, shm, st>>>(
+                m->n_rows, m->bk_nnz, m->bk_nch, m->bk_first, m->row_ptr, m->col,
+                (const float *)m->val, y, nullptr, x, nullptr, m->status);
+        }
+        PSF_LAUNCHED();
+        return PSF_OK;
+    }
     if (chunk < 0) chunk = 0;  // the streaming form is forward only
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
@@ -1367,6 +1758,9 @@ static int rows_fwd(const psf_matrix *m, const float *x, float *y, cudaStream_t 
 static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t st) {
     return rows_back_with(m, y, x, m->wq_chunk, m->wq_threads, st);
 }
+
+static int rows_back_pair(const psf_matrix *m, const float *qa, const float *qb, int form,
+                          cudaStream_t st);
 
 // S (adjoint == false) or S^T on LOR-space vectors of a factored plan.
 template <bool adjoint, int WA>
@@ -1542,7 +1936,18 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->topn = 0;
     m->tidx = nullptr;
     m->tw = nullptr;
-    if (cudaMalloc(&m->queue, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    m->bk_first = nullptr;
+    m->bk_nch = m->bk_nnz = 0;
+    m->pair_form = 0;
+    m->status = nullptr;
+    // row counters [2] and the status word, one allocation
+    if (cudaMalloc(&m->queue, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+        delete m;
+        return PSF_ECUDA;
+    }
+    m->status = reinterpret_cast<int *>(m->queue + 2);
+    if (cudaMemset(m->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(m->queue);
         delete m;
         return PSF_ECUDA;
     }
@@ -1625,6 +2030,7 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
     cudaFree(m->queue);
     cudaFree(m->img2);
     cudaFree(m->csum);
+    cudaFree(m->bk_first);
     delete m;
     return PSF_OK;
 }
@@ -1715,12 +2121,14 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
     cudaStream_t st = as_stream(stream);
     if (m->n_rows == 0) {
         m->wq_chunk = m->wq_threads = m->fwd_chunk = m->fwd_threads = 0;
+        m->pair_form = 0;
     } else {
         // candidates per direction: the grid-stride kernels (chunk 0), the work
         // queue at every (rows per take, threads per CTA) pair and, forward with
         // FP32 rows, the streaming tiles (chunk -1); each timed with CUDA events
         // on all-ones vectors (one warm-up, best of two), the fastest kept
-        static const int chunks[] = {-1, 0, 1, 2, 4, 8, 16, 32, 64, 128};
+        static const int chunks[] = {-2, -1, 0, 1, 2, 4, 8, 16, 32, 64, 128};
+        const bool bulk = bk_table(m, st) == PSF_OK;
         static const int threads[] = {128, 256, 512};
         float *x = nullptr;
         PSF_TRY(cudaMallocAsync(&x, sizeof(float) * m->n_cols, st));
@@ -1739,6 +2147,7 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
             int bc = 0, bt = 0;
             for (int c : chunks) {
                 if (c < 0 && (dir == 1 || m->dtype != PSF_F32)) continue;
+                if (c == -2 && !bulk) continue;
                 for (int t : threads) {
                     if (rc) break;
                     if (c <= 0 && t != PJ_T) continue;
@@ -1767,6 +2176,25 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
                 m->wq_chunk = bc;
                 m->wq_threads = bt;
             }
+        }
+        // the pair back-projection of psf_back_sens: the back launch or the
+        // bulk-staged kernel (the single back keeps the row-skipping launches:
+        // a bulk-staged pass streams every chunk whatever y holds)
+        m->pair_form = 0;
+        if (bulk && !rc) {
+            float best[2] = {1e30f, 1e30f};
+            for (int f = 0; f < 2 && !rc; ++f)
+                for (int rep = 0; rep < 3 && !rc; ++rep) {
+                    float ms = 0.0f;
+                    if (cudaEventRecord(e0, st) != cudaSuccess) rc = PSF_ECUDA;
+                    if (!rc) rc = rows_back_pair(m, y, y, f == 0 ? 0 : -2, st);
+                    if (!rc && (cudaEventRecord(e1, st) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                        rc = PSF_ECUDA;
+                    if (!rc && rep > 0 && ms < best[f]) best[f] = ms;
+                }
+            if (!rc && best[1] < best[0]) m->pair_form = -2;
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -1822,13 +2250,19 @@ extern "C" int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form) {
 }
 
 extern "C" int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads) {
-    if (!m || chunk < -1 || chunk > (1 << 20)) return PSF_EINVAL;
+    if (!m || chunk < -2 || chunk > (1 << 20)) return PSF_EINVAL;
     if (chunk > 0 && (threads < 32 || threads > 1024 || threads % 32)) return PSF_EINVAL;
     if (chunk < 0 && m->dtype != PSF_F32) return PSF_EINVAL;
+    if (chunk == -2) {
+        if (m->n_rows == 0) return PSF_EINVAL;
+        const int rc = bk_table(m, nullptr);
+        if (rc) return rc;
+    }
     m->fwd_chunk = chunk;
     m->fwd_threads = chunk > 0 ? threads : 0;
-    m->wq_chunk = chunk > 0 ? chunk : 0;
+    m->wq_chunk = chunk > 0 || chunk == -2 ? chunk : 0;
     m->wq_threads = chunk > 0 ? threads : 0;
+    m->pair_form = chunk == -2 ? -2 : 0;
     return PSF_OK;
 }
 
@@ -1912,10 +2346,41 @@ extern "C" int psf_back_sens(const psf_matrix *m, const float *y, float *x, floa
         qa = m->p;
         qb = y;
     }
+    int rc = rows_back_pair(m, qa, qb, m->pair_form, st);
+    if (rc) return rc;
+    {
+        PSF_TIMED("split_pair_kernel", st);
+        split_pair_kernel<<<grid_for(m->n_cols, 256), 256, 0, st>>>(m->img2, sens, x, m->n_cols);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
+namespace psf {
+
+// img2 = A^T (qa, qb) as an interleaved pair: form -2 the bulk-staged kernel,
+// else the pair kernel at the back projection's launch.
+static int rows_back_pair(const psf_matrix *m, const float *qa, const float *qb, int form,
+                          cudaStream_t st) {
     PSF_TRY(cudaMemsetAsync(m->img2, 0, sizeof(float2) * m->n_cols, st));
+    if (form == -2) {
+        if (!m->bk_first) return PSF_EINVAL;
+        int grid = 0;
+        size_t shm = 0;
+        int rc = bk_launch_shape(csr_back_bulk_kernel<true>, m->bk_nch, &grid, &shm);
+        if (rc) return rc;
+        {
+            PSF_TIMED("csr_back_bulk_kernel<pair>", st);
+            csr_back_bulk_kernel<true><<<grid, BK_T, shm, st>>>(
+                m->n_rows, m->bk_nnz, m->bk_nch, m->bk_first, m->row_ptr, m->col,
+                (const float *)m->val, qa, qb, nullptr, m->img2, m->status);
+        }
+        PSF_LAUNCHED();
+        return PSF_OK;
+    }
     const int chunk = m->wq_chunk > 0 ? m->wq_chunk : 0;
     const int threads = chunk > 0 ? m->wq_threads : PJ_T;
-    int rc = dispatch_dtype(m->dtype, [&](auto tag) -> int {
+    return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
         int grid = grid_for(m->n_rows * 32, PJ_T);
         if (chunk > 0) {
@@ -1932,11 +2397,16 @@ extern "C" int psf_back_sens(const psf_matrix *m, const float *y, float *x, floa
         PSF_LAUNCHED();
         return PSF_OK;
     });
-    if (rc) return rc;
-    {
-        PSF_TIMED("split_pair_kernel", st);
-        split_pair_kernel<<<grid_for(m->n_cols, 256), 256, 0, st>>>(m->img2, sens, x, m->n_cols);
-    }
-    PSF_LAUNCHED();
-    return PSF_OK;
+}
+
+}  // namespace psf
+
+extern "C" int psf_matrix_check(const psf_matrix *m, void *stream) {
+    if (!m) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    int h = 0;
+    PSF_TRY(cudaMemcpyAsync(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PSF_TRY(cudaStreamSynchronize(st));
+    if (h) PSF_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));
+    return h;
 }

@@ -30,6 +30,7 @@ FUNCTIONS = [
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
     "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
+    "psf_matrix_check",
 ]
 
 
@@ -98,6 +99,7 @@ _SIGS = {
     "psf_sino_bins": (C.c_int, [_P, _P, _P, _P, _P]),
     "psf_voxel_homog": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
     "psf_matrix_set_stencil_form": (C.c_int, [_P, _I32]),
+    "psf_matrix_check": (C.c_int, [_P, _P]),
 }
 
 _lock = threading.Lock()
@@ -387,10 +389,16 @@ class Matrix:
         return (c[0], t[0]), (c[1], t[1])
 
     def set_launch(self, chunk: int, threads: int = 256):
-        """Stored-row projector launch: chunk 0 = grid-stride kernels, else the
-        work-queue kernels taking `chunk` rows per warp."""
+        """Stored-row projector launch: chunk 0 = grid-stride kernels, -1 the
+        streaming forward, -2 the bulk-staged kernels, else the work-queue
+        kernels taking `chunk` rows per warp."""
         _ok(lib().psf_matrix_set_launch(self._h, int(chunk), int(threads)),
             "psf_matrix_set_launch")
+        return self
+
+    def check(self):
+        """Raise if a bounded device wait of this plan gave up (psf_matrix_check)."""
+        _ok(lib().psf_matrix_check(self._h, _stream()), "psf_matrix_check")
         return self
 
     def set_stencil_form(self, form: int):

@@ -50,6 +50,18 @@ def test_work_queue_launches_match(plan):
     if M.dtype_name == "f32":
         M.set_launch(-1)  # streaming forward tiles
         torch.testing.assert_close(M.forward(x), y0, rtol=1e-6, atol=1e-6 * y0.abs().max().item())
+        M.set_launch(-2)  # bulk-staged chunks, every direction
+        torch.testing.assert_close(M.forward(x), y0, rtol=1e-6, atol=1e-6 * y0.abs().max().item())
+        torch.testing.assert_close(M.back(r), b0, rtol=1e-6, atol=1e-6 * b0.abs().max().item())
+        bs, ss = M.back_sens(r)
+        M.set_launch(0)
+        s0 = M.sensitivity()
+        torch.testing.assert_close(bs, b0, rtol=1e-6, atol=1e-6 * b0.abs().max().item())
+        torch.testing.assert_close(ss, s0, rtol=1e-6, atol=1e-6 * s0.abs().max().item())
+        M.check()
+    else:
+        with pytest.raises(Exception):  # FP32 rows only
+            M.set_launch(-2)
     M.set_launch(0)
     with pytest.raises(Exception):
         M.set_launch(4, 100)
@@ -60,7 +72,7 @@ def test_autotune_and_graph_mlem(plan):
 
     M, x = plan["M"], plan["x"]
     for chunk, threads in M.autotune():
-        assert chunk >= -1 and (chunk <= 0 or threads % 32 == 0)
+        assert chunk >= -2 and (chunk <= 0 or threads % 32 == 0)
     y = M.forward(x).clone()
     xe = mlem(M, y, iters=10)
     xg = mlem(M, y, iters=10, graph=True)

@@ -113,7 +113,43 @@ def test_uneven_rows_every_launch(P, ring2d):
     y = torch.from_numpy(I.random_lor_values(M.n_rows, 5)).cuda()
     M.set_launch(0)
     f0, b0 = M.forward(x), M.back(y)
-    for chunk, threads in [(1, 128), (7, 256), (128, 512), (-1, 256)]:
+    for chunk, threads in [(1, 128), (7, 256), (128, 512), (-1, 256), (-2, 256)]:
         M.set_launch(chunk, threads)
         torch.testing.assert_close(M.forward(x), f0, rtol=1e-6, atol=1e-6 * f0.abs().max().item())
         torch.testing.assert_close(M.back(y), b0, rtol=1e-5, atol=1e-6 * b0.abs().max().item())
+    M.check()
+
+
+def test_bulk_staged_long_and_empty_rows(P):
+    """Bulk-staged projectors on rows longer than a staged chunk (4096
+    entries: chunks where no row starts), runs of empty rows, a row that
+    starts exactly on a chunk boundary and a ragged tail; misaligned arrays
+    are refused."""
+    rng = np.random.default_rng(7)
+    lens = np.array([5000, 0, 0, 3, 8192 - 5003, 9001, 0, 1, 17, 0, 4100, 2, 0, 0], dtype=np.int64)
+    assert lens.sum() % 4 != 0
+    ptr = np.concatenate([[0], np.cumsum(lens)])
+    assert 8192 in ptr  # a row starting on a chunk boundary
+    nv = 3000
+    col = rng.integers(0, nv, ptr[-1]).astype(np.int32)
+    val = rng.random(ptr[-1]).astype(np.float32)
+    ptr_t, col_t, val_t = (torch.from_numpy(a).cuda() for a in (ptr, col, val))
+    M = P.Matrix(ptr_t, col_t, val_t, nv)
+    x = torch.from_numpy(rng.random(nv).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.random(len(lens)).astype(np.float32)).cuda()
+    M.set_launch(0)
+    f0, b0 = M.forward(x).clone(), M.back(y).clone()
+    M.set_launch(-2)
+    torch.testing.assert_close(M.forward(x), f0, rtol=1e-5, atol=1e-6 * f0.abs().max().item())
+    torch.testing.assert_close(M.back(y), b0, rtol=1e-5, atol=1e-6 * b0.abs().max().item())
+    bs, _ = M.back_sens(y)
+    torch.testing.assert_close(bs, b0, rtol=1e-5, atol=1e-6 * b0.abs().max().item())
+    M.check()
+    ref = np.array([val[ptr[i]:ptr[i + 1]].astype(np.float64) @ x.cpu().numpy()[col[ptr[i]:ptr[i + 1]]]
+                    for i in range(len(lens))])
+    assert_close(M.forward(x).cpu().numpy(), ref, 1e-5, 1e-6 * np.abs(ref).max(), "bulk forward")
+    # column and value arrays off a 16-byte boundary: the bulk form is refused
+    col2 = torch.cat([torch.zeros(1, dtype=torch.int32, device="cuda"), col_t])[1:]
+    M2 = P.Matrix(ptr_t, col2, val_t, nv)
+    with pytest.raises(Exception):
+        M2.set_launch(-2)
