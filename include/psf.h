@@ -306,6 +306,19 @@ int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scanner,
                                const psf_lor_set *set, int32_t half_t, int32_t half_a,
                                int32_t n_keep, const int32_t *idx, const float *w);
 
+/* For a plan with top-N spreads (list-mode reconstruction, the next step of
+ * Sec. 5): build the transpose of S -- for every measured LOR the source LORs
+ * whose kept entries land on it, with their weights (plan-owned: 8 bytes per
+ * kept tap, 12 bytes per LOR) -- with two passes over the taps (count, scan,
+ * fill).  Afterwards S^T of an input with at most 1/16 nonzero entries (one
+ * subset's counts or ratios) lists those entries and scatters from them with
+ * FP32 atomics (the summation order varies between runs); denser inputs keep
+ * the gather.  The decision is taken on the device, so the calls stay
+ * capturable.  A later psf_matrix_set_spread(_topn) drops the transpose.
+ * Synchronises `stream`; PSF_EINVAL for other plans or more than 2^31 - 1
+ * rows. */
+int psf_matrix_build_sparse_adjoint(psf_matrix *m, void *stream);
+
 int psf_matrix_destroy(psf_matrix *m);
 
 /*

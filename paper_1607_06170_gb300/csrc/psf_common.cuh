@@ -91,6 +91,11 @@ int make_img(const psf_image *im, Img *out);
 // Grid for a grid-stride loop over n items: at most 8 CTAs per SM.
 int grid_for(int64_t n, int block);
 
+// In-place inclusive scan of an int64 array on `st` (three launches);
+// tile_sums needs scan_tile_count(n) slots.
+int64_t scan_tile_count(int64_t n);
+int inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t st);
+
 __host__ __device__ inline int64_t table_entry(const Tab &t, int kt, int ka, int iu, int iv) {
     return (((int64_t)kt * t.Ka + ka) * t.Pt + iu) * t.Pa + iv;
 }

@@ -55,6 +55,14 @@ struct psf_matrix {
     int64_t bk_nch, bk_nnz;
     int pair_form;
     int *status;  // plan-owned device status word (PSF_ETIMEOUT from a bounded wait)
+    // top-N plans after psf_matrix_build_sparse_adjoint (plan-owned): the
+    // transpose of S (per measured LOR, its sources and weights), a list of
+    // an input's nonzero entries and their count
+    int64_t *tr_ptr;
+    int32_t *tr_src;
+    float *tr_w;
+    int32_t *tr_list;
+    unsigned long long *tr_nz;
 };
 
 namespace psf {
@@ -1458,14 +1466,36 @@ __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, in
 // the crystal pair (a + dt1, ra + da1), (b + dt2, rb + da2), transaxial
 // indices wrapping around the ring; pairs outside the set, off the rings or
 // of one crystal with itself are dropped, as in the dense stencil.
+//
+// The same pass over the taps also builds the transpose of S (the sources of
+// every measured LOR, psf_matrix_build_sparse_adjoint): TS_COUNT counts each
+// target's sources, TS_FILL writes (source, weight) into the target's list at
+// a slot taken from a per-target cursor (the order inside a list depends on
+// the atomics).  With it, S^T of an input with at most 1/16 nonzero entries
+// is a scatter from those entries; the gather then returns at once.
 constexpr int TS_T = 256, TS_G = 8;
+enum { TS_FWD = 0, TS_ADJ = 1, TS_COUNT = 2, TS_FILL = 3 };
 
-template <bool adjoint>
+struct TsTr {
+    unsigned long long *cnt;      // TS_COUNT: [n] sources per target
+    const int64_t *ptr;           // TS_FILL: [n + 1] list offsets
+    int32_t *cur;                 // TS_FILL: [n] cursors (zeroed)
+    int32_t *src;                 // TS_FILL: sources
+    float *w;                     // TS_FILL: weights
+    const unsigned long long *nz;  // TS_ADJ: nonzero input count (NULL: always gather)
+};
+
+__host__ __device__ inline bool ts_sparse(unsigned long long nz, int64_t n) {
+    return nz <= (unsigned long long)(n >> 4);
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(TS_T, 4) topn_s_kernel(LorSet ls, int Wt, int Wa, int N,
                                                       const int32_t *__restrict__ tidx,
                                                       const float *__restrict__ tw,
                                                       const float *__restrict__ in,
-                                                      float *__restrict__ out) {
+                                                      float *__restrict__ out, TsTr tr) {
+    constexpr bool adjoint = MODE == TS_ADJ;
     extern __shared__ __align__(16) unsigned char raw[];
     const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, Nt = ls.Nt, NR = ls.NR;
     char4 *dec = reinterpret_cast<char4 *>(raw);  // [E*E] window index -> (dt1, da1, dt2, da2)
@@ -1487,11 +1517,12 @@ __global__ void __launch_bounds__(TS_T, 4) topn_s_kernel(LorSet ls, int Wt, int 
     }
     __syncthreads();
     const int64_t n = ls.ntp * ls.nrp;
+    if (adjoint && tr.nz && ts_sparse(*tr.nz, n)) return;  // the scatter has it
     for (int64_t g = (int64_t)blockIdx.x * TS_T + t; g < n; g += (int64_t)gridDim.x * TS_T) {
         const int64_t T = g / ls.nrp;
         const int j = (int)(g - T * ls.nrp);
         float pg = 0.0f;
-        if (!adjoint) {
+        if (MODE == TS_FWD) {
             pg = in[g];
             if (pg == 0.0f) continue;
         }
@@ -1535,13 +1566,50 @@ __global__ void __launch_bounds__(TS_T, 4) topn_s_kernel(LorSet ls, int Wt, int 
                     v[u] = m[u] >= 0 ? (in ? __ldg(in + m[u]) : 1.0f) : 0.0f;
 #pragma unroll
                 for (int u = 0; u < TS_G; ++u) acc = fmaf(wv[u], v[u], acc);
-            } else {
+            } else if (MODE == TS_FWD) {
 #pragma unroll
                 for (int u = 0; u < TS_G; ++u)
                     if (m[u] >= 0) atomicAdd(out + m[u], wv[u] * pg);
+            } else if (MODE == TS_COUNT) {
+#pragma unroll
+                for (int u = 0; u < TS_G; ++u)
+                    if (m[u] >= 0) atomicAdd(tr.cnt + m[u], 1ull);
+            } else {
+#pragma unroll
+                for (int u = 0; u < TS_G; ++u)
+                    if (m[u] >= 0) {
+                        const int64_t e = tr.ptr[m[u]] + atomicAdd(tr.cur + m[u], 1);
+                        tr.src[e] = (int32_t)g;
+                        tr.w[e] = wv[u];
+                    }
             }
         }
         if (adjoint) out[g] = acc;
+    }
+}
+
+// S^T of a sparse input through the transpose: out = 0, then every listed
+// nonzero input entry adds w * in[m] to each of its sources.  Both kernels
+// return at once when the input is not sparse (the gather runs instead).
+__global__ void ts_zero_kernel(float *__restrict__ out, int64_t n,
+                               const unsigned long long *nz) {
+    if (!ts_sparse(*nz, n)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = 0.0f;
+}
+
+__global__ void ts_scatter_kernel(const int32_t *__restrict__ list, const unsigned long long *nz,
+                                  int64_t n, const int64_t *__restrict__ ptr,
+                                  const int32_t *__restrict__ src, const float *__restrict__ w,
+                                  const float *__restrict__ in, float *__restrict__ out) {
+    const unsigned long long cnt = *nz;
+    if (!ts_sparse(cnt, n)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t mm = list[i];
+        const float v = in[mm];
+        for (int64_t e = ptr[mm]; e < ptr[mm + 1]; ++e) atomicAdd(out + src[e], w[e] * v);
     }
 }
 
@@ -1557,18 +1625,39 @@ static int topn_s(const psf_matrix *m, const float *in, float *out, bool adjoint
     const int64_t need = (n + TS_T - 1) / TS_T;
     const int grid = (int)(need < (int64_t)sms * 8 ? need : (int64_t)sms * 8);
     if (adjoint) {
-        PSF_TRY(cudaFuncSetAttribute(topn_s_kernel<true>,
+        TsTr tr{};
+        if (in && m->tr_ptr) {  // sparse inputs through the transpose
+            PSF_TRY(cudaMemsetAsync(m->tr_nz, 0, sizeof(unsigned long long), st));
+            {
+                PSF_TIMED("mask_rows_kernel", st);
+                mask_rows_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, n, m->tr_list, m->tr_nz);
+            }
+            PSF_LAUNCHED();
+            {
+                PSF_TIMED("ts_zero_kernel", st);
+                ts_zero_kernel<<<grid_for(n, 256), 256, 0, st>>>(out, n, m->tr_nz);
+            }
+            PSF_LAUNCHED();
+            {
+                PSF_TIMED("ts_scatter_kernel", st);
+                ts_scatter_kernel<<<grid_for(n >> 4, 256), 256, 0, st>>>(
+                    m->tr_list, m->tr_nz, n, m->tr_ptr, m->tr_src, m->tr_w, in, out);
+            }
+            PSF_LAUNCHED();
+            tr.nz = m->tr_nz;
+        }
+        PSF_TRY(cudaFuncSetAttribute(topn_s_kernel<TS_ADJ>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         PSF_TIMED("topn_s_kernel<adjoint>", st);
-        topn_s_kernel<true><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
-                                                      m->tw, in, out);
+        topn_s_kernel<TS_ADJ><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
+                                                        m->tw, in, out, tr);
     } else {
         PSF_TRY(cudaMemsetAsync(out, 0, sizeof(float) * n, st));
-        PSF_TRY(cudaFuncSetAttribute(topn_s_kernel<false>,
+        PSF_TRY(cudaFuncSetAttribute(topn_s_kernel<TS_FWD>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         PSF_TIMED("topn_s_kernel<forward>", st);
-        topn_s_kernel<false><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
-                                                       m->tw, in, out);
+        topn_s_kernel<TS_FWD><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
+                                                        m->tw, in, out, TsTr{});
     }
     PSF_LAUNCHED();
     return PSF_OK;
@@ -1940,6 +2029,11 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->bk_nch = m->bk_nnz = 0;
     m->pair_form = 0;
     m->status = nullptr;
+    m->tr_ptr = nullptr;
+    m->tr_src = nullptr;
+    m->tr_w = nullptr;
+    m->tr_list = nullptr;
+    m->tr_nz = nullptr;
     // row counters [2] and the status word, one allocation
     if (cudaMalloc(&m->queue, 3 * sizeof(unsigned long long)) != cudaSuccess) {
         delete m;
@@ -1970,6 +2064,21 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     return PSF_OK;
 }
 
+namespace psf {
+// A new spread makes the transpose of the previous one stale.
+static void drop_transpose(psf_matrix *m) {
+    cudaFree(m->tr_ptr);
+    cudaFree(m->tr_src);
+    cudaFree(m->tr_w);
+    cudaFree(m->tr_list);
+    m->tr_ptr = nullptr;
+    m->tr_src = nullptr;
+    m->tr_w = nullptr;
+    m->tr_list = nullptr;
+    m->tr_nz = nullptr;
+}
+}  // namespace psf
+
 extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
                                      const psf_lor_set *set, int32_t half_t, int32_t half_a,
                                      const float *class_spread) {
@@ -1988,6 +2097,7 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
         PSF_TRY(cudaMalloc(&m->csum, sizeof(float) * need));
         m->csum_n = need;
     }
+    drop_transpose(m);
     m->factored = true;
     m->ls = ls;
     m->Wt = half_t;
@@ -2011,6 +2121,7 @@ extern "C" int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scan
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;
     if (ls.ntp * ls.nrp != m->n_rows || ls.NR > 32000 || half_t >= ls.Nt) return PSF_EINVAL;
+    drop_transpose(m);
     m->factored = true;
     m->ls = ls;
     m->Wt = half_t;
@@ -2023,6 +2134,86 @@ extern "C" int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scan
     return PSF_OK;
 }
 
+extern "C" int psf_matrix_build_sparse_adjoint(psf_matrix *m, void *stream) {
+    if (!m || m->topn <= 0) return PSF_EINVAL;
+    if (m->tr_ptr) return PSF_OK;
+    const int64_t n = m->n_rows;
+    if (n == 0) return PSF_OK;
+    if (n > INT32_MAX) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const size_t shm = sizeof(char4) * (size_t)m->E * m->E +
+                       sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2) + sizeof(short2) * m->ls.nrp + 16;
+    if (shm > 200 * 1024) return PSF_EINVAL;
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t need = (n + TS_T - 1) / TS_T;
+    const int grid = (int)(need < (int64_t)sms * 8 ? need : (int64_t)sms * 8);
+    int64_t *ptr = nullptr, *tiles = nullptr;
+    int32_t *cur = nullptr, *src = nullptr, *list = nullptr;
+    float *w = nullptr;
+    int rc = PSF_OK;
+    auto fail = [&](int code) {
+        cudaFree(ptr);
+        cudaFree(tiles);
+        cudaFree(cur);
+        cudaFree(src);
+        cudaFree(w);
+        cudaFree(list);
+        return code;
+    };
+    if (cudaMalloc(&ptr, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&tiles, sizeof(int64_t) * scan_tile_count(n)) != cudaSuccess ||
+        cudaMalloc(&cur, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&list, sizeof(int32_t) * n + 2 * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(PSF_ECUDA);
+    if (cudaMemsetAsync(ptr, 0, sizeof(int64_t) * (n + 1), st) != cudaSuccess ||
+        cudaMemsetAsync(cur, 0, sizeof(int32_t) * n, st) != cudaSuccess ||
+        cudaFuncSetAttribute(topn_s_kernel<TS_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)shm) != cudaSuccess ||
+        cudaFuncSetAttribute(topn_s_kernel<TS_FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)shm) != cudaSuccess)
+        return fail(PSF_ECUDA);
+    TsTr tr{};
+    tr.cnt = reinterpret_cast<unsigned long long *>(ptr + 1);
+    {
+        PSF_TIMED("topn_s_kernel<count>", st);
+        topn_s_kernel<TS_COUNT><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
+                                                          m->tw, nullptr, nullptr, tr);
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(PSF_ECUDA);
+    rc = inclusive_scan(ptr + 1, n, tiles, st);
+    if (rc) return fail(rc);
+    int64_t total = 0;
+    if (cudaMemcpyAsync(&total, ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(PSF_ECUDA);
+    if (cudaMalloc(&src, sizeof(int32_t) * (total + 1)) != cudaSuccess ||
+        cudaMalloc(&w, sizeof(float) * (total + 1)) != cudaSuccess)
+        return fail(PSF_ECUDA);
+    tr = TsTr{};
+    tr.ptr = ptr;
+    tr.cur = cur;
+    tr.src = src;
+    tr.w = w;
+    {
+        PSF_TIMED("topn_s_kernel<fill>", st);
+        topn_s_kernel<TS_FILL><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
+                                                         m->tw, nullptr, nullptr, tr);
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(PSF_ECUDA);
+    cudaFree(cur);
+    cudaFree(tiles);
+    m->tr_ptr = ptr;
+    m->tr_src = src;
+    m->tr_w = w;
+    m->tr_list = list;
+    m->tr_nz = reinterpret_cast<unsigned long long *>(list + n + (n & 1));
+    return PSF_OK;
+}
+
 extern "C" int psf_matrix_destroy(psf_matrix *m) {
     if (!m) return PSF_EINVAL;
     cudaFree(m->p);
@@ -2031,6 +2222,10 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
     cudaFree(m->img2);
     cudaFree(m->csum);
     cudaFree(m->bk_first);
+    cudaFree(m->tr_ptr);
+    cudaFree(m->tr_src);
+    cudaFree(m->tr_w);
+    cudaFree(m->tr_list);  // the nonzero count shares this allocation
     delete m;
     return PSF_OK;
 }

@@ -214,8 +214,10 @@ __global__ void __launch_bounds__(SCAN_T) scan_apply_kernel(int64_t *__restrict_
     }
 }
 
+int64_t scan_tile_count(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
 // In-place inclusive scan of x[0..n) (int64); tile_sums has ceil(n/TILE) slots.
-static int inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t st) {
+int inclusive_scan(int64_t *x, int64_t n, int64_t *tile_sums, cudaStream_t st) {
     if (n <= 0) return PSF_OK;
     int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
     {

@@ -30,7 +30,7 @@ FUNCTIONS = [
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
     "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
-    "psf_matrix_check",
+    "psf_matrix_check", "psf_matrix_build_sparse_adjoint",
 ]
 
 
@@ -100,6 +100,7 @@ _SIGS = {
     "psf_voxel_homog": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
     "psf_matrix_set_stencil_form": (C.c_int, [_P, _I32]),
     "psf_matrix_check": (C.c_int, [_P, _P]),
+    "psf_matrix_build_sparse_adjoint": (C.c_int, [_P, _P]),
 }
 
 _lock = threading.Lock()
@@ -358,6 +359,7 @@ class Matrix:
         self._keep = [row_ptr, col, val, row_scale]
         self.n_rows = row_ptr.shape[0] - 1
         self.n_cols = int(n_cols)
+        self.topn = 0  # kept entries per class spread of a top-N plan
         self.dtype_name = {PSF_F32: "f32", PSF_BF16: "bf16", PSF_F16: "f16"}[dt]
         self._h = C.c_void_p()
         _ok(lib().psf_matrix_create(C.byref(self._h), self.n_rows, self.n_cols, _ptr(row_ptr),
@@ -369,6 +371,7 @@ class Matrix:
         s, l = scanner(sc), lor_set(ls)
         _ok(lib().psf_matrix_set_spread(self._h, C.byref(s), C.byref(l), half_t, half_a,
                                         _ptr(class_spread)), "psf_matrix_set_spread")
+        self.topn = 0
         return self
 
     def set_spread_topn(self, sc: dict, ls: dict, half_t: int, half_a: int, idx, w):
@@ -378,6 +381,14 @@ class Matrix:
         _ok(lib().psf_matrix_set_spread_topn(self._h, C.byref(s), C.byref(l), half_t, half_a,
                                              idx.shape[1], _ptr(idx), _ptr(w)),
             "psf_matrix_set_spread_topn")
+        self.topn = int(idx.shape[1])
+        return self
+
+    def build_sparse_adjoint(self):
+        """Transpose of the top-N S, so S^T of sparse inputs scatters from their
+        nonzero entries (psf_matrix_build_sparse_adjoint)."""
+        _ok(lib().psf_matrix_build_sparse_adjoint(self._h, _stream()),
+            "psf_matrix_build_sparse_adjoint")
         return self
 
     def autotune(self):

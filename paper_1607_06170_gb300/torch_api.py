@@ -88,7 +88,8 @@ def mlem(matrix, y, iters: int = 10, x0=None, sens=None, graph: bool = False):
     return x
 
 
-def listmode_osem(matrix, rows, n_subsets: int, iters: int = 1, x0=None, sens=None):
+def listmode_osem(matrix, rows, n_subsets: int, iters: int = 1, x0=None, sens=None,
+                  sparse_adjoint: bool = True):
     """List-mode OSEM over events (the next step named in Sec. 5, with the
     subsets of Sec. 3): the events (their set rows, psf_event_rows) are split
     into n_subsets consecutive subsets, and each sub-iteration is
@@ -96,8 +97,12 @@ def listmode_osem(matrix, rows, n_subsets: int, iters: int = 1, x0=None, sens=No
     formed as the MLEM update on the subset's counts weighted by n_subsets
     (psf_histogram, psf_forward_masked -- the projection only on the LORs the
     subset's events hit --, psf_em_ratio, psf_back, psf_em_update).
-    Voxels with sens < 1e-12 * max(sens) are held at zero."""
+    Voxels with sens < 1e-12 * max(sens) are held at zero.  With top-N spreads
+    and sparse_adjoint, the plan's transpose of S is built once so that S^T of
+    a subset's counts and ratios scatters from their nonzero entries."""
     n_ev = rows.numel()
+    if sparse_adjoint and matrix.topn > 0:
+        matrix.build_sparse_adjoint()
     if sens is None:
         sens = matrix.sensitivity(device=rows.device)
     floor = 1e-12 * float(sens.max())

@@ -138,6 +138,29 @@ def test_topn_projector(P, ref, orc, plan, N):
     xb, sb = M.back_sens(torch.from_numpy(r).cuda())
     assert_close(xb.cpu().numpy(), bo, 2e-5, 1e-6 * bo.max(), f"top-{N} back (pair pass)")
     assert_close(sb.cpu().numpy(), so, 2e-5, 1e-6 * so.max(), f"top-{N} sensitivity (pair pass)")
+    # a sparse LOR vector (1 % nonzero, as one list-mode subset's counts): the
+    # adjoint reads only the occupied entries
+    rs = np.where(np.random.default_rng(912).random(len(ref["L"])) < 0.01, r, 0.0)
+    assert 0 < np.count_nonzero(rs) <= len(rs) // 16
+    bs = M.back(torch.from_numpy(rs.astype(np.float32)).cuda()).cpu().numpy()
+    bso = orc.csr_back(ref["G"], orc.spread_adjoint(s, ref["L"], Wl, Wt, Wa, rs), ref["nv"])
+    assert_close(bs, bso, 2e-5, 1e-6 * bso.max(), f"top-{N} back of a sparse vector")
+    # with the transpose of S: sparse inputs scatter from their nonzero entries,
+    # dense ones keep the gather
+    M.build_sparse_adjoint()
+    bs2 = M.back(torch.from_numpy(rs.astype(np.float32)).cuda()).cpu().numpy()
+    assert_close(bs2, bso, 2e-5, 1e-6 * bso.max(), f"top-{N} back of a sparse vector (transpose)")
+    b2 = M.back(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert_close(b2, bo, 2e-5, 1e-6 * bo.max(), f"top-{N} back (transpose built)")
+    xb2, sb2 = M.back_sens(torch.from_numpy(rs.astype(np.float32)).cuda())
+    assert_close(xb2.cpu().numpy(), bso, 2e-5, 1e-6 * bso.max(), f"top-{N} pair pass, sparse")
+    assert_close(sb2.cpu().numpy(), so, 2e-5, 1e-6 * so.max(), f"top-{N} pair pass sensitivity")
+    xt = torch.from_numpy(x).cuda()
+    mask = torch.from_numpy((rs != 0).astype(np.float32)).cuda()
+    ym = M.forward_masked(xt, mask).cpu().numpy()
+    assert_close(ym, np.where(rs != 0, yo, 0.0), 2e-5, 1e-6 * yo.max(),
+                 f"top-{N} masked forward (transpose)")
+    M.check()
     for k in range(3):
         xk = torch.from_numpy(I.random_image(w["image"], 920 + k).reshape(-1)).cuda()
         yk = torch.from_numpy(I.random_lor_values(len(ref["L"]), 930 + k)).cuda()
