@@ -162,13 +162,11 @@ __global__ void __launch_bounds__(PJ_T) csr_back_kernel(int64_t n, const int64_t
 // (the work queue), so long and short rows balance across warps without a
 // launch per batch.  Per row the arithmetic is the grid-stride kernels'.
 template <typename VT>
-__device__ __forceinline__ float csr_row_dot(const int64_t *__restrict__ ptr,
-                                             const int32_t *__restrict__ col,
+__device__ __forceinline__ float csr_seg_dot(const int32_t *__restrict__ col,
                                              const VT *__restrict__ val,
-                                             const float *__restrict__ x, int64_t r, int lane) {
+                                             const float *__restrict__ x, int64_t j0, int nr,
+                                             int lane) {
     constexpr int U = 4;
-    const int64_t j0 = ptr[r];
-    const int nr = (int)(ptr[r + 1] - j0);
     const int32_t *cr = col + j0;
     const VT *vr = val + j0;
     float acc = 0.0f;
@@ -188,6 +186,15 @@ __device__ __forceinline__ float csr_row_dot(const int64_t *__restrict__ ptr,
     return warp_sum_f(acc);
 }
 
+template <typename VT>
+__device__ __forceinline__ float csr_row_dot(const int64_t *__restrict__ ptr,
+                                             const int32_t *__restrict__ col,
+                                             const VT *__restrict__ val,
+                                             const float *__restrict__ x, int64_t r, int lane) {
+    const int64_t j0 = ptr[r];
+    return csr_seg_dot(col, val, x, j0, (int)(ptr[r + 1] - j0), lane);
+}
+
 __device__ __forceinline__ int64_t wq_take(unsigned long long *queue, int chunk, int lane) {
     unsigned long long r0 = 0;
     if (lane == 0) r0 = atomicAdd(queue, (unsigned long long)chunk);
@@ -202,9 +209,24 @@ __global__ void csr_fwd_wq_kernel(int64_t n, const int64_t *__restrict__ ptr,
     const int lane = threadIdx.x & 31;
     for (int64_t r0 = wq_take(queue, chunk, lane); r0 < n; r0 = wq_take(queue, chunk, lane)) {
         const int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
-        for (int64_t r = r0; r < r1; ++r) {
-            const float acc = csr_row_dot(ptr, col, val, x, r, lane);
-            if (lane == 0) y[r] = scale ? acc * scale[r] : acc;
+        // 32 rows at a time: their extents loaded one per lane, each row's sum
+        // kept by its lane and stored together
+        for (int64_t rb = r0; rb < r1; rb += 32) {
+            const int64_t rr = rb + lane;
+            int64_t pa = 0, pb = 0;
+            if (rr < r1) {
+                pa = ptr[rr];
+                pb = ptr[rr + 1];
+            }
+            const int nb = r1 - rb < 32 ? (int)(r1 - rb) : 32;
+            float mine = 0.0f;
+            for (int i = 0; i < nb; ++i) {
+                const int64_t a = __shfl_sync(0xffffffffu, pa, i);
+                const int64_t b = __shfl_sync(0xffffffffu, pb, i);
+                const float acc = csr_seg_dot(col, val, x, a, (int)(b - a), lane);
+                if (lane == i) mine = acc;
+            }
+            if (rr < r1) y[rr] = scale ? mine * scale[rr] : mine;
         }
     }
 }
@@ -217,11 +239,28 @@ __global__ void csr_back_wq_kernel(int64_t n, const int64_t *__restrict__ ptr,
     const int lane = threadIdx.x & 31;
     for (int64_t r0 = wq_take(queue, chunk, lane); r0 < n; r0 = wq_take(queue, chunk, lane)) {
         const int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
-        for (int64_t r = r0; r < r1; ++r) {
-            float yr = y[r];
-            if (scale) yr *= scale[r];
-            if (yr == 0.0f) continue;
-            csr_row_scatter(col, val, ptr[r], ptr[r + 1], yr, x, lane);
+        // 32 rows at a time: values and extents loaded one per lane, rows with
+        // y = 0 skipped by a ballot
+        for (int64_t rb = r0; rb < r1; rb += 32) {
+            const int64_t rr = rb + lane;
+            float yr = 0.0f;
+            int64_t pa = 0, pb = 0;
+            if (rr < r1) {
+                yr = y[rr];
+                if (scale) yr *= scale[rr];
+                if (yr != 0.0f) {
+                    pa = ptr[rr];
+                    pb = ptr[rr + 1];
+                }
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, yr != 0.0f && pb > pa);
+            while (todo) {
+                const int i = __ffs(todo) - 1;
+                todo &= todo - 1;
+                csr_row_scatter(col, val, __shfl_sync(0xffffffffu, pa, i),
+                                __shfl_sync(0xffffffffu, pb, i), __shfl_sync(0xffffffffu, yr, i),
+                                x, lane);
+            }
         }
     }
 }
@@ -341,30 +380,48 @@ __global__ void csr_back_pair_kernel(int64_t n, const int64_t *__restrict__ ptr,
     const int step = queue ? chunk : 1;
     while (r0 < n) {
         const int64_t r1 = r0 + step < n ? r0 + step : n;
-        for (int64_t r = r0; r < r1; ++r) {
-            float a = ya[r], b = yb[r];
-            if (scale) {
-                a *= scale[r];
-                b *= scale[r];
-            }
-            if (a == 0.0f && b == 0.0f) continue;
-            const int64_t j0 = ptr[r];
-            const int nr = (int)(ptr[r + 1] - j0);
-            const int32_t *cr = col + j0;
-            const VT *vr = val + j0;
-            constexpr int U = 4;
-            for (int j = lane; j < nr; j += 32 * U) {
-                int c[U];
-                float v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int jj = j + 32 * u;
-                    c[u] = jj < nr ? __ldcs(cr + jj) : -1;
-                    v[u] = jj < nr ? ld_val_cs(vr, jj) : 0.0f;
+        // 32 rows at a time: values and extents loaded one per lane, rows with
+        // both values 0 skipped by a ballot
+        for (int64_t rb = r0; rb < r1; rb += 32) {
+            const int64_t rr = rb + lane;
+            float wa = 0.0f, wb = 0.0f;
+            int64_t pa = 0, pb = 0;
+            if (rr < r1) {
+                wa = ya[rr];
+                wb = yb[rr];
+                if (scale) {
+                    wa *= scale[rr];
+                    wb *= scale[rr];
                 }
+                if (wa != 0.0f || wb != 0.0f) {
+                    pa = ptr[rr];
+                    pb = ptr[rr + 1];
+                }
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, (wa != 0.0f || wb != 0.0f) && pb > pa);
+            while (todo) {
+                const int i = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const float a = __shfl_sync(0xffffffffu, wa, i);
+                const float b = __shfl_sync(0xffffffffu, wb, i);
+                const int64_t j0 = __shfl_sync(0xffffffffu, pa, i);
+                const int nr = (int)(__shfl_sync(0xffffffffu, pb, i) - j0);
+                const int32_t *cr = col + j0;
+                const VT *vr = val + j0;
+                constexpr int U = 4;
+                for (int j = lane; j < nr; j += 32 * U) {
+                    int c[U];
+                    float v[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (c[u] >= 0) atomicAdd(x2 + c[u], make_float2(v[u] * a, v[u] * b));
+                    for (int u = 0; u < U; ++u) {
+                        const int jj = j + 32 * u;
+                        c[u] = jj < nr ? __ldcs(cr + jj) : -1;
+                        v[u] = jj < nr ? ld_val_cs(vr, jj) : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (c[u] >= 0) atomicAdd(x2 + c[u], make_float2(v[u] * a, v[u] * b));
+                }
             }
         }
         r0 = queue ? wq_take(queue, chunk, lane) : r0 + wpg;
