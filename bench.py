@@ -319,7 +319,7 @@ def run_gpu(args):
           for k in stages}
     y_meas = None
 
-    def step(x_in, y_in, record=None):
+    def step(x_in, y_in, record=None, inputs_ready=None):
         def mark(k, i):
             if record is not None:
                 ev[k][i].record(st)
@@ -337,6 +337,8 @@ def run_gpu(args):
         P.sysmat_rows_set(s, im, ls, buffers=(row_ptr, col, val))
         mark("rows", 1)
         M.set_spread(s, ls, Wt, Wa, WC)
+        if inputs_ready is not None:  # image and data copied on a side stream
+            st.wait_event(inputs_ready)
         # one MLEM iteration from the current image, with the sensitivity image
         # A^T 1 formed in the same pass over the rows as the back-projection
         mark("forward", 0)
@@ -404,10 +406,19 @@ def run_gpu(args):
     torch.cuda.synchronize()
     te = time.perf_counter()
     out_host = torch.empty_like(x_host).pin_memory()
+    copy_st = torch.cuda.Stream(device=dev)
     for _ in range(e2e_steps):
-        xd = x_host.to(dev, non_blocking=True)
-        yd = y_host.to(dev, non_blocking=True)
-        xo = step(xd, yd)
+        # the step's inputs go up on a side stream while the table, spreads and
+        # rows are computed; the projections wait for them
+        copy_st.wait_stream(st)
+        with torch.cuda.stream(copy_st):
+            xd = x_host.to(dev, non_blocking=True)
+            yd = y_host.to(dev, non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(copy_st)
+        xd.record_stream(st)
+        yd.record_stream(st)
+        xo = step(xd, yd, inputs_ready=ready)
         out_host.copy_(xo, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / e2e_steps
