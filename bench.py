@@ -568,7 +568,7 @@ def run_profile_case(args):
             rp, col, val, _ = P.sysmat_rows(s, im, L)
             if case == "csr":
                 M = P.Matrix(rp, col, val, nv)
-                M.set_launch(32, 512)  # the work-queue launch the bench step's autotuner picks
+                M.set_launch(64, 512)  # the work-queue launch the bench step's autotuner picks
                 y = M.forward(torch.rand(nv, device=dev))
                 M.back(y)
                 M.back_sens(y)
