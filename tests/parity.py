@@ -1,6 +1,6 @@
 """Comparison helpers for the GPU-vs-oracle parity tests.
 
-Tolerances (derivations in the design doc):
+Tolerances and where they come from:
   * response table: |d| <= 1e-5 |ref| + TABLE_ATOL.  FP32 box bounds and
     crossing depths carry absolute errors of a few 1e-6 mm, so a path clipped
     through a crystal corner (tens of micrometres long) has a length error
