@@ -313,7 +313,9 @@ int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scanner,
  * fill).  Afterwards S^T of an input with at most 1/16 nonzero entries (one
  * subset's counts or ratios) lists those entries and scatters from them with
  * FP32 atomics (the summation order varies between runs); denser inputs keep
- * the gather.  The decision is taken on the device, so the calls stay
+ * the gather; psf_back then also lists the rows with S^T y != 0 and, when at
+ * most a quarter of the rows are listed, back-projects only those (one warp
+ * per listed row).  The decisions are taken on the device, so the calls stay
  * capturable.  A later psf_matrix_set_spread(_topn) drops the transpose.
  * Synchronises `stream`; PSF_EINVAL for other plans or more than 2^31 - 1
  * rows. */

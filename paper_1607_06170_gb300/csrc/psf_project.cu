@@ -235,8 +235,10 @@ template <typename VT>
 __global__ void csr_back_wq_kernel(int64_t n, const int64_t *__restrict__ ptr,
                                    const int32_t *__restrict__ col, const VT *__restrict__ val,
                                    const float *__restrict__ scale, const float *__restrict__ y,
-                                   float *__restrict__ x, unsigned long long *queue, int chunk) {
+                                   float *__restrict__ x, unsigned long long *queue, int chunk,
+                                   const unsigned long long *listed = nullptr) {
     const int lane = threadIdx.x & 31;
+    if (listed && *listed <= (unsigned long long)(n >> 2)) return;  // the list form has it
     for (int64_t r0 = wq_take(queue, chunk, lane); r0 < n; r0 = wq_take(queue, chunk, lane)) {
         const int64_t r1 = r0 + chunk < n ? r0 + chunk : n;
         // 32 rows at a time: values and extents loaded one per lane, rows with
@@ -325,6 +327,26 @@ static void list_nonzero(const float *mask, int64_t n, int32_t *list, unsigned l
         mask_rows_kernel<<<grid_for(n, 256), 256, 0, st>>>(mask, n, list, count);
     else
         mask_rows4_kernel<<<grid_for((n + 3) / 4, 256), 256, 0, st>>>(mask, n, list, count);
+}
+
+// x += A^T y over a list of rows (the rows with y != 0), one warp per listed
+// row; returns at once when more than a quarter of the rows are listed (the
+// work-queue pass runs instead).
+template <typename VT>
+__global__ void __launch_bounds__(PJ_T) csr_back_list_kernel(
+    const int32_t *__restrict__ list, const unsigned long long *count, int64_t n,
+    const int64_t *__restrict__ ptr, const int32_t *__restrict__ col, const VT *__restrict__ val,
+    const float *__restrict__ scale, const float *__restrict__ y, float *__restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nl = (int64_t)*count;
+    if (nl > (n >> 2)) return;
+    const int64_t wpb = PJ_T / 32;
+    for (int64_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nl; i += gridDim.x * wpb) {
+        const int64_t r = list[i];
+        float yr = y[r];
+        if (scale) yr *= scale[r];
+        csr_row_scatter(col, val, ptr[r], ptr[r + 1], yr, x, lane);
+    }
 }
 
 template <typename VT>
@@ -2390,6 +2412,48 @@ extern "C" int psf_forward_masked(const psf_matrix *m, const float *x, const flo
     return PSF_OK;
 }
 
+namespace psf {
+
+// x = A^T y for plans with the transpose of a top-N S (built for sparse
+// inputs): the rows with y != 0 are listed into the transpose's list buffer;
+// at most n/4 of them go through the list kernel, more through the work queue
+// (each kernel returns at once when the other one applies).
+static int rows_back_listed(const psf_matrix *m, const float *y, float *x, cudaStream_t st) {
+    PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
+    PSF_TRY(cudaMemsetAsync(m->tr_nz, 0, sizeof(unsigned long long), st));
+    list_nonzero(y, m->n_rows, m->tr_list, m->tr_nz, st);
+    PSF_LAUNCHED();
+    const int chunk = m->wq_chunk > 0 ? m->wq_chunk : 64;
+    const int threads = m->wq_chunk > 0 ? m->wq_threads : 256;
+    return dispatch_dtype(m->dtype, [&](auto tag) -> int {
+        using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+        int dev = 0, sms = 148;
+        PSF_TRY(cudaGetDevice(&dev));
+        PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        {
+            PSF_TIMED("csr_back_list_kernel", st);
+            csr_back_list_kernel<VT><<<sms * 8, PJ_T, 0, st>>>(
+                m->tr_list, m->tr_nz, m->n_rows, m->row_ptr, m->col, (const VT *)m->val,
+                m->row_scale, y, x);
+        }
+        PSF_LAUNCHED();
+        int grid = 0;
+        int rc = wq_grid(csr_back_wq_kernel<VT>, threads, &grid);
+        if (rc) return rc;
+        PSF_TRY(cudaMemsetAsync(m->queue + 1, 0, sizeof(unsigned long long), st));
+        {
+            PSF_TIMED("csr_back_wq_kernel", st);
+            csr_back_wq_kernel<VT><<<grid, threads, 0, st>>>(
+                m->n_rows, m->row_ptr, m->col, (const VT *)m->val, m->row_scale, y, x,
+                m->queue + 1, chunk, m->tr_nz);
+        }
+        PSF_LAUNCHED();
+        return PSF_OK;
+    });
+}
+
+}  // namespace psf
+
 extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *stream) {
     if (!m || !x) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
@@ -2401,6 +2465,7 @@ extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *str
     if (!m->factored) return rows_back(m, y, x, st);
     int rc = stencil(m, y, m->q, true, st);
     if (rc) return rc;
+    if (m->tr_ptr) return rows_back_listed(m, m->q, x, st);
     return rows_back(m, m->q, x, st);
 }
 
