@@ -237,12 +237,16 @@ def stencil_pairs(s, ls, Wt, Wa):
 def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
     if name == "set_fill_kernel":  # writes column + chord, reads row_ptr
         return "hbm", 8.0 * nnz + 8.0 * n_lors, "GB/s"
-    if name in ("csr_fwd_kernel", "csr_back_kernel"):
-        # column + value, row_ptr, LOR value, image
+    if name.startswith("csr_fwd"):  # column + value, row_ptr, LOR value, image
         return "hbm", 8.0 * nnz + 12.0 * n_lors + 4.0 * nv, "GB/s"
+    if name.startswith("csr_back_pair"):  # column + value, row_ptr, two LOR values, image pair
+        return "hbm", 8.0 * nnz + 16.0 * n_lors + 8.0 * nv, "GB/s"
     if name == "spread_q_kernel":  # one FMA per sub-LOR and quadrant entry pair
+        # of the classes of ring difference >= 0 (the others are axial mirrors)
+        Dm = ls["max_ring_diff"]
+        n_comp = n_cls * (Dm + 1) // (2 * Dm + 1)
         nsub = (t["n_sub_t"] * t["n_sub_a"]) ** 2
-        return "alu", 2.0 * n_cls * nsub * ((Wt + 1) * (Wa + 1)) ** 2, "TFLOP/s"
+        return "alu", 2.0 * n_comp * nsub * ((Wt + 1) * (Wa + 1)) ** 2, "TFLOP/s"
     if name.startswith("stencil"):  # one FMA per (output LOR, source LOR) pair
         return "alu", 2.0 * stencil_pairs(s, ls, Wt, Wa), "TFLOP/s"
     return None, None, None
@@ -331,7 +335,7 @@ def run_gpu(args):
         C = P.lor_set_classes(s, ls, device=dev)
         mark("classes", 1)
         mark("spread", 0)
-        WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)
+        WC = P.bin_spread_classes(s, t, T, eta, ls, C, Wt, Wa)
         mark("spread", 1)
         mark("rows", 0)
         P.sysmat_rows_set(s, im, ls, buffers=(row_ptr, col, val))
@@ -360,7 +364,7 @@ def run_gpu(args):
     # projection of the phantom (computed once)
     M = P.Matrix(row_ptr, col, val, nv)
     T0, e0 = P.response_build(s, t, device=dev)
-    WC0 = P.bin_spread(s, t, T0, e0, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+    WC0 = P.bin_spread_classes(s, t, T0, e0, ls, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
     P.sysmat_rows_set(s, im, ls, buffers=(row_ptr, col, val))
     M.set_spread(s, ls, Wt, Wa, WC0)
     M.autotune()  # launch choices of the projector kernels (CUDA-event timed, once)
@@ -549,7 +553,8 @@ def run_profile_case(args):
     for _ in range(2):
         if case in ("spread", "stencil"):
             T, eta = P.response_build(s, t, device=dev)
-            WC = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+            WC = P.bin_spread_classes(s, t, T, eta, ls, P.lor_set_classes(s, ls, device=dev),
+                                      Wt, Wa)
         if case == "stencil":
             n, _ = P.lor_set_size(s, ls)
             rp = torch.zeros(n + 1, dtype=torch.int64, device=dev)
@@ -666,7 +671,7 @@ def run_eplus(args):
 
     def generate():
         T, eta = P.response_build(s, t, device=dev)
-        WC = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+        WC = P.bin_spread_classes(s, t, T, eta, ls, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
         return WC, P.sysmat_rows_set(s, im, ls, device=dev)
 
     generate()  # warm-up (allocations, first launches)
@@ -730,7 +735,7 @@ def run_listmode(args):
     rows = P.event_rows(s, ls, events)
     del events
     T, eta = P.response_build(s, t, device=dev)
-    WCf = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+    WCf = P.bin_spread_classes(s, t, T, eta, ls, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
     idx, wk = P.spread_topn(WCf, Wt, Wa, lm["n_keep"])
     st = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -815,7 +820,7 @@ def run_topn_table(args):
     nv = im["nx"] * im["ny"] * im["nz"]
     x = torch.from_numpy(I.phantom_cylinder(im, 1).reshape(-1)).to(dev)
     T, eta = P.response_build(s, t, device=dev)
-    WC = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
+    WC = P.bin_spread_classes(s, t, T, eta, ls, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
     rp, col, val = P.sysmat_rows_set(s, im, ls, device=dev)
     M = P.Matrix(rp, col, val, nv).set_spread(s, ls, Wt, Wa, WC)
     _, (bc, bt) = M.autotune()

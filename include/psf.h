@@ -214,6 +214,24 @@ int psf_lor_set_classes(const psf_scanner *scanner, const psf_lor_set *set, int3
                         void *stream);
 
 /*
+ * Spreads of all classes of a structured set (Sec. 2.2 Eq. 10, Sec. 2.3
+ * Eq. 11-12), class_lors being the output of psf_lor_set_classes, spread as
+ * in psf_bin_spread ([n_classes][E][E]).  Classes of ring difference d >= 0
+ * go through the spread kernel; a class of d < 0 is the reflection of the
+ * class -d of its transaxial pair through the scanner's axial centre plane
+ * (ring r -> NR-1-r for both crystals; the ring lattice has one pitch), so
+ * its spread is that one with every axial offset negated:
+ *   W_{-d}[(dt1, da1)][(dt2, da2)] = W_d[(dt1, -da1)][(dt2, -da2)].
+ * Equal to psf_bin_spread on the class list up to FP32 rounding (the
+ * decisions of a sub-LOR and of its mirror image can round apart only on a
+ * node or cell boundary).
+ */
+int psf_bin_spread_classes(const psf_scanner *scanner, const psf_table_desc *desc,
+                           const float *table, const double *eta, const psf_lor_set *set,
+                           const int32_t *class_lors, int32_t half_t, int32_t half_a,
+                           int32_t norm, float *spread, void *stream);
+
+/*
  * System-matrix rows in CSR (row_ptr int64 [n_lors+1], col int32 sorted
  * ascending, duplicates merged).
  *  spread == NULL: geometric rows G -- chord lengths (mm) of the segment

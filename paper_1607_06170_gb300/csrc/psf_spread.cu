@@ -11,6 +11,7 @@
 // normalisation totals are FP64 block reductions.
 #include "psf_common.cuh"
 #include "psf_end.cuh"
+#include "psf_lorset.cuh"
 
 namespace psf {
 
@@ -31,7 +32,7 @@ struct SpreadSmem {
 __global__ void __launch_bounds__(SP_THREADS) spread_kernel(
     Scan sc, Tab tb, const float *__restrict__ T, const double *__restrict__ eta,
     const int32_t *__restrict__ lors, int64_t n_lors, int Wt, int Wa, int norm,
-    float *__restrict__ out) {
+    float *__restrict__ out, int skip_neg) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int Q = (Wt + 1) * (Wa + 1);
     const int E = (2 * Wt + 1) * (2 * Wa + 1);
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(SP_THREADS) spread_kernel(
         const int id1 = lors[2 * lor], id2 = lors[2 * lor + 1];
         const int ring1 = id1 / sc.Nt, c1 = id1 - ring1 * sc.Nt;
         const int ring2 = id2 / sc.Nt, c2 = id2 - ring2 * sc.Nt;
+        if (skip_neg && ring2 < ring1) continue;  // filled by the axial mirror
         const int b1 = c1 / sc.Nb, i1 = c1 - b1 * sc.Nb;
         const int b2 = c2 / sc.Nb, i2 = c2 - b2 * sc.Nb;
         float *o = out + lor * (int64_t)E * E;
@@ -332,7 +334,8 @@ static size_t spread_q_smem(const Tab &tb) {
 template <int WT, int WA>
 __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
     Scan sc, Tab tb, const float *__restrict__ T, const double *__restrict__ eta,
-    const int32_t *__restrict__ lors, int64_t n_lors, int norm, float *__restrict__ out) {
+    const int32_t *__restrict__ lors, int64_t n_lors, int norm, float *__restrict__ out,
+    int skip_neg) {
     using S = SqShape<WT, WA>;
     constexpr int Q = S::Q, E = S::E, RB = S::RB, CB = S::CB, QS = S::QS;
     constexpr int W2a = 2 * WA + 1;
@@ -357,6 +360,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
         const int id1 = lors[2 * lor], id2 = lors[2 * lor + 1];
         const int ring1 = id1 / sc.Nt, c1 = id1 - ring1 * sc.Nt;
         const int ring2 = id2 / sc.Nt, c2 = id2 - ring2 * sc.Nt;
+        if (skip_neg && ring2 < ring1) continue;  // filled by the axial mirror
         const int b1 = c1 / sc.Nb, i1 = c1 - b1 * sc.Nb;
         const int b2 = c2 / sc.Nb, i2 = c2 - b2 * sc.Nb;
         float *o = out + lor * (int64_t)E * E;
@@ -550,7 +554,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
 template <int WT, int WA>
 static int launch_spread_q(const Scan &sc, const Tab &tb, const float *T, const double *eta,
                            const int32_t *lors, int64_t n_lors, int norm, float *out,
-                           cudaStream_t st) {
+                           int skip_neg, cudaStream_t st) {
     const size_t shm = spread_q_smem<WT, WA>(tb);
     if (shm > 200 * 1024) return PSF_EINVAL;
     PSF_TRY(cudaFuncSetAttribute(spread_q_kernel<WT, WA>,
@@ -566,7 +570,7 @@ static int launch_spread_q(const Scan &sc, const Tab &tb, const float *T, const 
     {
         PSF_TIMED("spread_q_kernel", st);
         spread_q_kernel<WT, WA><<<(int)grid, SP_THREADS, shm, st>>>(sc, tb, T, eta, lors, n_lors,
-                                                                    norm, out);
+                                                                    norm, out, skip_neg);
     }
     PSF_LAUNCHED();
     return PSF_OK;
@@ -576,10 +580,40 @@ static int launch_spread_q(const Scan &sc, const Tab &tb, const float *T, const 
 
 using namespace psf;
 
-extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *desc,
-                              const float *table, const double *eta, const int32_t *lors,
-                              int64_t n_lors, int32_t half_t, int32_t half_a, int32_t norm,
-                              float *spread, void *stream) {
+
+namespace psf {
+
+// Axial mirror of the spread classes of a structured set: the class of ring
+// difference d < 0 is the reflection through the scanner's axial centre
+// plane of the class -d of the same transaxial pair (ring r -> NR-1-r for both
+// crystals; the ring lattice has one pitch), i.e. its spread with every axial
+// offset negated: W_{-d}[(dt1, da1)][(dt2, da2)] = W_d[(dt1, -da1)][(dt2, -da2)].
+// A CTA per mirrored class (d = -Dm..-1 of each transaxial pair class), the
+// flip permutation of the window in shared memory, coalesced writes.
+__global__ void spread_mirror_kernel(int64_t ntp_cls, int Dm, int Wt, int Wa,
+                                     float *__restrict__ out) {
+    extern __shared__ int mperm[];  // [E * E]
+    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, EE = E * E, D = 2 * Dm + 1;
+    for (int e = threadIdx.x; e < EE; e += blockDim.x) {
+        const int e1 = e / E, e2 = e - e1 * E;
+        mperm[e] = ((e1 / W2a) * W2a + (2 * Wa - e1 % W2a)) * E +
+                   (e2 / W2a) * W2a + (2 * Wa - e2 % W2a);
+    }
+    __syncthreads();
+    for (int64_t k = blockIdx.x; k < ntp_cls * Dm; k += gridDim.x) {
+        const int64_t tp = k / Dm;
+        const int d = (int)(k - tp * Dm) - Dm;  // -Dm .. -1
+        const int64_t c = tp * D + (d + Dm), src = c - 2 * d;
+        float *o = out + c * EE;
+        const float *sp = out + src * EE;
+        for (int e = threadIdx.x; e < EE; e += blockDim.x) o[e] = sp[mperm[e]];
+    }
+}
+
+static int bin_spread(const psf_scanner *scanner, const psf_table_desc *desc, const float *table,
+                      const double *eta, const int32_t *lors, int64_t n_lors, int32_t half_t,
+                      int32_t half_a, int32_t norm, float *spread, int skip_neg,
+                      cudaStream_t st) {
     Scan sc;
     Tab tb;
     int rc = make_scan(scanner, &sc);
@@ -592,13 +626,12 @@ extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *
     if (n_lors == 0) return PSF_OK;
     if (!table || !eta || !lors || !spread) return PSF_EINVAL;
     if (tb.Pt * tb.Pa > 1024) return PSF_EINVAL;
-    cudaStream_t st = as_stream(stream);
     if (half_t == 3 && half_a == 3)
-        return launch_spread_q<3, 3>(sc, tb, table, eta, lors, n_lors, norm, spread, st);
+        return launch_spread_q<3, 3>(sc, tb, table, eta, lors, n_lors, norm, spread, skip_neg, st);
     if (half_t == 3 && half_a == 2)
-        return launch_spread_q<3, 2>(sc, tb, table, eta, lors, n_lors, norm, spread, st);
+        return launch_spread_q<3, 2>(sc, tb, table, eta, lors, n_lors, norm, spread, skip_neg, st);
     if (half_t == 3 && half_a == 0)
-        return launch_spread_q<3, 0>(sc, tb, table, eta, lors, n_lors, norm, spread, st);
+        return launch_spread_q<3, 0>(sc, tb, table, eta, lors, n_lors, norm, spread, skip_neg, st);
     size_t shm = spread_smem(tb, half_t, half_a);
     if (shm > 200 * 1024) return PSF_EINVAL;
     PSF_TRY(cudaFuncSetAttribute(spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -608,9 +641,53 @@ extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int64_t grid = n_lors < (int64_t)sms * 8 ? n_lors : (int64_t)sms * 8;
     {
-        PSF_TIMED("spread_kernel", as_stream(stream));
-        spread_kernel<<<(int)grid, SP_THREADS, shm, as_stream(stream)>>>(
-            sc, tb, table, eta, lors, n_lors, half_t, half_a, norm, spread);
+        PSF_TIMED("spread_kernel", st);
+        spread_kernel<<<(int)grid, SP_THREADS, shm, st>>>(sc, tb, table, eta, lors, n_lors, half_t,
+                                                          half_a, norm, spread, skip_neg);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
+}  // namespace psf
+
+extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *desc,
+                              const float *table, const double *eta, const int32_t *lors,
+                              int64_t n_lors, int32_t half_t, int32_t half_a, int32_t norm,
+                              float *spread, void *stream) {
+    return bin_spread(scanner, desc, table, eta, lors, n_lors, half_t, half_a, norm, spread, 0,
+                      as_stream(stream));
+}
+
+extern "C" int psf_bin_spread_classes(const psf_scanner *scanner, const psf_table_desc *desc,
+                                      const float *table, const double *eta,
+                                      const psf_lor_set *set, const int32_t *class_lors,
+                                      int32_t half_t, int32_t half_a, int32_t norm,
+                                      float *spread, void *stream) {
+    LorSet ls;
+    int rc = make_lorset(scanner, set, &ls);
+    if (rc) return rc;
+    const int64_t n_cls = ls.ntp_cls * (2 * (int64_t)ls.Dm + 1);
+    cudaStream_t st = as_stream(stream);
+    // the classes of ring difference >= 0 through the spread kernel ...
+    rc = bin_spread(scanner, desc, table, eta, class_lors, n_cls, half_t, half_a, norm, spread, 1,
+                    st);
+    if (rc || n_cls == 0) return rc;
+    // ... and the others as their axial mirrors
+    const int64_t E = (2 * (int64_t)half_t + 1) * (2 * half_a + 1);
+    const int64_t n_mir = ls.ntp_cls * ls.Dm;
+    if (n_mir == 0) return PSF_OK;
+    const size_t shm = sizeof(int) * E * E;
+    if (shm > 200 * 1024) return PSF_EINVAL;
+    PSF_TRY(cudaFuncSetAttribute(spread_mirror_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    {
+        PSF_TIMED("spread_mirror_kernel", st);
+        spread_mirror_kernel<<<(int)(n_mir < (int64_t)sms * 8 ? n_mir : (int64_t)sms * 8), 256,
+                               shm, st>>>(ls.ntp_cls, ls.Dm, half_t, half_a, spread);
     }
     PSF_LAUNCHED();
     return PSF_OK;

@@ -30,7 +30,7 @@ FUNCTIONS = [
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
     "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
-    "psf_matrix_check", "psf_matrix_build_sparse_adjoint",
+    "psf_matrix_check", "psf_matrix_build_sparse_adjoint", "psf_bin_spread_classes",
 ]
 
 
@@ -71,6 +71,7 @@ _SIGS = {
     "psf_table_size": (C.c_int, [_P, _P, _P]),
     "psf_response_build": (C.c_int, [_P, _P, _P, _P, _P]),
     "psf_bin_spread": (C.c_int, [_P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _P, _P]),
+    "psf_bin_spread_classes": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P]),
     "psf_lor_set_size": (C.c_int, [_P, _P, _P, _P]),
     "psf_lor_set_list": (C.c_int, [_P, _P, _P, _P]),
     "psf_lor_set_classes": (C.c_int, [_P, _P, _P, _P]),
@@ -206,6 +207,22 @@ def bin_spread(sc: dict, tb: dict, T, eta, lors, half_t: int, half_a: int,
         out = torch.empty((n, E, E), dtype=torch.float32, device=lors.device)
     _ok(lib().psf_bin_spread(C.byref(s), C.byref(t), _ptr(T), _ptr(eta), _ptr(lors), n,
                              half_t, half_a, norm, _ptr(out), _stream()), "psf_bin_spread")
+    return out
+
+
+def bin_spread_classes(sc: dict, tb: dict, T, eta, ls: dict, class_lors, half_t: int,
+                       half_a: int, norm: int = NORM_EFF, out=None):
+    """Spreads [n_classes, E, E] of every class of a structured set (class_lors
+    from lor_set_classes): ring differences d >= 0 computed, d < 0 as their
+    axial mirrors (psf_bin_spread_classes)."""
+    s, t, l = scanner(sc), table_desc(tb), lor_set(ls)
+    n = class_lors.shape[0]
+    E = (2 * half_t + 1) * (2 * half_a + 1)
+    if out is None:
+        out = torch.empty((n, E, E), dtype=torch.float32, device=class_lors.device)
+    _ok(lib().psf_bin_spread_classes(C.byref(s), C.byref(t), _ptr(T), _ptr(eta), C.byref(l),
+                                     _ptr(class_lors), half_t, half_a, norm, _ptr(out),
+                                     _stream()), "psf_bin_spread_classes")
     return out
 
 

@@ -277,3 +277,29 @@ def test_spread_axial_translation(orc):
     moved = [[a + 2 * Nt, b + 2 * Nt] for a, b in base]
     np.testing.assert_allclose(orc.spread(s, t, T, moved, 3, 2), orc.spread(s, t, T, base, 3, 2),
                                rtol=1e-11, atol=1e-15)
+
+
+def test_spread_axial_mirror(orc):
+    """Reflection through the scanner's axial centre plane: ring r -> NR-1-r
+    for both crystals (the ring lattice has one pitch, so it maps onto
+    itself); every axial offset changes sign and the ring difference with
+    it, the transaxial offsets are unchanged."""
+    w = I.workload("RING3D_SMALL")
+    s, t = w["scanner"], w["table"]
+    Wt, Wa = w["window"]
+    Nt = I.n_transaxial(s)
+    NR = s["n_block_rings"] * s["na_block"]
+    T, _ = orc.table_build(s, t)
+    lors = I.workload_lors(w)
+    pick = lors[np.random.default_rng(5).choice(len(lors), 16, replace=False)]
+    assert any(a // Nt != b // Nt for a, b in pick)  # oblique LORs among them
+    mirrored = [((NR - 1 - a // Nt) * Nt + a % Nt, (NR - 1 - b // Nt) * Nt + b % Nt)
+                for a, b in pick]
+    W0 = orc.spread(s, t, T, pick, Wt, Wa)
+    W1 = orc.spread(s, t, T, mirrored, Wt, Wa)
+    assert (W0.sum(axis=(1, 2)) > 0).sum() >= 12
+    W2a = 2 * Wa + 1
+    E = (2 * Wt + 1) * W2a
+    flip = np.array([(e // W2a) * W2a + (2 * Wa - e % W2a) for e in range(E)])
+    for k in range(len(pick)):
+        np.testing.assert_allclose(W1[k], W0[k][np.ix_(flip, flip)], rtol=1e-11, atol=1e-15)
