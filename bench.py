@@ -234,6 +234,37 @@ def stencil_pairs(s, ls, Wt, Wa):
 
 # kernel -> (bound, algorithmic work per launch, unit): bytes a launch must move
 # through HBM, or FP32 FLOPs it must execute
+def n_comp_classes(s, ls):
+    """Classes that are the smallest index of their orbit under the axial and
+    transaxial reflections (the ones psf_bin_spread_classes computes)."""
+    Nb = s["nt_block"]
+    Nt = s["n_blocks"] * Nb
+    F, Dm = ls["fan_half"], ls["max_ring_diff"]
+    D = 2 * Dm + 1
+    lo = [max(a + Nt // 2 - F, a + 1) for a in range(Nb)]
+    start = [0]
+    for a in range(Nb):
+        start.append(start[-1] + max(min(a + Nt // 2 + F, Nt - 1) - lo[a] + 1, 0))
+
+    def t_image(tp):
+        a0 = max(a for a in range(Nb) if start[a] <= tp)
+        b0 = lo[a0] + tp - start[a0]
+        ma, mb = (Nb - 1 - a0) % Nt, (Nb - 1 - b0) % Nt
+        sw = ma > mb
+        a1, b1 = (mb, ma) if sw else (ma, mb)
+        a10 = a1 % Nb
+        return start[a10] + (b1 - (a1 - a10)) - lo[a10], sw
+
+    n = 0
+    for tp in range(start[Nb]):
+        tpt, sw = t_image(tp)
+        for d in range(-Dm, Dm + 1):
+            dt = -d if sw else d
+            c = tp * D + d + Dm
+            n += c == min(c, tp * D - d + Dm, tpt * D + dt + Dm, tpt * D - dt + Dm)
+    return n
+
+
 def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
     if name == "set_fill_kernel":  # writes column + chord, reads row_ptr
         return "hbm", 8.0 * nnz + 8.0 * n_lors, "GB/s"
@@ -242,11 +273,9 @@ def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
     if name.startswith("csr_back_pair"):  # column + value, row_ptr, two LOR values, image pair
         return "hbm", 8.0 * nnz + 16.0 * n_lors + 8.0 * nv, "GB/s"
     if name == "spread_q_kernel":  # one FMA per sub-LOR and quadrant entry pair
-        # of the classes of ring difference >= 0 (the others are axial mirrors)
-        Dm = ls["max_ring_diff"]
-        n_comp = n_cls * (Dm + 1) // (2 * Dm + 1)
+        # of the classes the kernel computes (one per orbit of the two reflections)
         nsub = (t["n_sub_t"] * t["n_sub_a"]) ** 2
-        return "alu", 2.0 * n_comp * nsub * ((Wt + 1) * (Wa + 1)) ** 2, "TFLOP/s"
+        return "alu", 2.0 * n_comp_classes(s, ls) * nsub * ((Wt + 1) * (Wa + 1)) ** 2, "TFLOP/s"
     if name.startswith("stencil"):  # one FMA per (output LOR, source LOR) pair
         return "alu", 2.0 * stencil_pairs(s, ls, Wt, Wa), "TFLOP/s"
     return None, None, None

@@ -216,15 +216,18 @@ int psf_lor_set_classes(const psf_scanner *scanner, const psf_lor_set *set, int3
 /*
  * Spreads of all classes of a structured set (Sec. 2.2 Eq. 10, Sec. 2.3
  * Eq. 11-12), class_lors being the output of psf_lor_set_classes, spread as
- * in psf_bin_spread ([n_classes][E][E]).  Classes of ring difference d >= 0
- * go through the spread kernel; a class of d < 0 is the reflection of the
- * class -d of its transaxial pair through the scanner's axial centre plane
- * (ring r -> NR-1-r for both crystals; the ring lattice has one pitch), so
- * its spread is that one with every axial offset negated:
- *   W_{-d}[(dt1, da1)][(dt2, da2)] = W_d[(dt1, -da1)][(dt2, -da2)].
- * Equal to psf_bin_spread on the class list up to FP32 rounding (the
- * decisions of a sub-LOR and of its mirror image can round apart only on a
- * node or cell boundary).
+ * in psf_bin_spread ([n_classes][E][E]).  Two reflections map the set's
+ * classes onto each other: A, through the scanner's axial centre plane (ring
+ * r -> NR-1-r for both crystals; the ring lattice has one pitch): ring
+ * difference d -> -d and every axial offset negated; T, through block 0's
+ * centre plane (crystal x -> (Nb-1-x) mod Nt): every transaxial offset
+ * negated, and when the reflected first crystal comes after the second the
+ * ends swap (the spread is transposed, d -> -d).  The smallest class index of
+ * each orbit {c, Ac, Tc, ATc} goes through the spread kernel, the others are
+ * its images.  Equal to psf_bin_spread on the class list up to FP32 rounding
+ * (the decisions of a sub-LOR and of its image can round apart only on a
+ * node or cell boundary).  Allocates 4 bytes per class of stream-ordered
+ * scratch; PSF_EINVAL beyond 2^28 classes or 256 window entries per end.
  */
 int psf_bin_spread_classes(const psf_scanner *scanner, const psf_table_desc *desc,
                            const float *table, const double *eta, const psf_lor_set *set,

@@ -32,7 +32,7 @@ struct SpreadSmem {
 __global__ void __launch_bounds__(SP_THREADS) spread_kernel(
     Scan sc, Tab tb, const float *__restrict__ T, const double *__restrict__ eta,
     const int32_t *__restrict__ lors, int64_t n_lors, int Wt, int Wa, int norm,
-    float *__restrict__ out, int skip_neg) {
+    float *__restrict__ out, const int32_t *__restrict__ sym) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int Q = (Wt + 1) * (Wa + 1);
     const int E = (2 * Wt + 1) * (2 * Wa + 1);
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(SP_THREADS) spread_kernel(
         const int id1 = lors[2 * lor], id2 = lors[2 * lor + 1];
         const int ring1 = id1 / sc.Nt, c1 = id1 - ring1 * sc.Nt;
         const int ring2 = id2 / sc.Nt, c2 = id2 - ring2 * sc.Nt;
-        if (skip_neg && ring2 < ring1) continue;  // filled by the axial mirror
+        if (sym && sym[lor] >= 0) continue;  // an image of another class under the mirrors
         const int b1 = c1 / sc.Nb, i1 = c1 - b1 * sc.Nb;
         const int b2 = c2 / sc.Nb, i2 = c2 - b2 * sc.Nb;
         float *o = out + lor * (int64_t)E * E;
@@ -335,7 +335,7 @@ template <int WT, int WA>
 __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
     Scan sc, Tab tb, const float *__restrict__ T, const double *__restrict__ eta,
     const int32_t *__restrict__ lors, int64_t n_lors, int norm, float *__restrict__ out,
-    int skip_neg) {
+    const int32_t *__restrict__ sym) {
     using S = SqShape<WT, WA>;
     constexpr int Q = S::Q, E = S::E, RB = S::RB, CB = S::CB, QS = S::QS;
     constexpr int W2a = 2 * WA + 1;
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
         const int id1 = lors[2 * lor], id2 = lors[2 * lor + 1];
         const int ring1 = id1 / sc.Nt, c1 = id1 - ring1 * sc.Nt;
         const int ring2 = id2 / sc.Nt, c2 = id2 - ring2 * sc.Nt;
-        if (skip_neg && ring2 < ring1) continue;  // filled by the axial mirror
+        if (sym && sym[lor] >= 0) continue;  // an image of another class under the mirrors
         const int b1 = c1 / sc.Nb, i1 = c1 - b1 * sc.Nb;
         const int b2 = c2 / sc.Nb, i2 = c2 - b2 * sc.Nb;
         float *o = out + lor * (int64_t)E * E;
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(SP_THREADS, 3) spread_q_kernel(
 template <int WT, int WA>
 static int launch_spread_q(const Scan &sc, const Tab &tb, const float *T, const double *eta,
                            const int32_t *lors, int64_t n_lors, int norm, float *out,
-                           int skip_neg, cudaStream_t st) {
+                           const int32_t *sym, cudaStream_t st) {
     const size_t shm = spread_q_smem<WT, WA>(tb);
     if (shm > 200 * 1024) return PSF_EINVAL;
     PSF_TRY(cudaFuncSetAttribute(spread_q_kernel<WT, WA>,
@@ -570,7 +570,7 @@ static int launch_spread_q(const Scan &sc, const Tab &tb, const float *T, const 
     {
         PSF_TIMED("spread_q_kernel", st);
         spread_q_kernel<WT, WA><<<(int)grid, SP_THREADS, shm, st>>>(sc, tb, T, eta, lors, n_lors,
-                                                                    norm, out, skip_neg);
+                                                                    norm, out, sym);
     }
     PSF_LAUNCHED();
     return PSF_OK;
@@ -583,36 +583,104 @@ using namespace psf;
 
 namespace psf {
 
-// Axial mirror of the spread classes of a structured set: the class of ring
-// difference d < 0 is the reflection through the scanner's axial centre
-// plane of the class -d of the same transaxial pair (ring r -> NR-1-r for both
-// crystals; the ring lattice has one pitch), i.e. its spread with every axial
-// offset negated: W_{-d}[(dt1, da1)][(dt2, da2)] = W_d[(dt1, -da1)][(dt2, -da2)].
-// A CTA per mirrored class (d = -Dm..-1 of each transaxial pair class), the
-// flip permutation of the window in shared memory, coalesced writes.
-__global__ void spread_mirror_kernel(int64_t ntp_cls, int Dm, int Wt, int Wa,
-                                     float *__restrict__ out) {
-    extern __shared__ int mperm[];  // [E * E]
-    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, EE = E * E, D = 2 * Dm + 1;
-    for (int e = threadIdx.x; e < EE; e += blockDim.x) {
-        const int e1 = e / E, e2 = e - e1 * E;
-        mperm[e] = ((e1 / W2a) * W2a + (2 * Wa - e1 % W2a)) * E +
-                   (e2 / W2a) * W2a + (2 * Wa - e2 % W2a);
+// Symmetries of the spread classes of a structured set.  A: reflection
+// through the axial centre plane (ring r -> NR-1-r for both crystals; the ring
+// lattice has one pitch): ring difference d -> -d, every axial window offset
+// negated.  T: reflection through block 0's centre plane (crystal x ->
+// (Nb-1-x) mod Nt): every transaxial offset negated; when the reflected first
+// crystal comes after the second the ends swap (the spread is transposed and
+// d -> -d).  A and T are commuting involutions, so a class's orbit is
+// {c, A c, T c, AT c}; the spread kernel computes the smallest class index of
+// each orbit and the others are its images.  sym[c] = -1 for a computed class,
+// else the computed class | SYM_A << 28 | SYM_T << 29 | SYM_SWAP << 30.
+constexpr int SYM_A = 1, SYM_T = 2, SYM_SWAP = 4;
+
+// T image of transaxial class tp: its class and whether the ends swap.
+__device__ __forceinline__ void t_image(const LorSet &ls, const int32_t *tp_start, int64_t tp,
+                                        int64_t *tp_t, bool *swap) {
+    int a0, b0;
+    ls.tp_decode(tp_start, tp, &a0, &b0);
+    const int ma = (ls.Nb - 1 - a0 + ls.Nt) % ls.Nt, mb = (ls.Nb - 1 - b0 + ls.Nt) % ls.Nt;
+    *swap = ma > mb;
+    const int a1 = *swap ? mb : ma, b1 = *swap ? ma : mb;
+    const int a10 = a1 % ls.Nb, b10 = b1 - (a1 - a10);
+    *tp_t = tp_start[a10] + (b10 - ls.tp_lo(a10));
+}
+
+__global__ void spread_sym_kernel(LorSet ls, int32_t *__restrict__ sym) {
+    extern __shared__ int32_t sy_pre[];  // tp_start [Nt + 1], rp_start [NR + 1]
+    ls.stage_prefix(sy_pre, sy_pre + ls.Nt + 1);
+    __syncthreads();
+    const int D = 2 * ls.Dm + 1;
+    const int64_t n_cls = ls.ntp_cls * D;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cls;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tp = c / D;
+        const int d = (int)(c - tp * D) - ls.Dm;
+        int64_t tpt;
+        bool sw;
+        t_image(ls, sy_pre, tp, &tpt, &sw);
+        const int dt = sw ? -d : d;
+        const int64_t cA = tp * D + (-d + ls.Dm), cT = tpt * D + (dt + ls.Dm),
+                      cAT = tpt * D + (-dt + ls.Dm);
+        int64_t can = c < cA ? c : cA;
+        can = can < cT ? can : cT;
+        can = can < cAT ? can : cAT;
+        if (can == c) {
+            sym[c] = -1;
+            continue;
+        }
+        // the map from the computed class to this one
+        const int64_t ctp = can / D;
+        const int cd = (int)(can - ctp * D) - ls.Dm;
+        int64_t ctpt;
+        bool csw;
+        t_image(ls, sy_pre, ctp, &ctpt, &csw);
+        const int cdt = csw ? -cd : cd;
+        int flags;
+        if (ctp * D + (-cd + ls.Dm) == c)
+            flags = SYM_A;
+        else if (ctpt * D + (cdt + ls.Dm) == c)
+            flags = SYM_T | (csw ? SYM_SWAP : 0);
+        else
+            flags = SYM_A | SYM_T | (csw ? SYM_SWAP : 0);
+        sym[c] = (int32_t)can | (flags << 28);
+    }
+}
+
+// The classes that are images: W_c[e1][e2] = W_s[h(e1')][h(e2')] with
+// (e1', e2') = (e2, e1) when the ends swap, h negating the axial offset
+// (A) and/or the transaxial offset (T) of a window index.
+__global__ void spread_mirror_kernel(int64_t n_cls, int Wt, int Wa,
+                                     const int32_t *__restrict__ sym, float *__restrict__ out) {
+    __shared__ int16_t hperm[4][256];  // window index maps per (A, T) flag pair
+    const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, EE = E * E;
+    for (int i = threadIdx.x; i < 4 * E; i += blockDim.x) {
+        const int f = i / E, e = i - f * E;
+        const int x = e / W2a, z = e - x * W2a;
+        hperm[f][e] = (int16_t)(((f & SYM_T) ? 2 * Wt - x : x) * W2a + ((f & SYM_A) ? 2 * Wa - z : z));
     }
     __syncthreads();
-    for (int64_t k = blockIdx.x; k < ntp_cls * Dm; k += gridDim.x) {
-        const int64_t tp = k / Dm;
-        const int d = (int)(k - tp * Dm) - Dm;  // -Dm .. -1
-        const int64_t c = tp * D + (d + Dm), src = c - 2 * d;
+    for (int64_t c = blockIdx.x; c < n_cls; c += gridDim.x) {
+        const int32_t sv = sym[c];
+        if (sv < 0) continue;
+        const int64_t src = sv & 0x0fffffff;
+        const int flags = sv >> 28;
+        const int16_t *h = hperm[flags & 3];
+        const bool swap = flags & SYM_SWAP;
         float *o = out + c * EE;
         const float *sp = out + src * EE;
-        for (int e = threadIdx.x; e < EE; e += blockDim.x) o[e] = sp[mperm[e]];
+        for (int e = threadIdx.x; e < EE; e += blockDim.x) {
+            const int e1 = e / E, e2 = e - e1 * E;
+            const int s1 = swap ? e2 : e1, s2 = swap ? e1 : e2;
+            o[e] = sp[h[s1] * E + h[s2]];
+        }
     }
 }
 
 static int bin_spread(const psf_scanner *scanner, const psf_table_desc *desc, const float *table,
                       const double *eta, const int32_t *lors, int64_t n_lors, int32_t half_t,
-                      int32_t half_a, int32_t norm, float *spread, int skip_neg,
+                      int32_t half_a, int32_t norm, float *spread, const int32_t *sym,
                       cudaStream_t st) {
     Scan sc;
     Tab tb;
@@ -627,11 +695,11 @@ static int bin_spread(const psf_scanner *scanner, const psf_table_desc *desc, co
     if (!table || !eta || !lors || !spread) return PSF_EINVAL;
     if (tb.Pt * tb.Pa > 1024) return PSF_EINVAL;
     if (half_t == 3 && half_a == 3)
-        return launch_spread_q<3, 3>(sc, tb, table, eta, lors, n_lors, norm, spread, skip_neg, st);
+        return launch_spread_q<3, 3>(sc, tb, table, eta, lors, n_lors, norm, spread, sym, st);
     if (half_t == 3 && half_a == 2)
-        return launch_spread_q<3, 2>(sc, tb, table, eta, lors, n_lors, norm, spread, skip_neg, st);
+        return launch_spread_q<3, 2>(sc, tb, table, eta, lors, n_lors, norm, spread, sym, st);
     if (half_t == 3 && half_a == 0)
-        return launch_spread_q<3, 0>(sc, tb, table, eta, lors, n_lors, norm, spread, skip_neg, st);
+        return launch_spread_q<3, 0>(sc, tb, table, eta, lors, n_lors, norm, spread, sym, st);
     size_t shm = spread_smem(tb, half_t, half_a);
     if (shm > 200 * 1024) return PSF_EINVAL;
     PSF_TRY(cudaFuncSetAttribute(spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -643,7 +711,7 @@ static int bin_spread(const psf_scanner *scanner, const psf_table_desc *desc, co
     {
         PSF_TIMED("spread_kernel", st);
         spread_kernel<<<(int)grid, SP_THREADS, shm, st>>>(sc, tb, table, eta, lors, n_lors, half_t,
-                                                          half_a, norm, spread, skip_neg);
+                                                          half_a, norm, spread, sym);
     }
     PSF_LAUNCHED();
     return PSF_OK;
@@ -655,8 +723,8 @@ extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *
                               const float *table, const double *eta, const int32_t *lors,
                               int64_t n_lors, int32_t half_t, int32_t half_a, int32_t norm,
                               float *spread, void *stream) {
-    return bin_spread(scanner, desc, table, eta, lors, n_lors, half_t, half_a, norm, spread, 0,
-                      as_stream(stream));
+    return bin_spread(scanner, desc, table, eta, lors, n_lors, half_t, half_a, norm, spread,
+                      nullptr, as_stream(stream));
 }
 
 extern "C" int psf_bin_spread_classes(const psf_scanner *scanner, const psf_table_desc *desc,
@@ -668,27 +736,34 @@ extern "C" int psf_bin_spread_classes(const psf_scanner *scanner, const psf_tabl
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;
     const int64_t n_cls = ls.ntp_cls * (2 * (int64_t)ls.Dm + 1);
+    if (n_cls == 0) return PSF_OK;
+    if (n_cls >= (1 << 28) || (2 * half_t + 1) * (2 * half_a + 1) > 256) return PSF_EINVAL;
+    if (!class_lors || !spread) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
-    // the classes of ring difference >= 0 through the spread kernel ...
-    rc = bin_spread(scanner, desc, table, eta, class_lors, n_cls, half_t, half_a, norm, spread, 1,
-                    st);
-    if (rc || n_cls == 0) return rc;
-    // ... and the others as their axial mirrors
-    const int64_t E = (2 * (int64_t)half_t + 1) * (2 * half_a + 1);
-    const int64_t n_mir = ls.ntp_cls * ls.Dm;
-    if (n_mir == 0) return PSF_OK;
-    const size_t shm = sizeof(int) * E * E;
-    if (shm > 200 * 1024) return PSF_EINVAL;
-    PSF_TRY(cudaFuncSetAttribute(spread_mirror_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shm));
+    int32_t *sym = nullptr;
+    PSF_TRY(cudaMallocAsync(&sym, sizeof(int32_t) * n_cls, st));
     int dev = 0, sms = 148;
-    PSF_TRY(cudaGetDevice(&dev));
-    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    {
-        PSF_TIMED("spread_mirror_kernel", st);
-        spread_mirror_kernel<<<(int)(n_mir < (int64_t)sms * 8 ? n_mir : (int64_t)sms * 8), 256,
-                               shm, st>>>(ls.ntp_cls, ls.Dm, half_t, half_a, spread);
+    rc = cudaGetDevice(&dev) != cudaSuccess ||
+                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess
+             ? PSF_ECUDA
+             : PSF_OK;
+    if (!rc) {
+        PSF_TIMED("spread_sym_kernel", st);
+        spread_sym_kernel<<<grid_for(n_cls, 256), 256, sizeof(int32_t) * (ls.Nt + ls.NR + 2),
+                            st>>>(ls, sym);
+        if (cudaGetLastError() != cudaSuccess) rc = PSF_ECUDA;
     }
-    PSF_LAUNCHED();
-    return PSF_OK;
+    // the smallest class of each orbit through the spread kernel ...
+    if (!rc)
+        rc = bin_spread(scanner, desc, table, eta, class_lors, n_cls, half_t, half_a, norm,
+                        spread, sym, st);
+    // ... the others as its images
+    if (!rc) {
+        PSF_TIMED("spread_mirror_kernel", st);
+        spread_mirror_kernel<<<(int)(n_cls < (int64_t)sms * 8 ? n_cls : (int64_t)sms * 8), 256, 0,
+                               st>>>(n_cls, half_t, half_a, sym, spread);
+        if (cudaGetLastError() != cudaSuccess) rc = PSF_ECUDA;
+    }
+    cudaFreeAsync(sym, st);
+    return rc;
 }
