@@ -380,6 +380,16 @@ int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out,
  * direction.  PSF_EINVAL otherwise. */
 int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads);
 
+/* Cycle limit of the library's bounded device waits (the bulk-staged
+ * projectors' waits for their copies; no counterpart in the paper): a wait
+ * that has not seen its event after `cycles` SM clock cycles gives up and
+ * records PSF_ETIMEOUT in the plan's status word (read by psf_matrix_check);
+ * the copies already in flight are still waited for, with the default limit,
+ * before a CTA exits.  Default 2^31 (about a second); a negative value makes
+ * the waits give up at once (a test of the timeout path).  Process-wide,
+ * read at launch. */
+int psf_set_wait_limit(int64_t cycles);
+
 /* Device status of the plan's bounded waits: synchronises `stream`, returns
  * PSF_OK, or PSF_ETIMEOUT when a bulk-staged kernel gave up waiting for a
  * copy since the last call (its outputs are then incomplete), and clears it. */

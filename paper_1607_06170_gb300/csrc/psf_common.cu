@@ -274,9 +274,18 @@ void timing_stop(const char *name, cudaStream_t st, cudaEvent_t start) {
     g_tpending.push_back({name, start, e});
 }
 
+static std::atomic<int64_t> g_wait_limit{int64_t(1) << 31};  // about a second at 2 GHz
+
+int64_t wait_limit() { return g_wait_limit.load(); }
+
 }  // namespace psf
 
 using namespace psf;
+
+extern "C" int psf_set_wait_limit(int64_t cycles) {
+    g_wait_limit.store(cycles);
+    return PSF_OK;
+}
 
 extern "C" int psf_timing_enable(int32_t on) {
     std::lock_guard<std::mutex> lock(g_tmu);
@@ -352,16 +361,19 @@ static int lorset_list(const psf_scanner *s, const psf_lor_set *set, int32_t *lo
 
 extern "C" int psf_lor_set_list(const psf_scanner *s, const psf_lor_set *set, int32_t *lors,
                                 void *stream) {
+    PSF_RANGE("psf_lor_set_list");
     return lorset_list(s, set, lors, stream, false);
 }
 
 extern "C" int psf_lor_set_classes(const psf_scanner *s, const psf_lor_set *set, int32_t *lors,
                                    void *stream) {
+    PSF_RANGE("psf_lor_set_classes");
     return lorset_list(s, set, lors, stream, true);
 }
 
 extern "C" int psf_em_ratio(const float *y, const float *yhat, float *ratio, int64_t n,
                             void *stream) {
+    PSF_RANGE("psf_em_ratio");
     if (n < 0 || (n > 0 && (!y || !yhat || !ratio))) return PSF_EINVAL;
     if (n == 0) return PSF_OK;
     {
@@ -374,6 +386,7 @@ extern "C" int psf_em_ratio(const float *y, const float *yhat, float *ratio, int
 
 extern "C" int psf_em_update(float *x, const float *bp, const float *sens, float floor_,
                              int64_t n, void *stream) {
+    PSF_RANGE("psf_em_update");
     if (n < 0 || (n > 0 && (!x || !bp || !sens))) return PSF_EINVAL;
     if (n == 0) return PSF_OK;
     {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdint>
 
@@ -55,6 +57,21 @@ struct KTimer {
     KTimer &operator=(const KTimer &) = delete;
 };
 #define PSF_TIMED(name, st) ::psf::KTimer psf_ktimer_(name, st)
+
+// NVTX range around an entry point (shown by Nsight tools; inert otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *n) { nvtxRangePushA(n); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define PSF_RANGE(name) ::psf::NvtxRange psf_nvtx_range_(name)
+
+// Cycle limit of the bounded device waits (psf_set_wait_limit): a wait that
+// has not seen its event after this many SM clock cycles gives up and records
+// PSF_ETIMEOUT; a negative limit makes the waits give up at once (a test of
+// the timeout path).
+int64_t wait_limit();
 
 // Scanner constants as the kernels use them (passed by value).
 struct Scan {

@@ -69,6 +69,7 @@ using namespace psf;
 
 extern "C" int psf_sino_bins(const psf_scanner *scanner, const psf_lor_set *set, int32_t *view,
                              int32_t *bin, void *stream) {
+    PSF_RANGE("psf_sino_bins");
     LorSet ls;
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;
@@ -88,6 +89,7 @@ extern "C" int psf_sino_bins(const psf_scanner *scanner, const psf_lor_set *set,
 extern "C" int psf_event_rows(const psf_scanner *scanner, const psf_lor_set *set,
                               const int32_t *events, int64_t n_events, int64_t *rows,
                               void *stream) {
+    PSF_RANGE("psf_event_rows");
     LorSet ls;
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;
@@ -106,6 +108,7 @@ extern "C" int psf_event_rows(const psf_scanner *scanner, const psf_lor_set *set
 
 extern "C" int psf_histogram(const int64_t *rows, int64_t n_events, float weight, float *counts,
                              int64_t n_rows, void *stream) {
+    PSF_RANGE("psf_histogram");
     if (n_events < 0 || n_rows < 0) return PSF_EINVAL;
     if (n_rows > 0 && !counts) return PSF_EINVAL;
     if (n_events > 0 && !rows) return PSF_EINVAL;

@@ -538,12 +538,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for a phase of the barrier; false after about 2^31 cycles (about a
-// second at the SM clock).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for a phase of the barrier; false after `limit` SM cycles (at once for
+// a negative limit).
+constexpr long long BK_DRAIN_LIMIT = 1ll << 31;  // about a second at the SM clock
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    if (limit < 0) return false;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -589,8 +591,9 @@ __device__ __forceinline__ void bk_give_up(unsigned char *raw, int it, bool next
                                            int *status) {
     if (threadIdx.x == 0) {
         atomicExch(status, PSF_ETIMEOUT);
-        mbar_wait(bk_stage(raw, it & 1).bar, (it >> 1) & 1);
-        if (next_issued) mbar_wait(bk_stage(raw, (it + 1) & 1).bar, ((it + 1) >> 1) & 1);
+        mbar_wait(bk_stage(raw, it & 1).bar, (it >> 1) & 1, BK_DRAIN_LIMIT);
+        if (next_issued)
+            mbar_wait(bk_stage(raw, (it + 1) & 1).bar, ((it + 1) >> 1) & 1, BK_DRAIN_LIMIT);
     }
 }
 
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(BK_T) csr_fwd_bulk_kernel(
     int64_t n, int64_t nnz, int64_t nch, const int64_t *__restrict__ first_row,
     const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y,
-    int *status) {
+    int *status, long long limit) {
     extern __shared__ __align__(128) unsigned char bk_raw[];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NW = BK_T / 32, PER_T = BK_CAP / BK_T;
@@ -639,7 +642,7 @@ __global__ void __launch_bounds__(BK_T) csr_fwd_bulk_kernel(
             pa = ptr[rr];
             pb = ptr[rr + 1];
         }
-        const bool ok = mbar_wait(g.bar, (it >> 1) & 1);
+        const bool ok = mbar_wait(g.bar, (it >> 1) & 1, limit);
         if (__syncthreads_or(!ok)) {
             bk_give_up(bk_raw, it, cn < nch, status);
             return;
@@ -708,7 +711,7 @@ __global__ void __launch_bounds__(BK_T) csr_back_bulk_kernel(
     int64_t n, int64_t nnz, int64_t nch, const int64_t *__restrict__ first_row,
     const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ ya, const float *__restrict__ yb,
-    float *__restrict__ x, float2 *__restrict__ x2, int *status) {
+    float *__restrict__ x, float2 *__restrict__ x2, int *status, long long limit) {
     extern __shared__ __align__(128) unsigned char bk_raw[];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NW = BK_T / 32;
@@ -737,7 +740,7 @@ __global__ void __launch_bounds__(BK_T) csr_back_bulk_kernel(
             wa = ya[rr];
             if (PAIR) wb = yb[rr];
         }
-        const bool ok = mbar_wait(g.bar, (it >> 1) & 1);
+        const bool ok = mbar_wait(g.bar, (it >> 1) & 1, limit);
         if (__syncthreads_or(!ok)) {
             bk_give_up(bk_raw, it, cn < nch, status);
             return;
@@ -1873,7 +1876,8 @@ static int rows_fwd_with(const psf_matrix *m, const float *x, float *y, int chun
             PSF_TIMED("csr_fwd_bulk_kernel", st);
             csr_fwd_bulk_kernel<<<grid, BK_T, shm, st>>>(m->n_rows, m->bk_nnz, m->bk_nch,
                                                          m->bk_first, m->row_ptr, m->col,
-                                                         (const float *)m->val, x, y, m->status);
+                                                         (const float *)m->val, x, y, m->status,
+                                                         (long long)wait_limit());
         }
         PSF_LAUNCHED();
         return PSF_OK;
@@ -1930,7 +1934,8 @@ static int rows_back_with(const psf_matrix *m, const float *y, float *x, int chu
             PSF_TIMED("csr_back_bulk_kernel", st);
             csr_back_bulk_kernel<false><<<grid, BK_T, shm, st>>>(
                 m->n_rows, m->bk_nnz, m->bk_nch, m->bk_first, m->row_ptr, m->col,
-                (const float *)m->val, y, nullptr, x, nullptr, m->status);
+                (const float *)m->val, y, nullptr, x, nullptr, m->status,
+                (long long)wait_limit());
         }
         PSF_LAUNCHED();
         return PSF_OK;
@@ -2118,6 +2123,7 @@ using namespace psf;
 extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_cols,
                                  const int64_t *row_ptr, const int32_t *col, const void *val,
                                  int32_t dtype, const float *row_scale, void *stream) {
+    PSF_RANGE("psf_matrix_create");
     (void)stream;
     if (!out || n_rows < 0 || n_cols < 1 || !row_ptr) return PSF_EINVAL;
     if (n_rows > 0 && (!col || !val)) return PSF_EINVAL;
@@ -2202,6 +2208,7 @@ static void drop_transpose(psf_matrix *m) {
 extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
                                      const psf_lor_set *set, int32_t half_t, int32_t half_a,
                                      const float *class_spread) {
+    PSF_RANGE("psf_matrix_set_spread");
     if (!m || !class_spread || half_t < 0 || half_a < 0) return PSF_EINVAL;
     LorSet ls;
     int rc = make_lorset(scanner, set, &ls);
@@ -2233,6 +2240,7 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
 extern "C" int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scanner,
                                           const psf_lor_set *set, int32_t half_t, int32_t half_a,
                                           int32_t n_keep, const int32_t *idx, const float *w) {
+    PSF_RANGE("psf_matrix_set_spread_topn");
     if (!m || !idx || !w || half_t < 0 || half_a < 0 || half_t > 127 || half_a > 127)
         return PSF_EINVAL;
     const int64_t E = (2 * (int64_t)half_t + 1) * (2 * (int64_t)half_a + 1);
@@ -2255,6 +2263,7 @@ extern "C" int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scan
 }
 
 extern "C" int psf_matrix_build_sparse_adjoint(psf_matrix *m, void *stream) {
+    PSF_RANGE("psf_matrix_build_sparse_adjoint");
     if (!m || m->topn <= 0) return PSF_EINVAL;
     if (m->tr_ptr) return PSF_OK;
     const int64_t n = m->n_rows;
@@ -2335,6 +2344,7 @@ extern "C" int psf_matrix_build_sparse_adjoint(psf_matrix *m, void *stream) {
 }
 
 extern "C" int psf_matrix_destroy(psf_matrix *m) {
+    PSF_RANGE("psf_matrix_destroy");
     if (!m) return PSF_EINVAL;
     cudaFree(m->p);
     cudaFree(m->q);
@@ -2351,6 +2361,7 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
 }
 
 extern "C" int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream) {
+    PSF_RANGE("psf_forward");
     if (!m || !x) return PSF_EINVAL;
     if (m->n_rows == 0) return PSF_OK;  // y has no entries (may be NULL)
     if (!y) return PSF_EINVAL;
@@ -2391,6 +2402,7 @@ static int rows_fwd_masked(const psf_matrix *m, const float *x, const float *mas
 
 extern "C" int psf_forward_masked(const psf_matrix *m, const float *x, const float *mask,
                                   float *y, void *stream) {
+    PSF_RANGE("psf_forward_masked");
     if (!m || !x) return PSF_EINVAL;
     if (m->n_rows == 0) return PSF_OK;  // mask and y have no entries (may be NULL)
     if (!mask || !y) return PSF_EINVAL;
@@ -2455,6 +2467,7 @@ static int rows_back_listed(const psf_matrix *m, const float *y, float *x, cudaS
 }  // namespace psf
 
 extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *stream) {
+    PSF_RANGE("psf_back");
     if (!m || !x) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (m->n_rows == 0) {  // y has no entries (may be NULL)
@@ -2471,6 +2484,7 @@ extern "C" int psf_back(const psf_matrix *m, const float *y, float *x, void *str
 
 extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *threads_out,
                                    void *stream) {
+    PSF_RANGE("psf_matrix_autotune");
     if (!m) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (m->n_rows == 0) {
@@ -2598,12 +2612,14 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
 }
 
 extern "C" int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form) {
+    PSF_RANGE("psf_matrix_set_stencil_form");
     if (!m || form < 0 || form > 4) return PSF_EINVAL;
     m->st_form[0] = m->st_form[1] = form;
     return PSF_OK;
 }
 
 extern "C" int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads) {
+    PSF_RANGE("psf_matrix_set_launch");
     if (!m || chunk < -2 || chunk > (1 << 20)) return PSF_EINVAL;
     if (chunk > 0 && (threads < 32 || threads > 1024 || threads % 32)) return PSF_EINVAL;
     if (chunk < 0 && m->dtype != PSF_F32) return PSF_EINVAL;
@@ -2653,6 +2669,7 @@ static int sens_spread(const psf_matrix *m, float *out, cudaStream_t st) {
 }  // namespace psf
 
 extern "C" int psf_sensitivity(const psf_matrix *m, float *x, void *stream) {
+    PSF_RANGE("psf_sensitivity");
     if (!m || !x) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (m->n_rows == 0) {
@@ -2675,6 +2692,7 @@ extern "C" int psf_sensitivity(const psf_matrix *m, float *x, void *stream) {
 // x = A^T y and sens = A^T 1 with one pass over the stored rows.
 extern "C" int psf_back_sens(const psf_matrix *m, const float *y, float *x, float *sens,
                              void *stream) {
+    PSF_RANGE("psf_back_sens");
     if (!m || !x || !sens) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (m->n_rows == 0) {  // y has no entries (may be NULL)
@@ -2727,7 +2745,8 @@ static int rows_back_pair(const psf_matrix *m, const float *qa, const float *qb,
             PSF_TIMED("csr_back_bulk_kernel<pair>", st);
             csr_back_bulk_kernel<true><<<grid, BK_T, shm, st>>>(
                 m->n_rows, m->bk_nnz, m->bk_nch, m->bk_first, m->row_ptr, m->col,
-                (const float *)m->val, qa, qb, nullptr, m->img2, m->status);
+                (const float *)m->val, qa, qb, nullptr, m->img2, m->status,
+                (long long)wait_limit());
         }
         PSF_LAUNCHED();
         return PSF_OK;
@@ -2756,6 +2775,7 @@ static int rows_back_pair(const psf_matrix *m, const float *qa, const float *qb,
 }  // namespace psf
 
 extern "C" int psf_matrix_check(const psf_matrix *m, void *stream) {
+    PSF_RANGE("psf_matrix_check");
     if (!m) return PSF_EINVAL;
     cudaStream_t st = as_stream(stream);
     int h = 0;

@@ -95,6 +95,7 @@ using namespace psf;
 
 extern "C" int psf_response_build(const psf_scanner *scanner, const psf_table_desc *desc,
                                   float *table, double *eta, void *stream) {
+    PSF_RANGE("psf_response_build");
     Scan sc;
     Tab tb;
     int rc = make_scan(scanner, &sc);

@@ -1054,6 +1054,7 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
 extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
                                    const psf_lor_set *set, int64_t *row_ptr, int32_t *col,
                                    float *val, int64_t capacity, int64_t *nnz_out, void *stream) {
+    PSF_RANGE("psf_sysmat_rows_set");
     Scan sc;
     Img im;
     LorSet ls;
@@ -1078,6 +1079,7 @@ extern "C" int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *imag
                                int32_t half_t, int32_t half_a, int32_t dtype, int64_t *row_ptr,
                                int32_t *col, void *val, float *row_scale, int64_t capacity,
                                int64_t *nnz_out, void *stream) {
+    PSF_RANGE("psf_sysmat_rows");
     Scan sc;
     Img im;
     int rc = make_scan(scanner, &sc);
@@ -1222,6 +1224,7 @@ extern "C" int psf_sysmat_rows_set_noalloc(const psf_scanner *scanner, const psf
                                            const psf_lor_set *set, int64_t *row_ptr,
                                            int32_t *col, float *val, int64_t capacity,
                                            int64_t *nnz_out, void *stream) {
+    PSF_RANGE("psf_sysmat_rows_set_noalloc");
     Scan sc;
     Img im;
     LorSet ls;

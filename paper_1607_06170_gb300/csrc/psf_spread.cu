@@ -723,6 +723,7 @@ extern "C" int psf_bin_spread(const psf_scanner *scanner, const psf_table_desc *
                               const float *table, const double *eta, const int32_t *lors,
                               int64_t n_lors, int32_t half_t, int32_t half_a, int32_t norm,
                               float *spread, void *stream) {
+    PSF_RANGE("psf_bin_spread");
     return bin_spread(scanner, desc, table, eta, lors, n_lors, half_t, half_a, norm, spread,
                       nullptr, as_stream(stream));
 }
@@ -732,6 +733,7 @@ extern "C" int psf_bin_spread_classes(const psf_scanner *scanner, const psf_tabl
                                       const psf_lor_set *set, const int32_t *class_lors,
                                       int32_t half_t, int32_t half_a, int32_t norm,
                                       float *spread, void *stream) {
+    PSF_RANGE("psf_bin_spread_classes");
     LorSet ls;
     int rc = make_lorset(scanner, set, &ls);
     if (rc) return rc;

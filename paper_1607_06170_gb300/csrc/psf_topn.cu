@@ -95,6 +95,7 @@ using namespace psf;
 extern "C" int psf_spread_topn(const float *spread, int64_t n_lors, int32_t half_t,
                                int32_t half_a, int32_t n_keep, int32_t *idx, float *w,
                                void *stream) {
+    PSF_RANGE("psf_spread_topn");
     if (n_lors < 0 || half_t < 0 || half_a < 0) return PSF_EINVAL;
     const int64_t E = (2 * (int64_t)half_t + 1) * (2 * (int64_t)half_a + 1);
     if (E * E > (int64_t)TN_T * TN_EPT) return PSF_EINVAL;

@@ -145,6 +145,7 @@ extern "C" int psf_voxel_homog(const psf_scanner *scanner, const psf_table_desc 
                                const float *table, const double *eta, const psf_image *image,
                                const psf_lor_set *set, int32_t k, int32_t half_t, float *A,
                                void *stream) {
+    PSF_RANGE("psf_voxel_homog");
     Scan sc;
     Tab tb;
     Img im;

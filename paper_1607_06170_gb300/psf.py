@@ -31,6 +31,7 @@ FUNCTIONS = [
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
     "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
     "psf_matrix_check", "psf_matrix_build_sparse_adjoint", "psf_bin_spread_classes",
+    "psf_set_wait_limit",
 ]
 
 
@@ -101,6 +102,7 @@ _SIGS = {
     "psf_voxel_homog": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
     "psf_matrix_set_stencil_form": (C.c_int, [_P, _I32]),
     "psf_matrix_check": (C.c_int, [_P, _P]),
+    "psf_set_wait_limit": (C.c_int, [_I64]),
     "psf_matrix_build_sparse_adjoint": (C.c_int, [_P, _P]),
 }
 
@@ -224,6 +226,15 @@ def bin_spread_classes(sc: dict, tb: dict, T, eta, ls: dict, class_lors, half_t:
                                      _ptr(class_lors), half_t, half_a, norm, _ptr(out),
                                      _stream()), "psf_bin_spread_classes")
     return out
+
+
+def set_wait_limit(cycles: int):
+    """Cycle limit of the library's bounded device waits (psf_set_wait_limit);
+    negative: give up at once (tests of the timeout path)."""
+    _ok(lib().psf_set_wait_limit(int(cycles)), "psf_set_wait_limit")
+
+
+WAIT_LIMIT_DEFAULT = 1 << 31
 
 
 def spread_topn(spread, half_t: int, half_a: int, n_keep: int):

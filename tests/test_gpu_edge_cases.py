@@ -153,3 +153,36 @@ def test_bulk_staged_long_and_empty_rows(P):
     M2 = P.Matrix(ptr_t, col2, val_t, nv)
     with pytest.raises(Exception):
         M2.set_launch(-2)
+
+
+def test_bounded_wait_reports_timeout(P, ring2d):
+    """The bulk-staged kernels' waits for their copies are bounded: with the
+    limit forced to give up at once, every launch records PSF_ETIMEOUT in the
+    plan's status word (psf_matrix_check raises it; the copies in flight are
+    still drained before a CTA exits), and with the default limit the same
+    plan projects normally again."""
+    from paper_1607_06170_gb300.psf import PSFError
+
+    w = ring2d["w"]
+    s, im = w["scanner"], w["image"]
+    Lt = torch.from_numpy(I.workload_lors(w)).cuda()
+    rp, col, val, _ = P.sysmat_rows(s, im, Lt)
+    M = P.Matrix(rp, col, val, ring2d["nv"])
+    x = torch.from_numpy(I.phantom_discs(im, 0).reshape(-1)).cuda()
+    M.set_launch(0)
+    f0 = M.forward(x).clone()
+    M.set_launch(-2)
+    M.check()
+    try:
+        P.set_wait_limit(-1)
+        M.forward(x)
+        with pytest.raises(PSFError, match="bounded device wait"):
+            M.check()
+        M.back_sens(f0)
+        with pytest.raises(PSFError, match="bounded device wait"):
+            M.check()
+    finally:
+        P.set_wait_limit(P.WAIT_LIMIT_DEFAULT)
+    M.check()  # cleared by the read
+    torch.testing.assert_close(M.forward(x), f0, rtol=1e-6, atol=1e-6 * f0.abs().max().item())
+    M.check()
