@@ -79,3 +79,21 @@ def test_autotune_and_graph_mlem(plan):
     torch.cuda.synchronize()
     rel = (torch.linalg.norm(xg - xe) / torch.linalg.norm(xe)).item()
     assert rel < 1e-5, rel
+
+
+def test_mlem_resume_from_saved_image(plan, tmp_path):
+    """Checkpoint / resume: the MLEM state is the image; 6 iterations equal 3,
+    a save and reload of the image (torch.save), then 3 more from it."""
+    from paper_1607_06170_gb300.torch_api import mlem
+
+    M, x = plan["M"], plan["x"]
+    y = M.forward(x).clone()
+    sens = M.sensitivity()
+    x6 = mlem(M, y, iters=6, sens=sens)
+    x3 = mlem(M, y, iters=3, sens=sens)
+    torch.save(x3.cpu(), tmp_path / "mlem_state.pt")
+    x3r = torch.load(tmp_path / "mlem_state.pt").cuda()
+    x6r = mlem(M, y, iters=3, x0=x3r, sens=sens)
+    torch.cuda.synchronize()
+    rel = (torch.linalg.norm(x6r - x6) / torch.linalg.norm(x6)).item()
+    assert rel < 1e-5, rel
