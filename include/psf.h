@@ -235,8 +235,11 @@ int psf_bin_spread_classes(const psf_scanner *scanner, const psf_table_desc *des
                            int32_t norm, float *spread, void *stream);
 
 /*
- * System-matrix rows in CSR (row_ptr int64 [n_lors+1], col int32 sorted
- * ascending, duplicates merged).
+ * System-matrix rows (Sec. 2.3, Eq. 12: each LOR's matrix row is the sum of
+ * its neighbouring geometric rows weighted by the homogenization spread; the
+ * geometric rows are the ray-driven chord lengths through the image that the
+ * paper's Sec. 3 reconstruction uses) in CSR (row_ptr int64 [n_lors+1], col
+ * int32 sorted ascending, duplicates merged).
  *  spread == NULL: geometric rows G -- chord lengths (mm) of the segment
  *    joining the two crystals' front-face centres through the voxel grid; a
  *    voxel belongs to a row iff its chord is positive.
@@ -287,13 +290,19 @@ int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
  *  - Limit: a set of at most PSF_NOALLOC_MAX_ROWS rows whose tile sums and
  *    ring-pair table fit in the array together; other sets return
  *    PSF_ENOSCRATCH before any device work.
- *  - The first call on a device (the current device) looks up the array's
- *    device address once; make that first call before any stream capture.
+ *  - Set-up: the first call on a device (the current device) looks up the
+ *    array's device address once and keeps it for later calls on that
+ *    device; make that first call before any stream capture.  The address
+ *    is not looked up again, so after cudaDeviceReset (by the caller, torch
+ *    or any other code in the process) this entry point must not be called
+ *    again on that device in the same process.
  *  - All calls share the array and leave their contents in it: calls whose
  *    work overlaps on the GPU (different streams, or host threads) race and
  *    must be serialised by the caller.
- * Arguments, results, size query, capacity rule and synchronisation are those
- * of psf_sysmat_rows_set.
+ *  - Like psf_sysmat_rows_set it synchronises `stream` (it reads the
+ *    nonzero count and the status word back to the host).
+ * Arguments, results, size query and capacity rule are those of
+ * psf_sysmat_rows_set.
  */
 #define PSF_NOALLOC_SCRATCH_BYTES (1 << 20)
 #define PSF_NOALLOC_MAX_ROWS ((int64_t)((PSF_NOALLOC_SCRATCH_BYTES - 64) / 8 - 1) * 2048)
@@ -422,13 +431,16 @@ int psf_sensitivity(const psf_matrix *m, float *x, void *stream);
  */
 int psf_back_sens(const psf_matrix *m, const float *y, float *x, float *sens, void *stream);
 
-/* y = A x (overwrite), x (device float [n_cols]), y (device float [n_rows]).
+/* Forward projection of the MLEM / OSEM iterations (Sec. 3; with a factored
+ * plan A = S G of Sec. 2.3, Eq. 12, applied as G then S): y = A x
+ * (overwrite), x (device float [n_cols]), y (device float [n_rows]).
  * A plan with no rows returns PSF_OK at once (y may then be NULL). */
 int psf_forward(const psf_matrix *m, const float *x, float *y, void *stream);
 
-/* x = A^T y (overwrite); with no rows x is zeroed (y may then be NULL).  The
- * same holds for the LOR-space arguments of psf_back_sens and
- * psf_forward_masked. */
+/* Back-projection of the MLEM / OSEM iterations (Sec. 3; factored plan:
+ * S^T then G^T), the exact adjoint of psf_forward: x = A^T y (overwrite);
+ * with no rows x is zeroed (y may then be NULL).  The same holds for the
+ * LOR-space arguments of psf_back_sens and psf_forward_masked. */
 int psf_back(const psf_matrix *m, const float *y, float *x, void *stream);
 
 /* y = A x on the rows with mask != 0 (mask: device float [n_rows],

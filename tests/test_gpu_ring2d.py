@@ -93,11 +93,21 @@ def test_set_rows_equal_list_rows(both, P):
 
 
 def test_psf_rows_and_projectors(both, orc):
+    # A row receives the spreads of every LOR whose window lands on it; a LOR
+    # with a rounding decision within MARGIN of its boundary has several
+    # correct spreads, so the rows it reaches (through a nonempty geometric
+    # row) are left out and counted.
     name, o, g = both
-    if name != "RING2D":
-        pytest.skip("PSF rows compared on the workload without ambiguous LORs")
     s = o["w"]["scanner"]
     A = orc.rows_psf_dense(s, o["L"], o["G"], o["W"][1], o["Wt"], o["Wa"], o["nv"])
+    amb = o["margin"] < MARGIN
+    E = (2 * o["Wt"] + 1) * (2 * o["Wa"] + 1)
+    reach = orc.rows_psf_dense(s, o["L"], o["G"], np.broadcast_to(
+        amb[:, None, None].astype(np.float64), (len(o["L"]), E, E)).copy(), o["Wt"], o["Wa"],
+        o["nv"])
+    keep = ~(reach != 0).any(1)
+    print(f"{name}: {amb.sum()} tie LORs, {(~keep).sum()} of {len(keep)} PSF rows left out")
+    assert keep.mean() > 0.9
     ptr, col, val, _ = g["A"]
     ptr, col, val = ptr.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
     Ag = np.zeros_like(A)
@@ -105,9 +115,9 @@ def test_psf_rows_and_projectors(both, orc):
     Ag[rows, col] = val
     wsum = o["W"][1].reshape(len(o["L"]), -1).sum(1)   # weight landing scale per row
     floor = 1e-6 * np.maximum(wsum, wsum.max() * 1e-3)[:, None]
-    assert_close(Ag, A, 1e-4, floor, "PSF rows")
+    assert_close(Ag[keep], A[keep], 1e-4, floor[keep], f"{name} PSF rows")
     # sparsity: entries above the floor agree
-    assert np.array_equal(Ag > 2 * floor, A > 2 * floor)
+    assert np.array_equal(Ag[keep] > 2 * floor[keep], A[keep] > 2 * floor[keep])
     # columns ascending within rows
     assert all(np.all(np.diff(col[ptr[i]:ptr[i + 1]]) > 0) for i in range(len(ptr) - 1))
 

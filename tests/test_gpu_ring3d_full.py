@@ -1,9 +1,12 @@
 """GPU parity at the full 3D workload (44.7M LORs, 160 x 160 x 104 voxels) in
-the launch configuration bench.py times, on outputs the oracle can compute
-one by one: the whole response table, sampled class spreads, sampled chord
-rows, sampled forward-projected LORs (each gathered from the oracle's
-per-LOR spreads of up to 2 x 2401 neighbouring LORs), and the dot-product
-identity of the factored projector."""
+the launch configuration bench.py times: class spreads from
+psf_bin_spread_classes (orbit classes through the spread kernel, the others as
+their mirror images) and a projector plan tuned by psf_matrix_autotune.
+Checked on outputs the oracle can compute one by one -- the whole response
+table, sampled class spreads (computed and mirrored), sampled chord rows,
+sampled forward-projected LORs (each gathered from the oracle's per-LOR
+spreads of up to 2 x 2401 neighbouring LORs) -- and, over every class, LOR
+and voxel, against the direct spread kernel and the plain projector forms."""
 import numpy as np
 import pytest
 import torch
@@ -13,6 +16,7 @@ from parity import SPREAD_ATOL_REL, TABLE_ATOL, assert_close, compare_chord_rows
 
 pytestmark = pytest.mark.gpu
 NAME = "RING3D"
+MARGIN = 1e-5  # classes with a rounding decision closer than this have several correct spreads
 
 
 @pytest.fixture(scope="module")
@@ -25,15 +29,45 @@ def setup(orc):
     Wt, Wa = w["window"]
     T, eta = P.response_build(s, t)
     C = P.lor_set_classes(s, ls)
-    WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)
+    WC = P.bin_spread(s, t, T, eta, C, Wt, Wa)  # every class through the spread kernel
+    WM = P.bin_spread_classes(s, t, T, eta, ls, C, Wt, Wa)  # as bench.py: orbits + images
     G = P.sysmat_rows_set(s, im, ls)
     nv = im["nx"] * im["ny"] * im["nz"]
-    M = P.Matrix(G[0], G[1], G[2], nv).set_spread(s, ls, Wt, Wa, WC)
+    M = P.Matrix(G[0], G[1], G[2], nv).set_spread(s, ls, Wt, Wa, WM)
+    tuned = M.autotune()
     torch.cuda.synchronize()
     To, eo = orc.table_build(s, t)
     tp = I.transaxial_pairs(s, ls["fan_half"]).astype(np.int64)
     rp = I.ring_pairs(s, ls["max_ring_diff"]).astype(np.int64)
-    return dict(w=w, P=P, T=T, eta=eta, C=C, WC=WC, G=G, M=M, To=To, eo=eo, tp=tp, rp=rp, nv=nv)
+    return dict(w=w, P=P, T=T, eta=eta, C=C, WC=WC, WM=WM, G=G, M=M, tuned=tuned, To=To, eo=eo,
+                tp=tp, rp=rp, nv=nv)
+
+
+def class_orbits(s, ls, C):
+    """For each class (rows of C, in class order): the smallest class index of
+    its orbit under the axial reflection (ring difference d -> -d) and the
+    transaxial reflection through block 0's centre plane (crystal x -> (Nb - 1
+    - x) mod Nt, ends swapped with d -> -d when the reflected first crystal
+    comes after the second, then rotated by whole blocks until the first
+    crystal is in block 0)."""
+    nt, nb = I.n_transaxial(s), s["nt_block"]
+    a, b = C[:, 0] % nt, C[:, 1] % nt
+    d = C[:, 1] // nt - C[:, 0] // nt
+    index = {(int(x), int(y), int(z)): k for k, (x, y, z) in enumerate(zip(a, b, d))}
+
+    def refl_t(x, y, z):
+        x2, y2 = (nb - 1 - x) % nt, (nb - 1 - y) % nt
+        if x2 > y2:
+            x2, y2, z = y2, x2, -z
+        k = x2 // nb
+        return x2 - k * nb, y2 - k * nb, z
+
+    out = np.empty(len(C), dtype=np.int64)
+    for k, key in enumerate(zip(a.tolist(), b.tolist(), d.tolist())):
+        x, y, z = key
+        orbit = [key, (x, y, -z), refl_t(x, y, z), refl_t(x, y, -z)]
+        out[k] = min(index[o] for o in orbit)
+    return out
 
 
 def lor_of(d, rows):
@@ -57,11 +91,69 @@ def test_sampled_class_spreads(setup, orc):
     C = d["C"].cpu().numpy()
     pick = np.random.default_rng(31).choice(len(C), 48, replace=False)
     Wo = orc.spread(w["scanner"], w["table"], d["To"], C[pick], Wt, Wa)
-    ok = orc.tie_margin(w["scanner"], w["table"], d["To"], C[pick]) >= 1e-5
+    ok = orc.tie_margin(w["scanner"], w["table"], d["To"], C[pick]) >= MARGIN
+    print(f"sampled classes: {(~ok).sum()} of {len(pick)} left out by the tie margin")
     assert ok.sum() >= 40
     got = d["WC"][torch.from_numpy(pick).cuda()].cpu().numpy()
     scale = np.abs(Wo).reshape(len(pick), -1).max(1)[:, None, None]
     assert_close(got[ok], Wo[ok], 1e-5, SPREAD_ATOL_REL * scale[ok] + 1e-30, "class spreads")
+
+
+def test_mirrored_classes_equal_direct(setup, orc):
+    """psf_bin_spread_classes against psf_bin_spread on all 84,227 classes:
+    the orbit classes are the same kernel's output (bit-equal), the images
+    equal the direct spread except where a sub-LOR decision of the class or of
+    its image sits within the working precision of a boundary; every class
+    outside tolerance must be one the oracle's tie margin flags."""
+    d = setup
+    w = d["w"]
+    s, ls = w["scanner"], w["lors"]
+    C = d["C"].cpu().numpy()
+    can = class_orbits(s, ls, C)
+    computed = can == np.arange(len(C))
+    print(f"{computed.sum()} orbit classes computed, {(~computed).sum()} images")
+    assert computed.sum() == 21744 and len(C) == 84227
+    WM, WC = d["WM"], d["WC"]
+    cidx = torch.from_numpy(np.flatnonzero(computed)).cuda()
+    assert torch.equal(WM[cidx], WC[cidx])
+    scale = WC.abs().amax(dim=(1, 2), keepdim=True)
+    tol = 1e-5 * WC.abs() + SPREAD_ATOL_REL * scale + 1e-30
+    bad = ((WM - WC).abs() > tol).any(2).any(1).cpu().numpy()
+    assert not (bad & computed).any()
+    nbad = int(bad.sum())
+    print(f"mirrored classes outside tolerance: {nbad} of {len(C)}")
+    assert nbad <= 0.2 * len(C)
+    if nbad:
+        m = orc.tie_margin(s, w["table"], d["To"], C[bad])
+        assert (m < MARGIN).all(), C[bad][m >= MARGIN][:5]
+
+
+def test_image_classes_against_oracle(setup, orc):
+    """Sampled image classes (written by the mirror kernel, never by the
+    spread kernel) against the oracle's own spread of the class LOR; half of
+    them with the first crystal at the centre of block 0 (Nb = 13 is odd, so
+    the transaxial reflection maps that crystal onto itself)."""
+    d = setup
+    w = d["w"]
+    s, ls = w["scanner"], w["lors"]
+    Wt, Wa = w["window"]
+    nt, nb = I.n_transaxial(s), s["nt_block"]
+    C = d["C"].cpu().numpy()
+    can = class_orbits(s, ls, C)
+    img = np.flatnonzero(can != np.arange(len(C)))
+    centre = img[(C[img, 0] % nt) == (nb - 1) // 2]
+    other = img[(C[img, 0] % nt) != (nb - 1) // 2]
+    assert len(centre) > 32
+    g = np.random.default_rng(34)
+    pick = np.concatenate([g.choice(centre, 32, replace=False), g.choice(other, 32, replace=False)])
+    Wo = orc.spread(s, w["table"], d["To"], C[pick], Wt, Wa)
+    ok = orc.tie_margin(s, w["table"], d["To"], C[pick]) >= MARGIN
+    print(f"image classes: {(~ok).sum()} of {len(pick)} left out by the tie margin "
+          f"({(~ok[:32]).sum()} of the 32 centre-crystal classes)")
+    assert ok[:32].sum() >= 24 and ok[32:].sum() >= 24
+    got = d["WM"][torch.from_numpy(pick).cuda()].cpu().numpy()
+    scale = np.abs(Wo).reshape(len(pick), -1).max(1)[:, None, None]
+    assert_close(got[ok], Wo[ok], 1e-5, SPREAD_ATOL_REL * scale[ok] + 1e-30, "image classes")
 
 
 def test_sampled_rows(setup, orc):
@@ -171,3 +263,28 @@ def test_sensitivity_full(setup):
     sens = M.sensitivity()
     back1 = M.back(torch.ones(M.n_rows, device="cuda"))
     torch.testing.assert_close(sens, back1, rtol=1e-5, atol=1e-6 * back1.abs().max().item())
+
+
+def test_tuned_launches_equal_plain_forms(setup):
+    """The autotuned launches bench.py times (work-queue forward, pair
+    back-projection with the sensitivity, staged stencils) against the plain
+    forms (grid-stride CSR kernels, one-output-per-thread stencil) of the same
+    rows and spreads, element by element over all LORs and voxels."""
+    d = setup
+    P, M, G, w = d["P"], d["M"], d["G"], d["w"]
+    s, ls, im = w["scanner"], w["lors"], w["image"]
+    Wt, Wa = w["window"]
+    (fc, ft), (bc, bt) = d["tuned"]
+    print(f"tuned launches: forward chunk {fc} x {ft} threads, back chunk {bc} x {bt}")
+    Mp = P.Matrix(G[0], G[1], G[2], d["nv"]).set_spread(s, ls, Wt, Wa, d["WM"])
+    Mp.set_launch(0).set_stencil_form(1)
+    x = torch.from_numpy(I.phantom_cylinder(im, 1).reshape(-1)).cuda()
+    y = torch.from_numpy(I.random_lor_values(M.n_rows, 920)).cuda()
+    yt, yp = M.forward(x), Mp.forward(x)
+    torch.testing.assert_close(yt, yp, rtol=1e-5, atol=1e-6 * yp.abs().max().item())
+    bt_, st_ = M.back_sens(y)
+    bp_, sp_ = Mp.back(y), Mp.back(torch.ones_like(y))
+    torch.testing.assert_close(bt_, bp_, rtol=1e-5, atol=1e-6 * bp_.abs().max().item())
+    torch.testing.assert_close(st_, sp_, rtol=1e-5, atol=1e-6 * sp_.abs().max().item())
+    torch.testing.assert_close(M.back(y), bp_, rtol=1e-5, atol=1e-6 * bp_.abs().max().item())
+    torch.testing.assert_close(M.sensitivity(), sp_, rtol=1e-5, atol=1e-6 * sp_.abs().max().item())
