@@ -721,8 +721,7 @@ struct SetSmem {
     Cells2D c;
     double *cs;
     long long *s_len;   // [SET_MAXC] chord (units) of the cell at each voxel-order position
-    int *s_xy;          // [SET_MAXC] iy * nx + ix, sign bit set for short cells
-    float *s_lenf;      // [SET_MAXC] chord as a float (rounded once)
+    int2 *s_xyl;        // [SET_MAXC] iy * nx + ix, chord as a float (bits, rounded once)
     int32_t *tp_start, *rp_start;
     int *next;          // next ring-pair group of the current transaxial pair
     SetWarp *w;         // [SET_T / 32]
@@ -732,9 +731,8 @@ __device__ __forceinline__ void set_smem_layout(SetSmem &m, unsigned char *raw, 
                                                 const LorSet &ls) {
     m.cs = reinterpret_cast<double *>(cells_layout(m.c, raw));
     m.s_len = reinterpret_cast<long long *>(m.cs + 2 * sc.R);
-    m.s_xy = reinterpret_cast<int *>(m.s_len + SET_MAXC);
-    m.s_lenf = reinterpret_cast<float *>(m.s_xy + SET_MAXC);
-    m.tp_start = reinterpret_cast<int32_t *>(m.s_lenf + SET_MAXC);
+    m.s_xyl = reinterpret_cast<int2 *>(m.s_len + SET_MAXC);
+    m.tp_start = reinterpret_cast<int32_t *>(m.s_xyl + SET_MAXC);
     m.rp_start = m.tp_start + ls.Nt + 1;
     m.next = m.rp_start + ls.NR + 1;
     m.w = reinterpret_cast<SetWarp *>(
@@ -743,7 +741,7 @@ __device__ __forceinline__ void set_smem_layout(SetSmem &m, unsigned char *raw, 
 
 static size_t set_smem(const Scan &sc, const LorSet &ls) {
     return cells_bytes() + sizeof(double) * 2 * sc.R +
-           (sizeof(long long) + sizeof(int) + sizeof(float)) * SET_MAXC +
+           (sizeof(long long) + sizeof(int2)) * SET_MAXC +
            sizeof(int32_t) * (ls.Nt + ls.NR + 2) + sizeof(int) * 4 + 16 +
            sizeof(SetWarp) * (SET_T / 32) + 64;
 }
@@ -777,13 +775,11 @@ __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const
     __syncthreads();
     const bool xinc = c.X->kind == 0 || c.X->inc;
     const bool yinc = c.Y->kind == 0 || c.Y->inc;
-    const long long thr2 = c.clip[2];
     for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
         const int p = sorted_pos(c, cc, xinc, yinc);
         const long long L = c.bnd[cc + 1] - c.bnd[cc];
         m.s_len[p] = L;
-        m.s_lenf[p] = units_to_f(L);
-        m.s_xy[p] = ((int)c.iy[cc] * im.nx + c.ix[cc]) | (L < thr2 ? (int)0x80000000 : 0);
+        m.s_xyl[p] = make_int2((int)c.iy[cc] * im.nx + c.ix[cc], float_bits(units_to_f(L)));
     }
     __syncthreads();
 }
@@ -841,12 +837,111 @@ __global__ void __launch_bounds__(SET_T, 3) set_count_kernel(Scan sc, Img im, Lo
     }
 }
 
-// K6 (set): the same walk; each round's slabs become at most three
-// voxel-order ranges each, laid end to end, and the lanes then store that
-// flattened list 32 entries at a time on consecutive slots (a slab's
-// interior cells carry their full 2D chord, only its first and last ray-order
-// cells are cut by the z planes).  The 32 rows of a group are consecutive in
-// the CSR, so the whole group is one contiguous output span.
+// Left shift that gives 0 for shift counts of 32 and more (PTX shl.b32
+// clamps the count; a C++ shift by 32 is undefined).
+__device__ __forceinline__ unsigned shl_clamped(unsigned v, int n) {
+    unsigned r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(n));
+    return r;
+}
+
+// General emission of one round (any keep pattern): a keep decision per cell
+// and a ballot compaction of the kept entries.  Used for the rare rounds where
+// a short interior cell of some slab is dropped.  Returns the entries stored.
+__device__ __forceinline__ int fill_round_general(const SetSmem &m, SetWarp &W, const SlabOf &so,
+                                               const SlabCells &s, bool xinc, bool yinc,
+                                               int nxy, long long pos, long long pend,
+                                               int32_t *__restrict__ col,
+                                               float *__restrict__ val) {
+    const Cells2D &c = m.c;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u, le = (2u << lane) - 1u;
+    int lo[3], hi[3], ns = 0;
+    if (so.q >= 0 && s.cb >= s.ca) {
+        ns = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
+        const long long La = piece(c.bnd, s.ca, so.zl, so.zh);
+        const long long Lb = piece(c.bnd, s.cb, so.zl, so.zh);
+        W.gen.sa[lane] = make_int4(so.iz * nxy, sorted_pos(c, s.ca, xinc, yinc),
+                                   sorted_pos(c, s.cb, xinc, yinc),
+                                   (La >= so.minu) | ((Lb >= so.minu) << 1));
+        W.gen.sf[lane] = make_float4(units_to_f(La) * so.to_mm, units_to_f(Lb) * so.to_mm,
+                                     so.to_mm, 0.0f);
+        W.gen.sm[lane] = so.minu;
+    }
+    int len = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (k < ns) len += hi[k] - lo[k] + 1;
+    int inc_len = len, inc_seg = ns;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a1 = __shfl_up_sync(0xffffffffu, inc_len, o);
+        const int a2 = __shfl_up_sync(0xffffffffu, inc_seg, o);
+        if (lane >= o) {
+            inc_len += a1;
+            inc_seg += a2;
+        }
+    }
+    const int total = __shfl_sync(0xffffffffu, inc_len, 31);
+    const int nseg = __shfl_sync(0xffffffffu, inc_seg, 31);
+    int off = inc_len - len;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (k < ns) {
+            W.gen.rs[inc_seg - ns + k] = make_int2(off, lo[k] | (lane << 16));
+            off += hi[k] - lo[k] + 1;
+        }
+    __syncwarp();
+    const long long pos0 = pos;
+    int gbase = -1;  // range holding the entry before the chunk
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        const int gq = gbase + 1 + lane;
+        unsigned bit = 0u;
+        if (gq < nseg) {
+            const int st = W.gen.rs[gq].x - e0;
+            if (st < 32) bit = 1u << st;
+        }
+        const unsigned B = __reduce_or_sync(0xffffffffu, bit);
+        const int e = e0 + lane;
+        bool keep = false;
+        int colv = 0;
+        float v = 0.0f;
+        if (e < total) {
+            const int gi = gbase + __popc(B & le);
+            const int2 R = W.gen.rs[gi];
+            const int p = (R.y & 0xffff) + (e - R.x), k = R.y >> 16;
+            const int4 A = W.gen.sa[k];
+            const float4 F = W.gen.sf[k];
+            const int2 xl = m.s_xyl[p];
+            // end cells take their cut chord and keep bit; interior cells
+            // their 2D chord, kept unless shorter than the row's threshold
+            const bool isa = p == A.y, isb = p == A.z;
+            v = isa ? F.x : (isb ? F.y : __int_as_float(xl.y) * F.z);
+            keep = isa ? (A.w & 1) : (isb ? ((A.w >> 1) & 1) : m.s_len[p] >= W.gen.sm[k]);
+            colv = A.x + xl.x;
+        }
+        gbase += __popc(B);
+        const unsigned msk = __ballot_sync(0xffffffffu, keep);
+        const long long wpos = pos + __popc(msk & lt);
+        if (keep && wpos < pend) {
+            col[wpos] = colv;
+            val[wpos] = v;
+        }
+        pos += __popc(msk);
+    }
+    __syncwarp();
+    return (int)(pos - pos0);
+}
+
+// K6 (set): the same walk.  Each round's slabs become at most three
+// voxel-order ranges each (a slab's first and last ray-order cells, cut by the
+// z planes, are always range endpoints, so a dropped end cell only trims its
+// range), laid end to end; the lanes then copy that flattened list 32 entries
+// at a time onto consecutive slots -- column = slab base + the cell's packed
+// x/y voxel, value = the cell's 2D chord x the row's mm per unit -- and the
+// slab lanes finally overwrite the values of the kept end cells with their cut
+// chords.  A round in which some slab drops a short interior cell takes the
+// general per-cell path.  The 32 rows of a group are consecutive in the CSR,
+// so the whole group is one contiguous output span.
 __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, LorSet ls,
                                                             const ZAx *__restrict__ zt,
                                                             const int64_t *__restrict__ row_ptr,
@@ -861,7 +956,7 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
     const Cells2D &c = m.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     SetWarp &W = m.w[warp];
-    const unsigned lt = (1u << lane) - 1u, le = (2u << lane) - 1u;
+    const unsigned le = (2u << lane) - 1u;
     const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
     const int nxy = im.nx * im.ny;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
@@ -883,87 +978,99 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
             long long pos = row_ptr[T * nrp + j0];
             const long long pend = row_ptr[T * nrp + j0 + nq];  // the group's span ends here
             for (int base = 0; base < total_slabs; base += 32) {
-                // 1. this round's slabs -> voxel-order ranges, flattened
                 SlabOf so;
                 slab_of(rp, incl, base + lane, total_slabs, so);
-                int lo[3], hi[3], ns = 0;
-                if (so.q >= 0) {
-                    const SlabCells s = cut_cells(c, so.zl, so.zh, so.minu);
-                    if (s.cb >= s.ca) {
-                        ns = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
-                        const long long La = piece(c.bnd, s.ca, so.zl, so.zh);
-                        const long long Lb = piece(c.bnd, s.cb, so.zl, so.zh);
-                        W.sa[lane] = make_int4(so.iz * nxy, sorted_pos(c, s.ca, xinc, yinc),
-                                               sorted_pos(c, s.cb, xinc, yinc),
-                                               (La >= so.minu) | ((Lb >= so.minu) << 1));
-                        W.sf[lane] = make_float4(units_to_f(La) * so.to_mm,
-                                                 units_to_f(Lb) * so.to_mm, so.to_mm, 0.0f);
-                        W.sm[lane] = so.minu;
-                    }
+                SlabCells s;
+                s.ca = 0;
+                s.cb = -1;
+                s.inner = 0;
+                if (so.q >= 0) s = cut_cells(c, so.zl, so.zh, so.minu);
+                if (__any_sync(0xffffffffu, s.inner > 0)) {
+                    pos += fill_round_general(m, W, so, s, xinc, yinc, nxy, pos, pend, col, val);
+                    continue;
                 }
-                int len = 0;
+                // 1. this round's slabs -> trimmed voxel-order ranges, flattened
+                int lo[3], hi[3], nr = 0, pa = 0, pb = 0;
+                bool ka = false, kb = false;
+                float va = 0.0f, vb = 0.0f;
+                if (s.cb >= s.ca) {
+                    nr = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
+                    pa = sorted_pos(c, s.ca, xinc, yinc);
+                    pb = sorted_pos(c, s.cb, xinc, yinc);
+                    const long long La = piece(c.bnd, s.ca, so.zl, so.zh);
+                    const long long Lb = piece(c.bnd, s.cb, so.zl, so.zh);
+                    ka = La >= so.minu;
+                    kb = s.cb != s.ca && Lb >= so.minu;
+                    const bool drop_b = s.cb != s.ca && !kb;
+                    va = units_to_f(La) * so.to_mm;
+                    vb = units_to_f(Lb) * so.to_mm;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (k < nr) {
+                            if (!ka) {
+                                if (pa == lo[k]) ++lo[k];
+                                else if (pa == hi[k]) --hi[k];
+                            }
+                            if (drop_b) {
+                                if (pb == lo[k]) ++lo[k];
+                                else if (pb == hi[k]) --hi[k];
+                            }
+                        }
+                }
+                int ns = 0, len = 0;
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                    if (k < ns) len += hi[k] - lo[k] + 1;
-                int inc_len = len, inc_seg = ns;
+                    if (k < nr && hi[k] >= lo[k]) {
+                        ++ns;
+                        len += hi[k] - lo[k] + 1;
+                    }
+                // one scan of (entries << 7 | ranges): at most 96 ranges a round
+                int inc = (len << 7) | ns;
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int a1 = __shfl_up_sync(0xffffffffu, inc_len, o);
-                    const int a2 = __shfl_up_sync(0xffffffffu, inc_seg, o);
-                    if (lane >= o) {
-                        inc_len += a1;
-                        inc_seg += a2;
-                    }
+                    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += t;
                 }
-                const int total = __shfl_sync(0xffffffffu, inc_len, 31);
-                const int nseg = __shfl_sync(0xffffffffu, inc_seg, 31);
-                int off = inc_len - len;
+                const int tot = __shfl_sync(0xffffffffu, inc, 31);
+                const int total = tot >> 7, nseg = tot & 127;
+                int off = (inc >> 7) - len, wr = (inc & 127) - ns;
+                int sa = -1, sb = -1;  // round slots of the kept end cells
+                const int colbase = so.iz * nxy, mm = __float_as_int(so.to_mm);
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                    if (k < ns) {
-                        W.rs[inc_seg - ns + k] = make_int2(off, lo[k] | (lane << 16));
+                    if (k < nr && hi[k] >= lo[k]) {
+                        W.cp.start[wr] = off;
+                        W.cp.rec[wr] = make_int4(lo[k] - off, colbase, mm, 0);
+                        if (pa >= lo[k] && pa <= hi[k]) sa = off + pa - lo[k];
+                        if (pb >= lo[k] && pb <= hi[k]) sb = off + pb - lo[k];
                         off += hi[k] - lo[k] + 1;
+                        ++wr;
                     }
+                W.cp.start[nseg + lane] = 0x7fffffff;  // no range starts past the last
                 __syncwarp();
-                // 2. every lane stores one voxel per step; the ranges starting
+                // 2. every lane copies one cell per step; the ranges starting
                 // inside each 32-entry chunk are found with one OR-reduction
+                const long long room = pend - pos;
+                const int lim = room < (long long)total ? (int)room : total;
+                int32_t *cdst = col + pos;
+                float *vdst = val + pos;
                 int gbase = -1;  // range holding the entry before the chunk
                 for (int e0 = 0; e0 < total; e0 += 32) {
-                    const int gq = gbase + 1 + lane;
-                    unsigned bit = 0u;
-                    if (gq < nseg) {
-                        const int st = W.rs[gq].x - e0;
-                        if (st < 32) bit = 1u << st;
-                    }
-                    const unsigned B = __reduce_or_sync(0xffffffffu, bit);
+                    const unsigned B = __reduce_or_sync(
+                        0xffffffffu, shl_clamped(1u, W.cp.start[gbase + 1 + lane] - e0));
                     const int e = e0 + lane;
-                    bool keep = false;
-                    int colv = 0;
-                    float v = 0.0f;
-                    if (e < total) {
-                        const int gi = gbase + __popc(B & le);
-                        const int2 R = W.rs[gi];
-                        const int p = (R.y & 0xffff) + (e - R.x), k = R.y >> 16;
-                        const int4 A = W.sa[k];
-                        const float4 F = W.sf[k];
-                        const int xy = m.s_xy[p];
-                        const float lf = m.s_lenf[p];
-                        // end cells take their cut chord and keep bit; interior
-                        // cells their 2D chord, kept unless flagged short
-                        const bool isa = p == A.y, isb = p == A.z;
-                        v = isa ? F.x : (isb ? F.y : lf * F.z);
-                        keep = isa ? (A.w & 1) : (isb ? ((A.w >> 1) & 1) : xy >= 0);
-                        if (xy < 0 && !isa && !isb) keep = m.s_len[p] >= W.sm[k];  // rare
-                        colv = A.x + (xy & 0x7fffffff);
+                    if (e < lim) {
+                        const int4 R = W.cp.rec[gbase + __popc(B & le)];
+                        const int2 xl = m.s_xyl[e + R.x];
+                        cdst[e] = R.y + xl.x;
+                        vdst[e] = __int_as_float(xl.y) * __int_as_float(R.z);
                     }
                     gbase += __popc(B);
-                    const unsigned msk = __ballot_sync(0xffffffffu, keep);
-                    const long long wpos = pos + __popc(msk & lt);
-                    if (keep && wpos < pend) {
-                        col[wpos] = colv;
-                        val[wpos] = v;
-                    }
-                    pos += __popc(msk);
                 }
+                __syncwarp();
+                // 3. the cut chords of the kept end cells
+                if (ka && sa < lim) vdst[sa] = va;
+                if (kb && sb < lim) vdst[sb] = vb;
+                pos += total;
                 __syncwarp();
             }
             if (lane == 0 && pos != pend) atomicExch(status, PSF_EDEBUG);

@@ -89,10 +89,11 @@ __host__ __device__ __forceinline__ int cell_at(const long long *bnd, int n, lon
     return first_cell_after(bnd, n, al);
 }
 
-// Cells [ca, cb] overlapping the (clipped) slab interval [zl, zh) and the
-// number of them that keep a chord of at least minu units.
+// Cells [ca, cb] overlapping the (clipped) slab interval [zl, zh), the
+// number of them that keep a chord of at least minu units, and how many of
+// the dropped ones are interior cells (not ca or cb).
 struct SlabCells {
-    int ca, cb, count;
+    int ca, cb, count, inner;
 };
 
 __host__ __device__ __forceinline__ SlabCells cut_cells(const Cells2D &c, long long zl,
@@ -101,6 +102,7 @@ __host__ __device__ __forceinline__ SlabCells cut_cells(const Cells2D &c, long l
     s.ca = 0;
     s.cb = -1;
     s.count = 0;
+    s.inner = 0;
     const int n = c.hdr[0], nflag = c.hdr[2];
     if (zh <= zl || n == 0) return s;
     // parameters are integers: the last cell starting before zh holds zh - 1
@@ -111,16 +113,18 @@ __host__ __device__ __forceinline__ SlabCells cut_cells(const Cells2D &c, long l
     int cnt = s.cb - s.ca + 1;
     if (piece(c.bnd, s.ca, zl, zh) < minu) --cnt;
     if (s.cb != s.ca && piece(c.bnd, s.cb, zl, zh) < minu) --cnt;
+    int inner = 0;
     if (nflag <= SET_MAXF) {
         for (int f = 0; f < nflag; ++f) {
             const int cc = c.flag[f];
-            if (cc > s.ca && cc < s.cb && c.bnd[cc + 1] - c.bnd[cc] < minu) --cnt;
+            if (cc > s.ca && cc < s.cb && c.bnd[cc + 1] - c.bnd[cc] < minu) ++inner;
         }
     } else {
         for (int cc = s.ca + 1; cc < s.cb; ++cc)
-            if (c.bnd[cc + 1] - c.bnd[cc] < minu) --cnt;
+            if (c.bnd[cc + 1] - c.bnd[cc] < minu) ++inner;
     }
-    s.count = cnt;
+    s.count = cnt - inner;
+    s.inner = inner;
     return s;
 }
 
@@ -237,15 +241,28 @@ __device__ __forceinline__ void slab_of(const RingPair &r, int incl, int f, int 
     s.zh = zh < amax ? zh : amax;
 }
 
-// Per-warp work area of the set kernels.
+// Per-warp work area of the set kernels.  A fill round uses one of two
+// layouts: the copy form (every cell of the round's ranges is stored, the
+// ranges trimmed of dropped end cells) or the general form (a keep decision
+// per cell, for rounds where a short interior cell is dropped).
 constexpr int SEG_MAX = 3 * 32;
 struct SetWarp {
-    int2 rs[SEG_MAX];  // range: flattened start, first voxel-order position | slab lane << 16
-    int4 sa[32];       // slab: z offset, voxel-order positions of its first / last
-                       // ray-order cells, keep bits of those two
-    float4 sf[32];     // slab: chords of those two (mm), mm per unit, -
-    long long sm[32];  // slab: shortest stored chord (units)
-    int cnt[32];       // count kernel: voxels of each row of the group
+    union {
+        struct {
+            int start[SEG_MAX + 32];  // range: flattened start; INT_MAX past the last
+            int4 rec[SEG_MAX];        // range: voxel-order position - start, column
+                                      // base of its slab, mm per unit (bits), -
+        } cp;
+        struct {
+            int2 rs[SEG_MAX];  // range: flattened start, first voxel-order position |
+                               // slab lane << 16
+            int4 sa[32];       // slab: z offset, voxel-order positions of its first /
+                               // last ray-order cells, keep bits of those two
+            float4 sf[32];     // slab: chords of those two (mm), mm per unit, -
+            long long sm[32];  // slab: shortest stored chord (units)
+        } gen;
+    };
+    int cnt[32];  // count kernel: voxels of each row of the group
 };
 
 }  // namespace psf
