@@ -265,13 +265,16 @@ def n_comp_classes(s, ls):
     return n
 
 
-def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
+def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv, vb=4):
+    # vb: bytes of a stored value (4 FP32; 2 for BF16/FP16 rows, which add a
+    # 4-byte FP32 scale per row)
+    ent = (4.0 + vb) * nnz + (4.0 * n_lors if vb < 4 else 0.0)
     if name == "set_fill_kernel":  # writes column + chord, reads row_ptr
-        return "hbm", 8.0 * nnz + 8.0 * n_lors, "GB/s"
+        return "hbm", ent + 8.0 * n_lors, "GB/s"
     if name.startswith("csr_fwd"):  # column + value, row_ptr, LOR value, image
-        return "hbm", 8.0 * nnz + 12.0 * n_lors + 4.0 * nv, "GB/s"
+        return "hbm", ent + 12.0 * n_lors + 4.0 * nv, "GB/s"
     if name.startswith("csr_back_pair"):  # column + value, row_ptr, two LOR values, image pair
-        return "hbm", 8.0 * nnz + 16.0 * n_lors + 8.0 * nv, "GB/s"
+        return "hbm", ent + 16.0 * n_lors + 8.0 * nv, "GB/s"
     if name == "spread_q_kernel":  # one FMA per sub-LOR and quadrant entry pair
         # of the classes the kernel computes (one per orbit of the two reflections)
         nsub = (t["n_sub_t"] * t["n_sub_a"]) ** 2
@@ -299,8 +302,16 @@ def kernel_traffic(name):
     return rec["bytes_per_launch"]
 
 
-def roofline(name, ms_per_launch, peaks, clocks, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv):
-    bound, work, unit = kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv)
+def kern_hbm_first(name, kern):
+    """Sort key of the mixed step's roofline kernel: the HBM-bound kernel with
+    the most device time (the 16-bit rows change only the HBM-bound kernels)."""
+    hbm = name == "set_fill_kernel" or name.startswith(("csr_fwd", "csr_back_pair"))
+    return (hbm, kern[name]["ms_per_step"])
+
+
+def roofline(name, ms_per_launch, peaks, clocks, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv,
+             vb=4):
+    bound, work, unit = kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv, vb)
     out = {"kernel": name, "ms_per_launch": ms_per_launch, "bound": bound}
     if bound is None:
         return out
@@ -311,7 +322,7 @@ def roofline(name, ms_per_launch, peaks, clocks, s, t, ls, Wt, Wa, n_lors, n_cls
     else:  # FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x sampled SM clock
         peak, src = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "derived"
         achieved = work / 1e12 / (ms_per_launch * 1e-3)
-    tr = kernel_traffic(name)
+    tr = kernel_traffic(name) if vb == 4 else None
     out.update({"achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": tr / 1e9 if tr is not None else None, "traffic_unit": "GB",
                 "work_per_launch": work, "peak_source": src})
@@ -517,15 +528,69 @@ def run_gpu(args):
              "stage_ms": {k: pev[k][0].elapsed_time(pev[k][1]) for k in plain_stages},
              "form": "per-LOR tracer rows, grid-stride CSR projectors, plain stencil, "
                      "sensitivity as a back-projection of ones; same spread kernel"}
-    del Mp
 
-    # roofline of the dominant kernel: the library kernel with the most device
-    # time per step (CUDA events around each launch, timed region only)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
+
+    # the same step with mixed-precision G rows (outside the timed region):
+    # BF16 values with a per-row FP32 scale, FP32 accumulation; columns and row
+    # pointers are those of the FP32 rows (the same buffers are rewritten)
+    mixed = None
+    if not args.no_mixed:
+        del Mp
+        Mp = None
+        val16 = torch.empty(nnz, dtype=torch.bfloat16, device=dev)
+        scale16 = torch.empty(n_lors, dtype=torch.float32, device=dev)
+        Mm = P.Matrix(row_ptr, col, val16, nv, row_scale=scale16)
+
+        def mixed_step(x_in, y_in):
+            T, eta = P.response_build(s, t, device=dev)
+            C = P.lor_set_classes(s, ls, device=dev)
+            WC = P.bin_spread_classes(s, t, T, eta, ls, C, Wt, Wa)
+            P.sysmat_rows_set_typed(s, im, ls, "bf16", buffers=(row_ptr, col, val16, scale16))
+            Mm.set_spread(s, ls, Wt, Wa, WC)
+            yh = Mm.forward(x_in)
+            r = P.em_ratio(y_in, yh)
+            bp, sens = Mm.back_sens(r)
+            x_out = x_in.clone()
+            P.em_update(x_out, bp, sens, 1e-12)
+            return x_out
+
+        P.sysmat_rows_set_typed(s, im, ls, "bf16", buffers=(row_ptr, col, val16, scale16))
+        Mm.set_spread(s, ls, Wt, Wa, WC0)
+        Mm.autotune()
+        for _ in range(max(1, args.warmup)):
+            mixed_step(x, y_meas)
+        torch.cuda.synchronize()
+        P.timing_enable(True)
+        ma, mb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ma.record(st)
+        for _ in range(args.steps):
+            xm = mixed_step(x, y_meas)
+        mb.record(st)
+        torch.cuda.synchronize()
+        mixed_ms = ma.elapsed_time(mb) / args.steps
+        mk = P.timing_read()
+        P.timing_enable(False)
+        mkern = {k: {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps,
+                     "ms_per_launch": ms / n} for k, (n, ms) in mk.items()}
+        mtop = max(mkern, key=lambda k: kern_hbm_first(k, mkern))
+        # the updated image against the FP32 step's from the same input
+        rel = float((xm - xi).norm() / xi.norm())
+        mixed = {"dtype": "bf16", "row_scale": "f32", "accumulate": "f32",
+                 "ms_per_step": mixed_ms, "value": nnz / (mixed_ms * 1e-3), "unit": UNIT,
+                 "speedup_vs_f32_step": ms_step / mixed_ms,
+                 "image_rel_l2_vs_f32_step": rel,
+                 "kernels": {k: v["ms_per_step"] for k, v in mkern.items()},
+                 "roofline": roofline(mtop, mkern[mtop]["ms_per_launch"], peaks, clocks, s, t,
+                                      ls, Wt, Wa, n_lors, n_cls, nnz, nv, vb=2)}
+        del Mm, val16, scale16
+
+    # roofline of the dominant kernel: the library kernel with the most device
+    # time per step (CUDA events around each launch, timed region only)
     kern = {k: {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps,
                 "ms_per_launch": ms / n} for k, (n, ms) in ktimes.items()}
     top = max(kern, key=lambda k: kern[k]["ms_per_step"])
@@ -549,6 +614,7 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": e2e,
         "plain_fp32": plain,
+        "mixed": mixed,
         "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -915,6 +981,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision (BF16 G rows) step")
     ap.add_argument("--profile-case", choices=["spread", "stencil", "rows", "rows_set", "csr"],
                     help="run one stage on a small-memory setup (for kernel captures)")
     ap.add_argument("--topn-table", action="store_true",

@@ -274,6 +274,25 @@ int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
                         int64_t capacity, int64_t *nnz_out, void *stream);
 
 /*
+ * psf_sysmat_rows_set with a choice of value format (the mixed-precision rows
+ * of the projectors used in Sec. 3's iterations): dtype PSF_F32 is exactly
+ * psf_sysmat_rows_set (row_scale must be NULL); PSF_BF16 / PSF_F16 store each
+ * chord divided by its row's scale, rounded to nearest, in val (device
+ * uint16 [capacity]), with row_scale (device float [n_rows], written with the
+ * fill) = (longest cell chord of the row's transaxial pair in the transaxial
+ * plane) x (the row's length per unit of that chord) -- an upper bound of
+ * the row's chords (mm), so every stored value lies in (0, 1] and the value
+ * is stored x row_scale.  Columns, row pointers, size query (col == NULL:
+ * row_scale may be NULL), capacity rule and synchronisation are those of
+ * psf_sysmat_rows_set.  PSF_EINVAL for another dtype or a missing/extra
+ * row_scale.
+ */
+int psf_sysmat_rows_set_typed(const psf_scanner *scanner, const psf_image *image,
+                              const psf_lor_set *set, int32_t dtype, int64_t *row_ptr,
+                              int32_t *col, void *val, float *row_scale, int64_t capacity,
+                              int64_t *nnz_out, void *stream);
+
+/*
  * psf_sysmat_rows_set_noalloc -- psf_sysmat_rows_set for callers that may not
  * allocate device memory.  The paper has no counterpart; this is a service
  * of the library.  Some callers cannot let a library call cudaMalloc or

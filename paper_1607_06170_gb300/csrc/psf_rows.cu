@@ -724,6 +724,7 @@ struct SetSmem {
     int2 *s_xyl;        // [SET_MAXC] iy * nx + ix, chord as a float (bits, rounded once)
     int32_t *tp_start, *rp_start;
     int *next;          // next ring-pair group of the current transaxial pair
+    unsigned long long *lmax;  // longest cell chord of the current pair (units)
     SetWarp *w;         // [SET_T / 32]
 };
 
@@ -735,14 +736,16 @@ __device__ __forceinline__ void set_smem_layout(SetSmem &m, unsigned char *raw, 
     m.tp_start = reinterpret_cast<int32_t *>(m.s_xyl + SET_MAXC);
     m.rp_start = m.tp_start + ls.Nt + 1;
     m.next = m.rp_start + ls.NR + 1;
+    m.lmax = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(m.next + 1) + 7) & ~uintptr_t(7));
     m.w = reinterpret_cast<SetWarp *>(
-        (reinterpret_cast<uintptr_t>(m.next + 4) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(m.lmax + 1) + 15) & ~uintptr_t(15));
 }
 
 static size_t set_smem(const Scan &sc, const LorSet &ls) {
     return cells_bytes() + sizeof(double) * 2 * sc.R +
            (sizeof(long long) + sizeof(int2)) * SET_MAXC +
-           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + sizeof(int) * 4 + 16 +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + sizeof(int) * 4 + 32 +
            sizeof(SetWarp) * (SET_T / 32) + 64;
 }
 
@@ -759,10 +762,14 @@ __global__ void __launch_bounds__(256) zaxis_kernel(Scan sc, Img im, LorSet ls,
     zaxis_of(sc, im, ra, rb, zt[j]);
 }
 
-// Per transaxial pair: one thread builds the 2D cells, then every thread
-// helps write the voxel-order copies.  Returns after the CTA barrier.
+// Per transaxial pair: the CTA builds the 2D cells, then every thread helps
+// write the voxel-order copies: each cell's packed x/y voxel and its chord as
+// a float -- in parameter units, or (norm: the 16-bit value forms) divided by
+// the pair's longest cell chord, so that every stored value lies in (0, 1].
+// Returns after the CTA barrier.
 __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const Img &im,
-                                               const LorSet &ls, int64_t T, int *status) {
+                                               const LorSet &ls, int64_t T, int *status,
+                                               bool norm = false) {
     __syncthreads();  // the previous pair's readers are done
     const Cells2D &c = m.c;
     int a, b;
@@ -771,18 +778,48 @@ __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const
     if (threadIdx.x == 0) {
         if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
         *m.next = 0;
+        *m.lmax = 1;
     }
     __syncthreads();
+    if (norm) {
+        unsigned long long mx = 1;
+        for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
+            const unsigned long long L = (unsigned long long)(c.bnd[cc + 1] - c.bnd[cc]);
+            mx = L > mx ? L : mx;
+        }
+        atomicMax(m.lmax, mx);
+        __syncthreads();
+    }
+    const float lmax = units_to_f((long long)*m.lmax);
     const bool xinc = c.X->kind == 0 || c.X->inc;
     const bool yinc = c.Y->kind == 0 || c.Y->inc;
     for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
         const int p = sorted_pos(c, cc, xinc, yinc);
         const long long L = c.bnd[cc + 1] - c.bnd[cc];
         m.s_len[p] = L;
-        m.s_xyl[p] = make_int2((int)c.iy[cc] * im.nx + c.ix[cc], float_bits(units_to_f(L)));
+        const float lf = norm ? __fdiv_rn(units_to_f(L), lmax) : units_to_f(L);
+        m.s_xyl[p] = make_int2((int)c.iy[cc] * im.nx + c.ix[cc], float_bits(lf));
     }
     __syncthreads();
 }
+
+// Value of a cut end cell (La units): mm, or (norm) as a fraction of the
+// pair's longest cell chord lmax, like the interior cells.
+__device__ __forceinline__ float end_value(long long La, float to_mm, bool norm, float lmax) {
+    return norm ? __fdiv_rn(units_to_f(La), lmax) : units_to_f(La) * to_mm;
+}
+
+// Store of a row value in the output format (round to nearest).
+template <typename VT>
+__device__ __forceinline__ void st_val(VT *p, float v);
+template <>
+__device__ __forceinline__ void st_val<float>(float *p, float v) { *p = v; }
+template <>
+__device__ __forceinline__ void st_val<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ void st_val<__half>(__half *p, float v) { *p = __float2half_rn(v); }
 
 // Next group of 32 ring pairs for this warp (groups handed out in order).
 __device__ __forceinline__ int set_next_group(int *next) {
@@ -821,10 +858,11 @@ __global__ void __launch_bounds__(SET_T, 3) set_count_kernel(Scan sc, Img im, Lo
                 if (lane >= o) incl += t;
             }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
+            slab_row_put(rp, incl - rp.nsl, W.row[lane]);
             __syncwarp();
             for (int base = 0; base < total; base += 32) {
                 SlabOf so;
-                slab_of(rp, incl, base + lane, total, so);
+                slab_of(W.row, incl, base + lane, total, so);
                 if (so.q >= 0) {
                     const SlabCells s = cut_cells(c, so.zl, so.zh, so.minu);
                     if (s.count) atomicAdd(&W.cnt[so.q], s.count);
@@ -848,11 +886,12 @@ __device__ __forceinline__ unsigned shl_clamped(unsigned v, int n) {
 // General emission of one round (any keep pattern): a keep decision per cell
 // and a ballot compaction of the kept entries.  Used for the rare rounds where
 // a short interior cell of some slab is dropped.  Returns the entries stored.
+template <typename VT>
 __device__ __forceinline__ int fill_round_general(const SetSmem &m, SetWarp &W, const SlabOf &so,
                                                const SlabCells &s, bool xinc, bool yinc,
-                                               int nxy, long long pos, long long pend,
-                                               int32_t *__restrict__ col,
-                                               float *__restrict__ val) {
+                                               int nxy, bool norm, float lmax, long long pos,
+                                               long long pend, int32_t *__restrict__ col,
+                                               VT *__restrict__ val) {
     const Cells2D &c = m.c;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u, le = (2u << lane) - 1u;
@@ -864,8 +903,9 @@ __device__ __forceinline__ int fill_round_general(const SetSmem &m, SetWarp &W, 
         W.gen.sa[lane] = make_int4(so.iz * nxy, sorted_pos(c, s.ca, xinc, yinc),
                                    sorted_pos(c, s.cb, xinc, yinc),
                                    (La >= so.minu) | ((Lb >= so.minu) << 1));
-        W.gen.sf[lane] = make_float4(units_to_f(La) * so.to_mm, units_to_f(Lb) * so.to_mm,
-                                     so.to_mm, 0.0f);
+        W.gen.sf[lane] = make_float4(end_value(La, so.to_mm, norm, lmax),
+                                     end_value(Lb, so.to_mm, norm, lmax),
+                                     norm ? 1.0f : so.to_mm, 0.0f);
         W.gen.sm[lane] = so.minu;
     }
     int len = 0;
@@ -924,7 +964,7 @@ __device__ __forceinline__ int fill_round_general(const SetSmem &m, SetWarp &W, 
         const long long wpos = pos + __popc(msk & lt);
         if (keep && wpos < pend) {
             col[wpos] = colv;
-            val[wpos] = v;
+            st_val(val + wpos, v);
         }
         pos += __popc(msk);
     }
@@ -942,12 +982,17 @@ __device__ __forceinline__ int fill_round_general(const SetSmem &m, SetWarp &W, 
 // chords.  A round in which some slab drops a short interior cell takes the
 // general per-cell path.  The 32 rows of a group are consecutive in the CSR,
 // so the whole group is one contiguous output span.
+template <typename VT>
 __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, LorSet ls,
                                                             const ZAx *__restrict__ zt,
                                                             const int64_t *__restrict__ row_ptr,
                                                             int32_t *__restrict__ col,
-                                                            float *__restrict__ val,
+                                                            VT *__restrict__ val,
+                                                            float *__restrict__ row_scale,
                                                             int *__restrict__ status) {
+    // FP32 values are chords in mm; the 16-bit forms store chord / row scale
+    // with row scale = (pair's longest cell chord) x (row's mm per unit)
+    constexpr bool norm = !std::is_same<VT, float>::value;
     extern __shared__ __align__(16) unsigned char raw[];
     SetSmem m;
     set_smem_layout(m, raw, sc, ls);
@@ -960,10 +1005,11 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
     const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
     const int nxy = im.nx * im.ny;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
-        set_pair_cells(m, sc, im, ls, T, status);
+        set_pair_cells(m, sc, im, ls, T, status, norm);
         const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
         const bool xinc = c.X->kind == 0 || c.X->inc;
         const bool yinc = c.Y->kind == 0 || c.Y->inc;
+        const float lmax = units_to_f((long long)*m.lmax);
         for (int g = set_next_group(m.next); g < ngroups; g = set_next_group(m.next)) {
             const int j0 = g * 32, j = j0 + lane;
             const int nq = nrp - j0 < 32 ? nrp - j0 : 32;
@@ -975,18 +1021,22 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                 if (lane >= o) incl += t;
             }
             const int total_slabs = __shfl_sync(0xffffffffu, incl, 31);
+            slab_row_put(rp, incl - rp.nsl, W.row[lane]);
+            if (norm && j < nrp) row_scale[T * nrp + j] = lmax * rp.to_mm;
             long long pos = row_ptr[T * nrp + j0];
             const long long pend = row_ptr[T * nrp + j0 + nq];  // the group's span ends here
+            __syncwarp();
             for (int base = 0; base < total_slabs; base += 32) {
                 SlabOf so;
-                slab_of(rp, incl, base + lane, total_slabs, so);
+                slab_of(W.row, incl, base + lane, total_slabs, so);
                 SlabCells s;
                 s.ca = 0;
                 s.cb = -1;
                 s.inner = 0;
                 if (so.q >= 0) s = cut_cells(c, so.zl, so.zh, so.minu);
                 if (__any_sync(0xffffffffu, s.inner > 0)) {
-                    pos += fill_round_general(m, W, so, s, xinc, yinc, nxy, pos, pend, col, val);
+                    pos += fill_round_general(m, W, so, s, xinc, yinc, nxy, norm, lmax, pos,
+                                              pend, col, val);
                     continue;
                 }
                 // 1. this round's slabs -> trimmed voxel-order ranges, flattened
@@ -1002,8 +1052,8 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                     ka = La >= so.minu;
                     kb = s.cb != s.ca && Lb >= so.minu;
                     const bool drop_b = s.cb != s.ca && !kb;
-                    va = units_to_f(La) * so.to_mm;
-                    vb = units_to_f(Lb) * so.to_mm;
+                    va = end_value(La, so.to_mm, norm, lmax);
+                    vb = end_value(Lb, so.to_mm, norm, lmax);
 #pragma unroll
                     for (int k = 0; k < 3; ++k)
                         if (k < nr) {
@@ -1034,7 +1084,8 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                 const int total = tot >> 7, nseg = tot & 127;
                 int off = (inc >> 7) - len, wr = (inc & 127) - ns;
                 int sa = -1, sb = -1;  // round slots of the kept end cells
-                const int colbase = so.iz * nxy, mm = __float_as_int(so.to_mm);
+                const int colbase = so.iz * nxy,
+                          mm = __float_as_int(norm ? 1.0f : so.to_mm);  // value per stored chord
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
                     if (k < nr && hi[k] >= lo[k]) {
@@ -1052,7 +1103,7 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                 const long long room = pend - pos;
                 const int lim = room < (long long)total ? (int)room : total;
                 int32_t *cdst = col + pos;
-                float *vdst = val + pos;
+                VT *vdst = val + pos;
                 int gbase = -1;  // range holding the entry before the chunk
                 for (int e0 = 0; e0 < total; e0 += 32) {
                     const unsigned B = __reduce_or_sync(
@@ -1062,14 +1113,14 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                         const int4 R = W.cp.rec[gbase + __popc(B & le)];
                         const int2 xl = m.s_xyl[e + R.x];
                         cdst[e] = R.y + xl.x;
-                        vdst[e] = __int_as_float(xl.y) * __int_as_float(R.z);
+                        st_val(vdst + e, __int_as_float(xl.y) * __int_as_float(R.z));
                     }
                     gbase += __popc(B);
                 }
                 __syncwarp();
                 // 3. the cut chords of the kept end cells
-                if (ka && sa < lim) vdst[sa] = va;
-                if (kb && sb < lim) vdst[sb] = vb;
+                if (ka && sa < lim) st_val(vdst + sa, va);
+                if (kb && sb < lim) st_val(vdst + sb, vb);
                 pos += total;
                 __syncwarp();
             }
@@ -1086,7 +1137,7 @@ namespace psf {
 
 // Validated arguments of the set row generator.
 static int set_args(const psf_scanner *scanner, const psf_image *image, const psf_lor_set *set,
-                    const int64_t *row_ptr, const int32_t *col, const float *val,
+                    const int64_t *row_ptr, const int32_t *col, const void *val,
                     const int64_t *nnz_out, Scan &sc, Img &im, LorSet &ls) {
     int rc = make_scan(scanner, &sc);
     if (rc) return rc;
@@ -1109,9 +1160,25 @@ static size_t set_scratch_bytes(const LorSet &ls, int64_t *ntiles_out) {
 }
 
 // Ring-pair table, count, scan, (size check,) fill.  row_ptr[0] is already 0.
+template <typename VT>
+static int set_fill_launch(const Scan &sc, const Img &im, const LorSet &ls, const ZAx *zt,
+                           const int64_t *row_ptr, int32_t *col, void *val, float *row_scale,
+                           int *status, int grid, size_t shm, cudaStream_t st) {
+    PSF_TRY(cudaFuncSetAttribute(set_fill_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm));
+    {
+        PSF_TIMED("set_fill_kernel", st);
+        set_fill_kernel<VT><<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr, col,
+                                                      static_cast<VT *>(val), row_scale, status);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
 static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t *row_ptr,
-                        int32_t *col, float *val, int64_t capacity, int64_t *nnz_out,
-                        unsigned char *scratch, int64_t ntiles, cudaStream_t st) {
+                        int32_t *col, void *val, int64_t capacity, int64_t *nnz_out,
+                        unsigned char *scratch, int64_t ntiles, cudaStream_t st,
+                        int32_t dtype = PSF_F32, float *row_scale = nullptr) {
     const int64_t n = ls.ntp * ls.nrp;
     int64_t *tiles = reinterpret_cast<int64_t *>(scratch);
     int *status = reinterpret_cast<int *>(tiles + ntiles);
@@ -1127,8 +1194,6 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
     const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
     const size_t shm = set_smem(sc, ls);
     PSF_TRY(cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shm));
-    PSF_TRY(cudaFuncSetAttribute(set_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)shm));
     {
         PSF_TIMED("set_count_kernel", st);
@@ -1146,11 +1211,15 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
     if (h_status) return h_status;
     if (!col) return PSF_OK;
     if (nnz > capacity) return PSF_ECAPACITY;
-    {
-        PSF_TIMED("set_fill_kernel", st);
-        set_fill_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr, col, val, status);
-    }
-    PSF_LAUNCHED();
+    rc = dtype == PSF_BF16
+             ? set_fill_launch<__nv_bfloat16>(sc, im, ls, zt, row_ptr, col, val, row_scale,
+                                              status, grid, shm, st)
+         : dtype == PSF_F16
+             ? set_fill_launch<__half>(sc, im, ls, zt, row_ptr, col, val, row_scale, status,
+                                       grid, shm, st)
+             : set_fill_launch<float>(sc, im, ls, zt, row_ptr, col, val, nullptr, status, grid,
+                                      shm, st);
+    if (rc) return rc;
     PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     PSF_TRY(cudaStreamSynchronize(st));
     return h_status;
@@ -1177,6 +1246,35 @@ extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *
     PSF_TRY(cudaMallocAsync(&scratch, bytes, st));
     rc = set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
                       static_cast<unsigned char *>(scratch), ntiles, st);
+    cudaFreeAsync(scratch, st);
+    return rc;
+}
+
+extern "C" int psf_sysmat_rows_set_typed(const psf_scanner *scanner, const psf_image *image,
+                                         const psf_lor_set *set, int32_t dtype,
+                                         int64_t *row_ptr, int32_t *col, void *val,
+                                         float *row_scale, int64_t capacity, int64_t *nnz_out,
+                                         void *stream) {
+    PSF_RANGE("psf_sysmat_rows_set_typed");
+    if (dtype != PSF_F32 && dtype != PSF_BF16 && dtype != PSF_F16) return PSF_EINVAL;
+    // F32: no scale; 16-bit forms: a scale per row, needed with the fill
+    if (dtype == PSF_F32 ? row_scale != nullptr : (col != nullptr && row_scale == nullptr))
+        return PSF_EINVAL;
+    Scan sc;
+    Img im;
+    LorSet ls;
+    int rc = set_args(scanner, image, set, row_ptr, col, val, nnz_out, sc, im, ls);
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream);
+    *nnz_out = 0;
+    PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
+    if (ls.ntp * ls.nrp == 0) return PSF_OK;
+    int64_t ntiles = 0;
+    const size_t bytes = set_scratch_bytes(ls, &ntiles);
+    void *scratch = nullptr;
+    PSF_TRY(cudaMallocAsync(&scratch, bytes, st));
+    rc = set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
+                      static_cast<unsigned char *>(scratch), ntiles, st, dtype, row_scale);
     cudaFreeAsync(scratch, st);
     return rc;
 }

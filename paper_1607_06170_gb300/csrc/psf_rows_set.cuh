@@ -199,16 +199,43 @@ __device__ __forceinline__ void rp_setup(const Cells2D &c, const ZAx *__restrict
     r.nsl = zb >= za ? zb - za + 1 : 0;
 }
 
+// A row's slab-walk parameters, staged once per group in the warp's shared
+// work area so that a slab lane reads its row's numbers instead of carrying
+// all 32 rows' z axes in registers.
+struct SlabRow {
+    long long A0, DA;             // z axis, linear kind
+    long long amin, amax, minu;   // clipped parameter interval, shortest stored chord
+    double S, D;                  // z axis, nearly parallel kind
+    float to_mm;                  // mm per parameter unit
+    int z0, start;                // first slab, its flattened index in the group
+    int kf;                       // axis kind | fixed voxel << 2
+};
+
+__device__ __forceinline__ void slab_row_put(const RingPair &r, int start, SlabRow &o) {
+    o.A0 = r.Z.A0;
+    o.DA = r.Z.DA;
+    o.amin = r.amin;
+    o.amax = r.amax;
+    o.minu = r.minu;
+    o.S = r.Z.S;
+    o.D = r.Z.D;
+    o.to_mm = r.to_mm;
+    o.z0 = r.z0;
+    o.start = start;
+    o.kf = r.Z.kind | (r.Z.fixed << 2);
+}
+
 // The slab with flattened index f of a warp's 32 rows (incl: inclusive
-// prefix of the rows' slab counts, held one per lane): its row q (-1 when
-// f >= total), slab iz and clipped parameter interval.  Every lane must call.
+// prefix of the rows' slab counts, held one per lane; rows: the rows'
+// parameters): its row q (-1 when f >= total), slab iz and clipped parameter
+// interval.  Every lane must call.
 struct SlabOf {
     int q, iz;
     long long zl, zh, minu;
     float to_mm;
 };
 
-__device__ __forceinline__ void slab_of(const RingPair &r, int incl, int f, int total,
+__device__ __forceinline__ void slab_of(const SlabRow *rows, int incl, int f, int total,
                                         SlabOf &s) {
     const unsigned F = 0xffffffffu;
     int q = 0;  // rows whose slabs end at or before f
@@ -218,27 +245,28 @@ __device__ __forceinline__ void slab_of(const RingPair &r, int incl, int f, int 
         if (v <= f) q += step;
     }
     q = q > 31 ? 31 : q;
-    Axis Z;
-    Z.kind = __shfl_sync(F, r.Z.kind, q);
-    Z.fixed = __shfl_sync(F, r.Z.fixed, q);
-    Z.A0 = __shfl_sync(F, r.Z.A0, q);
-    Z.DA = __shfl_sync(F, r.Z.DA, q);
-    Z.S = __shfl_sync(F, r.Z.S, q);
-    Z.D = __shfl_sync(F, r.Z.D, q);
-    const long long amin = __shfl_sync(F, r.amin, q), amax = __shfl_sync(F, r.amax, q);
-    s.minu = __shfl_sync(F, r.minu, q);
-    s.to_mm = __shfl_sync(F, r.to_mm, q);
-    const int z0 = __shfl_sync(F, r.z0, q);
-    const int start = __shfl_sync(F, incl - r.nsl, q);
     s.q = f < total ? q : -1;
-    s.iz = z0 + (f - start);
     s.zl = 0;
     s.zh = 0;
+    s.minu = 0;
+    s.to_mm = 0.0f;
+    s.iz = 0;
     if (s.q < 0) return;
+    const SlabRow &R = rows[q];
+    Axis Z;
+    Z.kind = R.kf & 3;
+    Z.fixed = R.kf >> 2;
+    Z.A0 = R.A0;
+    Z.DA = R.DA;
+    Z.S = R.S;
+    Z.D = R.D;
+    s.minu = R.minu;
+    s.to_mm = R.to_mm;
+    s.iz = R.z0 + (f - R.start);
     long long zl, zh;
     slab(Z, s.iz, zl, zh);
-    s.zl = zl > amin ? zl : amin;
-    s.zh = zh < amax ? zh : amax;
+    s.zl = zl > R.amin ? zl : R.amin;
+    s.zh = zh < R.amax ? zh : R.amax;
 }
 
 // Per-warp work area of the set kernels.  A fill round uses one of two
@@ -262,7 +290,8 @@ struct SetWarp {
             long long sm[32];  // slab: shortest stored chord (units)
         } gen;
     };
-    int cnt[32];  // count kernel: voxels of each row of the group
+    int cnt[32];       // count kernel: voxels of each row of the group
+    SlabRow row[32];   // the group's rows
 };
 
 }  // namespace psf

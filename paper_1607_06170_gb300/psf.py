@@ -24,7 +24,7 @@ _TORCH_DT = {PSF_F32: torch.float32, PSF_BF16: torch.bfloat16, PSF_F16: torch.fl
 FUNCTIONS = [
     "psf_strerror", "psf_table_size", "psf_response_build", "psf_bin_spread",
     "psf_lor_set_size", "psf_lor_set_list", "psf_lor_set_classes", "psf_sysmat_rows",
-    "psf_sysmat_rows_set", "psf_sysmat_rows_set_noalloc",
+    "psf_sysmat_rows_set", "psf_sysmat_rows_set_noalloc", "psf_sysmat_rows_set_typed",
     "psf_matrix_create", "psf_matrix_set_spread", "psf_matrix_destroy", "psf_forward",
     "psf_back", "psf_em_ratio", "psf_em_update", "psf_timing_enable", "psf_timing_read",
     "psf_matrix_autotune", "psf_matrix_set_launch", "psf_sensitivity", "psf_back_sens",
@@ -80,6 +80,7 @@ _SIGS = {
                                   _P, _P]),
     "psf_sysmat_rows_set": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _P, _P]),
     "psf_sysmat_rows_set_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P, _I64, _P, _P]),
+    "psf_sysmat_rows_set_typed": (C.c_int, [_P, _P, _P, _I32, _P, _P, _P, _P, _I64, _P, _P]),
     "psf_matrix_create": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _I32, _P, _P]),
     "psf_matrix_set_spread": (C.c_int, [_P, _P, _P, _I32, _I32, _P]),
     "psf_matrix_destroy": (C.c_int, [_P]),
@@ -377,6 +378,37 @@ def sysmat_rows_set(sc: dict, im: dict, ls: dict, buffers=None, device="cuda"):
     _ok(L.psf_sysmat_rows_set(C.byref(s), C.byref(i), C.byref(l), _ptr(row_ptr), _ptr(col),
                               _ptr(val), nnz.value, C.byref(nnz), _stream()), "psf_sysmat_rows_set")
     return row_ptr, col[: nnz.value], val[: nnz.value]
+
+
+def sysmat_rows_set_typed(sc: dict, im: dict, ls: dict, dtype: str = "bf16", buffers=None,
+                          device="cuda"):
+    """Geometric rows of a structured set with values in `dtype` ("f32",
+    "bf16", "f16"): (row_ptr, col, val, row_scale); row_scale is None for
+    "f32", else the per-row FP32 scale (value = stored x scale).  buffers =
+    (row_ptr, col, val, row_scale) of sufficient capacity are filled in one
+    call; otherwise a size query precedes the fill."""
+    s, i, l = scanner(sc), image(im), lor_set(ls)
+    dt = _DT[dtype]
+    nnz = C.c_int64()
+    L = lib()
+    if buffers is not None:
+        row_ptr, col, val, row_scale = buffers
+        _ok(L.psf_sysmat_rows_set_typed(C.byref(s), C.byref(i), C.byref(l), dt, _ptr(row_ptr),
+                                        _ptr(col), _ptr(val), _ptr(row_scale), col.numel(),
+                                        C.byref(nnz), _stream()), "psf_sysmat_rows_set_typed")
+        return row_ptr, col[: nnz.value], val[: nnz.value], row_scale
+    n, _ = lor_set_size(sc, ls)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=device)
+    _ok(L.psf_sysmat_rows_set_typed(C.byref(s), C.byref(i), C.byref(l), dt, _ptr(row_ptr), None,
+                                    None, None, 0, C.byref(nnz), _stream()),
+        "psf_sysmat_rows_set_typed(size)")
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=device)
+    val = torch.empty(max(nnz.value, 1), dtype=_TORCH_DT[dt], device=device)
+    row_scale = None if dt == PSF_F32 else torch.empty(n, dtype=torch.float32, device=device)
+    _ok(L.psf_sysmat_rows_set_typed(C.byref(s), C.byref(i), C.byref(l), dt, _ptr(row_ptr),
+                                    _ptr(col), _ptr(val), _ptr(row_scale), nnz.value,
+                                    C.byref(nnz), _stream()), "psf_sysmat_rows_set_typed")
+    return row_ptr, col[: nnz.value], val[: nnz.value], row_scale
 
 
 class Matrix:
