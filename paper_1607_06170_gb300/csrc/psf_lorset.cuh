@@ -73,6 +73,26 @@ struct LorSet {
         *b = tp_lo(lo) + (int)(idx - tp_start[lo]);
     }
 
+    // Transaxial pairs in order of their crystal difference d = b - a, then
+    // of a: the idx-th pair of that order.  Pairs of one difference cycle
+    // through the spread classes of that difference (and their rotations), so
+    // kernels that walk the pairs in this order touch few classes at a time.
+    __device__ void tp_decode_diff(int64_t idx, int *a, int *b) const {
+        const int dlo = Nt / 2 - F > 1 ? Nt / 2 - F : 1, dhi = Nt / 2 + F < Nt - 1 ? Nt / 2 + F : Nt - 1;
+        // pairs with difference below d: sum over e in [dlo, d) of (Nt - e)
+        auto before = [&](int d) -> int64_t {
+            const int64_t k = d - dlo;
+            return k * Nt - k * (dlo + d - 1) / 2;
+        };
+        int lo = dlo, hi = dhi;  // largest d with before(d) <= idx
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (before(mid) <= idx) lo = mid; else hi = mid - 1;
+        }
+        *a = (int)(idx - before(lo));
+        *b = *a + lo;
+    }
+
     __device__ void rp_decode(const int32_t *rp_start, int64_t idx, int *ra, int *rb) const {
         int lo = 0, hi = NR - 1;
         while (lo < hi) {

@@ -63,6 +63,13 @@ struct psf_matrix {
     float *tr_w;
     int32_t *tr_list;
     unsigned long long *tr_nz;
+    // stencil form 5 (plan-owned): the LOR-space input packed into padded
+    // ring-pair planes, and the class spreads re-laid out as one contiguous
+    // slice per (transaxial class, partner offset); wpad_dirty after
+    // psf_matrix_set_spread (rebuilt by the next form-5 stencil)
+    float *pin, *wpad;
+    int64_t pin_n, wpad_n;
+    bool wpad_dirty;
 };
 
 namespace psf {
@@ -1388,9 +1395,12 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
               strip = lane & ((1 << S.lpg_log) - 1);
     const bool active = q < S.nqg && strip < S.nstrip;
     const int dl0 = q * M - Dm, r0 = strip * K;
-    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < ls.ntp; it += gridDim.x) {
+        // pairs in crystal-difference order: concurrent CTAs share the
+        // partners' planes and the classes' weights in L2
         int a, b;
-        ls.tp_decode(tp_start, T, &a, &b);
+        ls.tp_decode_diff(it, &a, &b);
+        const int64_t T = tp_index(ls, tp_start, a, b);
         const int a0 = a % ls.Nb;
         const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
         float acc[M][K];
@@ -1454,6 +1464,339 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
             dt = nxt;
             P = Pn;
         }
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int ra = r0 + k, dl = dl0 + m, rb = ra + dl;
+                    if (ra < NR && dl <= Dm && rb >= 0 && rb < NR)
+                        out[T * nrp + rp_start[ra] + (rb - ls.rp_lo(ra))] = acc[m][k];
+                }
+        }
+    }
+}
+
+// Fifth form, a warp-specialised pipeline.  The tiling and arithmetic are
+// the fourth form's; what changes is how a partner's data reach shared
+// memory.  The input LOR vector is first packed into padded ring-pair planes
+// (st5_pack_kernel: [pair][ring difference][ring + WA], zero padding), and the
+// class spreads into one contiguous slice per (transaxial class, partner
+// offset) in the staged layout (st5_wpad_kernel), so that one producer warp
+// brings each partner's plane and weight slice into a ring of S stages with
+// two cp.async.bulk copies completing on the stage's "full" mbarrier, while
+// the consumer warps compute on earlier stages and release each one on its
+// "empty" mbarrier -- no CTA-wide barrier per partner.  Partners whose first
+// crystal wraps past the last one (a few per cent of the pairs near crystal
+// 0) need the transposed orientation; the producer writes those with plain
+// loads and stores.  Every wait is bounded (the wait limit): a wait that
+// gives up records PSF_ETIMEOUT in the status word, the CTA stops, and the
+// producer first waits (bounded) for the copies it has in flight.
+constexpr int ST5_S = 3;  // stages
+
+struct St5Shape {
+    St4Shape s4;
+    int cthreads;   // consumer threads
+    int plane_f;    // floats of one packed plane (a multiple of 4)
+    int w_f;        // floats of one weight slice
+    int stage_f;    // floats of one stage
+};
+
+__host__ __device__ inline St5Shape st5_shape(const LorSet &ls, int WA) {
+    St5Shape s;
+    s.s4 = st4_shape(ls, WA);
+    s.cthreads = s.s4.threads;
+    s.plane_f = (s.s4.nd * s.s4.PRp + 3) / 4 * 4;
+    s.w_f = s.s4.nd * s.s4.ne * 8;
+    s.stage_f = s.plane_f + s.w_f;
+    return s;
+}
+
+static size_t stencil5_smem_bytes(const LorSet &ls, int WA) {
+    const St5Shape s = st5_shape(ls, WA);
+    return sizeof(float) * (size_t)ST5_S * s.stage_f + sizeof(uint64_t) * 2 * ST5_S +
+           sizeof(short2) * ls.nrp + sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 64;
+}
+
+// in (set order) -> padded planes: cell (ring difference d, ring ra) of pair T
+// at T * plane_f + (d + Dm) * PRp + ra + WA.  Only in-set cells are written,
+// so the zero padding laid down at allocation stays zero.
+__global__ void st5_pack_kernel(LorSet ls, int PRp, int plane_f, int WA,
+                                const float *__restrict__ in, float *__restrict__ pin) {
+    extern __shared__ int32_t pk_pre[];  // rp_start [NR + 1] (tp part unused)
+    int32_t *rp_start = pk_pre + ls.Nt + 1;
+    ls.stage_prefix(pk_pre, rp_start);
+    __syncthreads();
+    const int64_t n = ls.ntp * ls.nrp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t T = i / ls.nrp;
+        int ra, rb;
+        ls.rp_decode(rp_start, i - T * ls.nrp, &ra, &rb);
+        pin[T * plane_f + (int64_t)(rb - ra + ls.Dm) * PRp + ra + WA] = in[i];
+    }
+}
+
+// Class spreads -> staged weight slices: slice (transaxial class ct, partner
+// offset dt) holds, per ring difference d, per e = o1 - o2 (slot e + 2 WA)
+// and per o1 (slot o1 + WA, 8 slots), the weight of window entries
+// e1 = (dt1 + Wt) W2a + o1 + WA and e2 = (dt2 + Wt) W2a + o2 + WA of class
+// (ct, d); 0 where o2 is outside the window.  One CTA per class (ct, d): its
+// E x E window is read into shared memory with coalesced loads, then each
+// of the nwin slices receives its NE x 8 run for this d.
+__global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, const float *__restrict__ w,
+                                float *__restrict__ wpad) {
+    extern __shared__ float wp_win[];  // [E * E]
+    const int W2a = 2 * WA + 1, NE = 4 * WA + 1, nd = 2 * ls.Dm + 1;
+    const int E = (2 * Wt + 1) * W2a, nwin = (2 * Wt + 1) * (2 * Wt + 1);
+    const int run = NE * 8;
+    const int64_t ncls = ls.ntp_cls * nd;
+    for (int64_t cl = blockIdx.x; cl < ncls; cl += gridDim.x) {
+        __syncthreads();  // the previous class's window is no longer read
+        const float *src = w + cl * E * E;
+        for (int i = threadIdx.x; i < E * E; i += blockDim.x) wp_win[i] = __ldg(src + i);
+        __syncthreads();
+        const int64_t ct = cl / nd;
+        const int d = (int)(cl - ct * nd);
+        for (int i = threadIdx.x; i < nwin * run; i += blockDim.x) {
+            const int dt = i / run, r = i - dt * run;
+            const int ei = r >> 3, L1 = r & 7, L2 = L1 - ei + 2 * WA;
+            float v = 0.0f;
+            if (L1 < W2a && L2 >= 0 && L2 < W2a)
+                v = wp_win[((dt / (2 * Wt + 1)) * W2a + L1) * E + (dt % (2 * Wt + 1)) * W2a + L2];
+            wpad[((ct * nwin + dt) * nd + d) * run + r] = v;
+        }
+    }
+}
+
+// Bounded wait for a phase in which the waiting thread may sleep: each test
+// asks the hardware to suspend it for up to hint_ns nanoseconds before the
+// phase completes (so a waiting warp does not take issue slots from the
+// computing ones); false after `limit` SM cycles (at once for a negative
+// limit).
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, long long limit,
+                                                uint32_t hint_ns) {
+    if (limit < 0) return false;
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_init_n(uint64_t *bar, int n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Global -> shared bulk copy completing on `bar` (L2 default policy: the
+// planes and weight slices are re-read by neighbouring pairs).
+__device__ __forceinline__ void bulk_g2s_keep(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <bool adjoint, int WA>
+__global__ void __launch_bounds__(160, 3) stencil5_kernel(LorSet ls, int Wt,
+                                                        const float *__restrict__ w,
+                                                        const float *__restrict__ wpad,
+                                                        const float *__restrict__ in,
+                                                        const float *__restrict__ pin,
+                                                        float *__restrict__ out, int *status,
+                                                        long long limit) {
+    constexpr int NE = 4 * WA + 1, K = ST4_K, M = ST4_M, NV = K + 2 * WA, S = ST5_S;
+    static_assert(NV % 2 == 0, "8-byte plane loads");
+    extern __shared__ __align__(128) unsigned char raw5[];
+    const St5Shape S5 = st5_shape(ls, WA);
+    const St4Shape &S4 = S5.s4;
+    const int Dm = ls.Dm, NR = ls.NR, PRp = S4.PRp;
+    const int nwin = (2 * Wt + 1) * (2 * Wt + 1);
+    float *stages = reinterpret_cast<float *>(raw5);  // [S][stage_f]
+    uint64_t *full = reinterpret_cast<uint64_t *>(stages + (size_t)S * S5.stage_f);
+    uint64_t *empty = full + S;
+    short2 *rp = reinterpret_cast<short2 *>(empty + S);
+    int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    int *abort_flag = rp_start + ls.NR + 1;
+    const int t = threadIdx.x, lane = t & 31;
+    const int ncw = S5.cthreads / 32;  // consumer warps
+    const bool producer = t >= S5.cthreads;
+    for (int i = t; i < S * S5.stage_f; i += blockDim.x) stages[i] = 0.0f;
+    ls.stage_prefix(tp_start, rp_start);
+    if (t == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init_n(full + k, 32);
+            mbar_init_n(empty + k, ncw);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    for (int j = t; j < ls.nrp; j += blockDim.x) {
+        int r1, r2;
+        ls.rp_decode(rp_start, j, &r1, &r2);
+        rp[j] = make_short2((short)r1, (short)r2);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // zeroed stages
+    __syncthreads();
+    const int nrp = (int)ls.nrp;
+    volatile int *abort_v = abort_flag;
+    long long q = 0;  // stages used so far (producer and consumers count alike)
+    if (producer) {
+        const uint32_t pbytes = (uint32_t)S5.plane_f * 4u, wbytes = (uint32_t)S5.w_f * 4u;
+        for (int64_t it = blockIdx.x; it < ls.ntp && !*abort_v; it += gridDim.x) {
+            int a, b;
+            ls.tp_decode_diff(it, &a, &b);
+            const int64_t T = tp_index(ls, tp_start, a, b);
+            const int a0 = a % ls.Nb;
+            const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
+            St3Partner P;
+            for (int dt = st3_next<adjoint>(ls, tp_start, a, b, 0, nwin, Wt, own_cls, P);
+                 dt < nwin; dt = st3_next<adjoint>(ls, tp_start, a, b, dt + 1, nwin, Wt, own_cls, P)) {
+                const int st = (int)(q % S);
+                const long long use = q / S;
+                bool ok = true;
+                if (use > 0) ok = mbar_wait_sleep(empty + st, (uint32_t)((use - 1) & 1), limit, 2000);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok || *abort_v) {
+                    if (lane == 0 && !ok) {
+                        atomicExch(status, PSF_ETIMEOUT);
+                        *abort_v = 1;
+                    }
+                    break;
+                }
+                float *plane = stages + (size_t)st * S5.stage_f, *w3 = plane + S5.plane_f;
+                const int64_t psrc = P.prow / nrp;  // the partner pair's index
+                const uint32_t tx = (P.sw ? 0u : pbytes) + (P.wsw ? 0u : wbytes);
+                if (P.sw || P.wsw) {
+                    // transposed orientation: plain loads and stores by the warp
+                    if (P.sw)
+                        for (int j = lane; j < nrp; j += 32) {
+                            const short2 rr = rp[j];
+                            plane[(rr.x - rr.y + Dm) * PRp + (rr.y + WA)] = __ldg(in + P.prow + j);
+                        }
+                    if (P.wsw) {
+                        constexpr int W2a = 2 * WA + 1;
+                        const int E = (2 * Wt + 1) * W2a;
+                        const float *wc = w + (int64_t)P.cls * S4.nd * E * E;
+                        const int ea0 = (P.dt1 + Wt) * W2a, eb0 = (P.dt2 + Wt) * W2a;
+                        for (int i = lane; i < S4.nd * W2a; i += 32) {
+                            const int d = i / W2a - Dm, u = i % W2a;
+                            const float *s0 = wc + (int64_t)(-d + Dm) * E * E + eb0 * E + ea0 + u;
+                            float *d0 = w3 + ((d + Dm) * NE + u + 2 * WA) * 8 + u;
+#pragma unroll
+                            for (int L2 = 0; L2 < W2a; ++L2) d0[-8 * L2] = __ldg(s0 + L2 * E);
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                }
+                if (lane == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 ::"r"(smem_u32(full + st)), "r"(tx) : "memory");
+                    if (!P.sw) bulk_g2s_keep(plane, pin + psrc * S5.plane_f, pbytes, full + st);
+                    if (!P.wsw)
+                        bulk_g2s_keep(w3, wpad + ((int64_t)P.cls * nwin + dt) * S5.w_f, wbytes,
+                                      full + st);
+                } else {
+                    mbar_arrive(full + st);
+                }
+                ++q;
+            }
+        }
+        // copies still in flight complete before the CTA exits
+        if (lane == 0)
+            for (long long k = q > S ? q - S : 0; k < q; ++k)
+                mbar_wait(full + (int)(k % S), (uint32_t)((k / S) & 1), BK_DRAIN_LIMIT);
+        return;
+    }
+    const int cw = t >> 5;
+    const int qg = (cw << (5 - S4.lpg_log)) + (lane >> S4.lpg_log),
+              strip = lane & ((1 << S4.lpg_log) - 1);
+    const bool active = qg < S4.nqg && strip < S4.nstrip;
+    const int dl0 = qg * M - Dm, r0 = strip * K;
+    for (int64_t it = blockIdx.x; it < ls.ntp; it += gridDim.x) {
+        int a, b;
+        ls.tp_decode_diff(it, &a, &b);
+        const int64_t T = tp_index(ls, tp_start, a, b);
+        const int a0 = a % ls.Nb;
+        const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
+        float acc[M][K];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[m][k] = 0.0f;
+        St3Partner P;
+        bool stop = false;
+        for (int dt = st3_next<adjoint>(ls, tp_start, a, b, 0, nwin, Wt, own_cls, P); dt < nwin;
+             dt = st3_next<adjoint>(ls, tp_start, a, b, dt + 1, nwin, Wt, own_cls, P)) {
+            const int st = (int)(q % S);
+            const bool ok =
+                __all_sync(0xffffffffu, mbar_wait_sleep(full + st, (uint32_t)((q / S) & 1), limit, 200));
+            if (!ok || *abort_v) {
+                if (lane == 0 && !ok) {
+                    atomicExch(status, PSF_ETIMEOUT);
+                    *abort_v = 1;
+                }
+                stop = true;
+                break;
+            }
+            if (active) {
+                const float *plane = stages + (size_t)st * S5.stage_f, *w3 = plane + S5.plane_f;
+#pragma unroll
+                for (int cc = 0; cc < M + 4 * WA; ++cc) {
+                    const int c = dl0 - 2 * WA + cc;  // partner column (ring difference)
+                    if (c < -Dm || c > Dm) continue;
+                    float v[NV];
+                    const float2 *pv =
+                        reinterpret_cast<const float2 *>(plane + (c + Dm) * PRp + r0);
+#pragma unroll
+                    for (int u = 0; u < NV / 2; ++u) {
+                        const float2 f = pv[u];
+                        v[2 * u] = f.x;
+                        v[2 * u + 1] = f.y;
+                    }
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int e = adjoint ? m + 2 * WA - cc : cc - 2 * WA - m;
+                        if (e < -2 * WA || e > 2 * WA) continue;
+                        const int wd = adjoint ? dl0 + m : c;
+                        if (adjoint && wd > Dm) continue;
+                        const float4 *pw = reinterpret_cast<const float4 *>(
+                            w3 + ((wd + Dm) * NE + e + 2 * WA) * 8);
+                        const float4 w0 = pw[0], w1 = pw[1];
+                        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                        for (int o1 = -WA; o1 <= WA; ++o1) {
+                            const int o2 = o1 - e;
+                            if (o2 < -WA || o2 > WA) continue;
+                            const float wgt = wv[o1 + WA];
+#pragma unroll
+                            for (int k = 0; k < K; ++k)
+                                acc[m][k] =
+                                    fmaf(wgt, v[adjoint ? k + o1 + WA : k - o1 + WA], acc[m][k]);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + st);
+            ++q;
+        }
+        if (stop) return;
         if (active) {
 #pragma unroll
             for (int m = 0; m < M; ++m)
@@ -2027,6 +2370,55 @@ static int launch_stencil3(const psf_matrix *m, const float *in, float *out, int
     return PSF_OK;
 }
 
+static bool stencil4_ok(const LorSet &ls, int Wa);
+
+static bool stencil5_ok(const LorSet &ls, int Wt, int Wa) {
+    const St5Shape s5 = st5_shape(ls, Wa);
+    const int64_t E = (2 * (int64_t)Wt + 1) * (2 * Wa + 1);
+    return stencil4_ok(ls, Wa) && s5.cthreads <= 128 &&
+           stencil5_smem_bytes(ls, Wa) <= 72 * 1024 && E * E * 4 <= 48 * 1024;
+}
+
+// Form 5: pack the input into planes, re-lay the class spreads out if they
+// changed since psf_matrix_set_spread, then the pipelined stencil.
+template <bool adjoint, int WA>
+static int launch_stencil5(const psf_matrix *mc, const float *in, float *out, cudaStream_t st) {
+    psf_matrix *m = const_cast<psf_matrix *>(mc);  // the plan's own scratch
+    const St5Shape s5 = st5_shape(m->ls, WA);
+    int dev = 0, sms = 148;
+    PSF_TRY(cudaGetDevice(&dev));
+    PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (m->wpad_dirty) {
+        PSF_TIMED("st5_wpad_kernel", st);
+        st5_wpad_kernel<<<sms * 8, 256, sizeof(float) * m->E * m->E, st>>>(m->ls, m->Wt, WA,
+                                                                           m->cls, m->wpad);
+        m->wpad_dirty = false;
+    }
+    PSF_LAUNCHED();
+    {
+        PSF_TIMED("st5_pack_kernel", st);
+        st5_pack_kernel<<<sms * 8, 256, sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2), st>>>(
+            m->ls, s5.s4.PRp, s5.plane_f, WA, in, m->pin);
+    }
+    PSF_LAUNCHED();
+    const size_t shm = stencil5_smem_bytes(m->ls, WA);
+    PSF_TRY(cudaFuncSetAttribute(stencil5_kernel<adjoint, WA>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    int per_sm = 0;
+    PSF_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stencil5_kernel<adjoint, WA>,
+                                                          s5.cthreads + 32, shm));
+    const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(m->ls.ntp < cap ? m->ls.ntp : cap);
+    {
+        PSF_TIMED(adjoint ? "stencil5_kernel<adjoint>" : "stencil5_kernel<forward>", st);
+        stencil5_kernel<adjoint, WA><<<grid, s5.cthreads + 32, shm, st>>>(
+            m->ls, m->Wt, m->cls, m->wpad, in, m->pin, out, m->status,
+            (long long)wait_limit());
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
 static bool stencil4_ok(const LorSet &ls, int Wa) {
     const St4Shape s4 = st4_shape(ls, Wa);
     return Wa <= 3 && s4.nstrip <= 32 && s4.threads <= 256 &&
@@ -2052,6 +2444,19 @@ static int stencil(const psf_matrix *m, const float *in, float *out, bool adjoin
     PSF_TRY(cudaGetDevice(&dev));
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int form = m->st_form[adjoint ? 1 : 0];
+    if (form == 5 && m->wpad && m->pin && stencil5_ok(m->ls, m->Wt, m->Wa)) {
+        switch (m->Wa * 2 + (adjoint ? 1 : 0)) {
+            case 0: return launch_stencil5<false, 0>(m, in, out, st);
+            case 1: return launch_stencil5<true, 0>(m, in, out, st);
+            case 2: return launch_stencil5<false, 1>(m, in, out, st);
+            case 3: return launch_stencil5<true, 1>(m, in, out, st);
+            case 4: return launch_stencil5<false, 2>(m, in, out, st);
+            case 5: return launch_stencil5<true, 2>(m, in, out, st);
+            case 6: return launch_stencil5<false, 3>(m, in, out, st);
+            case 7: return launch_stencil5<true, 3>(m, in, out, st);
+            default: break;
+        }
+    }
     const bool ok4 = stencil4_ok(m->ls, m->Wa), ok3 = stencil3_ok(m->ls, m->Wa);
     const bool use4 = form != 1 && form != 2 && ok4 && (form != 3 || !ok3);
     const bool use3 = form != 1 && form != 2 && !use4 && ok3;
@@ -2224,6 +2629,27 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
         PSF_TRY(cudaMalloc(&m->csum, sizeof(float) * need));
         m->csum_n = need;
     }
+    if (stencil5_ok(ls, half_t, half_a)) {  // form 5's packed input and weight slices
+        const St5Shape s5 = st5_shape(ls, half_a);
+        const int64_t np = ls.ntp * s5.plane_f;
+        const int64_t nw = ls.ntp_cls * (2 * half_t + 1) * (2 * half_t + 1) * s5.w_f;
+        if (np != m->pin_n) {
+            cudaFree(m->pin);
+            m->pin = nullptr;
+            m->pin_n = 0;
+            PSF_TRY(cudaMalloc(&m->pin, sizeof(float) * np));
+            PSF_TRY(cudaMemset(m->pin, 0, sizeof(float) * np));  // the planes' padding
+            m->pin_n = np;
+        }
+        if (nw > m->wpad_n) {
+            cudaFree(m->wpad);
+            m->wpad = nullptr;
+            m->wpad_n = 0;
+            PSF_TRY(cudaMalloc(&m->wpad, sizeof(float) * nw));
+            m->wpad_n = nw;
+        }
+    }
+    m->wpad_dirty = true;
     drop_transpose(m);
     m->factored = true;
     m->ls = ls;
@@ -2356,6 +2782,8 @@ extern "C" int psf_matrix_destroy(psf_matrix *m) {
     cudaFree(m->tr_src);
     cudaFree(m->tr_w);
     cudaFree(m->tr_list);  // the nonzero count shares this allocation
+    cudaFree(m->pin);
+    cudaFree(m->wpad);
     delete m;
     return PSF_OK;
 }
@@ -2577,7 +3005,8 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
             for (int dir = 0; dir < 2 && !rc; ++dir) {
                 float best_ms = 1e30f;
                 int best_form = 0;
-                for (int form = 3; form <= 4 && !rc; ++form) {
+                const int last = m->wpad && m->pin && stencil5_ok(m->ls, m->Wt, m->Wa) ? 5 : 4;
+                for (int form = 3; form <= last && !rc; ++form) {
                     m->st_form[dir] = form;
                     for (int rep = 0; rep < 2 && !rc; ++rep) {
                         float ms = 0.0f;
@@ -2613,7 +3042,7 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
 
 extern "C" int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form) {
     PSF_RANGE("psf_matrix_set_stencil_form");
-    if (!m || form < 0 || form > 4) return PSF_EINVAL;
+    if (!m || form < 0 || form > 5) return PSF_EINVAL;
     m->st_form[0] = m->st_form[1] = form;
     return PSF_OK;
 }

@@ -204,3 +204,48 @@ def test_factored_projector_tall_scanner(P, orc):
     M.set_stencil_form(1)
     torch.testing.assert_close(M.forward(torch.from_numpy(x).cuda()).cpu(), torch.from_numpy(y),
                                rtol=1e-5, atol=1e-6 * float(abs(y).max()))
+
+
+@pytest.mark.parametrize("form", [1, 2, 3, 4, 5])
+def test_every_stencil_form(P, gpu, ref, orc, form):
+    """Each stencil form of the factored projector (1 plain, 2 register-blocked,
+    3 and 4 cp.async-staged, 5 the bulk-copy pipeline) against the oracle, in
+    both directions; the form's own kernel must be the one that ran."""
+    w = ref["w"]
+    s, ls = w["scanner"], w["lors"]
+    Wt, Wa = w["window"]
+    G = gpu["G"]
+    M = P.Matrix(G[0], G[1], G[2], ref["nv"]).set_spread(s, ls, Wt, Wa, gpu["WC"])
+    M.set_stencil_form(form)
+    x = I.random_image(w["image"], 650).reshape(-1)
+    r = I.random_lor_values(len(ref["L"]), 651)
+    P.timing_enable(True)
+    y = M.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    b = M.back(torch.from_numpy(r).cuda()).cpu().numpy()
+    ran = P.timing_read()
+    P.timing_enable(False)
+    name = {1: "stencil_kernel", 2: "stencil2_kernel", 3: "stencil3_kernel",
+            4: "stencil4_kernel", 5: "stencil5_kernel"}[form]
+    assert f"{name}<forward>" in ran and f"{name}<adjoint>" in ran, sorted(ran)
+    yo = orc.spread_apply(s, ref["L"], ref["W"], Wt, Wa, orc.csr_fwd(ref["G"], x))
+    assert_close(y, yo, 2e-5, 1e-6 * yo.max(), f"form {form} forward")
+    bo = orc.csr_back(ref["G"], orc.spread_adjoint(s, ref["L"], ref["W"], Wt, Wa, r), ref["nv"])
+    assert_close(b, bo, 2e-5, 1e-6 * bo.max(), f"form {form} back")
+
+
+def test_stencil5_follows_new_spreads(P, gpu, ref):
+    """Form 5 keeps a re-laid-out copy of the class spreads: a later
+    psf_matrix_set_spread (here with halved spreads) must be picked up."""
+    w = ref["w"]
+    s, ls = w["scanner"], w["lors"]
+    Wt, Wa = w["window"]
+    G = gpu["G"]
+    M = P.Matrix(G[0], G[1], G[2], ref["nv"]).set_spread(s, ls, Wt, Wa, gpu["WC"])
+    M.set_stencil_form(5)
+    x = torch.from_numpy(I.random_image(w["image"], 652).reshape(-1)).cuda()
+    y1 = M.forward(x).clone()
+    half = gpu["WC"] * 0.5
+    M.set_spread(s, ls, Wt, Wa, half)
+    M.set_stencil_form(5)
+    y2 = M.forward(x)
+    torch.testing.assert_close(y2, 0.5 * y1, rtol=1e-6, atol=1e-7 * y1.abs().max().item())
