@@ -387,9 +387,10 @@ int psf_matrix_destroy(psf_matrix *m);
  * this plan; the pair back-projection of psf_back_sens takes the faster of
  * the back launch and the bulk-staged kernel (psf_back keeps launches that
  * skip rows with y = 0, which a bulk-staged pass cannot); for a
- * factored plan with full-window spreads it also times the two forms of the
- * LOR-space spread stencil in each direction and keeps the faster (call it after
- * psf_matrix_set_spread).  chunk_out / threads_out: host arrays of 2
+ * factored plan with full-window spreads it also times the staged forms of the
+ * LOR-space spread stencil in each direction and keeps the fastest (call it after
+ * psf_matrix_set_spread; the candidates are forms 3, 4 and, when it fits, 5).
+ * chunk_out / threads_out: host arrays of 2
  * (forward, back), may be NULL; chunk -2 = bulk-staged, -1 = streaming tiles,
  * 0 = grid-stride, > 0 = work queue.  Synchronises; allocates a temporary
  * image-sized buffer and, for the bulk-staged forms, a plan-owned table of 8
@@ -426,8 +427,14 @@ int psf_matrix_check(const psf_matrix *m, void *stream);
 /* Stencil form of a factored plan, both directions (no counterpart in the
  * paper): 0 the default (the fastest form that fits, or the autotuner's
  * choice), 1 the plain one-output-per-thread stencil, 2 the register-blocked
- * form, 3 and 4 the cp.async-staged forms (used when they fit).  For
- * comparisons against the plain forms; PSF_EINVAL outside 0..4. */
+ * form, 3 and 4 the cp.async-staged forms, 5 the bulk-copy pipeline (a
+ * producer warp stages each partner's ring-pair plane and weight slice with
+ * cp.async.bulk into a ring of shared-memory stages; it packs the LOR-space
+ * input into padded planes first and, after each psf_matrix_set_spread,
+ * re-lays the class spreads out into plan-owned slices -- so with form 5 the
+ * spreads are read at the first projection after psf_matrix_set_spread, and
+ * changing them in place needs another psf_matrix_set_spread).  Forms that
+ * do not fit the set fall back to the default.  PSF_EINVAL outside 0..5. */
 int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form);
 
 /*
