@@ -876,7 +876,47 @@ def run_listmode(args):
     torch.cuda.synchronize()
     ms_full = a.elapsed_time(b)
     del Mf
+
+    def timed_osem(Mx, sens_x):
+        """One OSEM iteration over the 10 subsets after a one-subset warm-up
+        (CUDA events), with the library's per-kernel times."""
+        listmode_osem(Mx, rows[: lm["subset_events"]].contiguous(), 1, 1, sens=sens_x)
+        torch.cuda.synchronize()
+        P.timing_enable(True)
+        a.record(st)
+        xx = listmode_osem(Mx, rows, n_sub, 1, sens=sens_x)
+        b.record(st)
+        torch.cuda.synchronize()
+        kx = P.timing_read()
+        P.timing_enable(False)
+        return a.elapsed_time(b), xx, {k: round(v[1], 3) for k, v in kx.items() if v[1] > 0.05}
+
+    # BF16 weights: the stored rows in BF16 with a per-row FP32 scale (FP32
+    # accumulation), same columns and row pointers, the same top-N spreads
+    val16 = torch.empty(nnz, dtype=torch.bfloat16, device=dev)
+    sc16 = torch.empty(rp.numel() - 1, dtype=torch.float32, device=dev)
+    P.sysmat_rows_set_typed(s, im, ls, "bf16", buffers=(rp, col, val16, sc16))
+    Mb = P.Matrix(rp, col, val16, nv, row_scale=sc16).set_spread_topn(s, ls, Wt, Wa, idx, wk)
+    Mb.autotune()
+    Mb.build_sparse_adjoint()
+    ms_b, xb, kb = timed_osem(Mb, sens)
+    del Mb, val16, sc16
+    # rows generated on the fly per subset (no stored matrix): the subset's
+    # source rows traced for the masked forward, the rows with S^T r != 0
+    # traced for the back-projection; same top-N spreads, same sensitivity
+    Mo = P.Matrix.traced(s, im, ls).set_spread_topn(s, ls, Wt, Wa, idx, wk)
+    Mo.build_sparse_adjoint()
+    ms_o, xo_img, ko = timed_osem(Mo, sens)
+    Mo.check()
+    del Mo
+    rel = lambda u, v: float((u - v).norm() / v.norm())
     print(json.dumps({
+        "bf16_rows": {"iteration_ms": ms_b, "events_per_s": lm["events"] / (ms_b * 1e-3),
+                      "stored_bytes": int(nnz * 6 + 4 * (rp.numel() - 1)),
+                      "image_rel_l2_vs_f32_rows": rel(xb, x), "kernels_ms": kb},
+        "traced_rows": {"iteration_ms": ms_o, "events_per_s": lm["events"] / (ms_o * 1e-3),
+                        "stored_bytes": 0, "image_rel_l2_vs_f32_rows": rel(xo_img, x),
+                        "kernels_ms": ko},
         "full_window": {"iteration_ms": ms_full, "events_per_s": lm["events"] / (ms_full * 1e-3)},
         "listmode": "RING3D_LM", "events": lm["events"], "subsets": n_sub,
         "n_keep": lm["n_keep"], "n_lors": int(rp.numel() - 1), "nnz": nnz,

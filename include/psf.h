@@ -339,6 +339,21 @@ int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_cols, const in
                       const int32_t *col, const void *val, int32_t dtype, const float *row_scale,
                       void *stream);
 
+/* A projector plan without stored rows, for list-mode reconstruction with
+ * rows generated on the fly (the next step the paper names in Sec. 5): its
+ * rows are the geometric rows of the structured set on the image -- the
+ * rows psf_sysmat_rows_set would store, from the same exact per-LOR tracer,
+ * so equal to them bit for bit -- and every projection traces the rows it
+ * needs, one thread per row: psf_forward_masked only the listed sources of
+ * the masked rows, psf_back after psf_matrix_build_sparse_adjoint only the
+ * rows with S^T y != 0, the full projections every row.  Combine with
+ * psf_matrix_set_spread / _topn for the factored form.  Not tunable
+ * (psf_matrix_autotune, psf_matrix_set_launch: PSF_EINVAL); psf_back_sens
+ * traces twice.  Rows < 2^31, voxels < 2^31; a tracer lookup that does not
+ * settle records PSF_EDEBUG (psf_matrix_check). */
+int psf_matrix_create_otf(psf_matrix **out, const psf_scanner *scanner, const psf_image *image,
+                          const psf_lor_set *set, void *stream);
+
 /* Factored PSF form A = S G (Sec. 2.3) for a structured LOR set: the rows of
  * the plan are G in set order, and S applies the class spreads
  * (device float [n_classes][E][E], kept by pointer) in LOR space. */

@@ -105,6 +105,21 @@ int make_scan(const psf_scanner *s, Scan *out);
 int make_tab(const psf_table_desc *d, const Scan &sc, Tab *out, bool check_reach);
 int make_img(const psf_image *im, Img *out);
 
+struct LorSet;
+
+// Rows traced on the fly (a plan without stored rows, psf_matrix_create_otf):
+// for the rows of a structured set listed in list[0 .. *count) -- or every row
+// when list is NULL -- y[row] = G_row . x (overwrites the listed entries of y),
+// or x += y[row] G_row (FP32 atomics; rows with y == 0 are skipped).  The
+// chords are the per-LOR tracer's, so they equal the stored rows bit for bit.
+// A tracer lookup that did not settle records PSF_EDEBUG in *status.
+int otf_rows_fwd(const Scan &sc, const Img &im, const LorSet &ls, const int32_t *list,
+                 const unsigned long long *count, const float *x, float *y, int *status,
+                 cudaStream_t st);
+int otf_rows_back(const Scan &sc, const Img &im, const LorSet &ls, const int32_t *list,
+                  const unsigned long long *count, const float *y, float *x, int *status,
+                  cudaStream_t st);
+
 // Grid for a grid-stride loop over n items: at most 8 CTAs per SM.
 int grid_for(int64_t n, int block);
 

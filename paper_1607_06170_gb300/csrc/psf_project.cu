@@ -70,6 +70,12 @@ struct psf_matrix {
     float *pin, *wpad;
     int64_t pin_n, wpad_n;
     bool wpad_dirty;
+    // a plan without stored rows (psf_matrix_create_otf): the rows of the
+    // structured set otf_ls are traced whenever they are needed
+    bool otf;
+    psf::Scan otf_sc;
+    psf::Img otf_im;
+    psf::LorSet otf_ls;
 };
 
 namespace psf {
@@ -2309,10 +2315,18 @@ static int rows_back_with(const psf_matrix *m, const float *y, float *x, int chu
 }
 
 static int rows_fwd(const psf_matrix *m, const float *x, float *y, cudaStream_t st) {
+    if (m->otf)
+        return otf_rows_fwd(m->otf_sc, m->otf_im, m->otf_ls, nullptr, nullptr, x, y, m->status,
+                            st);
     return rows_fwd_with(m, x, y, m->fwd_chunk, m->fwd_threads, st);
 }
 
 static int rows_back(const psf_matrix *m, const float *y, float *x, cudaStream_t st) {
+    if (m->otf) {
+        PSF_TRY(cudaMemsetAsync(x, 0, sizeof(float) * m->n_cols, st));
+        return otf_rows_back(m->otf_sc, m->otf_im, m->otf_ls, nullptr, nullptr, y, x, m->status,
+                             st);
+    }
     return rows_back_with(m, y, x, m->wq_chunk, m->wq_threads, st);
 }
 
@@ -2595,6 +2609,36 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     return PSF_OK;
 }
 
+extern "C" int psf_matrix_create_otf(psf_matrix **out, const psf_scanner *scanner,
+                                     const psf_image *image, const psf_lor_set *set,
+                                     void *stream) {
+    PSF_RANGE("psf_matrix_create_otf");
+    if (!out || !scanner || !image || !set) return PSF_EINVAL;
+    Scan sc;
+    Img im;
+    LorSet ls;
+    int rc = make_scan(scanner, &sc);
+    if (!rc) rc = make_img(image, &im);
+    if (!rc) rc = make_lorset(scanner, set, &ls);
+    if (rc) return rc;
+    const int64_t n = ls.ntp * ls.nrp, nv = (int64_t)im.nx * im.ny * im.nz;
+    if (n == 0 || n > INT32_MAX || nv > INT32_MAX) return PSF_EINVAL;
+    // the plan's scratch and status as for stored rows; no row arrays
+    static const int64_t dummy_ptr = 0;
+    rc = psf_matrix_create(out, n, nv, &dummy_ptr, reinterpret_cast<const int32_t *>(&dummy_ptr),
+                           &dummy_ptr, PSF_F32, nullptr, stream);
+    if (rc) return rc;
+    psf_matrix *m = *out;
+    m->row_ptr = nullptr;
+    m->col = nullptr;
+    m->val = nullptr;
+    m->otf = true;
+    m->otf_sc = sc;
+    m->otf_im = im;
+    m->otf_ls = ls;
+    return PSF_OK;
+}
+
 namespace psf {
 // A new spread makes the transpose of the previous one stale.
 static void drop_transpose(psf_matrix *m) {
@@ -2810,6 +2854,8 @@ static int rows_fwd_masked(const psf_matrix *m, const float *x, const float *mas
     list_nonzero(mask, m->n_rows, list, m->queue, st);
     PSF_LAUNCHED();
     PSF_TRY(cudaMemsetAsync(y, 0, sizeof(float) * m->n_rows, st));
+    if (m->otf)
+        return otf_rows_fwd(m->otf_sc, m->otf_im, m->otf_ls, list, m->queue, x, y, m->status, st);
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
         using VT = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
         int dev = 0, sms = 148;
@@ -2863,6 +2909,9 @@ static int rows_back_listed(const psf_matrix *m, const float *y, float *x, cudaS
     PSF_TRY(cudaMemsetAsync(m->tr_nz, 0, sizeof(unsigned long long), st));
     list_nonzero(y, m->n_rows, m->tr_list, m->tr_nz, st);
     PSF_LAUNCHED();
+    if (m->otf)
+        return otf_rows_back(m->otf_sc, m->otf_im, m->otf_ls, m->tr_list, m->tr_nz, y, x,
+                             m->status, st);
     const int chunk = m->wq_chunk > 0 ? m->wq_chunk : 64;
     const int threads = m->wq_chunk > 0 ? m->wq_threads : 256;
     return dispatch_dtype(m->dtype, [&](auto tag) -> int {
@@ -2914,6 +2963,7 @@ extern "C" int psf_matrix_autotune(psf_matrix *m, int32_t *chunk_out, int32_t *t
                                    void *stream) {
     PSF_RANGE("psf_matrix_autotune");
     if (!m) return PSF_EINVAL;
+    if (m->otf) return PSF_EINVAL;  // traced rows: no launch choices to time
     cudaStream_t st = as_stream(stream);
     if (m->n_rows == 0) {
         m->wq_chunk = m->wq_threads = m->fwd_chunk = m->fwd_threads = 0;
@@ -3049,6 +3099,7 @@ extern "C" int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form) {
 
 extern "C" int psf_matrix_set_launch(psf_matrix *m, int32_t chunk, int32_t threads) {
     PSF_RANGE("psf_matrix_set_launch");
+    if (m && m->otf) return PSF_EINVAL;
     if (!m || chunk < -2 || chunk > (1 << 20)) return PSF_EINVAL;
     if (chunk > 0 && (threads < 32 || threads > 1024 || threads % 32)) return PSF_EINVAL;
     if (chunk < 0 && m->dtype != PSF_F32) return PSF_EINVAL;
@@ -3147,6 +3198,10 @@ extern "C" int psf_back_sens(const psf_matrix *m, const float *y, float *x, floa
         qa = m->p;
         qb = y;
     }
+    if (m->otf) {  // two traced passes: A^T 1 then A^T y
+        int rc = rows_back(m, qa, sens, st);
+        return rc ? rc : rows_back(m, qb, x, st);
+    }
     int rc = rows_back_pair(m, qa, qb, m->pair_form, st);
     if (rc) return rc;
     {
@@ -3164,6 +3219,7 @@ namespace psf {
 static int rows_back_pair(const psf_matrix *m, const float *qa, const float *qb, int form,
                           cudaStream_t st) {
     PSF_TRY(cudaMemsetAsync(m->img2, 0, sizeof(float2) * m->n_cols, st));
+    if (m->otf) return PSF_EINVAL;  // psf_back_sens traces twice instead
     if (form == -2) {
         if (!m->bk_first) return PSF_EINVAL;
         int grid = 0;

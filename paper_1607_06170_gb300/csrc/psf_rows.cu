@@ -142,6 +142,80 @@ __global__ void __launch_bounds__(FILL_WARPS * 32) g_fill_kernel(
     }
 }
 
+// ------------------------------------------- rows traced on the fly
+// One thread per row (the per-LOR tracer is sequential along the ray); the
+// row of the set is decoded into its crystal pair, traced, and each voxel's
+// chord is used at once instead of being stored.
+template <bool BACK>
+__global__ void __launch_bounds__(ROWS_THREADS) otf_rows_kernel(
+    Scan sc, Img im, LorSet ls, const int32_t *__restrict__ list,
+    const unsigned long long *__restrict__ count, const float *__restrict__ in,
+    float *__restrict__ out, int *__restrict__ status) {
+    extern __shared__ double cs[];
+    int32_t *tp_start = reinterpret_cast<int32_t *>(cs + 2 * sc.R);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
+    stage_blocks(sc, cs);
+    ls.stage_prefix(tp_start, rp_start);
+    __syncthreads();
+    const int64_t nl = list ? (int64_t)*count : ls.ntp * ls.nrp;
+    const int nx = im.nx, nxy = im.nx * im.ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = list ? list[i] : i;
+        const float yr = BACK ? in[row] : 0.0f;
+        if (BACK && yr == 0.0f) continue;
+        const int64_t T = row / ls.nrp;
+        int a, b, ra, rb;
+        ls.tp_decode(tp_start, T, &a, &b);
+        ls.rp_decode(rp_start, row - T * ls.nrp, &ra, &rb);
+        Ray r;
+        lor_ray(r, sc, im, cs, ra * ls.Nt + a, rb * ls.Nt + b);
+        const float to_mm = r.len_mm * (float)(1.0 / FX);
+        float acc = 0.0f;
+        const bool ok = trace_rows(r, [&](int iz, int iy, int x0, int x1, long long lo,
+                                          long long hi) {
+            const int base = iz * nxy + iy * nx;
+            for (int ix = x0; ix <= x1; ++ix) {
+                const float ch = units_to_f(chord_in_row(r.ax[0], ix, lo, hi)) * to_mm;
+                if (BACK)
+                    atomicAdd(out + base + ix, ch * yr);
+                else
+                    acc = fmaf(ch, __ldg(in + base + ix), acc);
+            }
+        });
+        if (!ok) atomicExch(status, PSF_EDEBUG);
+        if (!BACK) out[row] = acc;
+    }
+}
+
+static int sm_count();
+
+template <bool BACK>
+static int otf_launch(const Scan &sc, const Img &im, const LorSet &ls, const int32_t *list,
+                      const unsigned long long *count, const float *in, float *out, int *status,
+                      cudaStream_t st) {
+    const size_t shm = sizeof(double) * 2 * sc.R + sizeof(int32_t) * (ls.Nt + ls.NR + 2);
+    {
+        PSF_TIMED(BACK ? "otf_rows_kernel<back>" : "otf_rows_kernel<forward>", st);
+        otf_rows_kernel<BACK><<<sm_count() * 16, ROWS_THREADS, shm, st>>>(sc, im, ls, list, count,
+                                                                          in, out, status);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
+int otf_rows_fwd(const Scan &sc, const Img &im, const LorSet &ls, const int32_t *list,
+                 const unsigned long long *count, const float *x, float *y, int *status,
+                 cudaStream_t st) {
+    return otf_launch<false>(sc, im, ls, list, count, x, y, status, st);
+}
+
+int otf_rows_back(const Scan &sc, const Img &im, const LorSet &ls, const int32_t *list,
+                  const unsigned long long *count, const float *y, float *x, int *status,
+                  cudaStream_t st) {
+    return otf_launch<true>(sc, im, ls, list, count, y, x, status, st);
+}
+
 // ---------------------------------------------------------------- K5 scan
 constexpr int SCAN_T = 256, SCAN_V = 8, SCAN_TILE = SCAN_T * SCAN_V;
 

@@ -31,7 +31,7 @@ FUNCTIONS = [
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
     "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
     "psf_matrix_check", "psf_matrix_build_sparse_adjoint", "psf_bin_spread_classes",
-    "psf_set_wait_limit",
+    "psf_set_wait_limit", "psf_matrix_create_otf",
 ]
 
 
@@ -105,6 +105,7 @@ _SIGS = {
     "psf_matrix_check": (C.c_int, [_P, _P]),
     "psf_set_wait_limit": (C.c_int, [_I64]),
     "psf_matrix_build_sparse_adjoint": (C.c_int, [_P, _P]),
+    "psf_matrix_create_otf": (C.c_int, [_P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -425,6 +426,24 @@ class Matrix:
         _ok(lib().psf_matrix_create(C.byref(self._h), self.n_rows, self.n_cols, _ptr(row_ptr),
                                     _ptr(col), _ptr(val), dt, _ptr(row_scale), _stream()),
             "psf_matrix_create")
+
+    @classmethod
+    def traced(cls, sc: dict, im: dict, ls: dict):
+        """A plan without stored rows whose geometric rows (those of the
+        structured set on this image) are traced whenever a projection needs
+        them (psf_matrix_create_otf)."""
+        self = cls.__new__(cls)
+        s, i, l = scanner(sc), image(im), lor_set(ls)
+        self._keep = []
+        n, _ = lor_set_size(sc, ls)
+        self.n_rows = n
+        self.n_cols = int(im["nx"]) * int(im["ny"]) * int(im["nz"])
+        self.topn = 0
+        self.dtype_name = "f32"
+        self._h = C.c_void_p()
+        _ok(lib().psf_matrix_create_otf(C.byref(self._h), C.byref(s), C.byref(i), C.byref(l),
+                                        _stream()), "psf_matrix_create_otf")
+        return self
 
     def set_spread(self, sc: dict, ls: dict, half_t: int, half_a: int, class_spread):
         self._spread = class_spread  # the plan keeps the pointer; keep the tensor alive
