@@ -69,6 +69,7 @@ struct psf_matrix {
     // psf_matrix_set_spread (rebuilt by the next form-5 stencil)
     float *pin, *wpad;
     int64_t pin_n, wpad_n;
+    int wpad_shape;  // window (half_t << 8 | half_a) whose padding slots are zeroed
     bool wpad_dirty;
     // a plan without stored rows (psf_matrix_create_otf): the rows of the
     // structured set otf_ls are traced whenever they are needed
@@ -1547,9 +1548,10 @@ __global__ void st5_pack_kernel(LorSet ls, int PRp, int plane_f, int WA,
 // offset dt) holds, per ring difference d, per e = o1 - o2 (slot e + 2 WA)
 // and per o1 (slot o1 + WA, 8 slots), the weight of window entries
 // e1 = (dt1 + Wt) W2a + o1 + WA and e2 = (dt2 + Wt) W2a + o2 + WA of class
-// (ct, d); 0 where o2 is outside the window.  One CTA per class (ct, d): its
-// E x E window is read into shared memory with coalesced loads, then each
-// of the nwin slices receives its NE x 8 run for this d.
+// (ct, d); 0 where o2 is outside the window (zeroed at allocation).  One CTA
+// per class (ct, d): its E x E window is read into shared memory with
+// coalesced loads, then each of the nwin slices receives the W2a x W2a
+// entries of its NE x 8 run for this d.
 __global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, const float *__restrict__ w,
                                 float *__restrict__ wpad) {
     extern __shared__ float wp_win[];  // [E * E]
@@ -1564,13 +1566,14 @@ __global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, const float *__restri
         __syncthreads();
         const int64_t ct = cl / nd;
         const int d = (int)(cl - ct * nd);
-        for (int i = threadIdx.x; i < nwin * run; i += blockDim.x) {
-            const int dt = i / run, r = i - dt * run;
-            const int ei = r >> 3, L1 = r & 7, L2 = L1 - ei + 2 * WA;
-            float v = 0.0f;
-            if (L1 < W2a && L2 >= 0 && L2 < W2a)
-                v = wp_win[((dt / (2 * Wt + 1)) * W2a + L1) * E + (dt % (2 * Wt + 1)) * W2a + L2];
-            wpad[((ct * nwin + dt) * nd + d) * run + r] = v;
+        // only the W2a x W2a slots that hold a window entry: the others were
+        // zeroed when the slices were allocated and are never written
+        const int nv = W2a * W2a;
+        for (int i = threadIdx.x; i < nwin * nv; i += blockDim.x) {
+            const int dt = i / nv, r = i - dt * nv;
+            const int L1 = r / W2a, L2 = r - L1 * W2a, ei = L1 - L2 + 2 * WA;
+            wpad[((ct * nwin + dt) * nd + d) * run + ei * 8 + L1] =
+                wp_win[((dt / (2 * Wt + 1)) * W2a + L1) * E + (dt % (2 * Wt + 1)) * W2a + L2];
         }
     }
 }
@@ -2689,8 +2692,15 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
             cudaFree(m->wpad);
             m->wpad = nullptr;
             m->wpad_n = 0;
+            m->wpad_shape = -1;
             PSF_TRY(cudaMalloc(&m->wpad, sizeof(float) * nw));
             m->wpad_n = nw;
+        }
+        // the slices' padding slots are zero for this window (never written later)
+        const int shape = (half_t << 8) | half_a;
+        if (m->wpad_shape != shape) {
+            PSF_TRY(cudaMemset(m->wpad, 0, sizeof(float) * nw));
+            m->wpad_shape = shape;
         }
     }
     m->wpad_dirty = true;
