@@ -1499,7 +1499,7 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
 // loads and stores.  Every wait is bounded (the wait limit): a wait that
 // gives up records PSF_ETIMEOUT in the status word, the CTA stops, and the
 // producer first waits (bounded) for the copies it has in flight.
-constexpr int ST5_S = 3;  // stages
+constexpr int ST5_S = 2;  // stages (2 x 20 KB: four CTAs per SM)
 
 struct St5Shape {
     St4Shape s4;
@@ -1619,7 +1619,7 @@ __device__ __forceinline__ void bulk_g2s_keep(void *dst, const void *src, uint32
 }
 
 template <bool adjoint, int WA>
-__global__ void __launch_bounds__(160, 3) stencil5_kernel(LorSet ls, int Wt,
+__global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                                                         const float *__restrict__ w,
                                                         const float *__restrict__ wpad,
                                                         const float *__restrict__ in,
