@@ -186,3 +186,67 @@ def test_bounded_wait_reports_timeout(P, ring2d):
     M.check()  # cleared by the read
     torch.testing.assert_close(M.forward(x), f0, rtol=1e-6, atol=1e-6 * f0.abs().max().item())
     M.check()
+
+
+def test_typed_rows_planar_ring_and_narrow_gap(P):
+    """The 16-bit set rows on the planar rings (one slab per row, the narrow-gap
+    ring with short chords at the block corners): same structure as the FP32
+    rows, values within BF16 rounding of them."""
+    for name in ("RING2D", "RING2D_NARROW"):
+        w = I.workload(name)
+        s, im, ls = w["scanner"], w["image"], w["lors"]
+        ptr, col, val = P.sysmat_rows_set(s, im, ls)
+        ptr2, col2, val2, sc = P.sysmat_rows_set_typed(s, im, ls, "bf16")
+        assert torch.equal(ptr, ptr2) and torch.equal(col, col2)
+        rows = torch.repeat_interleave(torch.arange(ptr.numel() - 1, device="cuda"),
+                                       ptr[1:] - ptr[:-1])
+        err = (val2.float() * sc[rows] - val).abs()
+        assert bool((err <= (2.0 ** -8 + 2.0 ** -22) * val).all()), name
+
+
+def test_stencil_form5_whole_warp_groups(P):
+    """On a scanner of 72 rings (18 ring strips: each group of 4 ring
+    differences takes a whole warp) the pipelined stencil form runs with
+    whole-warp groups and equals the fourth form in both directions."""
+    w = I.workload("RING3D_TALL")
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    nv = im["nx"] * im["ny"] * im["nz"]
+    T, eta = P.response_build(s, t)
+    WC = P.bin_spread(s, t, T, eta, P.lor_set_classes(s, ls), Wt, Wa)
+    G = P.sysmat_rows_set(s, im, ls)
+    M = P.Matrix(G[0], G[1], G[2], nv).set_spread(s, ls, Wt, Wa, WC)
+    x = torch.from_numpy(I.random_image(im, 660).reshape(-1)).cuda()
+    r = torch.from_numpy(I.random_lor_values(M.n_rows, 661)).cuda()
+    out = {}
+    for form in (4, 5):
+        M.set_stencil_form(form)
+        P.timing_enable(True)
+        out[form] = (M.forward(x).clone(), M.back(r).clone())
+        ran = P.timing_read()
+        P.timing_enable(False)
+        assert f"stencil{form}_kernel<forward>" in ran, sorted(ran)
+    for k in range(2):
+        b = out[4][k]
+        torch.testing.assert_close(out[5][k], b, rtol=1e-5, atol=1e-6 * b.abs().max().item())
+
+
+def test_traced_plan_arguments(P):
+    """A traced-row plan refuses launch tuning and a size it cannot index,
+    and its projections of zeros are zero."""
+    from paper_1607_06170_gb300.psf import PSFError
+
+    w = I.workload("RING3D_SMALL")
+    s, im, ls = w["scanner"], w["image"], w["lors"]
+    M = P.Matrix.traced(s, im, ls)
+    with pytest.raises(PSFError):
+        M.autotune()
+    with pytest.raises(PSFError):
+        M.set_launch(64, 256)
+    nv = im["nx"] * im["ny"] * im["nz"]
+    assert torch.count_nonzero(M.forward(torch.zeros(nv, device="cuda"))) == 0
+    assert torch.count_nonzero(M.back(torch.zeros(M.n_rows, device="cuda"))) == 0
+    M.check()
+    big = dict(im, nx=4096, ny=4096, nz=4096)  # 2^36 voxels: beyond int32 voxel ids
+    with pytest.raises(PSFError):
+        P.Matrix.traced(s, big, ls)
