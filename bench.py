@@ -660,6 +660,8 @@ def run_profile_case(args):
             M = P.Matrix(rp, torch.zeros(1, dtype=torch.int32, device=dev),
                          torch.zeros(1, device=dev), nv).set_spread(s, ls, Wt, Wa, WC)
             M.autotune()  # 8 stencil launches (2 forms x 2 directions x 2), then the tuned ones
+            if args.stencil_form is not None:
+                M.set_stencil_form(args.stencil_form)
             x = torch.rand(nv, device=dev)
             y = M.forward(x)
             M.back(y)

@@ -69,7 +69,6 @@ struct psf_matrix {
     // psf_matrix_set_spread (rebuilt by the next form-5 stencil)
     float *pin, *wpad;
     int64_t pin_n, wpad_n;
-    int wpad_shape;  // window (half_t << 8 | half_a) whose padding slots are zeroed
     bool wpad_dirty;
     // a plan without stored rows (psf_matrix_create_otf): the rows of the
     // structured set otf_ls are traced whenever they are needed
@@ -1484,45 +1483,97 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
     }
 }
 
-// Fifth form, a warp-specialised pipeline.  The tiling and arithmetic are
-// the fourth form's; what changes is how a partner's data reach shared
-// memory.  The input LOR vector is first packed into padded ring-pair planes
-// (st5_pack_kernel: [pair][ring difference][ring + WA], zero padding), and the
-// class spreads into one contiguous slice per (transaxial class, partner
-// offset) in the staged layout (st5_wpad_kernel), so that one producer warp
-// brings each partner's plane and weight slice into a ring of S stages with
-// two cp.async.bulk copies completing on the stage's "full" mbarrier, while
-// the consumer warps compute on earlier stages and release each one on its
-// "empty" mbarrier -- no CTA-wide barrier per partner.  Partners whose first
-// crystal wraps past the last one (a few per cent of the pairs near crystal
-// 0) need the transposed orientation; the producer writes those with plain
-// loads and stores.  Every wait is bounded (the wait limit): a wait that
-// gives up records PSF_ETIMEOUT in the status word, the CTA stops, and the
-// producer first waits (bounded) for the copies it has in flight.
-constexpr int ST5_S = 2;  // stages (2 x 20 KB: four CTAs per SM)
+// Fifth form, a warp-specialised pipeline.  A CTA takes transaxial pairs from
+// a pair counter (in the crystal-difference order of tp_decode_diff, so that
+// the pairs in flight on the whole GPU at any moment share their partners'
+// planes and weight slices in L2), and for each pair one producer warp brings
+// each partner's data into a ring of S shared-memory stages with two
+// cp.async.bulk copies completing on the stage's "full" mbarrier, while the
+// consumer warps compute on earlier stages and release each one on its
+// "empty" mbarrier -- no CTA-wide barrier per partner.  The input LOR vector
+// is first packed into padded ring-pair planes (st5_pack_kernel: [pair][ring
+// difference][ring + WA], zero padding), and the class spreads into one
+// contiguous slice per (transaxial class, partner offset) (st5_wpad_kernel).
+// Partners whose first crystal wraps past the last one (a few per cent of the
+// pairs near crystal 0) need the transposed orientation; the producer writes
+// those with plain loads and stores.
+//
+// Consumer tiling: a thread owns M = 4 ring differences x K = 4 rings of the
+// pair's (ring difference, ring) plane; only the (difference group, ring
+// strip) tiles that hold an in-set ring pair get a thread, packed densely into
+// warps (92 of the 8 x 13 tiles of 52 rings with |ra - rb| <= 15: three warps).
+// A tile's 4 + 2 WA plane rows are read with 16-byte loads.
+//
+// Weight slice layout: for ring difference d and offset e = o1 - o2 of the two
+// ends' axial window positions, the run of 2 WA + 1 - |e| weights over o1 =
+// max(-WA, e - WA) ... min(WA, e + WA), padded to a multiple of 4 floats; the
+// runs of one difference take st5_wrun(WA) floats (4 mod 8 words apart, so
+// that the consumer groups' weight loads fall on different banks).
+//
+// Every wait is bounded (the wait limit): a wait that gives up records
+// PSF_ETIMEOUT in the status word, the CTA stops, and the producer first waits
+// (bounded) for the copies it has in flight.
+constexpr int ST5_S = 2;  // stages (2 x 17 KB)
+
+__host__ __device__ constexpr int st5_rlen(int WA, int e) { return 2 * WA + 1 - (e < 0 ? -e : e); }
+// offset of run e (e = -2 WA ... 2 WA + 1) within one ring difference's block
+__host__ __device__ constexpr int st5_roff(int WA, int e) {
+    int o = 0;
+    for (int f = -2 * WA; f < e; ++f) o += (st5_rlen(WA, f) + 3) & ~3;
+    return o;
+}
+__host__ __device__ constexpr int st5_wrun(int WA) {
+    return st5_roff(WA, 2 * WA + 1) % 8 == 0 ? st5_roff(WA, 2 * WA + 1) + 4
+                                             : st5_roff(WA, 2 * WA + 1);
+}
 
 struct St5Shape {
-    St4Shape s4;
-    int cthreads;   // consumer threads
-    int plane_f;    // floats of one packed plane (a multiple of 4)
+    int nd, nstrip, nqg;
+    int ntask;      // (difference group, ring strip) tiles with an in-set ring pair
+    int cthreads;   // consumer threads (ntask rounded up to whole warps)
+    int PRp;        // floats per plane column (a multiple of 4, 4 mod 8)
+    int wrun;       // floats per ring difference in a weight slice
+    int plane_f;    // floats of one packed plane
     int w_f;        // floats of one weight slice
     int stage_f;    // floats of one stage
 };
 
+// Ring strips [s0, s1] of difference group g that hold an in-set ring pair:
+// rings ra with (ra, ra + d) in the set for some difference d of the group.
+__host__ __device__ inline void st5_strips(const LorSet &ls, int g, int *s0, int *s1) {
+    const int d0 = g * ST4_M - ls.Dm;
+    const int d1 = d0 + ST4_M - 1 < ls.Dm ? d0 + ST4_M - 1 : ls.Dm;
+    const int lo = d1 < 0 ? -d1 : 0, hi = ls.NR - 1 - (d0 > 0 ? d0 : 0);
+    const int nstrip = (ls.NR + ST4_K - 1) / ST4_K;
+    *s0 = lo / ST4_K;
+    *s1 = hi / ST4_K < nstrip - 1 ? hi / ST4_K : nstrip - 1;
+}
+
 __host__ __device__ inline St5Shape st5_shape(const LorSet &ls, int WA) {
     St5Shape s;
-    s.s4 = st4_shape(ls, WA);
-    s.cthreads = s.s4.threads;
-    s.plane_f = (s.s4.nd * s.s4.PRp + 3) / 4 * 4;
-    s.w_f = s.s4.nd * s.s4.ne * 8;
+    s.nd = 2 * ls.Dm + 1;
+    s.nstrip = (ls.NR + ST4_K - 1) / ST4_K;
+    s.nqg = (s.nd + ST4_M - 1) / ST4_M;
+    s.ntask = 0;
+    for (int g = 0; g < s.nqg; ++g) {
+        int s0, s1;
+        st5_strips(ls, g, &s0, &s1);
+        s.ntask += s1 - s0 + 1;
+    }
+    s.cthreads = (s.ntask + 31) / 32 * 32;
+    s.PRp = (s.nstrip * ST4_K + 2 * WA + 3) / 4 * 4;  // a strip reads 4 + 2 WA rows
+    if (s.PRp % 8 == 0) s.PRp += 4;
+    s.wrun = st5_wrun(WA);
+    s.plane_f = s.nd * s.PRp;
+    s.w_f = s.nd * s.wrun;
     s.stage_f = s.plane_f + s.w_f;
     return s;
 }
 
 static size_t stencil5_smem_bytes(const LorSet &ls, int WA) {
     const St5Shape s = st5_shape(ls, WA);
-    return sizeof(float) * (size_t)ST5_S * s.stage_f + sizeof(uint64_t) * 2 * ST5_S +
-           sizeof(short2) * ls.nrp + sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 64;
+    return sizeof(float) * (size_t)ST5_S * s.stage_f + sizeof(uint64_t) * 3 * ST5_S +
+           sizeof(short2) * ls.nrp + sizeof(int32_t) * (ls.Nt + ls.NR + 2 + 16) + 64;
 }
 
 // in (set order) -> padded planes: cell (ring difference d, ring ra) of pair T
@@ -1544,20 +1595,20 @@ __global__ void st5_pack_kernel(LorSet ls, int PRp, int plane_f, int WA,
     }
 }
 
-// Class spreads -> staged weight slices: slice (transaxial class ct, partner
-// offset dt) holds, per ring difference d, per e = o1 - o2 (slot e + 2 WA)
-// and per o1 (slot o1 + WA, 8 slots), the weight of window entries
-// e1 = (dt1 + Wt) W2a + o1 + WA and e2 = (dt2 + Wt) W2a + o2 + WA of class
-// (ct, d); 0 where o2 is outside the window (zeroed at allocation).  One CTA
-// per class (ct, d): its E x E window is read into shared memory with
-// coalesced loads, then each of the nwin slices receives the W2a x W2a
-// entries of its NE x 8 run for this d.
-__global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, const float *__restrict__ w,
+// Class spreads -> weight slices: slice (transaxial class ct, partner offset
+// dt) holds, per ring difference d and per e = L1 - L2, the run of window
+// entries e1 = (dt1 + Wt) W2a + L1, e2 = (dt2 + Wt) W2a + L2 of class (ct, d)
+// at d * wrun + roff(e) + L1 - max(e, 0).  One CTA per class (ct, d): its
+// E x E window is read into shared memory with coalesced loads, then each of
+// the nwin slices receives its W2a x W2a entries for this d.  The runs'
+// padding slots are never read.
+__global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, int wrun, const float *__restrict__ w,
                                 float *__restrict__ wpad) {
-    extern __shared__ float wp_win[];  // [E * E]
-    const int W2a = 2 * WA + 1, NE = 4 * WA + 1, nd = 2 * ls.Dm + 1;
+    extern __shared__ float wp_win[];  // [E * E], then the run offsets
+    const int W2a = 2 * WA + 1, nd = 2 * ls.Dm + 1;
     const int E = (2 * Wt + 1) * W2a, nwin = (2 * Wt + 1) * (2 * Wt + 1);
-    const int run = NE * 8;
+    int *roff = reinterpret_cast<int *>(wp_win + E * E);
+    if (threadIdx.x <= 4 * WA) roff[threadIdx.x] = st5_roff(WA, (int)threadIdx.x - 2 * WA);
     const int64_t ncls = ls.ntp_cls * nd;
     for (int64_t cl = blockIdx.x; cl < ncls; cl += gridDim.x) {
         __syncthreads();  // the previous class's window is no longer read
@@ -1566,13 +1617,12 @@ __global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, const float *__restri
         __syncthreads();
         const int64_t ct = cl / nd;
         const int d = (int)(cl - ct * nd);
-        // only the W2a x W2a slots that hold a window entry: the others were
-        // zeroed when the slices were allocated and are never written
         const int nv = W2a * W2a;
         for (int i = threadIdx.x; i < nwin * nv; i += blockDim.x) {
             const int dt = i / nv, r = i - dt * nv;
-            const int L1 = r / W2a, L2 = r - L1 * W2a, ei = L1 - L2 + 2 * WA;
-            wpad[((ct * nwin + dt) * nd + d) * run + ei * 8 + L1] =
+            const int L1 = r / W2a, L2 = r - L1 * W2a, e = L1 - L2;
+            wpad[(ct * nwin + dt) * nd * wrun + d * wrun + roff[e + 2 * WA] + L1 -
+                 (e > 0 ? e : 0)] =
                 wp_win[((dt / (2 * Wt + 1)) * W2a + L1) * E + (dt % (2 * Wt + 1)) * W2a + L2];
         }
     }
@@ -1624,27 +1674,33 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                                                         const float *__restrict__ wpad,
                                                         const float *__restrict__ in,
                                                         const float *__restrict__ pin,
-                                                        float *__restrict__ out, int *status,
+                                                        float *__restrict__ out,
+                                                        unsigned long long *pair_ctr, int *status,
                                                         long long limit) {
-    constexpr int NE = 4 * WA + 1, K = ST4_K, M = ST4_M, NV = K + 2 * WA, S = ST5_S;
-    static_assert(NV % 2 == 0, "8-byte plane loads");
+    constexpr int K = ST4_K, M = ST4_M, S = ST5_S, W2a = 2 * WA + 1;
+    constexpr int NV4 = (K + 2 * WA + 3) / 4;  // 16-byte plane loads per column
     extern __shared__ __align__(128) unsigned char raw5[];
     const St5Shape S5 = st5_shape(ls, WA);
-    const St4Shape &S4 = S5.s4;
-    const int Dm = ls.Dm, NR = ls.NR, PRp = S4.PRp;
+    constexpr int WR = st5_wrun(WA);
+    const int Dm = ls.Dm, NR = ls.NR, PRp = S5.PRp;
     const int nwin = (2 * Wt + 1) * (2 * Wt + 1);
     float *stages = reinterpret_cast<float *>(raw5);  // [S][stage_f]
     uint64_t *full = reinterpret_cast<uint64_t *>(stages + (size_t)S * S5.stage_f);
     uint64_t *empty = full + S;
-    short2 *rp = reinterpret_cast<short2 *>(empty + S);
+    // stage header: the output pair's index (-1: no more pairs) and whether
+    // the stage holds the pair's last partner
+    long long *hdr = reinterpret_cast<long long *>(empty + S);
+    short2 *rp = reinterpret_cast<short2 *>(hdr + S);
     int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
     int32_t *rp_start = tp_start + ls.Nt + 1;
-    int *abort_flag = rp_start + ls.NR + 1;
+    int *roff = rp_start + ls.NR + 1;  // [4 WA + 2]
+    int *abort_flag = roff + 15;
     const int t = threadIdx.x, lane = t & 31;
     const int ncw = S5.cthreads / 32;  // consumer warps
     const bool producer = t >= S5.cthreads;
     for (int i = t; i < S * S5.stage_f; i += blockDim.x) stages[i] = 0.0f;
     ls.stage_prefix(tp_start, rp_start);
+    if (t <= 4 * WA) roff[t] = st5_roff(WA, t - 2 * WA);
     if (t == 0) {
         for (int k = 0; k < S; ++k) {
             mbar_init_n(full + k, 32);
@@ -1666,15 +1722,27 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
     long long q = 0;  // stages used so far (producer and consumers count alike)
     if (producer) {
         const uint32_t pbytes = (uint32_t)S5.plane_f * 4u, wbytes = (uint32_t)S5.w_f * 4u;
-        for (int64_t it = blockIdx.x; it < ls.ntp && !*abort_v; it += gridDim.x) {
-            int a, b;
-            ls.tp_decode_diff(it, &a, &b);
-            const int64_t T = tp_index(ls, tp_start, a, b);
-            const int a0 = a % ls.Nb;
-            const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
-            St3Partner P;
-            for (int dt = st3_next<adjoint>(ls, tp_start, a, b, 0, nwin, Wt, own_cls, P);
-                 dt < nwin; dt = st3_next<adjoint>(ls, tp_start, a, b, dt + 1, nwin, Wt, own_cls, P)) {
+        bool more = true;
+        while (more && !*abort_v) {
+            long long it = 0;
+            if (lane == 0) it = (long long)atomicAdd(pair_ctr, 1ull);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            more = it < ls.ntp;
+            int a = 0, b = 0, own_cls = 0;
+            long long T = -1;
+            St3Partner P, Pn;
+            int dt = -1;  // the end mark's stage when the queue is exhausted
+            if (more) {
+                ls.tp_decode_diff(it, &a, &b);
+                T = tp_index(ls, tp_start, a, b);
+                const int a0 = a % ls.Nb;
+                own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
+                dt = st3_next<adjoint>(ls, tp_start, a, b, 0, nwin, Wt, own_cls, P);
+            }
+            while (dt < nwin) {
+                const int nxt =
+                    more ? st3_next<adjoint>(ls, tp_start, a, b, dt + 1, nwin, Wt, own_cls, Pn)
+                         : nwin;
                 const int st = (int)(q % S);
                 const long long use = q / S;
                 bool ok = true;
@@ -1685,6 +1753,14 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                         atomicExch(status, PSF_ETIMEOUT);
                         *abort_v = 1;
                     }
+                    more = false;
+                    break;
+                }
+                // header: pair index times 2, plus 1 on the pair's last partner
+                if (lane == 0) hdr[st] = more ? 2 * T + (nxt >= nwin ? 1 : 0) : -1;
+                if (!more) {  // end mark: no copies
+                    mbar_arrive(full + st);
+                    ++q;
                     break;
                 }
                 float *plane = stages + (size_t)st * S5.stage_f, *w3 = plane + S5.plane_f;
@@ -1698,16 +1774,18 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                             plane[(rr.x - rr.y + Dm) * PRp + (rr.y + WA)] = __ldg(in + P.prow + j);
                         }
                     if (P.wsw) {
-                        constexpr int W2a = 2 * WA + 1;
                         const int E = (2 * Wt + 1) * W2a;
-                        const float *wc = w + (int64_t)P.cls * S4.nd * E * E;
+                        const float *wc = w + (int64_t)P.cls * S5.nd * E * E;
                         const int ea0 = (P.dt1 + Wt) * W2a, eb0 = (P.dt2 + Wt) * W2a;
-                        for (int i = lane; i < S4.nd * W2a; i += 32) {
-                            const int d = i / W2a - Dm, u = i % W2a;
+                        for (int i = lane; i < S5.nd * W2a; i += 32) {
+                            const int d = i / W2a - Dm, u = i % W2a;  // u = L1
                             const float *s0 = wc + (int64_t)(-d + Dm) * E * E + eb0 * E + ea0 + u;
-                            float *d0 = w3 + ((d + Dm) * NE + u + 2 * WA) * 8 + u;
+                            float *d0 = w3 + (d + Dm) * WR + u;
 #pragma unroll
-                            for (int L2 = 0; L2 < W2a; ++L2) d0[-8 * L2] = __ldg(s0 + L2 * E);
+                            for (int L2 = 0; L2 < W2a; ++L2) {
+                                const int e = u - L2;
+                                d0[roff[e + 2 * WA] - (e > 0 ? e : 0)] = __ldg(s0 + L2 * E);
+                            }
                         }
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1724,6 +1802,8 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                     mbar_arrive(full + st);
                 }
                 ++q;
+                P = Pn;
+                dt = nxt;
             }
         }
         // copies still in flight complete before the CTA exits
@@ -1732,67 +1812,89 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                 mbar_wait(full + (int)(k % S), (uint32_t)((k / S) & 1), BK_DRAIN_LIMIT);
         return;
     }
-    const int cw = t >> 5;
-    const int qg = (cw << (5 - S4.lpg_log)) + (lane >> S4.lpg_log),
-              strip = lane & ((1 << S4.lpg_log) - 1);
-    const bool active = qg < S4.nqg && strip < S4.nstrip;
+    // this thread's tile: the t-th (difference group, ring strip) tile with an
+    // in-set ring pair, groups in order
+    int qg = 0, strip = 0;
+    {
+        int r = t;
+        for (; qg < S5.nqg; ++qg) {
+            int s0, s1;
+            st5_strips(ls, qg, &s0, &s1);
+            if (r <= s1 - s0) {
+                strip = s0 + r;
+                break;
+            }
+            r -= s1 - s0 + 1;
+        }
+    }
+    const bool active = qg < S5.nqg;
     const int dl0 = qg * M - Dm, r0 = strip * K;
-    for (int64_t it = blockIdx.x; it < ls.ntp; it += gridDim.x) {
-        int a, b;
-        ls.tp_decode_diff(it, &a, &b);
-        const int64_t T = tp_index(ls, tp_start, a, b);
-        const int a0 = a % ls.Nb;
-        const int own_cls = tp_index(ls, tp_start, a0, b - (a - a0));
+    // adjoint: the weight row of each owned difference (clamped to the last
+    // one for the padding column past Dm, whose sums are never stored)
+    int wrow[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) wrow[m] = ((dl0 + m < Dm ? dl0 + m : Dm) + Dm) * WR;
+    for (;;) {
+        int st = (int)(q % S);
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait_sleep(full + st, (uint32_t)((q / S) & 1), limit, 200))) {
+            if (lane == 0) {
+                atomicExch(status, PSF_ETIMEOUT);
+                *abort_v = 1;
+            }
+            return;
+        }
+        const long long h0 = hdr[st];
+        if (h0 < 0) return;  // end mark
+        const int64_t T = h0 >> 1;
         float acc[M][K];
 #pragma unroll
         for (int m = 0; m < M; ++m)
 #pragma unroll
             for (int k = 0; k < K; ++k) acc[m][k] = 0.0f;
-        St3Partner P;
-        bool stop = false;
-        for (int dt = st3_next<adjoint>(ls, tp_start, a, b, 0, nwin, Wt, own_cls, P); dt < nwin;
-             dt = st3_next<adjoint>(ls, tp_start, a, b, dt + 1, nwin, Wt, own_cls, P)) {
-            const int st = (int)(q % S);
-            const bool ok =
-                __all_sync(0xffffffffu, mbar_wait_sleep(full + st, (uint32_t)((q / S) & 1), limit, 200));
-            if (!ok || *abort_v) {
-                if (lane == 0 && !ok) {
-                    atomicExch(status, PSF_ETIMEOUT);
-                    *abort_v = 1;
-                }
-                stop = true;
-                break;
-            }
+        for (;;) {
             if (active) {
                 const float *plane = stages + (size_t)st * S5.stage_f, *w3 = plane + S5.plane_f;
 #pragma unroll
                 for (int cc = 0; cc < M + 4 * WA; ++cc) {
                     const int c = dl0 - 2 * WA + cc;  // partner column (ring difference)
                     if (c < -Dm || c > Dm) continue;
-                    float v[NV];
-                    const float2 *pv =
-                        reinterpret_cast<const float2 *>(plane + (c + Dm) * PRp + r0);
+                    float v[4 * NV4];
+                    const float4 *pv =
+                        reinterpret_cast<const float4 *>(plane + (c + Dm) * PRp + r0);
 #pragma unroll
-                    for (int u = 0; u < NV / 2; ++u) {
-                        const float2 f = pv[u];
-                        v[2 * u] = f.x;
-                        v[2 * u + 1] = f.y;
+                    for (int u = 0; u < NV4; ++u) {
+                        const float4 f = pv[u];
+                        v[4 * u] = f.x;
+                        v[4 * u + 1] = f.y;
+                        v[4 * u + 2] = f.z;
+                        v[4 * u + 3] = f.w;
                     }
 #pragma unroll
                     for (int m = 0; m < M; ++m) {
                         const int e = adjoint ? m + 2 * WA - cc : cc - 2 * WA - m;
                         if (e < -2 * WA || e > 2 * WA) continue;
-                        const int wd = adjoint ? dl0 + m : c;
-                        if (adjoint && wd > Dm) continue;
+                        const int n = st5_rlen(WA, e), lo1 = (e - WA > -WA ? e - WA : -WA);
                         const float4 *pw = reinterpret_cast<const float4 *>(
-                            w3 + ((wd + Dm) * NE + e + 2 * WA) * 8);
-                        const float4 w0 = pw[0], w1 = pw[1];
-                        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                            w3 + (adjoint ? wrow[m] : (c + Dm) * WR) + st5_roff(WA, e));
+                        float wv[8];
+                        const float4 w0 = pw[0];
+                        wv[0] = w0.x;
+                        wv[1] = w0.y;
+                        wv[2] = w0.z;
+                        wv[3] = w0.w;
+                        if (n > 4) {
+                            const float4 w1 = pw[1];
+                            wv[4] = w1.x;
+                            wv[5] = w1.y;
+                            wv[6] = w1.z;
+                            wv[7] = w1.w;
+                        }
 #pragma unroll
-                        for (int o1 = -WA; o1 <= WA; ++o1) {
-                            const int o2 = o1 - e;
-                            if (o2 < -WA || o2 > WA) continue;
-                            const float wgt = wv[o1 + WA];
+                        for (int j = 0; j < 8; ++j) {
+                            if (j >= n) continue;
+                            const int o1 = lo1 + j;
+                            const float wgt = wv[j];
 #pragma unroll
                             for (int k = 0; k < K; ++k)
                                 acc[m][k] =
@@ -1801,11 +1903,22 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                     }
                 }
             }
+            const bool last = hdr[st] & 1;
             __syncwarp();
             if (lane == 0) mbar_arrive(empty + st);
             ++q;
+            if (last) break;
+            st = (int)(q % S);
+            const bool ok = __all_sync(
+                0xffffffffu, mbar_wait_sleep(full + st, (uint32_t)((q / S) & 1), limit, 200));
+            if (!ok || *abort_v) {
+                if (lane == 0 && !ok) {
+                    atomicExch(status, PSF_ETIMEOUT);
+                    *abort_v = 1;
+                }
+                return;
+            }
         }
-        if (stop) return;
         if (active) {
 #pragma unroll
             for (int m = 0; m < M; ++m)
@@ -2407,15 +2520,15 @@ static int launch_stencil5(const psf_matrix *mc, const float *in, float *out, cu
     PSF_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (m->wpad_dirty) {
         PSF_TIMED("st5_wpad_kernel", st);
-        st5_wpad_kernel<<<sms * 8, 256, sizeof(float) * m->E * m->E, st>>>(m->ls, m->Wt, WA,
-                                                                           m->cls, m->wpad);
+        st5_wpad_kernel<<<sms * 8, 256, sizeof(float) * m->E * m->E + 16 * sizeof(int), st>>>(
+            m->ls, m->Wt, WA, s5.wrun, m->cls, m->wpad);
         m->wpad_dirty = false;
     }
     PSF_LAUNCHED();
     {
         PSF_TIMED("st5_pack_kernel", st);
         st5_pack_kernel<<<sms * 8, 256, sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2), st>>>(
-            m->ls, s5.s4.PRp, s5.plane_f, WA, in, m->pin);
+            m->ls, s5.PRp, s5.plane_f, WA, in, m->pin);
     }
     PSF_LAUNCHED();
     const size_t shm = stencil5_smem_bytes(m->ls, WA);
@@ -2426,10 +2539,11 @@ static int launch_stencil5(const psf_matrix *mc, const float *in, float *out, cu
                                                           s5.cthreads + 32, shm));
     const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     const int grid = (int)(m->ls.ntp < cap ? m->ls.ntp : cap);
+    PSF_TRY(cudaMemsetAsync(m->queue + 3, 0, sizeof(unsigned long long), st));  // pair counter
     {
         PSF_TIMED(adjoint ? "stencil5_kernel<adjoint>" : "stencil5_kernel<forward>", st);
         stencil5_kernel<adjoint, WA><<<grid, s5.cthreads + 32, shm, st>>>(
-            m->ls, m->Wt, m->cls, m->wpad, in, m->pin, out, m->status,
+            m->ls, m->Wt, m->cls, m->wpad, in, m->pin, out, m->queue + 3, m->status,
             (long long)wait_limit());
     }
     PSF_LAUNCHED();
@@ -2582,8 +2696,9 @@ extern "C" int psf_matrix_create(psf_matrix **out, int64_t n_rows, int64_t n_col
     m->tr_w = nullptr;
     m->tr_list = nullptr;
     m->tr_nz = nullptr;
-    // row counters [2] and the status word, one allocation
-    if (cudaMalloc(&m->queue, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+    // row counters [2], the status word and the stencil's pair counter, one
+    // allocation
+    if (cudaMalloc(&m->queue, 4 * sizeof(unsigned long long)) != cudaSuccess) {
         delete m;
         return PSF_ECUDA;
     }
@@ -2692,15 +2807,8 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
             cudaFree(m->wpad);
             m->wpad = nullptr;
             m->wpad_n = 0;
-            m->wpad_shape = -1;
             PSF_TRY(cudaMalloc(&m->wpad, sizeof(float) * nw));
             m->wpad_n = nw;
-        }
-        // the slices' padding slots are zero for this window (never written later)
-        const int shape = (half_t << 8) | half_a;
-        if (m->wpad_shape != shape) {
-            PSF_TRY(cudaMemset(m->wpad, 0, sizeof(float) * nw));
-            m->wpad_shape = shape;
         }
     }
     m->wpad_dirty = true;
