@@ -1500,15 +1500,16 @@ __global__ void __launch_bounds__(256) stencil4_kernel(LorSet ls, int Wt,
 //
 // Consumer tiling: a thread owns M = 4 ring differences x K = 4 rings of the
 // pair's (ring difference, ring) plane; only the (difference group, ring
-// strip) tiles that hold an in-set ring pair get a thread, packed densely into
-// warps (92 of the 8 x 13 tiles of 52 rings with |ra - rb| <= 15: three warps).
-// A tile's 4 + 2 WA plane rows are read with 16-byte loads.
+// strip) tiles that hold an in-set ring pair get a thread (92 of the 8 x 13
+// tiles of 52 rings with |ra - rb| <= 15: three warps), dealt to threads by
+// shared-memory bank group (st5_tile).  A tile's 4 + 2 WA plane rows are read
+// with 16-byte loads.
 //
 // Weight slice layout: for ring difference d and offset e = o1 - o2 of the two
 // ends' axial window positions, the run of 2 WA + 1 - |e| weights over o1 =
 // max(-WA, e - WA) ... min(WA, e + WA), padded to a multiple of 4 floats; the
-// runs of one difference take st5_wrun(WA) floats (4 mod 8 words apart, so
-// that the consumer groups' weight loads fall on different banks).
+// runs of one difference take st5_wrun(WA) floats, at row offset st5_wrow
+// (skewed so that the difference groups of one warp read different banks).
 //
 // Every wait is bounded (the wait limit): a wait that gives up records
 // PSF_ETIMEOUT in the status word, the CTA stops, and the producer first waits
@@ -1526,6 +1527,12 @@ __host__ __device__ constexpr int st5_wrun(int WA) {
     return st5_roff(WA, 2 * WA + 1) % 8 == 0 ? st5_roff(WA, 2 * WA + 1) + 4
                                              : st5_roff(WA, 2 * WA + 1);
 }
+
+// Offset of ring difference row r (0 ... nd - 1) in a weight slice: rows of
+// wrun floats with 16 bytes of padding after every 4 rows, so that the rows
+// of 8 consecutive consumer groups (4 rows apart, 4 wrun + 4 floats: an odd
+// number of 16-byte units) start in 8 different bank groups.
+__host__ __device__ constexpr int st5_wrow(int r, int wrun) { return r * wrun + 4 * (r >> 2); }
 
 struct St5Shape {
     int nd, nstrip, nqg;
@@ -1560,14 +1567,57 @@ __host__ __device__ inline St5Shape st5_shape(const LorSet &ls, int WA) {
         st5_strips(ls, g, &s0, &s1);
         s.ntask += s1 - s0 + 1;
     }
-    s.cthreads = (s.ntask + 31) / 32 * 32;
     s.PRp = (s.nstrip * ST4_K + 2 * WA + 3) / 4 * 4;  // a strip reads 4 + 2 WA rows
     if (s.PRp % 8 == 0) s.PRp += 4;
+    s.cthreads = (8 * ((s.ntask + 7) / 8) + 31) / 32 * 32;  // see st5_tile
     s.wrun = st5_wrun(WA);
     s.plane_f = s.nd * s.PRp;
-    s.w_f = s.nd * s.wrun;
+    s.w_f = s.nd * s.wrun + 4 * ((s.nd + 3) / 4);
     s.stage_f = s.plane_f + s.w_f;
     return s;
+}
+
+// Consumer thread t's tile (false: none).  A tile's plane reads start at the
+// 16-byte unit 4 g P + strip (+ a per-instruction constant) of the stage,
+// P = PRp / 4, so tiles of different bank groups b = (4 g P + strip) mod 8
+// never share a bank; threads 8 j + b (j < nq = ceil(ntask / 8)) take the
+// j-th tile of group b, and the tiles of groups with more than nq take the
+// remaining threads in order.  In a warp each bank then holds the plane
+// words of 4 threads at most, the 4 wavefronts a 16-byte warp load needs.
+__host__ __device__ __noinline__ bool st5_tile(const LorSet &ls, const St5Shape &S5, int t,
+                                               int *qg, int *strip) {
+    const int nq = (S5.ntask + 7) / 8, P = S5.PRp / 4;
+    if (t >= 8 * nq) return false;
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int g = 0; g < S5.nqg; ++g) {
+        int s0, s1;
+        st5_strips(ls, g, &s0, &s1);
+        for (int s = s0; s <= s1; ++s) ++cnt[(4 * g * P + s) & 7];
+    }
+    const int b = t & 7, j = t >> 3;
+    int want_rank = -1, want_extra = -1;
+    if (j < cnt[b]) {
+        want_rank = j;
+    } else {  // a free thread: its index among the free threads
+        want_extra = 0;
+        for (int u = 0; u < t; ++u)
+            if ((u >> 3) >= cnt[u & 7]) ++want_extra;
+    }
+    int rank[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int extra = 0;
+    for (int g = 0; g < S5.nqg; ++g) {
+        int s0, s1;
+        st5_strips(ls, g, &s0, &s1);
+        for (int s = s0; s <= s1; ++s) {
+            const int bs = (4 * g * P + s) & 7, r = rank[bs]++;
+            if (r < nq ? (bs == b && r == want_rank) : extra++ == want_extra) {
+                *qg = g;
+                *strip = s;
+                return true;
+            }
+        }
+    }
+    return false;
 }
 
 static size_t stencil5_smem_bytes(const LorSet &ls, int WA) {
@@ -1598,12 +1648,12 @@ __global__ void st5_pack_kernel(LorSet ls, int PRp, int plane_f, int WA,
 // Class spreads -> weight slices: slice (transaxial class ct, partner offset
 // dt) holds, per ring difference d and per e = L1 - L2, the run of window
 // entries e1 = (dt1 + Wt) W2a + L1, e2 = (dt2 + Wt) W2a + L2 of class (ct, d)
-// at d * wrun + roff(e) + L1 - max(e, 0).  One CTA per class (ct, d): its
+// at st5_wrow(d) + roff(e) + L1 - max(e, 0).  One CTA per class (ct, d): its
 // E x E window is read into shared memory with coalesced loads, then each of
 // the nwin slices receives its W2a x W2a entries for this d.  The runs'
 // padding slots are never read.
-__global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, int wrun, const float *__restrict__ w,
-                                float *__restrict__ wpad) {
+__global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, int wrun, int w_f,
+                                const float *__restrict__ w, float *__restrict__ wpad) {
     extern __shared__ float wp_win[];  // [E * E], then the run offsets
     const int W2a = 2 * WA + 1, nd = 2 * ls.Dm + 1;
     const int E = (2 * Wt + 1) * W2a, nwin = (2 * Wt + 1) * (2 * Wt + 1);
@@ -1621,7 +1671,7 @@ __global__ void st5_wpad_kernel(LorSet ls, int Wt, int WA, int wrun, const float
         for (int i = threadIdx.x; i < nwin * nv; i += blockDim.x) {
             const int dt = i / nv, r = i - dt * nv;
             const int L1 = r / W2a, L2 = r - L1 * W2a, e = L1 - L2;
-            wpad[(ct * nwin + dt) * nd * wrun + d * wrun + roff[e + 2 * WA] + L1 -
+            wpad[(ct * nwin + dt) * w_f + st5_wrow(d, wrun) + roff[e + 2 * WA] + L1 -
                  (e > 0 ? e : 0)] =
                 wp_win[((dt / (2 * Wt + 1)) * W2a + L1) * E + (dt % (2 * Wt + 1)) * W2a + L2];
         }
@@ -1780,7 +1830,7 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                         for (int i = lane; i < S5.nd * W2a; i += 32) {
                             const int d = i / W2a - Dm, u = i % W2a;  // u = L1
                             const float *s0 = wc + (int64_t)(-d + Dm) * E * E + eb0 * E + ea0 + u;
-                            float *d0 = w3 + (d + Dm) * WR + u;
+                            float *d0 = w3 + st5_wrow(d + Dm, WR) + u;
 #pragma unroll
                             for (int L2 = 0; L2 < W2a; ++L2) {
                                 const int e = u - L2;
@@ -1812,28 +1862,17 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                 mbar_wait(full + (int)(k % S), (uint32_t)((k / S) & 1), BK_DRAIN_LIMIT);
         return;
     }
-    // this thread's tile: the t-th (difference group, ring strip) tile with an
-    // in-set ring pair, groups in order
     int qg = 0, strip = 0;
-    {
-        int r = t;
-        for (; qg < S5.nqg; ++qg) {
-            int s0, s1;
-            st5_strips(ls, qg, &s0, &s1);
-            if (r <= s1 - s0) {
-                strip = s0 + r;
-                break;
-            }
-            r -= s1 - s0 + 1;
-        }
-    }
-    const bool active = qg < S5.nqg;
+    const bool active = st5_tile(ls, S5, t, &qg, &strip);
     const int dl0 = qg * M - Dm, r0 = strip * K;
+    // forward: the weight row of partner column c = dl0 - 2 WA + cc is row
+    // 4 qg + cc - 2 WA, at st5_wrow = wq + a constant of cc
+    const int wq = qg * (4 * WR + 4);
     // adjoint: the weight row of each owned difference (clamped to the last
     // one for the padding column past Dm, whose sums are never stored)
     int wrow[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) wrow[m] = ((dl0 + m < Dm ? dl0 + m : Dm) + Dm) * WR;
+    for (int m = 0; m < M; ++m) wrow[m] = st5_wrow((dl0 + m < Dm ? dl0 + m : Dm) + Dm, WR);
     for (;;) {
         int st = (int)(q % S);
         if (!__all_sync(0xffffffffu,
@@ -1876,7 +1915,8 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
                         if (e < -2 * WA || e > 2 * WA) continue;
                         const int n = st5_rlen(WA, e), lo1 = (e - WA > -WA ? e - WA : -WA);
                         const float4 *pw = reinterpret_cast<const float4 *>(
-                            w3 + (adjoint ? wrow[m] : (c + Dm) * WR) + st5_roff(WA, e));
+                            w3 + (adjoint ? wrow[m] : wq + st5_wrow(cc - 2 * WA, WR)) +
+                            st5_roff(WA, e));
                         float wv[8];
                         const float4 w0 = pw[0];
                         wv[0] = w0.x;
@@ -2521,7 +2561,7 @@ static int launch_stencil5(const psf_matrix *mc, const float *in, float *out, cu
     if (m->wpad_dirty) {
         PSF_TIMED("st5_wpad_kernel", st);
         st5_wpad_kernel<<<sms * 8, 256, sizeof(float) * m->E * m->E + 16 * sizeof(int), st>>>(
-            m->ls, m->Wt, WA, s5.wrun, m->cls, m->wpad);
+            m->ls, m->Wt, WA, s5.wrun, s5.w_f, m->cls, m->wpad);
         m->wpad_dirty = false;
     }
     PSF_LAUNCHED();
