@@ -1049,7 +1049,9 @@ __device__ __forceinline__ int fill_round_general(const SetSmem &m, SetWarp &W, 
 // K6 (set): the same walk.  Each round's slabs become at most three
 // voxel-order ranges each (a slab's first and last ray-order cells, cut by the
 // z planes, are always range endpoints, so a dropped end cell only trims its
-// range), laid end to end; the lanes then copy that flattened list 32 entries
+// range; one range when the segment's x and y directions have the same sign,
+// voxel order then being ray order or its reverse), laid end to end; the lanes
+// then copy that flattened list 32 entries
 // at a time onto consecutive slots -- column = slab base + the cell's packed
 // x/y voxel, value = the cell's 2D chord x the row's mm per unit -- and the
 // slab lanes finally overwrite the values of the kept end cells with their cut
@@ -1118,9 +1120,18 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                 bool ka = false, kb = false;
                 float va = 0.0f, vb = 0.0f;
                 if (s.cb >= s.ca) {
-                    nr = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
-                    pa = sorted_pos(c, s.ca, xinc, yinc);
-                    pb = sorted_pos(c, s.cb, xinc, yinc);
+                    if (xinc == yinc) {  // voxel order is ray order or its reverse
+                        const int nc1 = c.hdr[0] - 1;
+                        pa = xinc ? s.ca : nc1 - s.ca;
+                        pb = xinc ? s.cb : nc1 - s.cb;
+                        nr = 1;
+                        lo[0] = pa < pb ? pa : pb;
+                        hi[0] = pa < pb ? pb : pa;
+                    } else {
+                        nr = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
+                        pa = sorted_pos(c, s.ca, xinc, yinc);
+                        pb = sorted_pos(c, s.cb, xinc, yinc);
+                    }
                     const long long La = piece(c.bnd, s.ca, so.zl, so.zh);
                     const long long Lb = piece(c.bnd, s.cb, so.zl, so.zh);
                     ka = La >= so.minu;
@@ -1179,6 +1190,7 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                 int32_t *cdst = col + pos;
                 VT *vdst = val + pos;
                 int gbase = -1;  // range holding the entry before the chunk
+#pragma unroll 2
                 for (int e0 = 0; e0 < total; e0 += 32) {
                     const unsigned B = __reduce_or_sync(
                         0xffffffffu, shl_clamped(1u, W.cp.start[gbase + 1 + lane] - e0));
