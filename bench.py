@@ -672,6 +672,7 @@ def run_profile_case(args):
         if case in ("rows", "csr"):
             L = P.lor_set_list(s, ls, device=dev)[: 2_000_000].contiguous()
             rp, col, val, _ = P.sysmat_rows(s, im, L)
+            info = {"rows": rp.numel() - 1, "nnz": col.numel()}
             if case == "csr":
                 M = P.Matrix(rp, col, val, nv)
                 M.set_launch(64, 512)  # the work-queue launch the bench step's autotuner picks
@@ -679,7 +680,8 @@ def run_profile_case(args):
                 M.back(y)
                 M.back_sens(y)
         torch.cuda.synchronize()
-    print(json.dumps({"profile_case": case, "ok": True, **(info if case == "rows_set" else {})}))
+    print(json.dumps({"profile_case": case, "ok": True,
+                      **(info if case in ("rows_set", "rows", "csr") else {})}))
 
 
 VH_K = (60, 240, 960, 3840, 15360)
