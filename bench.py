@@ -402,7 +402,7 @@ def run_gpu(args):
 
     # one projector plan over the reused CSR buffers; measured data = noiseless
     # projection of the phantom (computed once)
-    M = P.Matrix(row_ptr, col, val, nv)
+    M = P.Matrix(row_ptr, col, val, nv).set_image(im)
     T0, e0 = P.response_build(s, t, device=dev)
     WC0 = P.bin_spread_classes(s, t, T0, e0, ls, P.lor_set_classes(s, ls, device=dev), Wt, Wa)
     P.sysmat_rows_set(s, im, ls, buffers=(row_ptr, col, val))
@@ -546,7 +546,7 @@ def run_gpu(args):
         Mp = None
         val16 = torch.empty(nnz, dtype=torch.bfloat16, device=dev)
         scale16 = torch.empty(n_lors, dtype=torch.float32, device=dev)
-        Mm = P.Matrix(row_ptr, col, val16, nv, row_scale=scale16)
+        Mm = P.Matrix(row_ptr, col, val16, nv, row_scale=scale16).set_image(im)
 
         def mixed_step(x_in, y_in):
             T, eta = P.response_build(s, t, device=dev)
@@ -635,7 +635,9 @@ def run_profile_case(args):
     """One stage of the step on a configuration small enough for a kernel
     capture (a few GB on the device): 'spread' = all class spreads; 'stencil' =
     S and S^T over the full LOR space with an empty G; 'rows' = chord rows of
-    the first 2M LORs; 'csr' = forward/back with those rows."""
+    the first 2M LORs; 'csr' = forward/back with those rows; 'back_patch' =
+    the pair back-projection with per-pair shared-memory accumulation over the
+    rows of the fan narrowed to +-10."""
     import torch
 
     from paper_1607_06170_gb300 import build as B
@@ -665,6 +667,18 @@ def run_profile_case(args):
             x = torch.rand(nv, device=dev)
             y = M.forward(x)
             M.back(y)
+        if case == "back_patch":
+            # the bench step's pair back-projection over the rows of the fan
+            # narrowed to +-10 (~7 GB on the device), pair form -3
+            l10 = dict(ls, fan_half=10)
+            T, eta = P.response_build(s, t, device=dev)
+            WC = P.bin_spread_classes(s, t, T, eta, l10, P.lor_set_classes(s, l10, device=dev),
+                                      Wt, Wa)
+            rp, col, val = P.sysmat_rows_set(s, im, l10, device=dev)
+            M = P.Matrix(rp, col, val, nv).set_spread(s, l10, Wt, Wa, WC).set_image(im)
+            r = torch.rand(rp.numel() - 1, device=dev)
+            M.back_sens(r)
+            info = {"rows": rp.numel() - 1, "nnz": col.numel()}
         if case == "rows_set":
             # same scanner and image, fan narrowed to +-10 so the capture holds ~3 GB
             rows_set = P.sysmat_rows_set(s, im, dict(ls, fan_half=10), device=dev)
@@ -681,7 +695,7 @@ def run_profile_case(args):
                 M.back_sens(y)
         torch.cuda.synchronize()
     print(json.dumps({"profile_case": case, "ok": True,
-                      **(info if case in ("rows_set", "rows", "csr") else {})}))
+                      **(info if case in ("rows_set", "rows", "csr", "back_patch") else {})}))
 
 
 VH_K = (60, 240, 960, 3840, 15360)
@@ -1033,7 +1047,8 @@ def main():
                     help="skip the mixed-precision (BF16 G rows) step")
     ap.add_argument("--stencil-form", type=int, default=None,
                     help="pin the LOR-space stencil form after autotuning (0-5)")
-    ap.add_argument("--profile-case", choices=["spread", "stencil", "rows", "rows_set", "csr"],
+    ap.add_argument("--profile-case",
+                    choices=["spread", "stencil", "rows", "rows_set", "csr", "back_patch"],
                     help="run one stage on a small-memory setup (for kernel captures)")
     ap.add_argument("--topn-table", action="store_true",
                     help="time the MLEM iteration with top-N truncated spreads (Table 3)")

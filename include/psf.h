@@ -452,6 +452,21 @@ int psf_matrix_check(const psf_matrix *m, void *stream);
  * do not fit the set fall back to the default.  PSF_EINVAL outside 0..5. */
 int psf_matrix_set_stencil_form(psf_matrix *m, int32_t form);
 
+/* Declare the voxel grid of the plan's columns (n_cols = nx * ny * nz, else
+ * PSF_EINVAL; nx <= 65535).  No counterpart in the paper: it lets the pair
+ * back-projection of psf_back_sens on a factored plan over a structured set
+ * (rows in set order) accumulate each transaxial pair's rows in shared memory
+ * and add each touched voxel to the image once (about 12 entries per voxel
+ * on the 3D ring), instead of one global FP32-pair atomic per entry.  The
+ * pair's cells are read from its direct-plane row of the middle ring; an
+ * entry whose voxel is not among them, or past the shared-memory capacity,
+ * takes the global atomic, so any rows give the same result up to FP32
+ * summation order.  Used by default once declared (psf_matrix_autotune times
+ * it against the other pair forms).  Host only; checks the division
+ * constants it derives over the grid's range (grids up to 2^26 voxels;
+ * PSF_EDEBUG if one fails). */
+int psf_matrix_set_image(psf_matrix *m, const psf_image *image);
+
 /*
  * x = A^T 1, the sensitivity image of MLEM (Sec. 3), x (device float
  * [n_cols], overwritten).  For a factored plan S^T 1 is formed from the class

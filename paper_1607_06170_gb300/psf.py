@@ -31,7 +31,7 @@ FUNCTIONS = [
     "psf_spread_topn", "psf_matrix_set_spread_topn", "psf_event_rows", "psf_histogram",
     "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
     "psf_matrix_check", "psf_matrix_build_sparse_adjoint", "psf_bin_spread_classes",
-    "psf_set_wait_limit", "psf_matrix_create_otf",
+    "psf_set_wait_limit", "psf_matrix_create_otf", "psf_matrix_set_image",
 ]
 
 
@@ -102,6 +102,7 @@ _SIGS = {
     "psf_sino_bins": (C.c_int, [_P, _P, _P, _P, _P]),
     "psf_voxel_homog": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
     "psf_matrix_set_stencil_form": (C.c_int, [_P, _I32]),
+    "psf_matrix_set_image": (C.c_int, [_P, _P]),
     "psf_matrix_check": (C.c_int, [_P, _P]),
     "psf_set_wait_limit": (C.c_int, [_I64]),
     "psf_matrix_build_sparse_adjoint": (C.c_int, [_P, _P]),
@@ -492,8 +493,14 @@ class Matrix:
         return self
 
     def set_stencil_form(self, form: int):
-        """Stencil form of a factored plan (0 default, 1 plain, 2 register-blocked, 3, 4)."""
+        """Stencil form of a factored plan (0 default, 1 plain, 2 register-blocked, 3, 4, 5)."""
         _ok(lib().psf_matrix_set_stencil_form(self._h, int(form)), "psf_matrix_set_stencil_form")
+        return self
+
+    def set_image(self, im: dict):
+        """Declare the voxel grid of the columns (psf_matrix_set_image)."""
+        i = image(im)
+        _ok(lib().psf_matrix_set_image(self._h, C.byref(i)), "psf_matrix_set_image")
         return self
 
     def forward(self, x, out=None):

@@ -33,7 +33,7 @@ def setup(orc):
     WM = P.bin_spread_classes(s, t, T, eta, ls, C, Wt, Wa)  # as bench.py: orbits + images
     G = P.sysmat_rows_set(s, im, ls)
     nv = im["nx"] * im["ny"] * im["nz"]
-    M = P.Matrix(G[0], G[1], G[2], nv).set_spread(s, ls, Wt, Wa, WM)
+    M = P.Matrix(G[0], G[1], G[2], nv).set_spread(s, ls, Wt, Wa, WM).set_image(im)
     tuned = M.autotune()
     torch.cuda.synchronize()
     To, eo = orc.table_build(s, t)
@@ -302,6 +302,29 @@ def test_tuned_launches_equal_plain_forms(setup):
     torch.testing.assert_close(st_, sp_, rtol=1e-5, atol=1e-6 * sp_.abs().max().item())
     torch.testing.assert_close(M.back(y), bp_, rtol=1e-5, atol=1e-6 * bp_.abs().max().item())
     torch.testing.assert_close(M.sensitivity(), sp_, rtol=1e-5, atol=1e-6 * sp_.abs().max().item())
+
+
+def test_pair_shared_memory_full_size(setup):
+    """The pair back-projection with each transaxial pair's voxels in shared
+    memory (the plan's image declared) against the global-atomic pair kernel,
+    over every voxel of the bench's rows (pairs with more cells than the
+    shared array holds send the rest to the global atomics)."""
+    d = setup
+    P, G, w = d["P"], d["G"], d["w"]
+    s, ls, im = w["scanner"], w["lors"], w["image"]
+    Wt, Wa = w["window"]
+    r = torch.from_numpy(I.random_lor_values(G[0].numel() - 1, 940)).cuda()
+    Ma = P.Matrix(G[0], G[1], G[2], d["nv"]).set_spread(s, ls, Wt, Wa, d["WM"]).set_image(im)
+    Mb = P.Matrix(G[0], G[1], G[2], d["nv"]).set_spread(s, ls, Wt, Wa, d["WM"])
+    P.timing_enable(True)
+    xa, sa = Ma.back_sens(r)
+    ran = P.timing_read()
+    P.timing_enable(False)
+    assert "csr_back_patch_kernel" in ran
+    xb, sb = Mb.back_sens(r)
+    torch.testing.assert_close(xa, xb, rtol=1e-5, atol=1e-6 * xb.abs().max().item())
+    torch.testing.assert_close(sa, sb, rtol=1e-5, atol=1e-6 * sb.abs().max().item())
+    del Ma, Mb
 
 
 def test_stencil5_full_size(setup):

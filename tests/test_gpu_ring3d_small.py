@@ -177,6 +177,65 @@ def test_back_sens_pair(gpu):
     torch.testing.assert_close(sens, s1, rtol=1e-5, atol=1e-6 * s1.abs().max().item())
 
 
+def _pair_patch_ran(P, M, r):
+    P.timing_enable(True)
+    out = M.back_sens(r)
+    ran = P.timing_read()
+    P.timing_enable(False)
+    return out, ran
+
+
+def test_back_sens_pair_shared_memory(P, gpu, ref, orc):
+    """With the image declared, psf_back_sens accumulates each transaxial
+    pair's rows in shared memory (pair form -3): A^T r and A^T 1 against the
+    oracle's G^T (S^T r) and G^T (S^T 1), and against the global-atomic pair
+    kernel of the same plan without the image."""
+    w = ref["w"]
+    s, ls, im = w["scanner"], w["lors"], w["image"]
+    Wt, Wa = w["window"]
+    G = gpu["G"]
+    M = P.Matrix(G[0], G[1], G[2], ref["nv"]).set_spread(s, ls, Wt, Wa, gpu["WC"]).set_image(im)
+    r = torch.from_numpy(I.random_lor_values(M.n_rows, 811)).cuda()
+    (x, sens), ran = _pair_patch_ran(P, M, r)
+    assert "csr_back_patch_kernel" in ran and "csr_back_pair_kernel" not in ran
+    x0, s0 = gpu["M"].back_sens(r)
+    torch.testing.assert_close(x, x0, rtol=1e-5, atol=1e-6 * x0.abs().max().item())
+    torch.testing.assert_close(sens, s0, rtol=1e-5, atol=1e-6 * s0.abs().max().item())
+    rn = r.cpu().numpy().astype(np.float64)
+    ones = np.ones(len(ref["L"]))
+    for got, q in ((x, rn), (sens, ones)):
+        want = orc.csr_back(ref["G"], orc.spread_adjoint(s, ref["L"], ref["W"], Wt, Wa, q),
+                            ref["nv"])
+        assert_close(got.cpu().numpy(), want, 2e-5, 1e-6 * np.abs(want).max(), "pair patch")
+
+
+def test_back_sens_pair_shared_memory_foreign_columns(P, gpu, ref):
+    """Rows whose voxels are not the pair's cells (the columns of every row
+    replaced by a seeded permutation of the grid) take the global atomics:
+    the shared-memory pair form still equals the plain pair kernel."""
+    w = ref["w"]
+    s, ls, im = w["scanner"], w["lors"], w["image"]
+    Wt, Wa = w["window"]
+    G = gpu["G"]
+    perm = torch.from_numpy(I.rng(812).permutation(ref["nv"]).astype(np.int32)).cuda()
+    col = perm[G[1].long()].contiguous()
+    Ma = P.Matrix(G[0], col, G[2], ref["nv"]).set_spread(s, ls, Wt, Wa, gpu["WC"]).set_image(im)
+    Mb = P.Matrix(G[0], col, G[2], ref["nv"]).set_spread(s, ls, Wt, Wa, gpu["WC"])
+    r = torch.from_numpy(I.random_lor_values(Ma.n_rows, 813)).cuda()
+    (x, sens), ran = _pair_patch_ran(P, Ma, r)
+    assert "csr_back_patch_kernel" in ran
+    x0, s0 = Mb.back_sens(r)
+    torch.testing.assert_close(x, x0, rtol=1e-5, atol=1e-6 * x0.abs().max().item())
+    torch.testing.assert_close(sens, s0, rtol=1e-5, atol=1e-6 * s0.abs().max().item())
+
+
+def test_set_image_rejects_other_grids(P, gpu, ref):
+    w = ref["w"]
+    im = dict(w["image"], nz=w["image"]["nz"] + 1)
+    with pytest.raises(P.PSFError):
+        gpu["M"].set_image(im)
+
+
 def test_factored_projector_tall_scanner(P, orc):
     """A set of 72 crystal rings (ring strips beyond one half-warp: the factored
     stencil takes whole warps per difference group) against the oracle."""
