@@ -2205,29 +2205,77 @@ __global__ void __launch_bounds__(160, 4) stencil5_kernel(LorSet ls, int Wt,
 // weights over the window entries whose measured LOR is in the set:
 //   q[g] = sum_{partner dt in set} sum_{(o1,o2): target rings in set}
 //          W_{class(g)}[d][(dt1,o1)][(dt2,o2)],   d = g's ring difference.
-// Per transaxial pair the partner sums C[d][o1][o2] = sum_{dt in set} W[...]
-// are formed once (shared memory), then each ring pair adds the C entries of
-// its in-set targets: 31 x 49 x 49 + 1372 x 49 additions per pair instead of
-// the stencil's 1372 x 2401 products.
+// The partner sums C[d][o1][o2] = sum_{dt in set} W[...] are formed once per
+// class (their partners in the set are the same for every pair of the class),
+// then each ring pair adds the C entries of its in-set targets (all of them,
+// one precomputed sum per d, away from the ends of the rings and the largest
+// ring differences): 31 x 49 x 49 per class + 1372 x 49 additions per pair at
+// most, instead of the stencil's 1372 x 2401 products.
 constexpr int SS_T = 128;
 
-// Per spread class c: C_c[d][o1][o2] summed over all 49 transaxial partners
-// (the partner sums of a transaxial pair whose partners are all in the set,
-// which is every pair but those near the edge of the fan).
+// Offset (floats, even) of the class partner masks after the class sums.
+__host__ __device__ __forceinline__ int64_t sens_mask_off(int64_t ncls, int nsum) {
+    return (ncls * nsum + 1) & ~int64_t(1);
+}
+
+// Partners of transaxial pair (a, b) in the set, one bit per window offset
+// pair, into mask[2] (zeroed by the caller, then a CTA barrier); threads
+// t < nwin take one offset each.  Membership depends only on the crystal
+// difference b - a (the fan is symmetric under b - a -> Nt - (b - a)), so all
+// pairs of a class share their mask.
+__device__ __forceinline__ void sens_partner_mask(const LorSet &ls, const int32_t *tp_start,
+                                                  int a, int b, int Wt, int nwin,
+                                                  unsigned long long *mask) {
+    const int dt = threadIdx.x;
+    if (dt >= nwin) return;
+    int pa = a + dt / (2 * Wt + 1) - Wt, pb = b + dt % (2 * Wt + 1) - Wt;
+    pa += pa < 0 ? ls.Nt : (pa >= ls.Nt ? -ls.Nt : 0);
+    pb += pb < 0 ? ls.Nt : (pb >= ls.Nt ? -ls.Nt : 0);
+    if (pa != pb && tp_member(ls, pa < pb ? pa : pb, pa < pb ? pb : pa))
+        atomicOr(mask + (dt >> 6), 1ull << (dt & 63));
+}
+
+// Per spread class c: C_c[d][o1][o2] summed over the class's transaxial
+// partners in the set (the partner sums of every pair of the class).
 __global__ void __launch_bounds__(SS_T) sens_class_kernel(LorSet ls, int Wt, int Wa,
                                                           const float *__restrict__ w,
                                                           float *__restrict__ csum) {
+    extern __shared__ __align__(16) unsigned char sc_raw[];
+    unsigned long long *mask = reinterpret_cast<unsigned long long *>(sc_raw);
+    int32_t *tp_start = reinterpret_cast<int32_t *>(mask + 2);
+    int32_t *rp_start = tp_start + ls.Nt + 1;
     const int W2a = 2 * Wa + 1, E = (2 * Wt + 1) * W2a, nd = 2 * ls.Dm + 1;
     const int nwin = (2 * Wt + 1) * (2 * Wt + 1), nsum = nd * W2a * W2a;
+    ls.stage_prefix(tp_start, rp_start);
     for (int64_t c = blockIdx.x; c < ls.ntp_cls; c += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x < 2) mask[threadIdx.x] = 0ull;
+        __syncthreads();
+        int a0, b0;
+        ls.tp_decode(tp_start, c, &a0, &b0);
+        sens_partner_mask(ls, tp_start, a0, b0, Wt, nwin, mask);
+        __syncthreads();
+        const unsigned long long m0 = mask[0], m1 = mask[1];
+        if (threadIdx.x < 2)
+            reinterpret_cast<unsigned long long *>(csum + sens_mask_off(ls.ntp_cls, nsum))
+                [2 * c + threadIdx.x] = mask[threadIdx.x];
         const float *wc = w + c * nd * E * E;
+        const bool all = __popcll(m0) + __popcll(m1) == nwin;
         for (int i = threadIdx.x; i < nsum; i += SS_T) {
             const int d = i / (W2a * W2a), L1 = (i / W2a) % W2a, L2 = i % W2a;
             const float *wd = wc + (int64_t)d * E * E + L1 * E + L2;
             float acc = 0.0f;
-            for (int dt = 0; dt < nwin; ++dt) {
-                const int dt1 = dt / (2 * Wt + 1), dt2 = dt % (2 * Wt + 1);
-                acc += __ldg(wd + dt1 * W2a * E + dt2 * W2a);
+            if (all) {
+                for (int dt = 0; dt < nwin; ++dt) {
+                    const int dt1 = dt / (2 * Wt + 1), dt2 = dt % (2 * Wt + 1);
+                    acc += __ldg(wd + dt1 * W2a * E + dt2 * W2a);
+                }
+            } else {
+                for (int dt = 0; dt < nwin; ++dt) {
+                    if (!(((dt < 64 ? m0 >> dt : m1 >> (dt - 64)) & 1ull))) continue;
+                    const int dt1 = dt / (2 * Wt + 1), dt2 = dt % (2 * Wt + 1);
+                    acc += __ldg(wd + dt1 * W2a * E + dt2 * W2a);
+                }
             }
             csum[c * nsum + i] = acc;
         }
@@ -2243,7 +2291,8 @@ __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, in
     const int nwin = (2 * Wt + 1) * (2 * Wt + 1), NR = ls.NR, Dm = ls.Dm;
     const int nsum = nd * W2a * W2a;
     float *C = reinterpret_cast<float *>(raw);                     // [nd][W2a][W2a]
-    short2 *rp = reinterpret_cast<short2 *>(C + nd * W2a * W2a);   // [nrp]
+    float *Ct = C + nd * W2a * W2a;                                // [nd] sums of C[d]
+    short2 *rp = reinterpret_cast<short2 *>(Ct + nd);              // [nrp]
     int32_t *tp_start = reinterpret_cast<int32_t *>(rp + ls.nrp);
     int32_t *rp_start = tp_start + ls.Nt + 1;
     unsigned long long *mask = reinterpret_cast<unsigned long long *>(
@@ -2261,25 +2310,19 @@ __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, in
         __syncthreads();
         int a, b;
         ls.tp_decode(tp_start, T, &a, &b);
-        if (t == 0) {  // partners in the set (one bit per window offset pair)
-            unsigned long long mk[2] = {0ull, 0ull};
-            for (int dt = 0; dt < nwin && dt < 128; ++dt) {
-                int pa = a + dt / (2 * Wt + 1) - Wt, pb = b + dt % (2 * Wt + 1) - Wt;
-                pa += pa < 0 ? ls.Nt : (pa >= ls.Nt ? -ls.Nt : 0);
-                pb += pb < 0 ? ls.Nt : (pb >= ls.Nt ? -ls.Nt : 0);
-                if (pa != pb && tp_member(ls, pa < pb ? pa : pb, pa < pb ? pb : pa))
-                    mk[dt >> 6] |= 1ull << (dt & 63);
-            }
-            mask[0] = mk[0];
-            mask[1] = mk[1];
-        }
+        if (t < 4) mask[t] = 0ull;
         __syncthreads();
-        const unsigned long long m0 = mask[0], m1 = mask[1];
         const int a0 = a % ls.Nb;
         const int64_t cls = tp_index(ls, tp_start, a0, b - (a - a0));
-        if (__popcll(m0) + __popcll(m1) == nwin) {
-            // every partner in the set: the class's sums (the same additions
-            // in the same order)
+        sens_partner_mask(ls, tp_start, a, b, Wt, nwin, mask);
+        __syncthreads();
+        const unsigned long long m0 = mask[0], m1 = mask[1];
+        const unsigned long long *cmask =
+            reinterpret_cast<const unsigned long long *>(csum + sens_mask_off(ls.ntp_cls, nsum)) +
+            2 * cls;
+        if (m0 == cmask[0] && m1 == cmask[1]) {
+            // the class's partners: its sums (the same additions in the same
+            // order)
             for (int i = t; i < nsum; i += SS_T) C[i] = __ldg(csum + cls * nsum + i);
         } else {
             const float *wc = w + cls * nd * E * E;
@@ -2296,9 +2339,21 @@ __global__ void __launch_bounds__(SS_T) sens_spread_kernel(LorSet ls, int Wt, in
             }
         }
         __syncthreads();
+        for (int d = t; d < nd; d += SS_T) {  // whole-window sums, in the loop's order
+            const float *Cd = C + d * W2a * W2a;
+            float acc = 0.0f;
+            for (int i = 0; i < W2a * W2a; ++i) acc += Cd[i];
+            Ct[d] = acc;
+        }
+        __syncthreads();
         for (int j = t; j < nrp; j += SS_T) {
             const short2 rr = rp[j];
             const int ra = rr.x, rb = rr.y, d = rb - ra;
+            if (ra >= Wa && ra + Wa < NR && rb >= Wa && rb + Wa < NR &&
+                (d < 0 ? -d : d) + 2 * Wa <= Dm) {  // every target in the set
+                q[T * nrp + j] = Ct[d + Dm];
+                continue;
+            }
             const float *Cd = C + (d + Dm) * W2a * W2a;
             float acc = 0.0f;
             for (int L1 = 0; L1 < W2a; ++L1) {
@@ -2521,8 +2576,8 @@ static int topn_s(const psf_matrix *m, const float *in, float *out, bool adjoint
 
 static size_t sens_smem_bytes(const LorSet &ls, int Wa) {
     const int W2a = 2 * Wa + 1, nd = 2 * ls.Dm + 1;
-    return sizeof(float) * nd * W2a * W2a + sizeof(short2) * ls.nrp +
-           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 8 + 2 * sizeof(unsigned long long) + 16;
+    return sizeof(float) * (nd * W2a * W2a + nd) + sizeof(short2) * ls.nrp +
+           sizeof(int32_t) * (ls.Nt + ls.NR + 2) + 8 + 4 * sizeof(unsigned long long) + 16;
 }
 
 constexpr int ST2_K = 8;  // rows per thread in stencil2_kernel
@@ -3051,7 +3106,10 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
     if (ls.ntp * ls.nrp != m->n_rows) return PSF_EINVAL;
     if (!(plain_stencil_ok(ls, half_a) || stencil4_ok(ls, half_a)) || ls.NR > 32000)
         return PSF_EINVAL;
-    const int64_t need = ls.ntp_cls * (2 * ls.Dm + 1) * (2 * half_a + 1) * (2 * half_a + 1);
+    // the class partner sums, then (8-byte aligned) each class's partner mask
+    // (2 x 64 bits)
+    const int64_t need =
+        ls.ntp_cls * ((2 * ls.Dm + 1) * (2 * half_a + 1) * (2 * half_a + 1) + 4) + 1;
     if (need > m->csum_n) {  // grows only: a plan reused over calls allocates once
         cudaFree(m->csum);
         m->csum = nullptr;
@@ -3555,7 +3613,9 @@ static int sens_spread(const psf_matrix *m, float *out, cudaStream_t st) {
     const int64_t cgrid = m->ls.ntp_cls < (int64_t)sms * 8 ? m->ls.ntp_cls : (int64_t)sms * 8;
     {
         PSF_TIMED("sens_class_kernel", st);
-        sens_class_kernel<<<(int)cgrid, SS_T, 0, st>>>(m->ls, m->Wt, m->Wa, m->cls, m->csum);
+        sens_class_kernel<<<(int)cgrid, SS_T,
+                            2 * sizeof(unsigned long long) + sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2),
+                            st>>>(m->ls, m->Wt, m->Wa, m->cls, m->csum);
     }
     PSF_LAUNCHED();
     const int64_t grid = m->ls.ntp < (int64_t)sms * 8 ? m->ls.ntp : (int64_t)sms * 8;
