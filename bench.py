@@ -273,7 +273,8 @@ def kernel_model(name, s, t, ls, Wt, Wa, n_lors, n_cls, nnz, nv, vb=4):
         return "hbm", ent + 8.0 * n_lors, "GB/s"
     if name.startswith("csr_fwd"):  # column + value, row_ptr, LOR value, image
         return "hbm", ent + 12.0 * n_lors + 4.0 * nv, "GB/s"
-    if name.startswith("csr_back_pair"):  # column + value, row_ptr, two LOR values, image pair
+    if name.startswith(("csr_back_pair", "csr_back_patch")):
+        # column + value, row_ptr, two LOR values, image pair
         return "hbm", ent + 16.0 * n_lors + 8.0 * nv, "GB/s"
     if name == "spread_q_kernel":  # one FMA per sub-LOR and quadrant entry pair
         # of the classes the kernel computes (one per orbit of the two reflections)
@@ -305,7 +306,8 @@ def kernel_traffic(name):
 def kern_hbm_first(name, kern):
     """Sort key of the mixed step's roofline kernel: the HBM-bound kernel with
     the most device time (the 16-bit rows change only the HBM-bound kernels)."""
-    hbm = name == "set_fill_kernel" or name.startswith(("csr_fwd", "csr_back_pair"))
+    hbm = name == "set_fill_kernel" or name.startswith(("csr_fwd", "csr_back_pair",
+                                                          "csr_back_patch"))
     return (hbm, kern[name]["ms_per_step"])
 
 
