@@ -924,6 +924,11 @@ def run_listmode(args):
     Mb.autotune()
     Mb.build_sparse_adjoint()
     ms_b, xb, kb = timed_osem(Mb, sens)
+    # and with the top-N weights in BF16 too (one FP32 scale per class)
+    w16, wsc = P.spread_topn_bf16(wk)
+    Mb.set_spread_topn(s, ls, Wt, Wa, idx, w16, scale=wsc)
+    Mb.build_sparse_adjoint()
+    ms_bw, xbw, kbw = timed_osem(Mb, sens)
     del Mb, val16, sc16
     # rows generated on the fly per subset (no stored matrix): the subset's
     # source rows traced for the masked forward, the rows with S^T r != 0
@@ -938,6 +943,10 @@ def run_listmode(args):
         "bf16_rows": {"iteration_ms": ms_b, "events_per_s": lm["events"] / (ms_b * 1e-3),
                       "stored_bytes": int(nnz * 6 + 4 * (rp.numel() - 1)),
                       "image_rel_l2_vs_f32_rows": rel(xb, x), "kernels_ms": kb},
+        "bf16_rows_bf16_weights": {"iteration_ms": ms_bw,
+                                   "events_per_s": lm["events"] / (ms_bw * 1e-3),
+                                   "weight_bytes": int(idx.numel() * 6 + 4 * idx.shape[0]),
+                                   "image_rel_l2_vs_f32_rows": rel(xbw, x), "kernels_ms": kbw},
         "traced_rows": {"iteration_ms": ms_o, "events_per_s": lm["events"] / (ms_o * 1e-3),
                         "stored_bytes": 0, "image_rel_l2_vs_f32_rows": rel(xo_img, x),
                         "kernels_ms": ko},

@@ -153,6 +153,17 @@ int psf_spread_topn(const float *spread, int64_t n_lors, int32_t half_t, int32_t
                     int32_t n_keep, int32_t *idx, float *w, void *stream);
 
 /*
+ * Top-N weights in BF16 with FP32 accumulation (the list-mode step after
+ * Sec. 5, no counterpart in the paper's text): for each of n_spreads rows of
+ * n_keep weights (device float, e.g. psf_spread_topn's w), scale[i] = the
+ * largest |w| of row i (1 when all are 0) and w16[i][k] = w[i][k] / scale[i]
+ * rounded to the nearest BF16 (ties to even): device bf16 [n_spreads][n_keep],
+ * device float [n_spreads], caller-owned.  1 <= n_keep <= 64, else PSF_EINVAL.
+ */
+int psf_spread_topn_bf16(const float *w, int64_t n_spreads, int32_t n_keep, void *w16,
+                         float *scale, void *stream);
+
+/*
  * List-mode data (the next step the paper names in Sec. 5; events stand for
  * the histogram organisation of Sec. 4, Table 1).  psf_event_rows writes the
  * row of each event's crystal pair (device int32 [n_events][2] crystal ids, in
@@ -369,6 +380,15 @@ int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner, const psf_l
 int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scanner,
                                const psf_lor_set *set, int32_t half_t, int32_t half_a,
                                int32_t n_keep, const int32_t *idx, const float *w);
+
+/* The same with the kept weights as BF16 codes and one FP32 scale per class
+ * (the output of psf_spread_topn_bf16 on the class weights: w16 device bf16
+ * [n_classes][n_keep], scale device float [n_classes], kept by pointer): each
+ * tap's weight is code x scale, products and sums in FP32. */
+int psf_matrix_set_spread_topn_bf16(psf_matrix *m, const psf_scanner *scanner,
+                                    const psf_lor_set *set, int32_t half_t, int32_t half_a,
+                                    int32_t n_keep, const int32_t *idx, const void *w16,
+                                    const float *scale);
 
 /* For a plan with top-N spreads (list-mode reconstruction, the next step of
  * Sec. 5): build the transpose of S -- for every measured LOR the source LORs

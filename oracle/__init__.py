@@ -22,6 +22,7 @@ from .oracle import (  # noqa: F401
     composed,
     spread,
     spread_topn,
+    topn_bf16,
     sino_index,
     voxel_homog,
     lor_normal,

@@ -409,6 +409,26 @@ def spread_topn(w: np.ndarray, Wt: int, Wa: int, N: int):
     return out.reshape(n, E, E), idx
 
 
+def topn_bf16(w: np.ndarray):
+    """Top-N weights (n x N) in their BF16 storage form for the list-mode
+    projector (a reading: the paper's list-mode step keeps the top-N weights;
+    16-bit storage with one scale per spread is this build's choice): scale =
+    the largest |w| of a row in FP32 (1 when all are 0), code = w / scale
+    (FP32 division) rounded to the nearest BF16, ties to even.  Returns the
+    codes' bit patterns (uint16, n x N), the scales (float32, n) and the
+    dequantized weights code x scale (float64, n x N)."""
+    w32 = np.ascontiguousarray(w, dtype=np.float32)
+    mx = np.abs(w32).max(axis=1) if w32.shape[1] else np.zeros(w32.shape[0], np.float32)
+    sc = np.where(mx > 0, mx, np.float32(1.0)).astype(np.float32)
+    q = (w32 / sc[:, None]).astype(np.float32)
+    b = q.view(np.uint32).astype(np.uint64)
+    # round to nearest even on the 16 bits dropped: add 0x7fff plus the kept
+    # part's lowest bit, then truncate
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+    deq = (r.astype(np.uint32) << 16).view(np.float32).astype(np.float64) * sc[:, None]
+    return r, sc, deq
+
+
 def mlem(fwd, back, y: np.ndarray, nvox: int, iters: int, x0=None):
     """MLEM (the EM iteration OSEM is built on, Sec. 3).
 

@@ -47,6 +47,10 @@ struct psf_matrix {
     int topn;
     const int32_t *tidx;
     const float *tw;
+    // or the kept weights as BF16 codes with one FP32 scale per class
+    // (psf_matrix_set_spread_topn_bf16): weight = code x scale
+    const __nv_bfloat16 *twh;
+    const float *tsc;
     // bulk-staged projector forms (launch form -2, FP32 rows): the first row
     // of each BK_CAP-entry chunk (plan-owned, built on first use), and the
     // form of the pair back-projection of psf_back_sens (-2 bulk, else the
@@ -2407,6 +2411,8 @@ template <int MODE>
 __global__ void __launch_bounds__(TS_T, 4) topn_s_kernel(LorSet ls, int Wt, int Wa, int N,
                                                       const int32_t *__restrict__ tidx,
                                                       const float *__restrict__ tw,
+                                                      const __nv_bfloat16 *__restrict__ twh,
+                                                      const float *__restrict__ tsc,
                                                       const float *__restrict__ in,
                                                       float *__restrict__ out, TsTr tr) {
     constexpr bool adjoint = MODE == TS_ADJ;
@@ -2446,7 +2452,9 @@ __global__ void __launch_bounds__(TS_T, 4) topn_s_kernel(LorSet ls, int Wt, int 
         const int ra = r2.x, rb = r2.y;
         const int64_t cls = ls.class_of(tp_start, a, b, ra, rb);
         const int32_t *ik = tidx + cls * N;
-        const float *wk = tw + cls * N;
+        const float *wk = tw ? tw + cls * N : nullptr;
+        const __nv_bfloat16 *wh = twh ? twh + cls * N : nullptr;
+        const float wsc = twh ? __ldg(tsc + cls) : 1.0f;
         float acc = 0.0f;
         // taps in groups of TS_G: the targets first, then their reads or
         // atomics, so a group's memory operations are in flight together
@@ -2459,7 +2467,7 @@ __global__ void __launch_bounds__(TS_T, 4) topn_s_kernel(LorSet ls, int Wt, int 
                 wv[u] = 0.0f;
                 const int k = k0 + u;
                 if (k >= N) continue;
-                const float w = __ldg(wk + k);
+                const float w = wh ? __bfloat162float(wh[k]) * wsc : __ldg(wk + k);
                 if (w == 0.0f) continue;
                 const char4 o = dec[__ldg(ik + k)];
                 const int qa = ra + o.y, qb = rb + o.w;
@@ -2561,14 +2569,14 @@ static int topn_s(const psf_matrix *m, const float *in, float *out, bool adjoint
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         PSF_TIMED("topn_s_kernel<adjoint>", st);
         topn_s_kernel<TS_ADJ><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
-                                                        m->tw, in, out, tr);
+                                                        m->tw, m->twh, m->tsc, in, out, tr);
     } else {
         PSF_TRY(cudaMemsetAsync(out, 0, sizeof(float) * n, st));
         PSF_TRY(cudaFuncSetAttribute(topn_s_kernel<TS_FWD>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         PSF_TIMED("topn_s_kernel<forward>", st);
         topn_s_kernel<TS_FWD><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
-                                                        m->tw, in, out, TsTr{});
+                                                        m->tw, m->twh, m->tsc, in, out, TsTr{});
     }
     PSF_LAUNCHED();
     return PSF_OK;
@@ -3148,6 +3156,8 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
     m->topn = 0;
     m->tidx = nullptr;
     m->tw = nullptr;
+    m->twh = nullptr;
+    m->tsc = nullptr;
     return PSF_OK;
 }
 
@@ -3173,6 +3183,25 @@ extern "C" int psf_matrix_set_spread_topn(psf_matrix *m, const psf_scanner *scan
     m->topn = n_keep;
     m->tidx = idx;
     m->tw = w;
+    m->twh = nullptr;
+    m->tsc = nullptr;
+    return PSF_OK;
+}
+
+extern "C" int psf_matrix_set_spread_topn_bf16(psf_matrix *m, const psf_scanner *scanner,
+                                               const psf_lor_set *set, int32_t half_t,
+                                               int32_t half_a, int32_t n_keep,
+                                               const int32_t *idx, const void *w16,
+                                               const float *scale) {
+    PSF_RANGE("psf_matrix_set_spread_topn_bf16");
+    if (!w16 || !scale) return PSF_EINVAL;
+    // validation and plan state as for FP32 weights, then the weights' form
+    const int rc = psf_matrix_set_spread_topn(m, scanner, set, half_t, half_a, n_keep, idx,
+                                              reinterpret_cast<const float *>(w16));
+    if (rc) return rc;
+    m->tw = nullptr;
+    m->twh = static_cast<const __nv_bfloat16 *>(w16);
+    m->tsc = scale;
     return PSF_OK;
 }
 
@@ -3222,7 +3251,7 @@ extern "C" int psf_matrix_build_sparse_adjoint(psf_matrix *m, void *stream) {
     {
         PSF_TIMED("topn_s_kernel<count>", st);
         topn_s_kernel<TS_COUNT><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
-                                                          m->tw, nullptr, nullptr, tr);
+                                                          m->tw, m->twh, m->tsc, nullptr, nullptr, tr);
     }
     if (cudaGetLastError() != cudaSuccess) return fail(PSF_ECUDA);
     rc = inclusive_scan(ptr + 1, n, tiles, st);
@@ -3243,7 +3272,7 @@ extern "C" int psf_matrix_build_sparse_adjoint(psf_matrix *m, void *stream) {
     {
         PSF_TIMED("topn_s_kernel<fill>", st);
         topn_s_kernel<TS_FILL><<<grid, TS_T, shm, st>>>(m->ls, m->Wt, m->Wa, m->topn, m->tidx,
-                                                         m->tw, nullptr, nullptr, tr);
+                                                         m->tw, m->twh, m->tsc, nullptr, nullptr, tr);
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
         return fail(PSF_ECUDA);

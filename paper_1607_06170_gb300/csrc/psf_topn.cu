@@ -3,6 +3,8 @@
 // total.  Ranking rule (a reading; the paper only says "descending order"):
 // a negative weight ranks as 0; equal weights rank the smaller offset
 // |dt1|+|da1|+|dt2|+|da2| first, then the lower window index e1*E + e2.
+#include <cuda_bf16.h>
+
 #include "psf_common.cuh"
 
 namespace psf {
@@ -110,6 +112,46 @@ extern "C" int psf_spread_topn(const float *spread, int64_t n_lors, int32_t half
     {
         PSF_TIMED("topn_kernel", st);
         topn_kernel<<<(int)grid, TN_T, 0, st>>>(spread, n_lors, half_t, half_a, n_keep, idx, w);
+    }
+    PSF_LAUNCHED();
+    return PSF_OK;
+}
+
+namespace psf {
+
+// Top-N weights -> BF16 codes with one FP32 scale per spread: scale = the
+// largest |w| of the spread's kept weights (1 when they are all 0), code =
+// w / scale rounded to the nearest BF16 (ties to even).  One warp per spread.
+__global__ void topn_bf16_kernel(const float *__restrict__ w, int64_t n, int N,
+                                 __nv_bfloat16 *__restrict__ w16, float *__restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < n;
+         g += warps) {
+        float mx = 0.0f;
+        for (int k = lane; k < N; k += 32) mx = fmaxf(mx, fabsf(w[g * N + k]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = mx > 0.0f ? mx : 1.0f;
+        for (int k = lane; k < N; k += 32) w16[g * N + k] = __float2bfloat16_rn(__fdiv_rn(w[g * N + k], sc));
+        if (lane == 0) scale[g] = sc;
+    }
+}
+
+}  // namespace psf
+
+extern "C" int psf_spread_topn_bf16(const float *w, int64_t n_spreads, int32_t n_keep,
+                                    void *w16, float *scale, void *stream) {
+    PSF_RANGE("psf_spread_topn_bf16");
+    if (n_spreads < 0 || n_keep < 1 || n_keep > TN_MAX) return PSF_EINVAL;
+    if (n_spreads == 0) return PSF_OK;
+    if (!w || !w16 || !scale) return PSF_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const int64_t blocks = (n_spreads + 7) / 8;
+    const int grid = (int)(blocks < 65535 * 16 ? blocks : 65535 * 16);
+    {
+        PSF_TIMED("topn_bf16_kernel", st);
+        topn_bf16_kernel<<<grid, 256, 0, st>>>(w, n_spreads, n_keep,
+                                               static_cast<__nv_bfloat16 *>(w16), scale);
     }
     PSF_LAUNCHED();
     return PSF_OK;

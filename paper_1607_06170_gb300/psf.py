@@ -32,6 +32,7 @@ FUNCTIONS = [
     "psf_forward_masked", "psf_sino_bins", "psf_voxel_homog", "psf_matrix_set_stencil_form",
     "psf_matrix_check", "psf_matrix_build_sparse_adjoint", "psf_bin_spread_classes",
     "psf_set_wait_limit", "psf_matrix_create_otf", "psf_matrix_set_image",
+    "psf_spread_topn_bf16", "psf_matrix_set_spread_topn_bf16",
 ]
 
 
@@ -103,6 +104,8 @@ _SIGS = {
     "psf_voxel_homog": (C.c_int, [_P, _P, _P, _P, _P, _P, _I32, _I32, _P, _P]),
     "psf_matrix_set_stencil_form": (C.c_int, [_P, _I32]),
     "psf_matrix_set_image": (C.c_int, [_P, _P]),
+    "psf_spread_topn_bf16": (C.c_int, [_P, _I64, _I32, _P, _P, _P]),
+    "psf_matrix_set_spread_topn_bf16": (C.c_int, [_P, _P, _P, _I32, _I32, _I32, _P, _P, _P]),
     "psf_matrix_check": (C.c_int, [_P, _P]),
     "psf_set_wait_limit": (C.c_int, [_I64]),
     "psf_matrix_build_sparse_adjoint": (C.c_int, [_P, _P]),
@@ -249,6 +252,17 @@ def spread_topn(spread, half_t: int, half_a: int, n_keep: int):
     _ok(lib().psf_spread_topn(_ptr(spread), n, half_t, half_a, n_keep, _ptr(idx), _ptr(w),
                               _stream()), "psf_spread_topn")
     return idx, w
+
+
+def spread_topn_bf16(w):
+    """Top-N weights [n, N] (FP32) as BF16 codes with one FP32 scale per row
+    (psf_spread_topn_bf16): weight = code x scale."""
+    n, N = w.shape
+    w16 = torch.empty((n, N), dtype=torch.bfloat16, device=w.device)
+    scale = torch.empty(n, dtype=torch.float32, device=w.device)
+    _ok(lib().psf_spread_topn_bf16(_ptr(w), n, N, _ptr(w16), _ptr(scale), _stream()),
+        "psf_spread_topn_bf16")
+    return w16, scale
 
 
 def event_rows(sc: dict, ls: dict, events):
@@ -454,13 +468,22 @@ class Matrix:
         self.topn = 0
         return self
 
-    def set_spread_topn(self, sc: dict, ls: dict, half_t: int, half_a: int, idx, w):
-        """Factored form with top-N class spreads (outputs of spread_topn)."""
-        self._spread = (idx, w)  # the plan keeps the pointers; keep the tensors alive
+    def set_spread_topn(self, sc: dict, ls: dict, half_t: int, half_a: int, idx, w,
+                        scale=None):
+        """Factored form with top-N class spreads (outputs of spread_topn); with
+        BF16 weights and their per-class scale (spread_topn_bf16) when scale is
+        given."""
+        self._spread = (idx, w, scale)  # the plan keeps the pointers; keep them alive
         s, l = scanner(sc), lor_set(ls)
-        _ok(lib().psf_matrix_set_spread_topn(self._h, C.byref(s), C.byref(l), half_t, half_a,
-                                             idx.shape[1], _ptr(idx), _ptr(w)),
-            "psf_matrix_set_spread_topn")
+        if scale is None:
+            _ok(lib().psf_matrix_set_spread_topn(self._h, C.byref(s), C.byref(l), half_t,
+                                                 half_a, idx.shape[1], _ptr(idx), _ptr(w)),
+                "psf_matrix_set_spread_topn")
+        else:
+            _ok(lib().psf_matrix_set_spread_topn_bf16(self._h, C.byref(s), C.byref(l), half_t,
+                                                      half_a, idx.shape[1], _ptr(idx), _ptr(w),
+                                                      _ptr(scale)),
+                "psf_matrix_set_spread_topn_bf16")
         self.topn = int(idx.shape[1])
         return self
 

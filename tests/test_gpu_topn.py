@@ -167,3 +167,107 @@ def test_topn_projector(P, ref, orc, plan, N):
         lhs = torch.dot(M.forward(xk).double(), yk.double()).item()
         rhs = torch.dot(xk.double(), M.back(yk).double()).item()
         assert lhs == pytest.approx(rhs, rel=1e-5)
+
+
+def test_topn_bf16_codes(P, orc):
+    """psf_spread_topn_bf16 against the oracle's BF16 storage form on the same
+    seeded FP32 weights: codes and scales bit-equal."""
+    rng = I.rng(4343)
+    w = (rng.random((2000, 5)) * rng.choice([1e-5, 1e-2, 1.0], (2000, 1))).astype(np.float32)
+    w[3] = 0.0
+    w16, sc = P.spread_topn_bf16(torch.from_numpy(w).cuda())
+    codes, sco, _ = orc.topn_bf16(w)
+    np.testing.assert_array_equal(w16.cpu().view(torch.int16).numpy(), codes.view(np.int16))
+    np.testing.assert_array_equal(sc.cpu().numpy(), sco)
+
+
+@pytest.mark.parametrize("N", [5, 25])
+def test_topn_projector_bf16(P, ref, orc, plan, N):
+    """The factored projector with BF16 top-N weights (one FP32 scale per
+    class, FP32 products and sums) against the oracle with its own top-N
+    weights in the same storage form (dequantized in FP64)."""
+    w = ref["w"]
+    s, ls = w["scanner"], w["lors"]
+    Wt, Wa = w["window"]
+    E = (2 * Wt + 1) * (2 * Wa + 1)
+    idx, wk = P.spread_topn(torch.from_numpy(ref["WC"]).cuda(), Wt, Wa, N)
+    w16, sc = P.spread_topn_bf16(wk)
+    M = P.Matrix(plan[0], plan[1], plan[2], ref["nv"]).set_spread_topn(s, ls, Wt, Wa, idx, w16,
+                                                                       scale=sc)
+    out_o, idx_o = orc.spread_topn(ref["WC"].astype(np.float64), Wt, Wa, N)
+    np.testing.assert_array_equal(idx.cpu().numpy(), idx_o)
+    flat = out_o.reshape(len(idx_o), E * E)
+    _, _, deq = orc.topn_bf16(np.take_along_axis(flat, idx_o.astype(np.int64), 1))
+    Wq = np.zeros_like(flat)
+    np.put_along_axis(Wq, idx_o.astype(np.int64), deq, 1)
+    Wl = Wq.reshape(-1, E, E)[ref["cls"]]
+    x = I.random_image(w["image"], 950).reshape(-1)
+    y = M.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    yo = orc.spread_apply(s, ref["L"], Wl, Wt, Wa, orc.csr_fwd(ref["G"], x))
+    assert_close(y, yo, 2e-5, 1e-6 * yo.max(), f"top-{N} BF16 forward")
+    r = I.random_lor_values(len(ref["L"]), 951)
+    b = M.back(torch.from_numpy(r).cuda()).cpu().numpy()
+    bo = orc.csr_back(ref["G"], orc.spread_adjoint(s, ref["L"], Wl, Wt, Wa, r), ref["nv"])
+    assert_close(b, bo, 2e-5, 1e-6 * bo.max(), f"top-{N} BF16 back")
+    ones = np.ones(len(ref["L"]))
+    so = orc.csr_back(ref["G"], orc.spread_adjoint(s, ref["L"], Wl, Wt, Wa, ones), ref["nv"])
+    assert_close(M.sensitivity().cpu().numpy(), so, 2e-5, 1e-6 * so.max(),
+                 f"top-{N} BF16 sensitivity")
+    M.build_sparse_adjoint()
+    rs = np.where(np.random.default_rng(952).random(len(ref["L"])) < 0.01, r, 0.0)
+    bs = M.back(torch.from_numpy(rs.astype(np.float32)).cuda()).cpu().numpy()
+    bso = orc.csr_back(ref["G"], orc.spread_adjoint(s, ref["L"], Wl, Wt, Wa, rs), ref["nv"])
+    assert_close(bs, bso, 2e-5, 1e-6 * bso.max(), f"top-{N} BF16 sparse back (transpose)")
+
+
+def test_listmode_osem_topn_bf16(P, orc):
+    """List-mode OSEM (the list-mode step after Sec. 5) with BF16 top-5 class
+    weights against the oracle's event-by-event list-mode OSEM with the same
+    weights in the same storage form, on the small list-mode ring; both sides
+    rank the oracle's class spreads rounded to FP32."""
+    from paper_1607_06170_gb300.torch_api import listmode_osem
+
+    w = I.workload("RING3D_SMALL_LM")
+    s, t, im, ls = w["scanner"], w["table"], w["image"], w["lors"]
+    Wt, Wa = w["window"]
+    E = (2 * Wt + 1) * (2 * Wa + 1)
+    Nk = w["listmode"]["n_keep"]
+    n_sub, iters = 4, 2
+    T, _ = orc.table_build(s, t)
+    C, tp_index = _class_lors(w)
+    WC = orc.spread(s, t, T, C, Wt, Wa).astype(np.float32)
+    L = I.workload_lors(w)
+    cls = _lor_classes(w, L, tp_index)
+    G = orc.rows_geom(s, im, L)
+    nv = im["nx"] * im["ny"] * im["nz"]
+    ev = I.listmode_events(w, w["listmode"]["events"], w["index"]).numpy()
+    nc = I.n_crystals(s)
+    rows_o = orc.pair_row_map(s, L)[ev[:, 0].astype(np.int64) * nc + ev[:, 1]]
+    # oracle weights: its top-N of the FP32 class spreads in BF16 storage form
+    out_o, idx_o = orc.spread_topn(WC.astype(np.float64), Wt, Wa, Nk)
+    flat = out_o.reshape(len(idx_o), E * E)
+    _, _, deq = orc.topn_bf16(np.take_along_axis(flat, idx_o.astype(np.int64), 1))
+    Wq = np.zeros_like(flat)
+    np.put_along_axis(Wq, idx_o.astype(np.int64), deq, 1)
+    Wl = Wq.reshape(-1, E, E)[cls]
+
+    def fwd(v):
+        return orc.spread_apply(s, L, Wl, Wt, Wa, orc.csr_fwd(G, v))
+
+    def back(r):
+        return orc.csr_back(G, orc.spread_adjoint(s, L, Wl, Wt, Wa, r), nv)
+
+    xo = orc.listmode_osem(fwd, back, rows_o, len(L), n_sub, iters)
+    Gd = P.sysmat_rows_set(s, im, ls)
+    idx, wk = P.spread_topn(torch.from_numpy(WC).cuda(), Wt, Wa, Nk)
+    w16, sc = P.spread_topn_bf16(wk)
+    M = P.Matrix(Gd[0], Gd[1], Gd[2], nv).set_spread_topn(s, ls, Wt, Wa, idx, w16, scale=sc)
+    M.build_sparse_adjoint()
+    rows = P.event_rows(s, ls, torch.from_numpy(ev).cuda())
+    np.testing.assert_array_equal(rows.cpu().numpy(), rows_o)
+    x = listmode_osem(M, rows, n_sub, iters).cpu().numpy()
+    rel = float(np.linalg.norm(x - xo) / np.linalg.norm(xo))
+    print(f"\nlist-mode OSEM, BF16 top-{Nk} ({n_sub} subsets x {iters}): image rel. L2 vs "
+          f"oracle {rel:.2e}")
+    assert rel < 1e-4
+    assert_close(x, xo, 1e-3, 1e-4 * xo.max(), "list-mode OSEM image (BF16 top-N)")

@@ -94,3 +94,27 @@ def test_real_spreads_keep_the_largest(orc):
         assert np.all(wg[idx[g]] >= thr)
         assert np.sum(wg > thr) <= N
         assert out[g].sum() == pytest.approx(wg.sum(), rel=1e-12)
+
+
+def test_topn_bf16_matches_library_rounding(orc):
+    """The oracle's BF16 storage of top-N weights: its codes equal torch's
+    round-to-nearest-even conversion of the same FP32 quotients (a library
+    routine), ties included, and code x scale reproduces each weight within
+    half a BF16 unit (at most 2^-8 of it)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4242)
+    w = rng.random((300, 5)).astype(np.float32) * rng.choice([1e-6, 1e-2, 1.0, 30.0], (300, 1))
+    w[7] = 0.0  # an all-zero row keeps scale 1
+    w[11, 1:] = w[11, 0]  # equal weights
+    # a row whose largest weight is 1 (quotients = weights) with values exactly
+    # between two BF16 numbers: ties to the even code, down and up
+    w[20] = np.array([1.0, 0.5 + 2.0 ** -9, 0.5 + 3 * 2.0 ** -9, 0.25 + 2.0 ** -10, 0.75],
+                     dtype=np.float32)
+    codes, sc, deq = orc.topn_bf16(w)
+    q = w / np.where(np.abs(w).max(1) > 0, np.abs(w).max(1), 1.0).astype(np.float32)[:, None]
+    want = torch.from_numpy(q.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
+    np.testing.assert_array_equal(codes.view(np.int16), want)
+    assert sc[7] == 1.0 and (deq[7] == 0).all()
+    np.testing.assert_array_equal(codes[20], [0x3F80, 0x3F00, 0x3F02, 0x3E80, 0x3F40])
+    nz = w != 0
+    assert (np.abs(deq[nz] - w[nz]) <= 2.0 ** -8 * np.abs(w[nz]) * (1 + 1e-6)).all()
