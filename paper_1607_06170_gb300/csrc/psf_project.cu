@@ -1859,21 +1859,29 @@ static size_t stencil5_smem_bytes(const LorSet &ls, int WA) {
 }
 
 // in (set order) -> padded planes: cell (ring difference d, ring ra) of pair T
-// at T * plane_f + (d + Dm) * PRp + ra + WA.  Only in-set cells are written,
-// so the zero padding laid down at allocation stays zero.
+// at T * plane_f + (d + Dm) * PRp + ra + WA, every other word of the plane 0.
+// A CTA per pair: the pair's ring-pair values are read into shared memory
+// with coalesced loads, then the whole plane is written with coalesced
+// stores (the scattered form ran at 1.1 TB/s).
 __global__ void st5_pack_kernel(LorSet ls, int PRp, int plane_f, int WA,
                                 const float *__restrict__ in, float *__restrict__ pin) {
-    extern __shared__ int32_t pk_pre[];  // rp_start [NR + 1] (tp part unused)
+    extern __shared__ int32_t pk_pre[];  // tp part (unused), rp_start [NR + 1], values [nrp]
     int32_t *rp_start = pk_pre + ls.Nt + 1;
+    float *v = reinterpret_cast<float *>(rp_start + ls.NR + 1);
     ls.stage_prefix(pk_pre, rp_start);
-    __syncthreads();
-    const int64_t n = ls.ntp * ls.nrp;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t T = i / ls.nrp;
-        int ra, rb;
-        ls.rp_decode(rp_start, i - T * ls.nrp, &ra, &rb);
-        pin[T * plane_f + (int64_t)(rb - ra + ls.Dm) * PRp + ra + WA] = in[i];
+    const int nrp = (int)ls.nrp, Dm = ls.Dm;
+    for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
+        __syncthreads();  // the previous pair's values are no longer read
+        for (int j = threadIdx.x; j < nrp; j += blockDim.x) v[j] = __ldcs(in + T * nrp + j);
+        __syncthreads();
+        float *dst = pin + T * plane_f;
+        for (int i = threadIdx.x; i < plane_f; i += blockDim.x) {
+            const int dd = i / PRp, ra = i - dd * PRp - WA, rb = ra + dd - Dm;
+            float x = 0.0f;
+            if (dd <= 2 * Dm && ra >= 0 && ra < ls.NR && rb >= 0 && rb < ls.NR)
+                x = v[rp_start[ra] + (rb - ls.rp_lo(ra))];
+            dst[i] = x;
+        }
     }
 }
 
@@ -2858,8 +2866,9 @@ static int launch_stencil5(const psf_matrix *mc, const float *in, float *out, cu
     PSF_LAUNCHED();
     {
         PSF_TIMED("st5_pack_kernel", st);
-        st5_pack_kernel<<<sms * 8, 256, sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2), st>>>(
-            m->ls, s5.PRp, s5.plane_f, WA, in, m->pin);
+        st5_pack_kernel<<<sms * 8, 256,
+                          sizeof(int32_t) * (m->ls.Nt + m->ls.NR + 2) + sizeof(float) * m->ls.nrp,
+                          st>>>(m->ls, s5.PRp, s5.plane_f, WA, in, m->pin);
     }
     PSF_LAUNCHED();
     const size_t shm = stencil5_smem_bytes(m->ls, WA);
@@ -3134,7 +3143,6 @@ extern "C" int psf_matrix_set_spread(psf_matrix *m, const psf_scanner *scanner,
             m->pin = nullptr;
             m->pin_n = 0;
             PSF_TRY(cudaMalloc(&m->pin, sizeof(float) * np));
-            PSF_TRY(cudaMemset(m->pin, 0, sizeof(float) * np));  // the planes' padding
             m->pin_n = np;
         }
         if (nw > m->wpad_n) {
