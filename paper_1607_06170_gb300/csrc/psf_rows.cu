@@ -816,6 +816,34 @@ __device__ __forceinline__ void set_smem_layout(SetSmem &m, unsigned char *raw, 
         (reinterpret_cast<uintptr_t>(m.lmax + 1) + 15) & ~uintptr_t(15));
 }
 
+// The count kernel's layout: the pair's cells, block trig and prefix tables
+// as above, without the voxel-order copies, and per warp only its rows and
+// their counts.
+struct CountWarp {
+    int cnt[32];
+    SlabRow row[32];
+};
+
+__device__ __forceinline__ CountWarp *count_smem_layout(SetSmem &m, unsigned char *raw,
+                                                        const Scan &sc, const LorSet &ls) {
+    m.cs = reinterpret_cast<double *>(cells_layout(m.c, raw));
+    m.s_len = nullptr;
+    m.s_xyl = nullptr;
+    m.tp_start = reinterpret_cast<int32_t *>(m.cs + 2 * sc.R);
+    m.rp_start = m.tp_start + ls.Nt + 1;
+    m.next = m.rp_start + ls.NR + 1;
+    m.lmax = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(m.next + 1) + 7) & ~uintptr_t(7));
+    m.w = nullptr;
+    return reinterpret_cast<CountWarp *>(
+        (reinterpret_cast<uintptr_t>(m.lmax + 1) + 15) & ~uintptr_t(15));
+}
+
+static size_t count_smem(const Scan &sc, const LorSet &ls) {
+    return cells_bytes() + sizeof(double) * 2 * sc.R + sizeof(int32_t) * (ls.Nt + ls.NR + 2) +
+           sizeof(int) * 4 + 32 + sizeof(CountWarp) * (SET_T / 32) + 64;
+}
+
 static size_t set_smem(const Scan &sc, const LorSet &ls) {
     return cells_bytes() + sizeof(double) * 2 * sc.R +
            (sizeof(long long) + sizeof(int2)) * SET_MAXC +
@@ -843,7 +871,7 @@ __global__ void __launch_bounds__(256) zaxis_kernel(Scan sc, Img im, LorSet ls,
 // Returns after the CTA barrier.
 __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const Img &im,
                                                const LorSet &ls, int64_t T, int *status,
-                                               bool norm = false) {
+                                               bool norm = false, bool voxel_order = true) {
     __syncthreads();  // the previous pair's readers are done
     const Cells2D &c = m.c;
     int a, b;
@@ -855,6 +883,7 @@ __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const
         *m.lmax = 1;
     }
     __syncthreads();
+    if (!voxel_order) return;  // (the count kernel cuts the ray-order cells only)
     if (norm) {
         unsigned long long mx = 1;
         for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
@@ -905,21 +934,21 @@ __device__ __forceinline__ int set_next_group(int *next) {
 // K4 (set): a warp takes 32 ring pairs of the CTA's transaxial pair; its
 // lanes cut the z slabs of all of them, 32 slabs at a time, and add each
 // slab's stored voxels to its ring pair's count.
-__global__ void __launch_bounds__(SET_T, 3) set_count_kernel(Scan sc, Img im, LorSet ls,
+__global__ void __launch_bounds__(SET_T, 4) set_count_kernel(Scan sc, Img im, LorSet ls,
                                                              const ZAx *__restrict__ zt,
                                                              int64_t *__restrict__ counts,
                                                              int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char raw[];
     SetSmem m;
-    set_smem_layout(m, raw, sc, ls);
+    CountWarp *cw = count_smem_layout(m, raw, sc, ls);
     stage_blocks(sc, m.cs);
     ls.stage_prefix(m.tp_start, m.rp_start);
     const Cells2D &c = m.c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    SetWarp &W = m.w[warp];
+    CountWarp &W = cw[warp];
     const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
-        set_pair_cells(m, sc, im, ls, T, status);
+        set_pair_cells(m, sc, im, ls, T, status, false, false);
         const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
         for (int g = set_next_group(m.next); g < ngroups; g = set_next_group(m.next)) {
             const int j = g * 32 + lane;
@@ -1276,14 +1305,21 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
         zaxis_kernel<<<(int)((ls.nrp + 255) / 256), 256, zshm, st>>>(sc, im, ls, zt);
     }
     PSF_LAUNCHED();
-    const int grid_max = sm_count() * 3;  // resident CTAs (launch bounds 3 per SM)
+    const int grid_max = sm_count() * 3;  // the fill's resident CTAs (launch bounds 3 per SM)
     const int grid = (int)(ls.ntp < grid_max ? ls.ntp : grid_max);
-    const size_t shm = set_smem(sc, ls);
-    PSF_TRY(cudaFuncSetAttribute(set_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shm));
+    const size_t shm = set_smem(sc, ls);  // the fill's
     {
+        // the count kernel's own (smaller) layout and grid
+        const size_t cshm = count_smem(sc, ls);
+        PSF_TRY(cudaFuncSetAttribute(set_count_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cshm));
+        int per_sm = 0;
+        PSF_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, set_count_kernel, SET_T,
+                                                              cshm));
+        const int cmax = sm_count() * (per_sm > 0 ? per_sm : 1);
+        const int cgrid = (int)(ls.ntp < cmax ? ls.ntp : cmax);
         PSF_TIMED("set_count_kernel", st);
-        set_count_kernel<<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr + 1, status);
+        set_count_kernel<<<cgrid, SET_T, cshm, st>>>(sc, im, ls, zt, row_ptr + 1, status);
     }
     PSF_LAUNCHED();
     int rc = inclusive_scan(row_ptr + 1, n, tiles, st);
