@@ -322,8 +322,7 @@ int psf_sysmat_rows_set_typed(const psf_scanner *scanner, const psf_image *image
  *    PSF_ENOSCRATCH before any device work.
  *  - Set-up: the first call on a device (the current device) looks up the
  *    array's device address once and keeps it for later calls on that
- *    device; make that first call before any stream capture.  The address
- *    is not looked up again, so after cudaDeviceReset (by the caller, torch
+ *    device.  The address is not looked up again, so after cudaDeviceReset (by the caller, torch
  *    or any other code in the process) this entry point must not be called
  *    again on that device in the same process.
  *  - All calls share the array and leave their contents in it: calls whose
