@@ -864,19 +864,90 @@ __global__ void __launch_bounds__(256) zaxis_kernel(Scan sc, Img im, LorSet ls,
     zaxis_of(sc, im, ra, rb, zt[j]);
 }
 
-// Per transaxial pair: the CTA builds the 2D cells, then every thread helps
-// write the voxel-order copies: each cell's packed x/y voxel and its chord as
+// Cache of the 2D cells of every transaxial pair in device memory: the count
+// kernel stores each pair's cells as it builds them and the fill reads them
+// back instead of building them a second time (base == nullptr: no cache,
+// both kernels build).  A slot holds the header block (clip, endpoints, axes,
+// header words: contiguous in the shared-memory layout), the boundaries, the
+// cells' voxels and runs, the run starts and the short-cell list, for at most
+// maxc = nx + ny + 1 cells.
+struct CellCache {
+    unsigned char *base;
+    int maxc;
+    int64_t stride;  // bytes per pair, a multiple of 16
+};
+
+constexpr int CELL_HEAD = 32 + 32 + 2 * (int)sizeof(Axis) + 64;  // clip .. hdr
+static_assert(CELL_HEAD % 16 == 0, "cell cache header block");
+
+__host__ __device__ inline int64_t cell_slot_bytes(int maxc) {
+    const int64_t b = (int64_t)sizeof(long long) * (maxc + 1);
+    const int64_t sh = (int64_t)sizeof(short) * (4 * maxc + 1 + SET_MAXF);
+    return CELL_HEAD + ((b + 15) & ~15LL) + ((sh + 15) & ~15LL);
+}
+
+// Store (or, with load, read back) the current cells of the CTA; every thread
+// calls.  The counts come from the header (clamped to the slot).
+__device__ __forceinline__ void cells_copy(Cells2D &c, const CellCache &cc, int64_t T, bool load) {
+    unsigned char *slot = cc.base + T * cc.stride;
+    int *head_g = reinterpret_cast<int *>(slot);
+    int *head_s = reinterpret_cast<int *>(c.clip);
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (load) {
+        for (int i = t; i < CELL_HEAD / 4; i += nt) head_s[i] = head_g[i];
+        __syncthreads();
+    } else {
+        for (int i = t; i < CELL_HEAD / 4; i += nt) head_g[i] = head_s[i];
+    }
+    const int n = min(c.hdr[0], cc.maxc), nr = min(c.hdr[1], cc.maxc),
+              nf = min(c.hdr[2], SET_MAXF);
+    long long *bnd = reinterpret_cast<long long *>(slot + CELL_HEAD);
+    short *sh = reinterpret_cast<short *>(
+        slot + CELL_HEAD + ((sizeof(long long) * (cc.maxc + 1) + 15) & ~(size_t)15));
+    short *ix = sh, *iy = sh + cc.maxc, *run = sh + 2 * cc.maxc, *rs = sh + 3 * cc.maxc,
+          *fl = sh + 4 * cc.maxc + 1;
+    if (load) {
+        for (int i = t; i <= n; i += nt) c.bnd[i] = bnd[i];
+        for (int i = t; i < n; i += nt) {
+            c.ix[i] = ix[i];
+            c.iy[i] = iy[i];
+            c.run[i] = run[i];
+        }
+        for (int i = t; i <= nr; i += nt) c.rstart[i] = rs[i];
+        for (int i = t; i < nf; i += nt) c.flag[i] = fl[i];
+    } else {
+        for (int i = t; i <= n; i += nt) bnd[i] = c.bnd[i];
+        for (int i = t; i < n; i += nt) {
+            ix[i] = c.ix[i];
+            iy[i] = c.iy[i];
+            run[i] = c.run[i];
+        }
+        for (int i = t; i <= nr; i += nt) rs[i] = c.rstart[i];
+        for (int i = t; i < nf; i += nt) fl[i] = c.flag[i];
+    }
+}
+
+// Per transaxial pair: the CTA builds the 2D cells (or reads them from the
+// cache the count kernel filled), then every thread helps write the
+// voxel-order copies: each cell's packed x/y voxel and its chord as
 // a float -- in parameter units, or (norm: the 16-bit value forms) divided by
 // the pair's longest cell chord, so that every stored value lies in (0, 1].
 // Returns after the CTA barrier.
 __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const Img &im,
                                                const LorSet &ls, int64_t T, int *status,
-                                               bool norm = false, bool voxel_order = true) {
+                                               bool norm, bool voxel_order,
+                                               const CellCache &cache, bool load) {
     __syncthreads();  // the previous pair's readers are done
     const Cells2D &c = m.c;
-    int a, b;
-    ls.tp_decode(m.tp_start, T, &a, &b);
-    build_cells_par(sc, im, m.cs, a, b, m.c);
+    if (load) {
+        cells_copy(m.c, cache, T, true);
+        __syncthreads();
+    } else {
+        int a, b;
+        ls.tp_decode(m.tp_start, T, &a, &b);
+        build_cells_par(sc, im, m.cs, a, b, m.c);
+        if (cache.base) cells_copy(m.c, cache, T, false);
+    }
     if (threadIdx.x == 0) {
         if (!c.hdr[3]) atomicExch(status, PSF_EDEBUG);
         *m.next = 0;
@@ -937,7 +1008,8 @@ __device__ __forceinline__ int set_next_group(int *next) {
 __global__ void __launch_bounds__(SET_T, 4) set_count_kernel(Scan sc, Img im, LorSet ls,
                                                              const ZAx *__restrict__ zt,
                                                              int64_t *__restrict__ counts,
-                                                             int *__restrict__ status) {
+                                                             int *__restrict__ status,
+                                                             CellCache cache) {
     extern __shared__ __align__(16) unsigned char raw[];
     SetSmem m;
     CountWarp *cw = count_smem_layout(m, raw, sc, ls);
@@ -948,7 +1020,7 @@ __global__ void __launch_bounds__(SET_T, 4) set_count_kernel(Scan sc, Img im, Lo
     CountWarp &W = cw[warp];
     const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
-        set_pair_cells(m, sc, im, ls, T, status, false, false);
+        set_pair_cells(m, sc, im, ls, T, status, false, false, cache, false);
         const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
         for (int g = set_next_group(m.next); g < ngroups; g = set_next_group(m.next)) {
             const int j = g * 32 + lane;
@@ -1094,7 +1166,8 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                                                             int32_t *__restrict__ col,
                                                             VT *__restrict__ val,
                                                             float *__restrict__ row_scale,
-                                                            int *__restrict__ status) {
+                                                            int *__restrict__ status,
+                                                            CellCache cache) {
     // FP32 values are chords in mm; the 16-bit forms store chord / row scale
     // with row scale = (pair's longest cell chord) x (row's mm per unit)
     constexpr bool norm = !std::is_same<VT, float>::value;
@@ -1110,7 +1183,7 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
     const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
     const int nxy = im.nx * im.ny;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
-        set_pair_cells(m, sc, im, ls, T, status, norm);
+        set_pair_cells(m, sc, im, ls, T, status, norm, true, cache, cache.base != nullptr);
         const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
         const bool xinc = c.X->kind == 0 || c.X->inc;
         const bool yinc = c.Y->kind == 0 || c.Y->inc;
@@ -1274,30 +1347,44 @@ static size_t set_scratch_bytes(const LorSet &ls, int64_t *ntiles_out) {
     return sizeof(int64_t) * ntiles + 64 + sizeof(ZAx) * ls.nrp;
 }
 
+// The allocating entry points add the per-pair cell cache after the scratch
+// (16-byte aligned).
+static size_t set_cache_bytes(const LorSet &ls, const Img &im) {
+    return 16 + (size_t)ls.ntp * (size_t)cell_slot_bytes(im.nx + im.ny + 1);
+}
+
 // Ring-pair table, count, scan, (size check,) fill.  row_ptr[0] is already 0.
 template <typename VT>
 static int set_fill_launch(const Scan &sc, const Img &im, const LorSet &ls, const ZAx *zt,
                            const int64_t *row_ptr, int32_t *col, void *val, float *row_scale,
-                           int *status, int grid, size_t shm, cudaStream_t st) {
+                           int *status, int grid, size_t shm, const CellCache &cache,
+                           cudaStream_t st) {
     PSF_TRY(cudaFuncSetAttribute(set_fill_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)shm));
     {
         PSF_TIMED("set_fill_kernel", st);
         set_fill_kernel<VT><<<grid, SET_T, shm, st>>>(sc, im, ls, zt, row_ptr, col,
-                                                      static_cast<VT *>(val), row_scale, status);
+                                                      static_cast<VT *>(val), row_scale, status,
+                                                      cache);
     }
     PSF_LAUNCHED();
     return PSF_OK;
 }
 
+// cached: the scratch is followed by set_cache_bytes of room for the cell
+// cache (else both kernels build the cells).
 static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t *row_ptr,
                         int32_t *col, void *val, int64_t capacity, int64_t *nnz_out,
-                        unsigned char *scratch, int64_t ntiles, cudaStream_t st,
+                        unsigned char *scratch, int64_t ntiles, cudaStream_t st, bool cached,
                         int32_t dtype = PSF_F32, float *row_scale = nullptr) {
     const int64_t n = ls.ntp * ls.nrp;
     int64_t *tiles = reinterpret_cast<int64_t *>(scratch);
     int *status = reinterpret_cast<int *>(tiles + ntiles);
     ZAx *zt = reinterpret_cast<ZAx *>(reinterpret_cast<unsigned char *>(status) + 64);
+    CellCache cache{nullptr, im.nx + im.ny + 1, cell_slot_bytes(im.nx + im.ny + 1)};
+    if (cached)
+        cache.base = reinterpret_cast<unsigned char *>(
+            (reinterpret_cast<uintptr_t>(zt + ls.nrp) + 15) & ~uintptr_t(15));
     PSF_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     const size_t zshm = sizeof(int32_t) * (ls.Nt + ls.NR + 2);
     {
@@ -1319,7 +1406,8 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
         const int cmax = sm_count() * (per_sm > 0 ? per_sm : 1);
         const int cgrid = (int)(ls.ntp < cmax ? ls.ntp : cmax);
         PSF_TIMED("set_count_kernel", st);
-        set_count_kernel<<<cgrid, SET_T, cshm, st>>>(sc, im, ls, zt, row_ptr + 1, status);
+        set_count_kernel<<<cgrid, SET_T, cshm, st>>>(sc, im, ls, zt, row_ptr + 1, status,
+                                                     cache);
     }
     PSF_LAUNCHED();
     int rc = inclusive_scan(row_ptr + 1, n, tiles, st);
@@ -1335,12 +1423,12 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
     if (nnz > capacity) return PSF_ECAPACITY;
     rc = dtype == PSF_BF16
              ? set_fill_launch<__nv_bfloat16>(sc, im, ls, zt, row_ptr, col, val, row_scale,
-                                              status, grid, shm, st)
+                                              status, grid, shm, cache, st)
          : dtype == PSF_F16
              ? set_fill_launch<__half>(sc, im, ls, zt, row_ptr, col, val, row_scale, status,
-                                       grid, shm, st)
+                                       grid, shm, cache, st)
              : set_fill_launch<float>(sc, im, ls, zt, row_ptr, col, val, nullptr, status, grid,
-                                      shm, st);
+                                      shm, cache, st);
     if (rc) return rc;
     PSF_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     PSF_TRY(cudaStreamSynchronize(st));
@@ -1363,11 +1451,11 @@ extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *
     PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
     if (ls.ntp * ls.nrp == 0) return PSF_OK;
     int64_t ntiles = 0;
-    const size_t bytes = set_scratch_bytes(ls, &ntiles);
+    const size_t bytes = set_scratch_bytes(ls, &ntiles) + set_cache_bytes(ls, im);
     void *scratch = nullptr;
     PSF_TRY(cudaMallocAsync(&scratch, bytes, st));
     rc = set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
-                      static_cast<unsigned char *>(scratch), ntiles, st);
+                      static_cast<unsigned char *>(scratch), ntiles, st, true);
     cudaFreeAsync(scratch, st);
     return rc;
 }
@@ -1392,11 +1480,11 @@ extern "C" int psf_sysmat_rows_set_typed(const psf_scanner *scanner, const psf_i
     PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
     if (ls.ntp * ls.nrp == 0) return PSF_OK;
     int64_t ntiles = 0;
-    const size_t bytes = set_scratch_bytes(ls, &ntiles);
+    const size_t bytes = set_scratch_bytes(ls, &ntiles) + set_cache_bytes(ls, im);
     void *scratch = nullptr;
     PSF_TRY(cudaMallocAsync(&scratch, bytes, st));
     rc = set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
-                      static_cast<unsigned char *>(scratch), ntiles, st, dtype, row_scale);
+                      static_cast<unsigned char *>(scratch), ntiles, st, true, dtype, row_scale);
     cudaFreeAsync(scratch, st);
     return rc;
 }
@@ -1570,5 +1658,5 @@ extern "C" int psf_sysmat_rows_set_noalloc(const psf_scanner *scanner, const psf
     // tile sums and the ring-pair table are fully rewritten; set_pipeline
     // clears the status word an earlier call may have left set
     return set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
-                        static_cast<unsigned char *>(scratch), ntiles, st);
+                        static_cast<unsigned char *>(scratch), ntiles, st, false);
 }
