@@ -1437,6 +1437,23 @@ static int set_pipeline(const Scan &sc, const Img &im, const LorSet &ls, int64_t
 
 }  // namespace psf
 
+namespace psf {
+// Scratch of the allocating entry points: with room for the cell cache, or,
+// when that much device memory is not available, without it (the count and
+// fill kernels then both build the cells).
+static int set_scratch_alloc(const LorSet &ls, const Img &im, cudaStream_t st, void **scratch,
+                             int64_t *ntiles, bool *cached) {
+    const size_t base = set_scratch_bytes(ls, ntiles);
+    *cached = true;
+    if (cudaMallocAsync(scratch, base + set_cache_bytes(ls, im), st) == cudaSuccess)
+        return PSF_OK;
+    (void)cudaGetLastError();  // the failed request leaves no sticky error
+    *cached = false;
+    PSF_TRY(cudaMallocAsync(scratch, base, st));
+    return PSF_OK;
+}
+}  // namespace psf
+
 extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
                                    const psf_lor_set *set, int64_t *row_ptr, int32_t *col,
                                    float *val, int64_t capacity, int64_t *nnz_out, void *stream) {
@@ -1451,11 +1468,12 @@ extern "C" int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *
     PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
     if (ls.ntp * ls.nrp == 0) return PSF_OK;
     int64_t ntiles = 0;
-    const size_t bytes = set_scratch_bytes(ls, &ntiles) + set_cache_bytes(ls, im);
     void *scratch = nullptr;
-    PSF_TRY(cudaMallocAsync(&scratch, bytes, st));
+    bool cached = false;
+    rc = set_scratch_alloc(ls, im, st, &scratch, &ntiles, &cached);
+    if (rc) return rc;
     rc = set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
-                      static_cast<unsigned char *>(scratch), ntiles, st, true);
+                      static_cast<unsigned char *>(scratch), ntiles, st, cached);
     cudaFreeAsync(scratch, st);
     return rc;
 }
@@ -1480,11 +1498,13 @@ extern "C" int psf_sysmat_rows_set_typed(const psf_scanner *scanner, const psf_i
     PSF_TRY(cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), st));
     if (ls.ntp * ls.nrp == 0) return PSF_OK;
     int64_t ntiles = 0;
-    const size_t bytes = set_scratch_bytes(ls, &ntiles) + set_cache_bytes(ls, im);
     void *scratch = nullptr;
-    PSF_TRY(cudaMallocAsync(&scratch, bytes, st));
+    bool cached = false;
+    rc = set_scratch_alloc(ls, im, st, &scratch, &ntiles, &cached);
+    if (rc) return rc;
     rc = set_pipeline(sc, im, ls, row_ptr, col, val, capacity, nnz_out,
-                      static_cast<unsigned char *>(scratch), ntiles, st, true, dtype, row_scale);
+                      static_cast<unsigned char *>(scratch), ntiles, st, cached, dtype,
+                      row_scale);
     cudaFreeAsync(scratch, st);
     return rc;
 }
