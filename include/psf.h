@@ -278,7 +278,11 @@ int psf_sysmat_rows(const psf_scanner *scanner, const psf_image *image, const in
  * ring pairs of a transaxial pair share the transaxial projection of their
  * segment, so its crossings with the x and y planes are traced once per pair
  * and only split at each ring pair's z-plane crossings.  F32 values only.
- * PSF_EINVAL if nx + ny + 1 > 1024.
+ * PSF_EINVAL if nx + ny + 1 > 1024.  Allocates stream-ordered scratch for
+ * the call: 8 bytes per 2048 rows, 80 bytes per ring pair and, when the
+ * device has room, a cache of each transaxial pair's cells (about
+ * 16 (nx + ny) bytes per transaxial pair) that saves the fill a second
+ * tracing of the pair; freed before the call returns.
  */
 int psf_sysmat_rows_set(const psf_scanner *scanner, const psf_image *image,
                         const psf_lor_set *set, int64_t *row_ptr, int32_t *col, float *val,
