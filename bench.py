@@ -473,12 +473,15 @@ def run_gpu(args):
 
     e2e_step()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     te = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - te) / e2e_steps
-    e2e = {"value": world * nnz / e2e_s, "unit": UNIT,
+    # the slowest rank's wall time, the units of all ranks
+    _, e2e_rate = job_rate((time.perf_counter() - te) * 1e3, nnz * e2e_steps, dev)
+    e2e = {"value": e2e_rate, "unit": UNIT,
            "h2d_bytes_per_step": int(x_host.numel() * 4 + y_host.numel() * 4),
            "d2h_bytes_per_step": int(out_host.numel() * 4)}
 
