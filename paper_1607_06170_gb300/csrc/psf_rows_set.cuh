@@ -253,18 +253,25 @@ __device__ __forceinline__ void slab_of(const SlabRow *rows, int incl, int f, in
     s.iz = 0;
     if (s.q < 0) return;
     const SlabRow &R = rows[q];
-    Axis Z;
-    Z.kind = R.kf & 3;
-    Z.fixed = R.kf >> 2;
-    Z.A0 = R.A0;
-    Z.DA = R.DA;
-    Z.S = R.S;
-    Z.D = R.D;
+    const int kf = R.kf;
     s.minu = R.minu;
     s.to_mm = R.to_mm;
     s.iz = R.z0 + (f - R.start);
     long long zl, zh;
-    slab(Z, s.iz, zl, zh);
+    if ((kf & 3) == 1) {  // linear axis (nearly every row): slab() without the FP64 fields
+        const long long DA = R.DA, p = R.A0 + (long long)s.iz * DA, p1 = p + DA;
+        zl = p < p1 ? p : p1;
+        zh = p < p1 ? p1 : p;
+    } else {
+        Axis Z;
+        Z.kind = kf & 3;
+        Z.fixed = kf >> 2;
+        Z.A0 = R.A0;
+        Z.DA = R.DA;
+        Z.S = R.S;
+        Z.D = R.D;
+        slab(Z, s.iz, zl, zh);
+    }
     s.zl = zl > R.amin ? zl : R.amin;
     s.zh = zh < R.amax ? zh : R.amax;
 }
