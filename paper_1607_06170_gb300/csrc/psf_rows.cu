@@ -968,7 +968,7 @@ __device__ __forceinline__ void set_pair_cells(SetSmem &m, const Scan &sc, const
     const bool xinc = c.X->kind == 0 || c.X->inc;
     const bool yinc = c.Y->kind == 0 || c.Y->inc;
     for (int cc = threadIdx.x; cc < c.hdr[0]; cc += SET_T) {
-        const int p = sorted_pos(c, cc, xinc, yinc);
+        const int p = sorted_pos(c, cc, xinc, yinc, c.hdr[0]);
         const long long L = c.bnd[cc + 1] - c.bnd[cc];
         m.s_len[p] = L;
         const float lf = norm ? __fdiv_rn(units_to_f(L), lmax) : units_to_f(L);
@@ -1021,6 +1021,7 @@ __global__ void __launch_bounds__(SET_T, 4) set_count_kernel(Scan sc, Img im, Lo
     const int nrp = (int)ls.nrp, ngroups = (nrp + 31) / 32;
     for (int64_t T = blockIdx.x; T < ls.ntp; T += gridDim.x) {
         set_pair_cells(m, sc, im, ls, T, status, false, false, cache, false);
+        const CellsHead hd = cells_head(c);
         const float lx = (float)(c.xy[2] - c.xy[0]), ly = (float)(c.xy[3] - c.xy[1]);
         for (int g = set_next_group(m.next); g < ngroups; g = set_next_group(m.next)) {
             const int j = g * 32 + lane;
@@ -1039,7 +1040,7 @@ __global__ void __launch_bounds__(SET_T, 4) set_count_kernel(Scan sc, Img im, Lo
                 SlabOf so;
                 slab_of(W.row, incl, base + lane, total, so);
                 if (so.q >= 0) {
-                    const SlabCells s = cut_cells(c, so.zl, so.zh, so.minu);
+                    const SlabCells s = cut_cells(c, hd, so.zl, so.zh, so.minu);
                     if (s.count) atomicAdd(&W.cnt[so.q], s.count);
                 }
             }
@@ -1072,11 +1073,11 @@ __device__ __forceinline__ int fill_round_general(const SetSmem &m, SetWarp &W, 
     const unsigned lt = (1u << lane) - 1u, le = (2u << lane) - 1u;
     int lo[3], hi[3], ns = 0;
     if (so.q >= 0 && s.cb >= s.ca) {
-        ns = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
+        ns = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi, c.hdr[0]);
         const long long La = piece(c.bnd, s.ca, so.zl, so.zh);
         const long long Lb = piece(c.bnd, s.cb, so.zl, so.zh);
-        W.gen.sa[lane] = make_int4(so.iz * nxy, sorted_pos(c, s.ca, xinc, yinc),
-                                   sorted_pos(c, s.cb, xinc, yinc),
+        W.gen.sa[lane] = make_int4(so.iz * nxy, sorted_pos(c, s.ca, xinc, yinc, c.hdr[0]),
+                                   sorted_pos(c, s.cb, xinc, yinc, c.hdr[0]),
                                    (La >= so.minu) | ((Lb >= so.minu) << 1));
         W.gen.sf[lane] = make_float4(end_value(La, so.to_mm, norm, lmax),
                                      end_value(Lb, so.to_mm, norm, lmax),
@@ -1211,7 +1212,9 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                 s.ca = 0;
                 s.cb = -1;
                 s.inner = 0;
-                if (so.q >= 0) s = cut_cells(c, so.zl, so.zh, so.minu);
+                // (the header words are re-read per slab here: holding them in
+                // registers across the round costs the fill more in spills)
+                if (so.q >= 0) s = cut_cells(c, cells_head(c), so.zl, so.zh, so.minu);
                 if (__any_sync(0xffffffffu, s.inner > 0)) {
                     pos += fill_round_general(m, W, so, s, xinc, yinc, nxy, norm, lmax, pos,
                                               pend, col, val);
@@ -1230,9 +1233,9 @@ __global__ void __launch_bounds__(SET_T, 3) set_fill_kernel(Scan sc, Img im, Lor
                         lo[0] = pa < pb ? pa : pb;
                         hi[0] = pa < pb ? pb : pa;
                     } else {
-                        nr = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi);
-                        pa = sorted_pos(c, s.ca, xinc, yinc);
-                        pb = sorted_pos(c, s.cb, xinc, yinc);
+                        nr = slab_segments(c, s.ca, s.cb, xinc, yinc, lo, hi, c.hdr[0]);
+                        pa = sorted_pos(c, s.ca, xinc, yinc, c.hdr[0]);
+                        pb = sorted_pos(c, s.cb, xinc, yinc, c.hdr[0]);
                     }
                     const long long La = piece(c.bnd, s.ca, so.zl, so.zh);
                     const long long Lb = piece(c.bnd, s.cb, so.zl, so.zh);

@@ -18,10 +18,25 @@
 
 namespace psf {
 
-// Voxel-order position of ray-order cell cc.
+// The pair-constant header words the slab walk uses (cell count, short-cell
+// count, cells per parameter unit), read once per pair into registers.
+struct CellsHead {
+    int n, nflag;
+    float per_unit;
+};
+
+__host__ __device__ __forceinline__ CellsHead cells_head(const Cells2D &c) {
+    CellsHead h;
+    h.n = c.hdr[0];
+    h.nflag = c.hdr[2];
+    h.per_unit = bits_float(c.hdr[13]);
+    return h;
+}
+
+// Voxel-order position of ray-order cell cc (n: the pair's cell count).
 __host__ __device__ __forceinline__ int sorted_pos(const Cells2D &c, int cc, bool xinc,
-                                                   bool yinc) {
-    const int r = c.run[cc], n = c.hdr[0];
+                                                   bool yinc, int n) {
+    const int r = c.run[cc];
     const int rs = c.rstart[r], re = c.rstart[r + 1];
     const int spos = yinc ? rs : n - re;
     return spos + (xinc ? cc - rs : re - 1 - cc);
@@ -39,21 +54,20 @@ __host__ __device__ __forceinline__ void cswap_range(int lo[3], int hi[3], int i
 
 __host__ __device__ __forceinline__ int slab_segments(const Cells2D &c, int ca, int cb,
                                                       bool xinc, bool yinc, int lo[3],
-                                                      int hi[3]) {
-    const int n = c.hdr[0];
+                                                      int hi[3], int n) {
     const int ra = c.run[ca], rb = c.run[cb];
-    int p0 = sorted_pos(c, ca, xinc, yinc), p1;
+    int p0 = sorted_pos(c, ca, xinc, yinc, n), p1;
     if (ra == rb) {
-        p1 = sorted_pos(c, cb, xinc, yinc);
+        p1 = sorted_pos(c, cb, xinc, yinc, n);
         lo[0] = p0 < p1 ? p0 : p1;
         hi[0] = p0 < p1 ? p1 : p0;
         return 1;
     }
-    p1 = sorted_pos(c, c.rstart[ra + 1] - 1, xinc, yinc);  // first run: ca .. end of its run
+    p1 = sorted_pos(c, c.rstart[ra + 1] - 1, xinc, yinc, n);  // first run: ca .. end of its run
     lo[0] = p0 < p1 ? p0 : p1;
     hi[0] = p0 < p1 ? p1 : p0;
-    p0 = sorted_pos(c, c.rstart[rb], xinc, yinc);  // last run: its start .. cb
-    p1 = sorted_pos(c, cb, xinc, yinc);
+    p0 = sorted_pos(c, c.rstart[rb], xinc, yinc, n);  // last run: its start .. cb
+    p1 = sorted_pos(c, cb, xinc, yinc, n);
     lo[1] = p0 < p1 ? p0 : p1;
     hi[1] = p0 < p1 ? p1 : p0;
     if (rb > ra + 1) {  // whole runs in between: one block in voxel order
@@ -96,17 +110,18 @@ struct SlabCells {
     int ca, cb, count, inner;
 };
 
-__host__ __device__ __forceinline__ SlabCells cut_cells(const Cells2D &c, long long zl,
-                                                        long long zh, long long minu) {
+__host__ __device__ __forceinline__ SlabCells cut_cells(const Cells2D &c, const CellsHead &h,
+                                                        long long zl, long long zh,
+                                                        long long minu) {
     SlabCells s;
     s.ca = 0;
     s.cb = -1;
     s.count = 0;
     s.inner = 0;
-    const int n = c.hdr[0], nflag = c.hdr[2];
+    const int n = h.n, nflag = h.nflag;
     if (zh <= zl || n == 0) return s;
     // parameters are integers: the last cell starting before zh holds zh - 1
-    const float per_unit = bits_float(c.hdr[13]);
+    const float per_unit = h.per_unit;
     s.ca = cell_at(c.bnd, n, zl, per_unit);
     s.cb = cell_at(c.bnd, n, zh - 1, per_unit);
     if (s.cb < s.ca) return s;
